@@ -1,0 +1,195 @@
+/*
+ * cwthf.h -- C ABI of libcwthf.so, the GB300 (sm_103a) implementation of the
+ * single-scale hot path of CWTHF, the continuous-wavelet-transform halo finder
+ * of Li, Wang & He (arXiv:2501.10622).
+ *
+ * The path, in the order of the paper's step list (Sec. 2):
+ *   cwthf_deposit    Sec. 2.1, Eq. 1   cloud-in-cell mass grid (int64 fixed point)
+ *   cwthf_transform  Sec. 2.1, Eq. 2-4 grid CWT with the 3D Mexican-hat wavelet
+ *   cwthf_segment    Sec. 2 steps 4-5, Sec. 2.3  26-neighbour maxima and
+ *                                      steepest-ascent segments of the CWT
+ *   cwthf_assign     Sec. 2 steps 6-7, Sec. 2.3-2.4, Table 1  particles to
+ *                                      segments, per-halo sums, thresholds
+ *   cwthf_find       all of the above, for one or more wavelet scales
+ *
+ * Conventions shared by every entry point
+ *   - Grids are row-major [z][y][x] with x fastest; grid node g sits at
+ *     g * (L / ng) in a periodic box of side L.  ng must be 2^a 3^b with
+ *     a >= 1 and 8 <= ng <= 1024 (otherwise CWTHF_E_UNSUPPORTED_SIZE).
+ *   - Positions are float [np][3] (x, y, z), in the units of L.  Any finite
+ *     value with |x * ng / L| < 2^30 is accepted and wrapped into the box;
+ *     others make the call fail with CWTHF_E_BAD_INPUT (reported by
+ *     cwthf_sync, see below).
+ *   - Positions are quantised to CWTHF_FRAC_BITS fractional bits of a cell:
+ *     q = floor(x * ((ng / L) * 2^10)) mod ng*2^10, with one fp64 product.
+ *   - Masses: mass == NULL means every particle has mass mass_unit.
+ *     Otherwise particle i has integer mass m_q = rint(mass[i] / mass_unit)
+ *     in units of mass_unit; 0 <= m_q < 2^31 is required per particle and
+ *     sum m_q < 2^33 in total (CWTHF_E_OVERFLOW), which keeps every int64
+ *     grid cell exact.
+ *   - Every pointer argument named *device* is device memory owned by the
+ *     caller, and must stay valid until the work queued on `stream` is done.
+ *     `stream` is a cudaStream_t (NULL = legacy default stream).  All calls
+ *     are asynchronous with respect to the host.
+ *   - Return values: CWTHF_OK, or an error detected on the host before any
+ *     work is queued (nothing was queued then).  Errors that only the GPU can
+ *     see (bad positions, int64 budget, capacity, convergence) are recorded
+ *     in the context's status word and returned by the next cwthf_sync().
+ *   - A context serialises its own scratch memory: calls that share a
+ *     context must be issued on one stream (or be otherwise ordered).
+ *   - Nothing throws across this ABI; no function calls exit().
+ */
+#ifndef CWTHF_H
+#define CWTHF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CWTHF_API __attribute__((visibility("default")))
+#else
+#define CWTHF_API
+#endif
+
+#define CWTHF_FRAC_BITS 10
+#define CWTHF_MAX_NG 1024
+#define CWTHF_MIN_NG 8
+
+enum {
+    CWTHF_OK = 0,
+    CWTHF_E_INVALID_ARG = 1,      /* NULL pointer, non-positive size or box, ... */
+    CWTHF_E_UNSUPPORTED_SIZE = 2, /* ng not 2^a 3^b (a >= 1) in [8, 1024], or above the context's limits */
+    CWTHF_E_OVERFLOW = 3,         /* integer mass budget: m_q >= 2^31 or sum m_q >= 2^33 */
+    CWTHF_E_OOM = 4,              /* device allocation failed in cwthf_create */
+    CWTHF_E_CUDA = 5,             /* a CUDA runtime call failed */
+    CWTHF_E_NOT_CONVERGED = 6,    /* label propagation hit its round limit */
+    CWTHF_E_TIMEOUT = 7,          /* a bounded device wait gave up */
+    CWTHF_E_CAPACITY = 8,         /* more halos than cat_cap; the count is still reported */
+    CWTHF_E_BAD_INPUT = 9         /* non-finite or out-of-range position / mass / CWT value */
+};
+
+typedef struct cwthf_ctx cwthf_ctx;
+
+/* Per-scale parameters (Table 1 of the paper gives dens_th = 4 and
+ * particle_th = 15; Sec. 2.3 seeds halos at positive CWT peaks, cwt_min = 0). */
+typedef struct {
+    double w;            /* wavelet scale in 1/length (k_w = w * L / 1000, Sec. 2 footnote) */
+    float cwt_min;       /* a maximum seeds a halo iff its CWT value > cwt_min */
+    float reserved0;
+    double dens_th;      /* keep iff segment mass / (n_cells * cell volume) >= dens_th * mean density */
+    int64_t particle_th; /* keep iff the halo has >= particle_th particles */
+} cwthf_params;
+
+/* One halo of the catalogue (64 bytes).  Halos are sorted by seed. */
+typedef struct {
+    int64_t seed;      /* linear index (z*ng + y)*ng + x of the maximum that seeds the halo */
+    int64_t n_part;    /* particles assigned to the halo */
+    int64_t n_cells;   /* grid cells of its segment (the "grid volume" of Sec. 2.4) */
+    double mass;       /* sum of particle masses (m_q * mass_unit) */
+    double centre[3];  /* centre of mass (Sec. 2.3), minimum image about the seed, in [0, L) */
+    float peak;        /* CWT value at the seed */
+    int32_t reserved;
+} cwthf_halo;
+
+/* Fills *p with the defaults above for scale w. */
+CWTHF_API void cwthf_default_params(double w, cwthf_params *p);
+
+/* Creates a context on `device` with scratch for grids up to max_ng and up
+ * to max_np particles; max_scales (>= 1) is the largest scale count a
+ * cwthf_find call will use (scales beyond the first need a second complex
+ * workspace).  Allocates all device memory up front (cudaMalloc), so later
+ * calls allocate nothing.  Returns CWTHF_E_OOM if that fails (nothing is
+ * leaked), CWTHF_E_CUDA if the device cannot be used. */
+CWTHF_API int cwthf_create(int device, int max_ng, int64_t max_np, int max_scales, cwthf_ctx **out);
+CWTHF_API void cwthf_destroy(cwthf_ctx *ctx);
+
+/* Device bytes a context created with these limits holds (for admission
+ * against a memory budget).  Host-only; needs no GPU. */
+CWTHF_API int cwthf_workspace_bytes(int max_ng, int64_t max_np, int max_scales, size_t *out);
+
+/* Checks a grid size against the supported set (CWTHF_OK or
+ * CWTHF_E_UNSUPPORTED_SIZE).  Host-only. */
+CWTHF_API int cwthf_check_ng(int ng);
+
+/* Sec. 2.1, Eq. 1.  CIC deposit of np particles onto the periodic ng^3 grid.
+ *   pos   device, float [np][3]
+ *   mass  device, float [np], or NULL (all masses equal mass_unit)
+ *   grid  device, int64 [ng][ng][ng]; fully overwritten with the CIC mass in
+ *         units of mass_unit * 2^-30 (each particle spreads m_q * 2^30 over
+ *         at most 8 nodes with integer weights); bit-exact and independent
+ *         of particle order.
+ *   mtot  device, int64 [1] or NULL: receives sum_i m_q. */
+CWTHF_API int cwthf_deposit(cwthf_ctx *ctx, const float *pos, const float *mass, double mass_unit, int64_t np,
+                  double L, int ng, int64_t *grid, int64_t *mtot, void *stream);
+
+/* Sec. 2.1, Eq. 2-4.  Grid CWT at scale w of the CIC mass grid: the circular
+ * convolution C(x_g) = sum_g' m_g' Psi(w, x_g - x_g') with the Mexican hat
+ * Psi(w, r) = w^1.5 (6 - w^2 r^2) exp(-w^2 r^2 / 4) sampled at minimum-image
+ * node offsets, computed as a forward 3D real FFT, a multiply by the exact
+ * DFT of the sampled wavelet, and an inverse FFT, in fp32.
+ *   grid  device, int64 [ng^3] as written by cwthf_deposit (units mass_unit*2^-30)
+ *   cwt   device, float [ng][ng][ng]; overwritten.  Must not alias grid. */
+CWTHF_API int cwthf_transform(cwthf_ctx *ctx, const int64_t *grid, int ng, double L, double mass_unit, double w,
+                    float *cwt, void *stream);
+
+/* Sec. 2 steps 4-5, Sec. 2.3.  Every cell points at the best of itself and
+ * its 26 periodic neighbours under the strict order (C[a] > C[b]) or
+ * (C[a] == C[b] and a < b); chains end at local maxima.  A maximum with
+ * C > cwt_min seeds a segment; every cell gets the linear index of the seed
+ * its chain reaches, or -1.
+ *   cwt         device, float [ng^3] (NaN -> CWTHF_E_BAD_INPUT)
+ *   cell_label  device, int32 [ng^3]; overwritten. */
+CWTHF_API int cwthf_segment(cwthf_ctx *ctx, const float *cwt, int ng, float cwt_min, int32_t *cell_label,
+                  void *stream);
+
+/* Sec. 2 steps 6-7, Sec. 2.3-2.4, Table 1.  Each particle takes the label of
+ * its nearest node ((q + 2^9) >> 10 per axis, wrapped).  Per seed: particle
+ * count, integer mass, integer first moment about the seed node (minimum
+ * image) and the number of cells with its label.  A seed is kept iff
+ * n_part >= particle_th and (double)M_halo * ng^3 >= (dens_th * (double)M_tot)
+ * * n_cells in integer mass units (M_tot = all particles).  Kept halos are
+ * written to cat in increasing seed order; halo_id[i] is the particle's seed
+ * or -1.
+ *   pos, mass, mass_unit, np, L, ng  as for cwthf_deposit (same quantisation)
+ *   cell_label  device, int32 [ng^3] from cwthf_segment
+ *   cwt         device, float [ng^3] or NULL (then cat[].peak = 0)
+ *   params      host; w is ignored here
+ *   halo_id     device, int32 [np]; overwritten
+ *   cat         device, cwthf_halo [cat_cap]
+ *   n_halo      device, int64 [1]: the number of kept halos (even when it
+ *               exceeds cat_cap, which also records CWTHF_E_CAPACITY). */
+CWTHF_API int cwthf_assign(cwthf_ctx *ctx, const float *pos, const float *mass, double mass_unit, int64_t np, double L,
+                 int ng, const int32_t *cell_label, const float *cwt, const cwthf_params *params,
+                 int32_t *halo_id, cwthf_halo *cat, int64_t cat_cap, int64_t *n_halo, void *stream);
+
+/* The whole path for n_scales wavelet scales on one particle set: one
+ * deposit and one forward transform shared by all scales, then per scale the
+ * wavelet multiply, inverse transform, segmentation and assignment.
+ *   params   host, cwthf_params [n_scales]
+ *   halo_id  device, int32 [n_scales][np]
+ *   cat      device, cwthf_halo [n_scales][cat_cap]
+ *   n_halo   device, int64 [n_scales]
+ * Intermediate grids live in the context (n_scales <= max_scales). */
+CWTHF_API int cwthf_find(cwthf_ctx *ctx, const float *pos, const float *mass, double mass_unit, int64_t np, double L,
+               int ng, const cwthf_params *params, int n_scales, int32_t *halo_id, cwthf_halo *cat,
+               int64_t cat_cap, int64_t *n_halo, void *stream);
+
+/* Waits for `stream`, then returns (and clears) the first error the device
+ * recorded since the last cwthf_sync, or CWTHF_E_CUDA if the stream failed. */
+CWTHF_API int cwthf_sync(cwthf_ctx *ctx, void *stream);
+
+/* Static English text for a status code. */
+CWTHF_API const char *cwthf_error_string(int code);
+
+/* Number of kernel launches queued by this context since it was created
+ * (instrumentation for launch accounting). */
+CWTHF_API int64_t cwthf_launch_count(const cwthf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CWTHF_H */

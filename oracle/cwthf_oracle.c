@@ -185,22 +185,40 @@ static int smallest_factor(int n) {
     return n;
 }
 
-static double complex unit_root(int sign, int64_t e, int n) {
-    double ang = TWO_PI * (double)(e % n) / (double)n;
-    return cos(ang) + (double)sign * sin(ang) * I;
+/* Roots of unity exp(-2 pi i e / n) for one top-level length n, fp64. */
+typedef struct {
+    int n;
+    double complex *w;
+} roots_t;
+
+static int roots_init(roots_t *r, int n) {
+    r->n = n;
+    r->w = malloc(sizeof(double complex) * (size_t)n);
+    if (!r->w) return ORC_E_NOMEM;
+    for (int e = 0; e < n; e++) {
+        double ang = TWO_PI * (double)e / (double)n;
+        r->w[e] = cos(ang) - sin(ang) * I;
+    }
+    return ORC_OK;
+}
+
+/* exp(sign * 2 pi i e / m) for a length m that divides the table's length. */
+static double complex unit_root(const roots_t *r, int sign, int64_t e, int m) {
+    double complex v = r->w[(e % m) * (r->n / m)];
+    return sign < 0 ? v : conj(v);
 }
 
 /* x: input with element stride `stride`; X: n outputs; scratch: n entries. */
 static void dft_rec(const double complex *x, int64_t stride, int n, double complex *X, int sign,
-                    double complex *scratch) {
+                    double complex *scratch, const roots_t *roots) {
     if (n == 1) { X[0] = x[0]; return; }
     int p = smallest_factor(n), m = n / p;
     /* Y_r = DFT_m of x[r + p j], j = 0..m-1, stored in X[r m .. r m + m). */
-    for (int r = 0; r < p; r++) dft_rec(x + r * stride, stride * p, m, X + (int64_t)r * m, sign, scratch);
+    for (int r = 0; r < p; r++) dft_rec(x + r * stride, stride * p, m, X + (int64_t)r * m, sign, scratch, roots);
     /* X[k] = sum_r w_n^{r k} Y_r[k mod m]. */
     for (int k = 0; k < n; k++) {
         double complex acc = 0;
-        for (int r = 0; r < p; r++) acc += unit_root(sign, (int64_t)r * k, n) * X[(int64_t)r * m + k % m];
+        for (int r = 0; r < p; r++) acc += unit_root(roots, sign, (int64_t)r * k, n) * X[(int64_t)r * m + k % m];
         scratch[k] = acc;
     }
     memcpy(X, scratch, sizeof(double complex) * (size_t)n);
@@ -212,9 +230,12 @@ int orc_dft1d(double *re, double *im, int n, int sign) {
     double complex *in = malloc(sizeof(double complex) * (size_t)n * 3);
     if (!in) return ORC_E_NOMEM;
     double complex *out = in + n, *scr = in + 2 * n;
+    roots_t roots;
+    if (roots_init(&roots, n)) { free(in); return ORC_E_NOMEM; }
     for (int i = 0; i < n; i++) in[i] = re[i] + im[i] * I;
-    dft_rec(in, 1, n, out, sign, scr);
+    dft_rec(in, 1, n, out, sign, scr, &roots);
     for (int i = 0; i < n; i++) { re[i] = creal(out[i]); im[i] = cimag(out[i]); }
+    free(roots.w);
     free(in);
     return ORC_OK;
 }
@@ -224,6 +245,8 @@ static int dft3d(double complex *a, int n, int sign) {
     double complex *line = malloc(sizeof(double complex) * (size_t)n * 3);
     if (!line) return ORC_E_NOMEM;
     double complex *out = line + n, *scr = line + 2 * n;
+    roots_t roots;
+    if (roots_init(&roots, n)) { free(line); return ORC_E_NOMEM; }
     int64_t n2 = (int64_t)n * n;
     for (int axis = 0; axis < 3; axis++) {
         int64_t step = axis == 0 ? 1 : axis == 1 ? n : n2;
@@ -231,10 +254,11 @@ static int dft3d(double complex *a, int n, int sign) {
             for (int64_t v = 0; v < n; v++) {
                 int64_t base = axis == 0 ? (u * n + v) * n : axis == 1 ? u * n2 + v : u * n + v;
                 for (int i = 0; i < n; i++) line[i] = a[base + i * step];
-                dft_rec(line, 1, n, out, sign, scr);
+                dft_rec(line, 1, n, out, sign, scr, &roots);
                 for (int i = 0; i < n; i++) a[base + i * step] = out[i];
             }
     }
+    free(roots.w);
     free(line);
     return ORC_OK;
 }

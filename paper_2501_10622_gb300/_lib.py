@@ -1,0 +1,231 @@
+"""ctypes binding of libcwthf.so (see include/cwthf.h).
+
+Argument marshalling only: every step of the halo-finding path runs in the
+library's CUDA kernels.  Tensors are PyTorch CUDA tensors (device memory and
+streams); host-side scalars go by value.  If the library is missing this
+module raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libcwthf.so"
+HEADER = _PKG.parent / "include" / "cwthf.h"
+
+OK = 0
+E_INVALID_ARG, E_UNSUPPORTED_SIZE, E_OVERFLOW, E_OOM, E_CUDA, E_NOT_CONVERGED, E_TIMEOUT, E_CAPACITY, E_BAD_INPUT = range(1, 10)
+FRAC_BITS = 10
+MIN_NG, MAX_NG = 8, 1024
+
+HALO_DTYPE = np.dtype([("seed", "<i8"), ("n_part", "<i8"), ("n_cells", "<i8"), ("mass", "<f8"),
+                       ("centre", "<f8", (3,)), ("peak", "<f4"), ("reserved", "<i4")])
+assert HALO_DTYPE.itemsize == 64
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_double), ("cwt_min", ctypes.c_float), ("reserved0", ctypes.c_float),
+                ("dens_th", ctypes.c_double), ("particle_th", ctypes.c_int64)]
+
+
+assert ctypes.sizeof(Params) == 32
+
+
+class CwthfError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {error_string(code)} (code {code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads the in-tree libcwthf.so (built by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(str(LIB_PATH))
+        P, i64, i32, d, f = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_float
+        L.cwthf_default_params.argtypes = [d, ctypes.POINTER(Params)]
+        L.cwthf_default_params.restype = None
+        L.cwthf_create.argtypes = [i32, i32, i64, i32, ctypes.POINTER(P)]
+        L.cwthf_destroy.argtypes = [P]
+        L.cwthf_destroy.restype = None
+        L.cwthf_workspace_bytes.argtypes = [i32, i64, i32, ctypes.POINTER(ctypes.c_size_t)]
+        L.cwthf_check_ng.argtypes = [i32]
+        L.cwthf_deposit.argtypes = [P, P, P, d, i64, d, i32, P, P, P]
+        L.cwthf_transform.argtypes = [P, P, i32, d, d, d, P, P]
+        L.cwthf_segment.argtypes = [P, P, i32, f, P, P]
+        L.cwthf_assign.argtypes = [P, P, P, d, i64, d, i32, P, P, ctypes.POINTER(Params), P, P, i64, P, P]
+        L.cwthf_find.argtypes = [P, P, P, d, i64, d, i32, ctypes.POINTER(Params), i32, P, P, i64, P, P]
+        L.cwthf_sync.argtypes = [P, P]
+        L.cwthf_error_string.argtypes = [i32]
+        L.cwthf_error_string.restype = ctypes.c_char_p
+        L.cwthf_launch_count.argtypes = [P]
+        L.cwthf_launch_count.restype = i64
+        _lib = L
+    return _lib
+
+
+def header_symbols() -> list[str]:
+    """Function names declared in include/cwthf.h."""
+    text = HEADER.read_text()
+    return sorted(set(re.findall(r"CWTHF_API\s+[\w\s\*]+?\b(cwthf_\w+)\s*\(", text)))
+
+
+def error_string(code: int) -> str:
+    return lib().cwthf_error_string(int(code)).decode()
+
+
+def check_ng(ng: int) -> bool:
+    return lib().cwthf_check_ng(int(ng)) == OK
+
+
+def workspace_bytes(max_ng: int, max_np: int, max_scales: int = 1) -> int:
+    out = ctypes.c_size_t(0)
+    rc = lib().cwthf_workspace_bytes(int(max_ng), int(max_np), int(max_scales), ctypes.byref(out))
+    if rc:
+        raise CwthfError(rc, "cwthf_workspace_bytes")
+    return int(out.value)
+
+
+def default_params(w: float, cwt_min: float = 0.0, dens_th: float = 4.0, particle_th: int = 15) -> Params:
+    p = Params()
+    lib().cwthf_default_params(float(w), ctypes.byref(p))
+    p.cwt_min = cwt_min
+    p.dens_th = dens_th
+    p.particle_th = particle_th
+    return p
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise CwthfError(rc, what)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A cwthf_ctx: device scratch sized for grids up to max_ng and up to
+    max_np particles (and max_scales scales per find call)."""
+
+    def __init__(self, device: int = 0, max_ng: int = 256, max_np: int = 1 << 24, max_scales: int = 1):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.max_ng, self.max_np, self.max_scales = max_ng, max_np, max_scales
+        h = ctypes.c_void_p()
+        _check(lib().cwthf_create(int(device), int(max_ng), int(max_np), int(max_scales), ctypes.byref(h)),
+               "cwthf_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cwthf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self, stream):
+        s = stream if stream is not None else self.torch.cuda.current_stream(self.device)
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def _pos(self, pos):
+        t = self.torch
+        assert pos.is_cuda and pos.dtype == t.float32 and pos.ndim == 2 and pos.shape[1] == 3
+        return pos.contiguous()
+
+    def launch_count(self) -> int:
+        return int(lib().cwthf_launch_count(self._h))
+
+    def sync(self, stream=None) -> int:
+        return int(lib().cwthf_sync(self._h, self._stream(stream)))
+
+    def check(self, stream=None, what="device status"):
+        _check(self.sync(stream), what)
+
+    # -- stages -------------------------------------------------------------
+    def deposit(self, pos, L, ng, mass=None, mass_unit=1.0, grid=None, mtot=None, stream=None):
+        t = self.torch
+        pos = self._pos(pos)
+        if grid is None:
+            grid = t.empty((ng, ng, ng), dtype=t.int64, device=self.device)
+        _check(lib().cwthf_deposit(self._h, _ptr(pos), _ptr(mass), float(mass_unit), pos.shape[0], float(L), int(ng),
+                                   _ptr(grid), _ptr(mtot), self._stream(stream)), "cwthf_deposit")
+        return grid
+
+    def transform(self, grid, L, w, mass_unit=1.0, cwt=None, stream=None):
+        t = self.torch
+        ng = grid.shape[0]
+        if cwt is None:
+            cwt = t.empty((ng, ng, ng), dtype=t.float32, device=self.device)
+        _check(lib().cwthf_transform(self._h, _ptr(grid), int(ng), float(L), float(mass_unit), float(w), _ptr(cwt),
+                                     self._stream(stream)), "cwthf_transform")
+        return cwt
+
+    def segment(self, cwt, cwt_min=0.0, label=None, stream=None):
+        t = self.torch
+        ng = cwt.shape[0]
+        if label is None:
+            label = t.empty((ng, ng, ng), dtype=t.int32, device=self.device)
+        _check(lib().cwthf_segment(self._h, _ptr(cwt.contiguous()), int(ng), float(cwt_min), _ptr(label),
+                                   self._stream(stream)), "cwthf_segment")
+        return label
+
+    def assign(self, pos, L, label, cwt=None, mass=None, mass_unit=1.0, dens_th=4.0, particle_th=15,
+               cat_cap=None, stream=None):
+        """Returns (halo_id, catalogue bytes [cap, 64] on device, n_halo tensor)."""
+        t = self.torch
+        pos = self._pos(pos)
+        ng = label.shape[0]
+        if cat_cap is None:
+            cat_cap = max(1, ng ** 3 // 8)
+        halo_id = t.empty(pos.shape[0], dtype=t.int32, device=self.device)
+        cat = t.empty((cat_cap, 64), dtype=t.uint8, device=self.device)
+        n_halo = t.zeros(1, dtype=t.int64, device=self.device)
+        p = default_params(1.0, 0.0, dens_th, particle_th)
+        _check(lib().cwthf_assign(self._h, _ptr(pos), _ptr(mass), float(mass_unit), pos.shape[0], float(L), int(ng),
+                                  _ptr(label), _ptr(cwt), ctypes.byref(p), _ptr(halo_id), _ptr(cat), int(cat_cap),
+                                  _ptr(n_halo), self._stream(stream)), "cwthf_assign")
+        return halo_id, cat, n_halo
+
+    def find(self, pos, L, ng, params, mass=None, mass_unit=1.0, cat_cap=None, halo_id=None, cat=None, n_halo=None,
+             stream=None):
+        """params: list of Params (one per scale).  Returns (halo_id [n_scales, np],
+        catalogue bytes [n_scales, cap, 64], n_halo [n_scales]) on device."""
+        t = self.torch
+        pos = self._pos(pos)
+        ns = len(params)
+        if cat_cap is None:
+            cat_cap = max(1, ng ** 3 // 8)
+        if halo_id is None:
+            halo_id = t.empty((ns, pos.shape[0]), dtype=t.int32, device=self.device)
+        if cat is None:
+            cat = t.empty((ns, cat_cap, 64), dtype=t.uint8, device=self.device)
+        if n_halo is None:
+            n_halo = t.zeros(ns, dtype=t.int64, device=self.device)
+        arr = (Params * ns)(*params)
+        _check(lib().cwthf_find(self._h, _ptr(pos), _ptr(mass), float(mass_unit), pos.shape[0], float(L), int(ng),
+                                arr, ns, _ptr(halo_id), _ptr(cat), int(cat_cap), _ptr(n_halo), self._stream(stream)),
+               "cwthf_find")
+        return halo_id, cat, n_halo
+
+
+def catalogue_to_numpy(cat, n) -> np.ndarray:
+    """Device catalogue bytes -> numpy structured array of the first n halos."""
+    n = int(n)
+    raw = cat[:n].contiguous().cpu().numpy()
+    return raw.view(HALO_DTYPE).reshape(n)

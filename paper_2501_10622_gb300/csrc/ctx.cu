@@ -1,0 +1,292 @@
+// ctx.cu -- the public C ABI of libcwthf.so: context lifetime, argument
+// checks, and the order of the stages (Sec. 2 step list of the paper).
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace cwthf {
+
+bool fft_size_supported(int ng);
+
+int check_ng(int ng) {
+    if (ng < CWTHF_MIN_NG || ng > CWTHF_MAX_NG || ng % 2) return CWTHF_E_UNSUPPORTED_SIZE;
+    int m = ng;
+    while (m % 2 == 0) m /= 2;
+    while (m % 3 == 0) m /= 3;
+    if (m != 1) return CWTHF_E_UNSUPPORTED_SIZE;
+    return fft_size_supported(ng) ? CWTHF_OK : CWTHF_E_UNSUPPORTED_SIZE;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? CWTHF_OK : CWTHF_E_CUDA; }
+
+namespace {
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+struct Sizes {
+    int64_t cells, nwords, slots, keys, np;
+    size_t scan_words;
+};
+
+Sizes sizes_for(int max_ng, int64_t max_np) {
+    Sizes z;
+    z.cells = int64_t(max_ng) * max_ng * max_ng;
+    z.nwords = (z.cells + 31) / 32;
+    z.slots = z.cells / 8 + 8;  // at most one maximum per 2x2x2 block of cells
+    z.keys = deposit_geom(max_ng).ntiles * kDepClasses;
+    z.np = std::max<int64_t>(max_np, 1);
+    int64_t scan_n = std::max(z.keys, std::max(z.nwords, z.slots));
+    z.scan_words = scan_tmp_words(scan_n) + 2;
+    return z;
+}
+
+// The allocation plan: (pointer slot, bytes).  One list drives both
+// cwthf_create and cwthf_workspace_bytes.
+template <class F>
+void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, F&& f) {
+    Sizes z = sizes_for(max_ng, max_np);
+    f(reinterpret_cast<void**>(&c->d_status), sizeof(int) * 4);
+    f(reinterpret_cast<void**>(&c->dep_count), size_t(z.keys + 1) * 4);
+    f(reinterpret_cast<void**>(&c->dep_off), size_t(z.keys + 2) * 4);
+    f(reinterpret_cast<void**>(&c->dep_cursor), size_t(z.keys + 1) * 4);
+    f(reinterpret_cast<void**>(&c->dep_rec), size_t(z.np) * 8);
+    f(reinterpret_cast<void**>(&c->dep_mq), size_t(z.np) * 4);
+    f(reinterpret_cast<void**>(&c->d_mtot), 16);
+    f(reinterpret_cast<void**>(&c->n_seeds), 16);
+    f(reinterpret_cast<void**>(&c->spec), spec_bytes(max_ng));
+    if (max_scales > 1) f(reinterpret_cast<void**>(&c->spec2), spec_bytes(max_ng));
+    f(reinterpret_cast<void**>(&c->seed_bits), size_t(z.nwords + 1) * 4);
+    f(reinterpret_cast<void**>(&c->seed_prefix), size_t(z.nwords + 2) * 4);
+    f(reinterpret_cast<void**>(&c->seed_list), size_t(z.slots) * 4);
+    f(reinterpret_cast<void**>(&c->acc), size_t(z.slots) * sizeof(HaloAcc));
+    f(reinterpret_cast<void**>(&c->keep_off), size_t(z.slots + 2) * 4);
+    f(reinterpret_cast<void**>(&c->part_slot), size_t(z.np) * 4);
+    f(reinterpret_cast<void**>(&c->jump_changed), sizeof(int) * (kMaxJumpRounds + 2));
+    f(reinterpret_cast<void**>(&c->scan_tmp), z.scan_words * 4);
+    f(reinterpret_cast<void**>(&c->grid), size_t(z.cells) * 8);
+    f(reinterpret_cast<void**>(&c->cwt), size_t(z.cells) * 4);
+    f(reinterpret_cast<void**>(&c->label), size_t(z.cells) * 4);
+}
+
+void release(cwthf_ctx* c) {
+    for_each_buffer(c, c->max_ng, c->max_np, c->max_scales, [](void** p, size_t) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    });
+    if (c->h_status) cudaFreeHost(c->h_status);
+    c->h_status = nullptr;
+    free_tables(c);
+}
+
+int check_common(const cwthf_ctx* ctx, int ng, double L) {
+    if (!ctx) return CWTHF_E_INVALID_ARG;
+    if (!(L > 0) || !std::isfinite(L)) return CWTHF_E_INVALID_ARG;
+    int rc = check_ng(ng);
+    if (rc) return rc;
+    if (ng > ctx->max_ng) return CWTHF_E_UNSUPPORTED_SIZE;
+    return CWTHF_OK;
+}
+
+int check_particles(const cwthf_ctx* ctx, const float* pos, int64_t np, double mass_unit) {
+    if (np < 0 || np > ctx->max_np) return CWTHF_E_INVALID_ARG;
+    if (np > 0 && !pos) return CWTHF_E_INVALID_ARG;
+    if (!(mass_unit > 0) || !std::isfinite(mass_unit)) return CWTHF_E_INVALID_ARG;
+    return CWTHF_OK;
+}
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+}  // namespace cwthf
+
+using namespace cwthf;
+
+extern "C" {
+
+void cwthf_default_params(double w, cwthf_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->w = w;
+    p->cwt_min = 0.0f;
+    p->dens_th = 4.0;
+    p->particle_th = 15;
+}
+
+int cwthf_check_ng(int ng) { return check_ng(ng) ? CWTHF_E_UNSUPPORTED_SIZE : CWTHF_OK; }
+
+int cwthf_workspace_bytes(int max_ng, int64_t max_np, int max_scales, size_t* out) {
+    if (!out || max_np < 0 || max_np >= (int64_t(1) << 31) || max_scales < 1) return CWTHF_E_INVALID_ARG;
+    if (check_ng(max_ng)) return CWTHF_E_UNSUPPORTED_SIZE;
+    cwthf_ctx probe;
+    size_t total = 0;
+    for_each_buffer(&probe, max_ng, max_np, max_scales, [&](void**, size_t b) { total += (b + 255) / 256 * 256; });
+    *out = total;
+    return CWTHF_OK;
+}
+
+int cwthf_create(int device, int max_ng, int64_t max_np, int max_scales, cwthf_ctx** out) {
+    if (!out) return CWTHF_E_INVALID_ARG;
+    *out = nullptr;
+    if (max_np < 0 || max_np >= (int64_t(1) << 31) || max_scales < 1) return CWTHF_E_INVALID_ARG;
+    if (check_ng(max_ng)) return CWTHF_E_UNSUPPORTED_SIZE;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return CWTHF_E_CUDA;
+    DeviceGuard g(device);
+    if (!g.ok) return CWTHF_E_CUDA;
+    cwthf_ctx* c = new (std::nothrow) cwthf_ctx;
+    if (!c) return CWTHF_E_OOM;
+    c->device = device;
+    c->max_ng = max_ng;
+    c->max_np = max_np;
+    c->max_scales = max_scales;
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return CWTHF_E_CUDA;
+    }
+    bool failed = false;
+    for_each_buffer(c, max_ng, max_np, max_scales, [&](void** p, size_t b) {
+        if (failed) return;
+        if (cudaMalloc(p, b) != cudaSuccess) {
+            *p = nullptr;
+            failed = true;
+        }
+    });
+    if (!failed && cudaMallocHost(&c->h_status, sizeof(int)) != cudaSuccess) failed = true;
+    if (!failed) {
+        Sizes z = sizes_for(max_ng, max_np);
+        c->scan_tmp_cap = z.scan_words;
+        if (cudaMemset(c->d_status, 0, sizeof(int) * 4) != cudaSuccess) failed = true;
+    }
+    if (failed) {
+        cudaGetLastError();  // clear the sticky allocation error
+        release(c);
+        delete c;
+        return CWTHF_E_OOM;
+    }
+    *out = c;
+    return CWTHF_OK;
+}
+
+void cwthf_destroy(cwthf_ctx* ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    release(ctx);
+    delete ctx;
+}
+
+int cwthf_deposit(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L,
+                  int ng, int64_t* grid, int64_t* mtot, void* stream) {
+    int rc = check_common(ctx, ng, L);
+    if (!rc) rc = check_particles(ctx, pos, np, mass_unit);
+    if (!rc && !grid) rc = CWTHF_E_INVALID_ARG;
+    if (rc) return rc;
+    DeviceGuard g(ctx->device);
+    return deposit_impl(ctx, pos, mass, mass_unit, np, L, ng, grid, mtot, as_stream(stream));
+}
+
+int cwthf_transform(cwthf_ctx* ctx, const int64_t* grid, int ng, double L, double mass_unit, double w, float* cwt,
+                    void* stream) {
+    int rc = check_common(ctx, ng, L);
+    if (rc) return rc;
+    if (!grid || !cwt || !(w > 0) || !std::isfinite(w) || !(mass_unit > 0)) return CWTHF_E_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    rc = transform_forward_xy(ctx, grid, ng, mass_unit, ctx->spec, s);
+    if (!rc) rc = transform_wavelet_inverse(ctx, ctx->spec, ctx->spec, ng, L, w, cwt, s);
+    return rc;
+}
+
+int cwthf_segment(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_t* cell_label, void* stream) {
+    int rc = check_common(ctx, ng, 1.0);
+    if (rc) return rc;
+    if (!cwt || !cell_label || std::isnan(cwt_min)) return CWTHF_E_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    return segment_impl(ctx, cwt, ng, cwt_min, cell_label, false, as_stream(stream));
+}
+
+int cwthf_assign(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L, int ng,
+                 const int32_t* cell_label, const float* cwt, const cwthf_params* params, int32_t* halo_id,
+                 cwthf_halo* cat, int64_t cat_cap, int64_t* n_halo, void* stream) {
+    int rc = check_common(ctx, ng, L);
+    if (!rc) rc = check_particles(ctx, pos, np, mass_unit);
+    if (rc) return rc;
+    if (!cell_label || !params || (np > 0 && !halo_id) || cat_cap < 0 || (cat_cap > 0 && !cat) || !n_halo ||
+        std::isnan(params->dens_th))
+        return CWTHF_E_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    return assign_impl(ctx, pos, mass, mass_unit, np, L, ng, cell_label, cwt, params, halo_id, cat, cat_cap, n_halo,
+                       false, as_stream(stream));
+}
+
+int cwthf_find(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L, int ng,
+               const cwthf_params* params, int n_scales, int32_t* halo_id, cwthf_halo* cat, int64_t cat_cap,
+               int64_t* n_halo, void* stream) {
+    int rc = check_common(ctx, ng, L);
+    if (!rc) rc = check_particles(ctx, pos, np, mass_unit);
+    if (rc) return rc;
+    if (!params || n_scales < 1 || n_scales > ctx->max_scales || (np > 0 && !halo_id) || cat_cap < 0 ||
+        (cat_cap > 0 && !cat) || !n_halo)
+        return CWTHF_E_INVALID_ARG;
+    for (int i = 0; i < n_scales; i++)
+        if (!(params[i].w > 0) || !std::isfinite(params[i].w) || std::isnan(params[i].cwt_min) ||
+            std::isnan(params[i].dens_th))
+            return CWTHF_E_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    rc = deposit_impl(ctx, pos, mass, mass_unit, np, L, ng, ctx->grid, nullptr, s);
+    if (!rc) rc = transform_forward_xy(ctx, ctx->grid, ng, mass_unit, ctx->spec, s);
+    for (int i = 0; i < n_scales && !rc; i++) {
+        float2* dst = n_scales > 1 ? ctx->spec2 : ctx->spec;
+        rc = transform_wavelet_inverse(ctx, ctx->spec, dst, ng, L, params[i].w, ctx->cwt, s);
+        if (!rc) rc = segment_impl(ctx, ctx->cwt, ng, params[i].cwt_min, ctx->label, true, s);
+        if (!rc)
+            rc = assign_impl(ctx, pos, mass, mass_unit, np, L, ng, ctx->label, ctx->cwt, &params[i],
+                             halo_id + int64_t(i) * np, cat + int64_t(i) * cat_cap, cat_cap, n_halo + i, true, s);
+    }
+    return rc;
+}
+
+int cwthf_sync(cwthf_ctx* ctx, void* stream) {
+    if (!ctx) return CWTHF_E_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CWTHF_E_CUDA;
+    if (cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        return CWTHF_E_CUDA;
+    return *ctx->h_status;
+}
+
+const char* cwthf_error_string(int code) {
+    switch (code) {
+        case CWTHF_OK: return "ok";
+        case CWTHF_E_INVALID_ARG: return "invalid argument";
+        case CWTHF_E_UNSUPPORTED_SIZE: return "unsupported grid size (need 2^a 3^b, a >= 1, 8 <= ng <= 1024, within the context's limits)";
+        case CWTHF_E_OVERFLOW: return "integer mass budget exceeded (m_q >= 2^31 or sum m_q >= 2^33)";
+        case CWTHF_E_OOM: return "device allocation failed";
+        case CWTHF_E_CUDA: return "CUDA runtime error";
+        case CWTHF_E_NOT_CONVERGED: return "label propagation did not converge within its round limit";
+        case CWTHF_E_TIMEOUT: return "a bounded device wait timed out";
+        case CWTHF_E_CAPACITY: return "more halos than the catalogue capacity";
+        case CWTHF_E_BAD_INPUT: return "non-finite or out-of-range input value";
+        default: return "unknown status";
+    }
+}
+
+int64_t cwthf_launch_count(const cwthf_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
+}  // extern "C"

@@ -1,0 +1,216 @@
+// deposit.cu -- cloud-in-cell deposit (Sec. 2.1, Eq. 1) as exact int64 fixed
+// point, binned by grid tile so that each tile is accumulated once in shared
+// memory and written with plain coalesced stores (no global atomics on the
+// grid, no memset of the grid).
+//
+// Particle i with fixed-point coordinate q = n*2^10 + f per axis gives node n
+// the weight 2^10 - f and node n+1 (periodic) the weight f; the product of the
+// three axis weights times the integer mass m_q is added to each of the 8
+// nodes.  Integer sums are exact and independent of order, so the grid is
+// bit-for-bit deterministic.
+//
+// Binning: a particle belongs to the tile holding its base node (n_x, n_y,
+// n_z).  Its boundary class has bit a set when the node n+1 along axis a lies
+// in another tile (or wraps around the box).  The tile kernel reads its own
+// bin plus, from each of its 7 lower neighbours, the classes whose bits cover
+// that neighbour's offset: exactly the particles that reach into the tile.
+#include "internal.cuh"
+#include "quant.cuh"
+
+namespace cwthf {
+namespace {
+
+constexpr int kCountThreads = 256;
+constexpr int kTileThreads = 256;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint32_t kInvalidKey = 0xffffffffu;
+using u64 = unsigned long long;
+
+struct PartBin {
+    uint32_t key;  // tile * 8 + class, or kInvalidKey
+    unsigned long long rec;
+    uint32_t mq;
+    int status;
+};
+
+__device__ __forceinline__ PartBin bin_particle(const DepArgs& a, int64_t i) {
+    PartBin b;
+    b.key = kInvalidKey;
+    b.rec = 0;
+    b.mq = 0;
+    b.status = CWTHF_OK;
+    int64_t q[3];
+    const float* p = a.pos + 3 * i;
+    bool ok = quantise(p[0], a.scale, a.modulus, q[0]) && quantise(p[1], a.scale, a.modulus, q[1]) &&
+              quantise(p[2], a.scale, a.modulus, q[2]);
+    if (!ok) { b.status = CWTHF_E_BAD_INPUT; return b; }
+    int ms = mass_quantum(a, i, b.mq);
+    if (ms != CWTHF_OK) { b.status = ms; b.mq = 0; return b; }
+    const int T[3] = {kDepTX, kDepTY, kDepTZ};
+    int n[3], t[3], l[3], f[3], cls = 0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        n[d] = int(q[d] >> kFracBits);
+        f[d] = int(q[d] & (kFracOne - 1));
+        t[d] = n[d] / T[d];
+        l[d] = n[d] - t[d] * T[d];
+        if (n[d] + 1 == a.ng || (n[d] + 1) % T[d] == 0) cls |= 1 << d;
+    }
+    uint32_t tile = uint32_t((int64_t(t[2]) * a.nty + t[1]) * a.ntx + t[0]);
+    b.key = tile * kDepClasses + uint32_t(cls);
+    b.rec = (unsigned long long)l[0] | ((unsigned long long)l[1] << 6) | ((unsigned long long)l[2] << 12) |
+            ((unsigned long long)f[0] << 18) | ((unsigned long long)f[1] << 28) | ((unsigned long long)f[2] << 38);
+    return b;
+}
+
+// Pass 1: particles per (tile, class) and the integer mass total.
+__global__ void __launch_bounds__(kCountThreads) k_dep_count(DepArgs a, uint32_t* __restrict__ count,
+                                                            unsigned long long* __restrict__ mtot, int* status) {
+    int lane = threadIdx.x & 31;
+    int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    unsigned long long msum = 0;
+    for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < a.np; base += stride) {
+        int64_t i = base + lane;  // base is warp-uniform: every lane runs every iteration
+        PartBin b;
+        b.key = kInvalidKey;
+        b.mq = 0;
+        b.status = CWTHF_OK;
+        if (i < a.np) b = bin_particle(a, i);
+        if (b.status != CWTHF_OK) set_status(status, b.status);
+        msum += b.mq;
+        unsigned peers = __match_any_sync(kFull, b.key);
+        if (b.key != kInvalidKey && lane == __ffs(peers) - 1) atomicAdd(&count[b.key], uint32_t(__popc(peers)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) msum += __shfl_xor_sync(kFull, msum, o);
+    if (lane == 0 && msum) atomicAdd(mtot, msum);
+}
+
+// Pass 2: write each particle's packed record into its (tile, class) segment.
+__global__ void __launch_bounds__(kCountThreads) k_dep_scatter(DepArgs a, uint32_t* __restrict__ cursor,
+                                                              unsigned long long* __restrict__ rec,
+                                                              uint32_t* __restrict__ rec_mq) {
+    int lane = threadIdx.x & 31;
+    int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < a.np; base += stride) {
+        int64_t i = base + lane;
+        PartBin b;
+        b.key = kInvalidKey;
+        b.status = CWTHF_OK;
+        if (i < a.np) b = bin_particle(a, i);
+        unsigned peers = __match_any_sync(kFull, b.key);
+        int leader = __ffs(peers) - 1;
+        uint32_t slot = 0;
+        if (b.key != kInvalidKey && lane == leader) slot = atomicAdd(&cursor[b.key], uint32_t(__popc(peers)));
+        slot = __shfl_sync(kFull, slot, leader);
+        if (b.key != kInvalidKey) {
+            slot += __popc(peers & ((1u << lane) - 1));
+            rec[slot] = b.rec;
+            if (a.mass) rec_mq[slot] = b.mq;
+        }
+    }
+}
+
+// Pass 3: one tile at a time per CTA; shared-memory int64 accumulation of the
+// tile's own bin and the reaching-in particles of its 7 lower neighbours.
+__global__ void __launch_bounds__(kTileThreads) k_dep_tile(DepArgs a, const uint32_t* __restrict__ off,
+                                                          const unsigned long long* __restrict__ rec,
+                                                          const uint32_t* __restrict__ rec_mq,
+                                                          const unsigned long long* __restrict__ mtot,
+                                                          int64_t* __restrict__ grid, int* status) {
+    __shared__ unsigned long long acc[kDepTZ][kDepTY][kDepTX];
+    constexpr int kCells = kDepTX * kDepTY * kDepTZ;
+    int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && *mtot >= (1ull << 33)) set_status(status, CWTHF_E_OVERFLOW);
+    int64_t ntiles = int64_t(a.ntx) * a.nty * a.ntz;
+    const int64_t ng = a.ng;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        int tx = int(t % a.ntx), ty = int((t / a.ntx) % a.nty), tz = int(t / (int64_t(a.ntx) * a.nty));
+        int x0 = tx * kDepTX, y0 = ty * kDepTY, z0 = tz * kDepTZ;
+        int wx = min(kDepTX, a.ng - x0), wy = min(kDepTY, a.ng - y0), wz = min(kDepTZ, a.ng - z0);
+        for (int c = threadIdx.x; c < kCells; c += kTileThreads) (&acc[0][0][0])[c] = 0ull;
+        __syncthreads();
+#pragma unroll 1
+        for (int m = 0; m < 8; m++) {
+            int dx = m & 1, dy = (m >> 1) & 1, dz = (m >> 2) & 1;
+            int sx = tx - dx < 0 ? a.ntx - 1 : tx - dx;
+            int sy = ty - dy < 0 ? a.nty - 1 : ty - dy;
+            int sz = tz - dz < 0 ? a.ntz - 1 : tz - dz;
+            int64_t src = (int64_t(sz) * a.nty + sy) * a.ntx + sx;
+#pragma unroll 1
+            for (int cls = 0; cls < 8; cls++) {
+                if ((cls & m) != m) continue;
+                uint32_t beg = off[src * kDepClasses + cls], end = off[src * kDepClasses + cls + 1];
+                // warp-uniform trip count so that the warp collectives see all lanes
+                for (uint32_t r0 = beg + (threadIdx.x & ~31u); r0 < end; r0 += kTileThreads) {
+                    uint32_t r = r0 + uint32_t(lane);
+                    bool live = r < end;
+                    unsigned long long e = live ? rec[r] : 0ull;
+                    uint32_t mq = live ? (a.mass ? rec_mq[r] : 1u) : 0u;
+                    int lx = int(e & 63), ly = int((e >> 6) & 63), lz = int((e >> 12) & 63);
+                    int fx = int((e >> 18) & 1023), fy = int((e >> 28) & 1023), fz = int((e >> 38) & 1023);
+                    // a particle from a lower neighbour only reaches in with its upper node
+                    if (dx) lx = -1;
+                    if (dy) ly = -1;
+                    if (dz) lz = -1;
+                    u64 wxv[2] = {u64(kFracOne - fx), u64(fx)};
+                    u64 wyv[2] = {u64(kFracOne - fy), u64(fy)};
+                    u64 wzv[2] = {u64(kFracOne - fz), u64(fz)};
+                    uint32_t key = live ? uint32_t(((lz + 1) * (kDepTY + 2) + (ly + 1)) * (kDepTX + 2) + (lx + 1))
+                                        : kInvalidKey;
+                    unsigned peers = __match_any_sync(kFull, key);
+                    int big = __reduce_max_sync(kFull, unsigned(__popc(peers)));
+                    int rank = __popc(peers & ((1u << lane) - 1));
+                    bool writer = live && (big < 6 || rank == 0);
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        int ex = k & 1, ey = (k >> 1) & 1, ez = (k >> 2) & 1;
+                        u64 v = u64(mq) * wxv[ex] * wyv[ey] * wzv[ez];
+                        if (big >= 6) v = group_sum<u64>(v, peers, lane, rank);  // warp-uniform branch
+                        int cx = lx + ex, cy = ly + ey, cz = lz + ez;
+                        if (writer && v && cx >= 0 && cx < wx && cy >= 0 && cy < wy && cz >= 0 && cz < wz)
+                            atomicAdd(&acc[cz][cy][cx], v);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < kCells; c += kTileThreads) {
+            int cx = c % kDepTX, cy = (c / kDepTX) % kDepTY, cz = c / (kDepTX * kDepTY);
+            if (cx < wx && cy < wy && cz < wz)
+                grid[(int64_t(z0 + cz) * ng + (y0 + cy)) * ng + (x0 + cx)] = (int64_t)acc[cz][cy][cx];
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int deposit_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L,
+                 int ng, int64_t* grid, int64_t* mtot, cudaStream_t s) {
+    DepositGeom g = deposit_geom(ng);
+    DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
+    int64_t nkeys = g.ntiles * kDepClasses;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(ctx->dep_count, 0, size_t(nkeys) * 4, s)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(ctx->d_mtot, 0, 8, s)) != cudaSuccess) return cuda_status(e);
+    int blocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kCountThreads), int64_t(ctx->sm_count) * 16));
+    k_dep_count<<<blocks, kCountThreads, 0, s>>>(a, ctx->dep_count, ctx->d_mtot, ctx->d_status);
+    count_launch(ctx);
+    int rc = scan_u32(ctx, ctx->dep_count, ctx->dep_off, nkeys, s);
+    if (rc) return rc;
+    if ((e = cudaMemcpyAsync(ctx->dep_cursor, ctx->dep_off, size_t(nkeys) * 4, cudaMemcpyDeviceToDevice, s)) !=
+        cudaSuccess)
+        return cuda_status(e);
+    k_dep_scatter<<<blocks, kCountThreads, 0, s>>>(a, ctx->dep_cursor, ctx->dep_rec, ctx->dep_mq);
+    count_launch(ctx);
+    int tblocks = int(std::min<int64_t>(g.ntiles, int64_t(ctx->sm_count) * 8));
+    k_dep_tile<<<tblocks, kTileThreads, 0, s>>>(a, ctx->dep_off, ctx->dep_rec, ctx->dep_mq, ctx->d_mtot, grid,
+                                                ctx->d_status);
+    count_launch(ctx);
+    if (mtot && (e = cudaMemcpyAsync(mtot, ctx->d_mtot, 8, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return cuda_status(e);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace cwthf

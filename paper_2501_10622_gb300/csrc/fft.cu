@@ -1,0 +1,868 @@
+// fft.cu -- the grid CWT of Sec. 2.1 (Eq. 2-4) as a 3D real FFT, a multiply
+// by the exact DFT of the sampled Mexican-hat wavelet, and an inverse FFT.
+//
+// Data flow for an ng^3 grid (M = ng/2, P = complex row pitch, even):
+//   x-fwd   int64 grid -> fp32 -> real FFT along x -> spec [z][y][0..M]   (k_fft_x_fwd)
+//   y-fwd   complex FFT along y, in place                                (k_fft_yz, TMA)
+//   z       complex FFT along z, multiply by Psi^, inverse FFT along z    (k_fft_yz, TMA)
+//   y-inv   inverse complex FFT along y, in place                        (k_fft_yz, TMA)
+//   x-inv   half spectrum -> real row, written to the CWT field          (k_fft_x_inv)
+//
+// Every 1D transform of length L runs in shared memory as a Stockham
+// autosort FFT with at most three radix stages (radices 2^a 3^b <= 32); each
+// thread performs one radix-R butterfly per stage entirely in registers, with
+// compile-time constants inside the butterfly and fp32 twiddles (rounded once
+// from fp64 on the host) between stages.  Inverse transforms use
+// IDFT(x) = conj(DFT(conj(x))).  The forward transform is unnormalised; the
+// 1/ng^3 of the inverse is folded into the wavelet spectrum.
+//
+// Wavelet spectrum (exact DFT of the sampled kernel): with G(u) =
+// exp(-w^2 u^2/4) and H(u) = w^2 u^2 G(u) sampled at minimum-image offsets,
+//   Psi = w^1.5 [6 G_x G_y G_z - H_x G_y G_z - G_x H_y G_z - G_x G_y H_z],
+// so its DFT is the same combination of the 1D DFTs G^ and H^ (real, even),
+// tabulated per grid size and scale in fp64 on the host.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <type_traits>
+
+#include "internal.cuh"
+
+namespace cwthf {
+
+struct Tables {
+    int ng = 0;
+    float2* twN = nullptr;  // [ng]   exp(-2 pi i m / ng)
+    float2* twM = nullptr;  // [ng/2] exp(-2 pi i m / (ng/2))
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Compile-time twiddle constants (series evaluated in fp64, rounded to fp32).
+// ---------------------------------------------------------------------------
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+__host__ __device__ constexpr double cx_sin(double x) {
+    double term = x, sum = x;
+    for (int k = 1; k < 30; k++) {
+        term *= -x * x / double((2 * k) * (2 * k + 1));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double cx_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 30; k++) {
+        term *= -x * x / double((2 * k - 1) * (2 * k));
+        sum += term;
+    }
+    return sum;
+}
+// angle 2 pi e / n reduced into [-pi, pi]
+__host__ __device__ constexpr double cx_angle(int e, int n) {
+    int r = ((e % n) + n) % n;
+    if (2 * r > n) r -= n;
+    return 2.0 * kPi * double(r) / double(n);
+}
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+
+// a * exp(-2 pi i E / N), exact for the quarter turns.
+template <int N, int E>
+__device__ __forceinline__ float2 mul_w(float2 a) {
+    constexpr int e = ((E % N) + N) % N;
+    if constexpr (e == 0) {
+        return a;
+    } else if constexpr (4 * e == N) {
+        return make_float2(a.y, -a.x);
+    } else if constexpr (2 * e == N) {
+        return make_float2(-a.x, -a.y);
+    } else if constexpr (4 * e == 3 * N) {
+        return make_float2(-a.y, a.x);
+    } else {
+        constexpr float wr = float(cx_cos(cx_angle(e, N)));
+        constexpr float wi = float(-cx_sin(cx_angle(e, N)));
+        return make_float2(a.x * wr - a.y * wi, a.x * wi + a.y * wr);
+    }
+}
+
+template <int I, int End, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (I < End) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, End>(f);
+    }
+}
+
+// Smallest prime factor of n (2 or 3 for the supported radices).
+__host__ __device__ constexpr int small_factor(int n) { return n % 2 == 0 ? 2 : 3; }
+
+// Position of output k of the in-place DIF below: for N = p*M, X[p*m + s]
+// ends in block s at the position its length-M sub-transform gives m.
+__host__ __device__ constexpr int dig_rev(int n, int k) {
+    int pos = 0, base = 0;
+    while (n > 1) {
+        int p = small_factor(n), m = n / p;
+        base += m * (k % p);
+        k /= p;
+        n = m;
+    }
+    return base + pos;
+}
+
+// In-register forward DFT of N values (N = 2^a 3^b), decimation in
+// frequency, in place on v[OFF .. OFF+N): input in natural order, output
+// X[k] at v[OFF + dig_rev(N, k)].  All indices are compile-time constants.
+template <int N>
+struct RegDif {
+    static constexpr int P = small_factor(N);
+    static constexpr int M = N / P;
+    template <int OFF>
+    static __device__ __forceinline__ void run(float2* v) {
+        if constexpr (N > 1) {
+            if constexpr (P == 2) {
+                static_for<0, M>([&](auto kc) {
+                    constexpr int k = decltype(kc)::value;
+                    float2 a = v[OFF + k], b = v[OFF + k + M];
+                    v[OFF + k] = cadd(a, b);
+                    v[OFF + k + M] = mul_w<N, k>(csub(a, b));
+                });
+            } else {
+                constexpr float h = 0.866025403784438646763723170752936f;  // sqrt(3)/2
+                static_for<0, M>([&](auto kc) {
+                    constexpr int k = decltype(kc)::value;
+                    float2 a = v[OFF + k], b = v[OFF + k + M], c = v[OFF + k + 2 * M];
+                    float2 t1 = cadd(b, c);
+                    float2 t2 = make_float2(a.x - 0.5f * t1.x, a.y - 0.5f * t1.y);
+                    float2 d = make_float2(h * (b.x - c.x), h * (b.y - c.y));
+                    v[OFF + k] = cadd(a, t1);
+                    v[OFF + k + M] = mul_w<N, k>(make_float2(t2.x + d.y, t2.y - d.x));          // t2 - i d
+                    v[OFF + k + 2 * M] = mul_w<N, 2 * k>(make_float2(t2.x - d.y, t2.y + d.x));  // t2 + i d
+                });
+            }
+            static_for<0, P>([&](auto sc) {
+                constexpr int sblk = decltype(sc)::value;
+                RegDif<M>::template run<OFF + sblk * M>(v);
+            });
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Stockham stages over a shared-memory tile holding C sequences of length L.
+// Element l of sequence c lives at Addr(l, c).
+// ---------------------------------------------------------------------------
+struct Plan {
+    int L;       // transform length
+    int nst;     // number of stages (1..3)
+    int rad[3];  // radices, applied in this order (Ns = product of the earlier ones)
+    int C;       // sequences per tile
+    int T;       // threads per block (multiple of 32)
+};
+
+struct AddrPlain {  // [L][C], row-major (TMA tiles)
+    int C;
+    __device__ __forceinline__ int operator()(int l, int c) const { return l * C + c; }
+};
+struct AddrSwz {  // [L][C] with the column XOR-swizzled by the row (C a power of 2)
+    int C;
+    __device__ __forceinline__ int operator()(int l, int c) const { return l * C + (c ^ (l & (C - 1))); }
+};
+
+// Load the R inputs of butterfly j, apply the inter-stage twiddles, DFT.
+template <int R, class A>
+__device__ __forceinline__ void bfly_load(const float2* tile, A addr, const float2* tw, int L, int Ns, int j, int c,
+                                          float2 (&v)[R]) {
+    const int stride = L / R;
+#pragma unroll
+    for (int r = 0; r < R; r++) v[r] = tile[addr(j + r * stride, c)];
+    if (Ns > 1) {
+        const int k = j % Ns;
+        const int step = L / (Ns * R);
+#pragma unroll
+        for (int r = 1; r < R; r++) v[r] = cmul(v[r], tw[r * k * step]);  // r*k*step < Ns*R*step = L
+    }
+    RegDif<R>::template run<0>(v);  // output r now sits at v[dig_rev(R, r)]
+}
+
+template <int R, class A>
+__device__ __forceinline__ void bfly_store(float2* tile, A addr, int Ns, int j, int c, const float2 (&v)[R]) {
+    const int k = j % Ns;
+    const int base = (j / Ns) * Ns * R + k;
+    static_for<0, R>([&](auto rc) {
+        constexpr int r = decltype(rc)::value;
+        tile[addr(base + r * Ns, c)] = v[dig_rev(R, r)];
+    });
+}
+
+// One full stage: every active thread reads, the block syncs, every active thread writes.
+// Not inlined: each radix gets its own register allocation.
+template <int R, class A>
+__device__ __noinline__ void stage_r(float2* tile, A addr, const float2* tw, int L, int Ns, int C) {
+    const int c = threadIdx.x % C, j = threadIdx.x / C;
+    const bool on = j < L / R;
+    float2 v[R];
+    if (on) bfly_load<R>(tile, addr, tw, L, Ns, j, c, v);
+    __syncthreads();
+    if (on) bfly_store<R>(tile, addr, Ns, j, c, v);
+    __syncthreads();
+}
+
+template <class A>
+__device__ __forceinline__ void stage(int R, float2* tile, A addr, const float2* tw, int L, int Ns, int C) {
+    switch (R) {
+        case 2: stage_r<2>(tile, addr, tw, L, Ns, C); break;
+        case 3: stage_r<3>(tile, addr, tw, L, Ns, C); break;
+        case 4: stage_r<4>(tile, addr, tw, L, Ns, C); break;
+        case 6: stage_r<6>(tile, addr, tw, L, Ns, C); break;
+        case 8: stage_r<8>(tile, addr, tw, L, Ns, C); break;
+        case 9: stage_r<9>(tile, addr, tw, L, Ns, C); break;
+        case 12: stage_r<12>(tile, addr, tw, L, Ns, C); break;
+        case 16: stage_r<16>(tile, addr, tw, L, Ns, C); break;
+        case 18: stage_r<18>(tile, addr, tw, L, Ns, C); break;
+        case 24: stage_r<24>(tile, addr, tw, L, Ns, C); break;
+        case 27: stage_r<27>(tile, addr, tw, L, Ns, C); break;
+        case 32: stage_r<32>(tile, addr, tw, L, Ns, C); break;
+        default: break;
+    }
+}
+
+// Forward DFT of all C sequences of the tile (natural order in and out).
+template <class A>
+__device__ __forceinline__ void fft_tile(const Plan& p, float2* tile, A addr, const float2* tw) {
+    const int r0 = p.rad[0], r1 = p.rad[1], r2 = p.rad[2];
+    stage(r0, tile, addr, tw, p.L, 1, p.C);
+    if (p.nst > 1) stage(r1, tile, addr, tw, p.L, r0, p.C);
+    if (p.nst > 2) stage(r2, tile, addr, tw, p.L, r0 * r1, p.C);
+}
+
+// Wavelet multiply between the forward and inverse z transforms, done in the
+// registers of the last forward stage: the thread that finishes forward
+// butterfly j holds X[j + r L/R], exactly the inputs of inverse butterfly j of
+// an inverse plan that starts with the same radix R.
+struct Wave {
+    float a, b;            // this column's coefficients: Psi^(kz) = a G^(kz) + b H^(kz)
+    const float* gz;       // G^ table (shared memory)
+    const float* hz;       // H^ table (shared memory)
+};
+
+template <int R, class A>
+__device__ __noinline__ void stage_fused_r(float2* tile, A addr, const float2* tw, int L, int Ns, int C,
+                                              const Wave& wv) {
+    const int c = threadIdx.x % C, j = threadIdx.x / C;
+    const bool on = j < L / R;
+    float2 v[R];
+    if (on) {
+        bfly_load<R>(tile, addr, tw, L, Ns, j, c, v);  // last forward stage: Ns * R == L
+        // forward output r (frequency kz = j + r*Ns) sits at v[dig_rev(R, r)]; the first
+        // inverse butterfly needs its inputs in natural order r
+        float2 u[R];
+        static_for<0, R>([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            int kz = j + r * Ns;
+            float psi = wv.a * wv.gz[kz] + wv.b * wv.hz[kz];
+            float2 x = v[dig_rev(R, r)];
+            u[r] = make_float2(x.x * psi, -(x.y * psi));  // multiply, then conj for the inverse
+        });
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = u[r];
+        RegDif<R>::template run<0>(v);  // first inverse stage (Ns = 1, no twiddles)
+    }
+    __syncthreads();
+    if (on) bfly_store<R>(tile, addr, 1, j, c, v);
+    __syncthreads();
+}
+
+template <class A>
+__device__ __forceinline__ void stage_fused(int R, float2* tile, A addr, const float2* tw, int L, int Ns, int C,
+                                            const Wave& wv) {
+    switch (R) {
+        case 2: stage_fused_r<2>(tile, addr, tw, L, Ns, C, wv); break;
+        case 3: stage_fused_r<3>(tile, addr, tw, L, Ns, C, wv); break;
+        case 4: stage_fused_r<4>(tile, addr, tw, L, Ns, C, wv); break;
+        case 6: stage_fused_r<6>(tile, addr, tw, L, Ns, C, wv); break;
+        case 8: stage_fused_r<8>(tile, addr, tw, L, Ns, C, wv); break;
+        case 9: stage_fused_r<9>(tile, addr, tw, L, Ns, C, wv); break;
+        case 12: stage_fused_r<12>(tile, addr, tw, L, Ns, C, wv); break;
+        case 16: stage_fused_r<16>(tile, addr, tw, L, Ns, C, wv); break;
+        case 18: stage_fused_r<18>(tile, addr, tw, L, Ns, C, wv); break;
+        case 24: stage_fused_r<24>(tile, addr, tw, L, Ns, C, wv); break;
+        case 27: stage_fused_r<27>(tile, addr, tw, L, Ns, C, wv); break;
+        case 32: stage_fused_r<32>(tile, addr, tw, L, Ns, C, wv); break;
+        default: break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// TMA and mbarrier helpers (inline PTX).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bounded wait on phase `parity`; returns false if the limit was reached.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+    uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < limit; it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store_commit_and_drain() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// y / z pencil pass: one CTA transforms C adjacent columns of one plane.
+// ---------------------------------------------------------------------------
+enum YzMode : int { kYzForward = 0, kYzInverse = 1, kYzWavelet = 2 };
+
+struct YzArgs {
+    Plan p;
+    int ncc;         // column chunks per plane
+    int boxr;        // rows per TMA box
+    int nbox;        // boxes per tile (boxr * nbox == L)
+    int mode;
+    int along_z;     // 1: transform along z (plane index o = y), 0: along y (o = z)
+    int M;           // ng / 2 (highest valid kx)
+    const float2* tw;   // [L]
+    const float* ghat;  // [L]  G^(k)   (wavelet mode)
+    const float* hhat;  // [L]  H^(k)
+    float scale;        // w^1.5 / ng^3
+    int* status;
+};
+
+__global__ void __launch_bounds__(512, 1)
+    k_fft_yz(const __grid_constant__ CUtensorMap in_map, const __grid_constant__ CUtensorMap out_map, YzArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const Plan& p = a.p;
+    const int L = p.L, C = p.C;
+    // TMA boxes land at 128-byte aligned offsets of the tile
+    unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    float2* tile = reinterpret_cast<float2*>(base);
+    float2* tw = tile + L * C;
+    float* gz = reinterpret_cast<float*>(tw + L);
+    float* hz = gz + L;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(hz + L);  // 8-byte aligned: 8 * (L*C + 2L) bytes in
+    const int cc = blockIdx.x % a.ncc, o = blockIdx.x / a.ncc;
+
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, uint32_t(L) * C * 8u);
+        for (int b = 0; b < a.nbox; b++) {
+            int r = b * a.boxr;
+            if (a.along_z) tma_load_3d(tile + r * C, &in_map, bar, 2 * cc * C, o, r);
+            else tma_load_3d(tile + r * C, &in_map, bar, 2 * cc * C, r, o);
+        }
+    }
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        tw[i] = a.tw[i];
+        if (a.mode == kYzWavelet) {
+            gz[i] = a.ghat[i];
+            hz[i] = a.hhat[i];
+        }
+    }
+    Wave wv{0.f, 0.f, gz, hz};
+    if (a.mode == kYzWavelet) {
+        // column c <-> kx = cc*C + c, this plane <-> ky = o
+        int kx = cc * C + int(threadIdx.x % C);
+        if (kx <= a.M) {
+            float gx = a.ghat[kx], hx = a.hhat[kx], gy = a.ghat[o], hy = a.hhat[o];
+            wv.a = a.scale * (6.f * gx * gy - hx * gy - gx * hy);
+            wv.b = -a.scale * gx * gy;
+        }
+    }
+    __syncthreads();
+    if (!mbar_wait(bar, 0, kSpinLimit)) {
+        set_status(a.status, CWTHF_E_TIMEOUT);
+        mbar_wait(bar, 0, kSpinLimit);  // give the copy a second bounded chance before leaving
+        return;
+    }
+    AddrPlain addr{C};
+    const int n = L * C;
+    if (a.mode == kYzInverse) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) tile[i] = conjf2(tile[i]);
+        __syncthreads();
+        fft_tile(p, tile, addr, tw);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) tile[i] = conjf2(tile[i]);
+    } else if (a.mode == kYzForward) {
+        fft_tile(p, tile, addr, tw);
+    } else {
+        // forward stages, the last fused with the multiply and the first inverse
+        // stage, then the remaining inverse stages with the radices reversed
+        const int r0 = p.rad[0], r1 = p.rad[1], r2 = p.rad[2];
+        if (p.nst == 1) {
+            stage_fused(r0, tile, addr, tw, L, 1, C, wv);
+        } else if (p.nst == 2) {
+            stage(r0, tile, addr, tw, L, 1, C);
+            stage_fused(r1, tile, addr, tw, L, r0, C, wv);
+            stage(r0, tile, addr, tw, L, r1, C);
+        } else {
+            stage(r0, tile, addr, tw, L, 1, C);
+            stage(r1, tile, addr, tw, L, r0, C);
+            stage_fused(r2, tile, addr, tw, L, r0 * r1, C, wv);
+            stage(r1, tile, addr, tw, L, r2, C);
+            stage(r0, tile, addr, tw, L, r2 * r1, C);
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) tile[i] = conjf2(tile[i]);
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < a.nbox; b++) {
+            int r = b * a.boxr;
+            if (a.along_z) tma_store_3d(&out_map, tile + r * C, 2 * cc * C, o, r);
+            else tma_store_3d(&out_map, tile + r * C, 2 * cc * C, r, o);
+        }
+        tma_store_commit_and_drain();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// x passes: C rows of one real transform each (plain coalesced loads).
+// ---------------------------------------------------------------------------
+struct XArgs {
+    Plan p;          // complex FFT of length M = ng / 2 over C rows
+    int ng, M, P;
+    int64_t rows;    // ng * ng
+    double unit;     // physical mass of one grid unit (mass_unit * 2^-30)
+    const float2* twM;  // [M]   exp(-2 pi i m / M)
+    const float2* twN;  // [ng]  exp(-2 pi i k / ng)
+};
+
+__global__ void __launch_bounds__(512, 1) k_fft_x_fwd(XArgs a, const int64_t* __restrict__ grid,
+                                                      float2* __restrict__ spec) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const Plan& p = a.p;
+    const int M = a.M, C = p.C;
+    float2* tile = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = tile + M * C;
+    double* rowdc = reinterpret_cast<double*>(tw + M);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = a.twM[i];
+    AddrSwz addr{C};
+    // load, exact row sum, remove the row mean in fp64, round to fp32
+    for (int r = warp; r < C; r += nwarp) {
+        int64_t row = int64_t(blockIdx.x) * C + r;
+        longlong2 v[16];
+        long long sum = 0;
+        const longlong2* src = reinterpret_cast<const longlong2*>(grid + row * a.ng);
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            int k = lane + 32 * i;
+            v[i] = (row < a.rows && k < M) ? src[k] : make_longlong2(0, 0);
+            sum += v[i].x + v[i].y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        double mean = __ddiv_rn(__dmul_rn(double(sum), a.unit), double(a.ng));
+        if (lane == 0) rowdc[r] = __dmul_rn(double(sum), a.unit);
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            int k = lane + 32 * i;
+            if (k < M) {
+                float re = float(__dsub_rn(__dmul_rn(double(v[i].x), a.unit), mean));
+                float im = float(__dsub_rn(__dmul_rn(double(v[i].y), a.unit), mean));
+                tile[addr(k, r)] = make_float2(re, im);
+            }
+        }
+    }
+    __syncthreads();
+    fft_tile(p, tile, addr, tw);
+    // r2c post-processing: X[k] = (Z[k] + Z*[M-k])/2 - (i/2) W_N^k (Z[k] - Z*[M-k])
+    for (int r = warp; r < C; r += nwarp) {
+        int64_t row = int64_t(blockIdx.x) * C + r;
+        if (row >= a.rows) continue;
+        float2* out = spec + row * a.P;
+        for (int k = lane; k <= M / 2; k += 32) {
+            float2 zk = tile[addr(k, r)];
+            float2 zm = tile[addr((M - k) % M, r)];
+            if (k == 0) {
+                out[0] = make_float2(float(rowdc[r]), 0.f);
+                out[M] = make_float2(zk.x - zk.y, 0.f);
+                continue;
+            }
+            float2 w = a.twN[k];
+            // k side
+            float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));   // (Z[k] + conj Z[M-k]) / 2
+            float2 d = make_float2(0.5f * (zk.x - zm.x), 0.5f * (zk.y + zm.y));   // (Z[k] - conj Z[M-k]) / 2
+            float2 wd = cmul(w, d);
+            out[k] = make_float2(e.x + wd.y, e.y - wd.x);  // e - i w d
+            if (2 * k != M) {
+                // M-k side: the same with Z[k] and Z[M-k] swapped and W^(M-k) = -conj(W^k)
+                float2 e2 = make_float2(e.x, -e.y);
+                float2 d2 = make_float2(-d.x, d.y);
+                float2 w2 = make_float2(-w.x, w.y);
+                float2 wd2 = cmul(w2, d2);
+                out[M - k] = make_float2(e2.x + wd2.y, e2.y - wd2.x);
+            }
+        }
+        for (int k = M + 1 + lane; k < a.P; k += 32) out[k] = make_float2(0.f, 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(512, 1) k_fft_x_inv(XArgs a, const float2* __restrict__ spec,
+                                                      float* __restrict__ cwt) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const Plan& p = a.p;
+    const int M = a.M, C = p.C;
+    float2* tile = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = tile + M * C;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = a.twM[i];
+    AddrSwz addr{C};
+    // c2r pre-processing: Z'[k] = (X[k] + X*[M-k]) + i W_N^-k (X[k] - X*[M-k]); stored conjugated
+    for (int r = warp; r < C; r += nwarp) {
+        int64_t row = int64_t(blockIdx.x) * C + r;
+        const float2* in = spec + (row < a.rows ? row : 0) * a.P;
+        for (int k = lane; k <= M / 2; k += 32) {
+            float2 xk = in[k], xm = in[M - k];
+            if (k == 0) {
+                xk.y = 0.f;
+                xm.y = 0.f;
+            }
+            float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);  // X[k] + conj X[M-k]
+            float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);  // X[k] - conj X[M-k]
+            float2 winv = conjf2(a.twN[k]);                    // W_N^-k
+            float2 wd = cmul(winv, d);
+            float2 zk = make_float2(e.x - wd.y, e.y + wd.x);   // e + i W^-k d
+            tile[addr(k, r)] = conjf2(zk);
+            if (k != 0 && 2 * k != M) {
+                float2 e2 = make_float2(e.x, -e.y);
+                float2 d2 = make_float2(-d.x, d.y);
+                float2 w2 = make_float2(-winv.x, winv.y);      // W_N^-(M-k) = -conj(W_N^-k)
+                float2 wd2 = cmul(w2, d2);
+                float2 zm = make_float2(e2.x - wd2.y, e2.y + wd2.x);
+                tile[addr(M - k, r)] = conjf2(zm);
+            }
+        }
+    }
+    __syncthreads();
+    fft_tile(p, tile, addr, tw);
+    for (int r = warp; r < C; r += nwarp) {
+        int64_t row = int64_t(blockIdx.x) * C + r;
+        if (row >= a.rows) continue;
+        float2* out = reinterpret_cast<float2*>(cwt + row * a.ng);
+        for (int n = lane; n < M; n += 32) {
+            float2 z = tile[addr(n, r)];
+            out[n] = make_float2(z.x, -z.y);  // conj back; z[n] = x[2n] + i x[2n+1]
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side: plans, tables, tensor maps, launches.
+// ---------------------------------------------------------------------------
+constexpr int kRadices[] = {2, 3, 4, 6, 8, 9, 12, 16, 18, 24, 27, 32};
+
+bool is_radix(int r) {
+    for (int x : kRadices)
+        if (x == r) return true;
+    return false;
+}
+
+// Up to three radices from kRadices whose product is L, maximising the
+// smallest radix (fewest threads, least shared-memory traffic).
+bool make_plan(int L, Plan& p) {
+    int best = -1;
+    p.L = L;
+    if (is_radix(L)) {
+        p.nst = 1;
+        p.rad[0] = L;
+        return true;
+    }
+    for (int a : kRadices) {
+        if (L % a) continue;
+        int rem = L / a;
+        if (is_radix(rem) && std::min(a, rem) > best) {
+            best = std::min(a, rem);
+            p.nst = 2;
+            p.rad[0] = a;
+            p.rad[1] = rem;
+        }
+    }
+    if (best > 0) return true;
+    for (int a : kRadices)
+        for (int b : kRadices) {
+            if (L % (a * b)) continue;
+            int c = L / (a * b);
+            if (!is_radix(c)) continue;
+            int m = std::min(a, std::min(b, c));
+            if (m > best) {
+                best = m;
+                p.nst = 3;
+                p.rad[0] = a;
+                p.rad[1] = b;
+                p.rad[2] = c;
+            }
+        }
+    return best > 0;
+}
+
+int plan_threads(const Plan& p) {
+    int rmin = 64;
+    for (int s = 0; s < p.nst; s++) rmin = std::min(rmin, p.rad[s]);
+    int t = p.C * (p.L / rmin);
+    return (t + 31) / 32 * 32;
+}
+
+// Columns per y/z tile: <= 64 KB of complex data and <= 512 threads.
+bool yz_plan(int L, Plan& p) {
+    if (!make_plan(L, p)) return false;
+    for (int C : {16, 8, 4, 2}) {
+        p.C = C;
+        p.T = plan_threads(p);
+        if (size_t(L) * C * 8 <= 65536 && p.T <= 512) return true;
+    }
+    return false;
+}
+
+bool x_plan(int M, Plan& p) {
+    if (!make_plan(M, p)) return false;
+    for (int C : {16, 8, 4, 2}) {
+        p.C = C;
+        p.T = std::max(plan_threads(p), 32 * std::min(C, 16));  // at least one warp per row for the load
+        if (size_t(M) * C * 8 <= 65536 && p.T <= 512) return true;
+    }
+    return false;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+// 3D view of a spectrum as floats: dim0 = 2P floats (contiguous), dim1 = y,
+// dim2 = z.  A box is C complex columns by boxr rows of the transform axis
+// (y: {2C, boxr, 1}; z: {2C, 1, boxr}); either lands in shared memory as a
+// dense [boxr][C] complex tile.
+int make_spec_map(CUtensorMap* map, float2* base, int ng, bool along_z, int C, int boxr) {
+    auto fn = encode_fn();
+    if (!fn) return CWTHF_E_CUDA;
+    const int P = spec_pitch(ng);
+    cuuint64_t dims[3] = {cuuint64_t(2 * P), cuuint64_t(ng), cuuint64_t(ng)};
+    cuuint64_t row = cuuint64_t(P) * 8, plane = row * ng;
+    cuuint64_t strides[2] = {row, plane};
+    cuuint32_t box[3] = {cuuint32_t(2 * C), along_z ? 1u : cuuint32_t(boxr), along_z ? cuuint32_t(boxr) : 1u};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? CWTHF_OK : CWTHF_E_CUDA;
+}
+
+int pick_boxr(int L, int C) {
+    for (int b = std::min(L, 256); b >= 1; b--)
+        if (L % b == 0 && (size_t(b) * C * 8) % 128 == 0) return b;
+    return -1;
+}
+
+size_t yz_smem(const Plan& p) { return 128 + size_t(p.L) * p.C * 8 + size_t(p.L) * 8 + size_t(p.L) * 8 + 16; }
+size_t x_smem(const Plan& p) { return size_t(p.L) * p.C * 8 + size_t(p.L) * 8 + size_t(p.C) * 8; }
+
+void host_twiddles(int n, std::vector<float2>& out) {
+    out.resize(n);
+    for (int m = 0; m < n; m++) {
+        double ang = 2.0 * kPi * double(m) / double(n);
+        out[m] = make_float2(float(std::cos(ang)), float(-std::sin(ang)));
+    }
+}
+
+Tables* get_tables(cwthf_ctx* ctx, int ng, cudaStream_t s) {
+    std::lock_guard<std::mutex> g(ctx->table_mu);
+    auto it = ctx->fft_tables.find(ng);
+    if (it != ctx->fft_tables.end()) return it->second;
+    Tables* t = new Tables;
+    t->ng = ng;
+    std::vector<float2> a, b;
+    host_twiddles(ng, a);
+    host_twiddles(ng / 2, b);
+    if (cudaMalloc(&t->twN, a.size() * 8) != cudaSuccess || cudaMalloc(&t->twM, b.size() * 8) != cudaSuccess ||
+        cudaMemcpy(t->twN, a.data(), a.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t->twM, b.data(), b.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(t->twN);
+        cudaFree(t->twM);
+        delete t;
+        return nullptr;
+    }
+    (void)s;
+    ctx->fft_tables[ng] = t;
+    return t;
+}
+
+// G^(k) and H^(k), k < ng: 1D DFTs (real, even sequences) of the sampled
+// Gaussian factor and of its w^2 u^2 multiple, in fp64, stored as fp32.
+float* get_wavelet_tables(cwthf_ctx* ctx, int ng, double L, double w) {
+    std::lock_guard<std::mutex> g(ctx->table_mu);
+    auto key = std::make_tuple(ng, L, w);
+    auto it = ctx->wavelet_tables.find(key);
+    if (it != ctx->wavelet_tables.end()) return it->second;
+    const double dx = L / ng;
+    std::vector<double> gn(ng), hn(ng), cosn(ng);
+    for (int n = 0; n < ng; n++) {
+        int d = (2 * n <= ng) ? n : n - ng;
+        double u2 = (dx * d) * (dx * d);
+        gn[n] = std::exp(-0.25 * w * w * u2);
+        hn[n] = w * w * u2 * gn[n];
+        cosn[n] = std::cos(2.0 * kPi * double(n) / double(ng));
+    }
+    std::vector<float> tab(2 * size_t(ng));
+    for (int k = 0; k < ng; k++) {
+        double sg = 0.0, sh = 0.0;
+        for (int n = 0; n < ng; n++) {
+            double c = cosn[(int64_t(k) * n) % ng];
+            sg += gn[n] * c;
+            sh += hn[n] * c;
+        }
+        tab[k] = float(sg);
+        tab[ng + k] = float(sh);
+    }
+    float* d = nullptr;
+    if (cudaMalloc(&d, tab.size() * 4) != cudaSuccess) return nullptr;
+    if (cudaMemcpy(d, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return nullptr;
+    }
+    ctx->wavelet_tables[key] = d;
+    return d;
+}
+
+int launch_yz(cwthf_ctx* ctx, float2* src, float2* dst, int ng, bool along_z, int mode, const Tables* t,
+              const float* wtab, double w, cudaStream_t s) {
+    Plan p;
+    if (!yz_plan(ng, p)) return CWTHF_E_UNSUPPORTED_SIZE;
+    int boxr = pick_boxr(ng, p.C);
+    if (boxr < 0) return CWTHF_E_UNSUPPORTED_SIZE;
+    CUtensorMap in_map, out_map;
+    int rc = make_spec_map(&in_map, src, ng, along_z, p.C, boxr);
+    if (!rc) rc = make_spec_map(&out_map, dst, ng, along_z, p.C, boxr);
+    if (rc) return rc;
+    YzArgs a;
+    a.p = p;
+    a.M = ng / 2;
+    a.ncc = div_up(a.M + 1, p.C);
+    a.boxr = boxr;
+    a.nbox = ng / boxr;
+    a.mode = mode;
+    a.along_z = along_z ? 1 : 0;
+    a.tw = t->twN;
+    a.ghat = wtab;
+    a.hhat = wtab ? wtab + ng : nullptr;
+    a.scale = float(std::pow(w, 1.5) / (double(ng) * ng * ng));
+    a.status = ctx->d_status;
+    size_t smem = yz_smem(p);
+    cudaFuncSetAttribute(k_fft_yz, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    k_fft_yz<<<unsigned(a.ncc) * ng, p.T, smem, s>>>(in_map, out_map, a);
+    count_launch(ctx);
+    return cuda_status(cudaGetLastError());
+}
+
+int x_args(int ng, double unit, const Tables* t, XArgs& a) {
+    Plan p;
+    if (!x_plan(ng / 2, p)) return CWTHF_E_UNSUPPORTED_SIZE;
+    a.p = p;
+    a.ng = ng;
+    a.M = ng / 2;
+    a.P = spec_pitch(ng);
+    a.rows = int64_t(ng) * ng;
+    a.unit = unit;
+    a.twM = t->twM;
+    a.twN = t->twN;
+    return CWTHF_OK;
+}
+
+}  // namespace
+
+int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, double mass_unit, float2* spec,
+                         cudaStream_t s) {
+    if (ng / 2 > 512) return CWTHF_E_UNSUPPORTED_SIZE;
+    Tables* t = get_tables(ctx, ng, s);
+    if (!t) return CWTHF_E_CUDA;
+    XArgs a;
+    int rc = x_args(ng, mass_unit / double(int64_t(1) << (3 * kFracBits)), t, a);
+    if (rc) return rc;
+    cudaFuncSetAttribute(k_fft_x_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(x_smem(a.p)));
+    k_fft_x_fwd<<<div_up(a.rows, a.p.C), a.p.T, x_smem(a.p), s>>>(a, grid, spec);
+    count_launch(ctx);
+    if ((rc = cuda_status(cudaGetLastError()))) return rc;
+    return launch_yz(ctx, spec, spec, ng, false, kYzForward, t, nullptr, 0.0, s);
+}
+
+int transform_wavelet_inverse(cwthf_ctx* ctx, float2* src, float2* dst, int ng, double L, double w, float* cwt,
+                              cudaStream_t s) {
+    Tables* t = get_tables(ctx, ng, s);
+    float* wtab = get_wavelet_tables(ctx, ng, L, w);
+    if (!t || !wtab) return CWTHF_E_CUDA;
+    int rc = launch_yz(ctx, src, dst, ng, true, kYzWavelet, t, wtab, w, s);
+    if (!rc) rc = launch_yz(ctx, dst, dst, ng, false, kYzInverse, t, nullptr, 0.0, s);
+    if (rc) return rc;
+    XArgs a;
+    if ((rc = x_args(ng, 0.0, t, a))) return rc;
+    cudaFuncSetAttribute(k_fft_x_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(x_smem(a.p)));
+    k_fft_x_inv<<<div_up(a.rows, a.p.C), a.p.T, x_smem(a.p), s>>>(a, dst, cwt);
+    count_launch(ctx);
+    return cuda_status(cudaGetLastError());
+}
+
+bool fft_size_supported(int ng) {
+    Plan p;
+    return (ng % 2 == 0) && ng / 2 <= 512 && yz_plan(ng, p) && x_plan(ng / 2, p) && pick_boxr(ng, p.C) > 0;
+}
+
+void free_tables(cwthf_ctx* ctx) {
+    for (auto& kv : ctx->fft_tables) {
+        cudaFree(kv.second->twN);
+        cudaFree(kv.second->twM);
+        delete kv.second;
+    }
+    ctx->fft_tables.clear();
+    for (auto& kv : ctx->wavelet_tables) cudaFree(kv.second);
+    ctx->wavelet_tables.clear();
+}
+
+}  // namespace cwthf

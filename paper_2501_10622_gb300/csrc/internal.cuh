@@ -1,0 +1,179 @@
+// internal.cuh -- declarations shared by the CUDA translation units of
+// libcwthf.so (not part of the public ABI; see include/cwthf.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "../../include/cwthf.h"
+
+namespace cwthf {
+
+constexpr int kFracBits = CWTHF_FRAC_BITS;
+constexpr int64_t kFracOne = int64_t(1) << kFracBits;
+
+// Deposit tiles: the grid is cut into tiles of kDepTX x kDepTY x kDepTZ cells
+// (the last tile along an axis may be partial).
+constexpr int kDepTX = 32, kDepTY = 8, kDepTZ = 8;
+constexpr int kDepClasses = 8;  // boundary class bits (x, y, z) per particle
+
+// Segmentation tiles (owned cells; one halo layer is staged around them).
+constexpr int kSegTX = 32, kSegTY = 8, kSegTZ = 4;
+constexpr int kMaxJumpRounds = 40;
+
+// A bounded device wait gives up after this many polls.
+constexpr long long kSpinLimit = 1ll << 26;
+
+struct Tables;  // FFT and wavelet tables for one grid size (fft.cu)
+
+struct cwthf_ctx_impl;
+
+// Shape of one complex half-spectrum workspace [ng][ng][pitch] (float2).
+inline int spec_pitch(int ng) {
+    int m = ng / 2 + 1;
+    return (m % 2) ? m + 1 : m;  // even number of complex -> 16-byte aligned rows
+}
+inline size_t spec_bytes(int ng) { return size_t(ng) * ng * spec_pitch(ng) * 8; }
+
+inline int div_up(int64_t a, int64_t b) { return int((a + b - 1) / b); }
+
+struct DepositGeom {
+    int ng, ntx, nty, ntz;
+    int64_t ntiles;
+};
+inline DepositGeom deposit_geom(int ng) {
+    DepositGeom g;
+    g.ng = ng;
+    g.ntx = div_up(ng, kDepTX);
+    g.nty = div_up(ng, kDepTY);
+    g.ntz = div_up(ng, kDepTZ);
+    g.ntiles = int64_t(g.ntx) * g.nty * g.ntz;
+    return g;
+}
+
+// Per-slot accumulators of the halo reduction (one slot per seed).
+struct HaloAcc {
+    unsigned long long n_part;
+    unsigned long long mq;
+    long long mom[3];
+    unsigned long long n_cells;
+};
+
+}  // namespace cwthf
+
+// The opaque context of the public ABI.
+struct cwthf_ctx {
+    int device = 0;
+    int max_ng = 0;
+    int64_t max_np = 0;
+    int max_scales = 1;
+    int sm_count = 0;
+
+    int* d_status = nullptr;   // first device-side error since the last cwthf_sync
+    int* h_status = nullptr;   // pinned mirror
+
+    // deposit scratch
+    uint32_t* dep_count = nullptr;   // [max_tiles * 8 + 1]
+    uint32_t* dep_off = nullptr;     // [max_tiles * 8 + 1]
+    uint32_t* dep_cursor = nullptr;  // [max_tiles * 8]
+    unsigned long long* dep_rec = nullptr;  // [max_np] packed fixed-point records
+    uint32_t* dep_mq = nullptr;             // [max_np] integer masses of the records
+    unsigned long long* d_mtot = nullptr;   // [1] sum of m_q of the last deposit / assign
+
+    // transform scratch
+    float2* spec = nullptr;    // complex half spectrum [ng][ng][pitch]
+    float2* spec2 = nullptr;   // second spectrum (multi-scale), or nullptr
+
+    // segmentation / assignment scratch
+    uint32_t* seed_bits = nullptr;    // [ng^3 / 32 + 1] seed bitmap
+    uint32_t* seed_prefix = nullptr;  // [ng^3 / 32 + 1] exclusive popcount prefix
+    int32_t* seed_list = nullptr;     // [ng^3 / 8 + 1] seed cell of each slot
+    uint32_t* n_seeds = nullptr;      // [1]
+    cwthf::HaloAcc* acc = nullptr;    // [ng^3 / 8 + 1]
+    uint32_t* keep_off = nullptr;     // [ng^3 / 8 + 2] kept-halo prefix
+    int32_t* part_slot = nullptr;     // [max_np]
+    int* jump_changed = nullptr;      // [kMaxJumpRounds + 1]
+    uint32_t* scan_tmp = nullptr;     // block sums of the device scan
+    size_t scan_tmp_cap = 0;          // words
+
+    // cwthf_find internals
+    int64_t* grid = nullptr;
+    float* cwt = nullptr;
+    int32_t* label = nullptr;
+
+    std::atomic<int64_t> launches{0};
+
+    std::mutex table_mu;
+    std::map<int, cwthf::Tables*> fft_tables;                                 // per ng
+    std::map<std::tuple<int, double, double>, float*> wavelet_tables;        // (ng, L, w) -> device [2*ng]
+};
+
+namespace cwthf {
+
+// ---- status helpers ---------------------------------------------------------
+__device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+
+// ---- warp helpers -------------------------------------------------------------
+// Lane of the n-th (0-based) member of the lane set `group`, or 32 if the
+// group has no more than n members.
+__device__ __forceinline__ int nth_member(unsigned group, int n) {
+    if (n >= __popc(group)) return 32;
+    int pos = 0;  // largest pos with popc(group below pos) <= n
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1)
+        if (__popc(group & ((1u << (pos + w)) - 1u)) <= n) pos += w;
+    return pos;
+}
+
+// Sum of v over the lanes of `peers` (lanes sharing one key, as returned by
+// __match_any_sync), delivered to the group's lowest lane (rank 0): a
+// log-depth tree over the ranks within the group.  All 32 lanes must call it.
+template <class T>
+__device__ __forceinline__ T group_sum(T v, unsigned peers, int lane, int rank) {
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        int src = nth_member(peers, rank + s);
+        T t = __shfl_sync(0xffffffffu, v, src < 32 ? src : lane);
+        if ((rank & (2 * s - 1)) == 0 && src < 32) v += t;
+    }
+    return v;
+}
+
+// ---- host helpers (ctx.cu) --------------------------------------------------
+int check_ng(int ng);
+int cuda_status(cudaError_t e);
+inline void count_launch(cwthf_ctx* c, int n = 1) { c->launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---- scan (scan.cu) ----------------------------------------------------------
+// Exclusive scan of n uint32 values (n given on the host): out[i] = sum_{j<i} in[j],
+// out[n] = total.  in and out may alias.
+int scan_u32(cwthf_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s);
+// Same, with the length read from device memory (*d_n <= n_cap).
+int scan_u32_dev(cwthf_ctx* ctx, const uint32_t* in, uint32_t* out, const uint32_t* d_n, int64_t n_cap,
+                 cudaStream_t s);
+size_t scan_tmp_words(int64_t n_cap);
+
+// ---- stages -------------------------------------------------------------------
+int deposit_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L,
+                 int ng, int64_t* grid, int64_t* mtot, cudaStream_t s);
+// Forward half of the transform: x r2c and y c2c -> ctx spectrum `spec`.
+int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, double mass_unit, float2* spec,
+                         cudaStream_t s);
+// z forward, wavelet multiply, z inverse (src -> dst, may alias), then
+// y inverse and x c2r into cwt.
+int transform_wavelet_inverse(cwthf_ctx* ctx, float2* src, float2* dst, int ng, double L, double w, float* cwt,
+                              cudaStream_t s);
+int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_t* label, bool seeds_ready,
+                 cudaStream_t s);
+int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L,
+                int ng, const int32_t* label, const float* cwt, const cwthf_params* p, int32_t* halo_id,
+                cwthf_halo* cat, int64_t cat_cap, int64_t* n_halo, bool seeds_ready, cudaStream_t s);
+void free_tables(cwthf_ctx* ctx);
+
+}  // namespace cwthf

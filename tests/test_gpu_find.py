@@ -1,0 +1,58 @@
+"""The whole path through cwthf_find against the oracle run end to end."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2501_10622_gb300 as pkg
+from paper_2501_10622_gb300 import synth
+from tests.gpu_util import dev
+
+pytestmark = pytest.mark.gpu
+
+
+def test_workload64_agreement(gctx, work64):
+    wl, pos, ref = work64
+    hid, cat, nh = gctx.find(dev(pos), wl.box, wl.ng, [pkg.default_params(2.0)])
+    gctx.check()
+    agree = float(np.mean(hid[0].cpu().numpy() == ref["halo_id"]))
+    assert agree >= 0.999, agree
+    n = int(nh[0])
+    assert abs(n - len(ref["cat"]["seed"])) <= max(2, n // 50)
+
+
+def test_multi_scale_equals_single_scale(gctx, work64):
+    wl, pos, ref = work64
+    p = dev(pos)
+    scales = [pkg.default_params(w) for w in (2.0, 3.0, 4.0)]
+    hid, cat, nh = gctx.find(p, wl.box, wl.ng, scales)
+    gctx.check()
+    for i, sp in enumerate(scales):
+        h1, c1, n1 = gctx.find(p, wl.box, wl.ng, [sp])
+        gctx.check()
+        assert torch.equal(hid[i], h1[0])
+        assert int(nh[i]) == int(n1[0])
+        assert torch.equal(cat[i, :int(n1[0])], c1[0, :int(n1[0])])
+
+
+def test_find_equals_stage_by_stage(gctx, work64):
+    wl, pos, ref = work64
+    p = dev(pos)
+    g = gctx.deposit(p, wl.box, wl.ng)
+    c = gctx.transform(g, wl.box, 2.0)
+    lab = gctx.segment(c)
+    hid, cat, nh = gctx.assign(p, wl.box, lab, c)
+    h2, c2, n2 = gctx.find(p, wl.box, wl.ng, [pkg.default_params(2.0)])
+    gctx.check()
+    assert torch.equal(hid, h2[0]) and int(nh) == int(n2[0])
+
+
+def test_workload256_agreement(gctx):
+    wl = synth.WORKLOADS["clumped-256cube-L200"]
+    pos = wl.positions("cuda")
+    hid, cat, nh = gctx.find(pos, wl.box, wl.ng, [pkg.default_params(2.0)])
+    gctx.check()
+    ref = oracle.find(pos.cpu().numpy(), wl.box, wl.ng, 2.0)
+    agree = float(np.mean(hid[0].cpu().numpy() == ref["halo_id"]))
+    print(f"256^3 particle agreement {agree:.6f}, halos {int(nh[0])} vs {len(ref['cat']['seed'])}")
+    assert agree >= 0.999
