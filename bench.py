@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Throughput of the CWTHF single-scale hot path on GB300.
+
+One step = one cwthf_find call on the resident particle set: CIC deposit,
+forward FFT, then for each of the workload's wavelet scales the wavelet
+multiply + inverse FFT, segmentation and particle assignment with the
+per-halo catalogue.  Default workload: 512^3 = 134,217,728 clumped particles
+in a 500 Mpc/h box on a 1024^3 grid, scales w = 2, 3, 4 h/Mpc.
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own
+replica (independent synthetic box, no collective on the data path); the
+throughput is the sum over ranks of particles / max-over-ranks step time.
+`--impl reference` times the fp64 CPU oracle on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "Mparticles/s end-to-end halo ID at 512³/1024³ grid, % HBM roofline; served p50/p99"
+UNIT = "Mparticles/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="clumped-512cube-grid1024-L500")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-ng", type=int, default=128)
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic bytes per launch of each kernel (what the method itself must
+# move; see the design notes).  u = dict(ng, np, cells, half) with half =
+# ng * ng * (ng/2 + 1) complex values of the half spectrum.
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(name, u):
+    cells, half, npart = u["cells"], u["half"], u["np"]
+    table = {
+        "k_fft_yz": 2 * 8 * half,                      # read + write the half spectrum
+        "k_fft_x_fwd": 8 * cells + 8 * half,           # int64 grid in, half spectrum out
+        "k_fft_x_inv": 8 * half + 4 * cells,           # half spectrum in, fp32 CWT out
+        "k_dep_tile": 8 * cells + 8 * npart,           # records in once, int64 grid out
+        "k_dep_count": 12 * npart,
+        "k_dep_scatter": 12 * npart + 8 * npart,
+        "k_seg_tile": 4 * cells + 4 * cells,           # CWT in, labels out
+        "k_seg_jump": 4 * cells,
+        "k_count_cells": 4 * cells,
+        "k_assign": 12 * npart + 4 * npart + 4 * npart,
+        "k_finalize": 8 * npart,
+    }
+    return table.get(name)
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def stored_traffic(name, u):
+    """DRAM bytes per launch from a committed ncu capture, scaled to this
+    workload, if the kernel's source is unchanged since the capture."""
+    f = ROOT / "profiles" / "traffic.json"
+    if not f.exists():
+        return None
+    d = json.loads(f.read_text()).get(name)
+    if not d:
+        return None
+    src = ROOT / "paper_2501_10622_gb300" / "csrc" / d["source"]
+    if not src.exists() or hashlib.sha256(src.read_bytes()).hexdigest()[:16] != d["source_sha"]:
+        return None
+    return d["dram_bytes_per_launch"] * (u["ng"] / d["ng"]) ** 3
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), float(f[3]) if f[3] not in ("[N/A]", "N/A") else 0.0, f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r[0] for r in rows if r[2] > 200.0] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, sample_ng):
+    """Same generator, same cell size and particle density, smaller box."""
+    from paper_2501_10622_gb300 import synth
+    f = sample_ng / wl.ng
+    box = wl.box * f
+    npart = int(round(wl.n_particles * f ** 3))
+    nclumps = max(1, int(round(wl.n_clumps * f ** 3)))
+    pos = synth.clumped_box(npart, box, nclumps, seed=wl.seed).numpy()
+    desc = (f"{sample_ng}^3 grid, {npart:,} particles, L={box:g} Mpc/h, {nclumps} clumps (same cell size and "
+            f"particle density as the {wl.name} workload), scales {list(wl.scales)}")
+    return pos, box, desc
+
+
+def oracle_step(pos, box, ng, scales):
+    import numpy as np
+    import oracle
+    grid, _ = oracle.cic(pos, box, ng)
+    for w in scales:
+        C = oracle.cwt(grid, box, w)
+        C32 = C.astype(np.float32)
+        lab = oracle.segment(C32)
+        oracle.assign(pos, box, lab, C32)
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return os.uname().machine
+
+
+def run_reference(args, wl, rank):
+    if rank != 0:
+        return
+    pos, box, desc = oracle_sample(wl, args.cpu_sample_ng)
+    for _ in range(args.warmup):
+        oracle_step(pos, box, args.cpu_sample_ng, wl.scales)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(pos, box, args.cpu_sample_ng, wl.scales)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    v = pos.shape[0] / t / 1e6
+    cores = f"1 of {os.cpu_count()} ({cpu_model()})"
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "sample": desc},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "cores_note": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    from paper_2501_10622_gb300 import synth
+    wl = synth.WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, wl, rank)
+        return
+
+    import numpy as np
+    import torch
+    import paper_2501_10622_gb300 as pkg
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    # replicas: each rank finds halos in its own synthetic box (weak scaling)
+    pos = synth.clumped_box(wl.n_particles, wl.box, wl.n_clumps, seed=wl.seed + 1000 * rank, device=dev)
+    npart, ng = pos.shape[0], wl.ng
+    params = [pkg.default_params(w) for w in wl.scales]
+    ns = len(params)
+    cat_cap = 1 << 22
+    ctx = pkg.Context(local, max_ng=ng, max_np=npart, max_scales=ns)
+    hid = torch.empty((ns, npart), dtype=torch.int32, device=dev)
+    cat = torch.empty((ns, cat_cap, 64), dtype=torch.uint8, device=dev)
+    nh = torch.zeros(ns, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(p):
+        ctx.find(p, wl.box, ng, params, cat_cap=cat_cap, halo_id=hid, cat=cat, n_halo=nh, stream=stream)
+
+    for _ in range(max(args.warmup, 1)):
+        step(pos)
+    ctx.check(what="warm-up")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    # ---- device-resident timed region --------------------------------------
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize(dev)
+    ctx.profile(True)
+    launches0 = ctx.launch_count()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(pos)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop()
+    launches = ctx.launch_count() - launches0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ctx.check(what="timed steps")
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t)
+    value = world * npart / (ms / 1e3) / 1e6
+
+    # ---- per-kernel roofline --------------------------------------------------
+    peak, peak_kind = measured_peaks()
+    u = dict(ng=ng, np=npart, cells=ng ** 3, half=ng * ng * (ng // 2 + 1))
+    kernels = {}
+    for name, (tot, n) in prof.items():
+        b = algorithmic_bytes(name, u)
+        avg = tot / n
+        ent = {"launches": n, "avg_ms": avg, "share": tot / (ms * args.steps)}
+        if b:
+            ent["algorithmic_bytes"] = b
+            ent["gbs"] = b / (avg / 1e3) / 1e9
+            ent["frac"] = ent["gbs"] / peak
+        kernels[name] = ent
+    dom = max((k for k in kernels if "gbs" in kernels[k]), key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
+    d = kernels[dom]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": d["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": d["gbs"] / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": stored_traffic(dom, u), "algorithmic_bytes_per_launch": d["algorithmic_bytes"]}
+    step_bytes = sum(v["algorithmic_bytes"] * v["launches"] for v in kernels.values() if "algorithmic_bytes" in v)
+    step_bytes /= args.steps
+
+    # ---- end to end through host buffers ---------------------------------------
+    e2e = None
+    if not args.no_e2e:
+        pos_h = pos.cpu().pin_memory()
+        hid_h = torch.empty(hid.shape, dtype=hid.dtype).pin_memory()
+        nh_h = torch.empty(nh.shape, dtype=nh.dtype).pin_memory()
+        pos_d = torch.empty_like(pos)
+
+        def e2e_step():
+            pos_d.copy_(pos_h, non_blocking=True)
+            step(pos_d)
+            hid_h.copy_(hid, non_blocking=True)
+            nh_h.copy_(nh, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ems = f0.elapsed_time(f1) / args.steps
+        if dist:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t)
+        ctx.check(what="e2e steps")
+        e2e = {"value": world * npart / (ems / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ems,
+               "h2d_bytes_per_step": pos.numel() * 4, "d2h_bytes_per_step": hid.numel() * 4 + nh.numel() * 8}
+
+    # ---- CPU oracle baseline (rank 0, N = 1) ------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        spos, sbox, desc = oracle_sample(wl, args.cpu_sample_ng)
+        t0 = time.perf_counter()
+        oracle_step(spos, sbox, args.cpu_sample_ng, wl.scales)
+        t = time.perf_counter() - t0
+        cpu = {"value": spos.shape[0] / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": t, "cpu": cpu_model()}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic",
+                "config": {"workload": wl.name, "n_particles": npart, "ng": ng, "box_mpc_h": wl.box,
+                           "scales_h_per_mpc": list(wl.scales), "n_clumps": wl.n_clumps,
+                           "l2": "inputs larger than L2 (1.6 GB positions, 8.6 GB grid): no flush",
+                           "parallelism": f"replicas x{world}"},
+                "grid_cells_per_s": world * ng ** 3 / (ms / 1e3),
+                "algorithmic_bytes_per_step": step_bytes,
+                "step_roofline_frac": step_bytes / (ms / 1e3) / 1e9 / peak,
+                "roofline": roofline, "kernels": kernels, "gpu_launches": launches,
+                "halos_per_scale": [int(x) for x in nh.cpu()],
+                "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -189,6 +189,19 @@ CWTHF_API const char *cwthf_error_string(int code);
  * (instrumentation for launch accounting). */
 CWTHF_API int64_t cwthf_launch_count(const cwthf_ctx *ctx);
 
+/* Per-kernel timing (instrumentation).  With enable != 0 every later kernel
+ * launch of this context is bracketed by two CUDA events recorded on its own
+ * stream; any call clears the totals.  Do not enable it while a stream is
+ * being captured into a CUDA graph.
+ * cwthf_profile_count waits for the recorded events, folds them into the
+ * per-kernel totals and returns the number of distinct kernels seen (or a
+ * negative CWTHF_E_* code); cwthf_profile_read then returns kernel i's name
+ * (a static string), summed device time in ms and launch count. */
+CWTHF_API int cwthf_profile(cwthf_ctx *ctx, int enable);
+CWTHF_API int cwthf_profile_count(cwthf_ctx *ctx);
+CWTHF_API int cwthf_profile_read(const cwthf_ctx *ctx, int i, const char **name, double *total_ms,
+                                 int64_t *launches);
+
 #ifdef __cplusplus
 }
 #endif

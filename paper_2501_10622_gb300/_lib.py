@@ -70,6 +70,10 @@ def lib() -> ctypes.CDLL:
         L.cwthf_error_string.restype = ctypes.c_char_p
         L.cwthf_launch_count.argtypes = [P]
         L.cwthf_launch_count.restype = i64
+        L.cwthf_profile.argtypes = [P, i32]
+        L.cwthf_profile_count.argtypes = [P]
+        L.cwthf_profile_read.argtypes = [P, i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(d),
+                                         ctypes.POINTER(i64)]
         _lib = L
     return _lib
 
@@ -150,6 +154,23 @@ class Context:
 
     def launch_count(self) -> int:
         return int(lib().cwthf_launch_count(self._h))
+
+    def profile(self, enable: bool = True):
+        """Turn per-kernel CUDA-event timing on/off (clears the totals)."""
+        _check(lib().cwthf_profile(self._h, 1 if enable else 0), "cwthf_profile")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since profiling was enabled."""
+        n = lib().cwthf_profile_count(self._h)
+        if n < 0:
+            raise CwthfError(-n, "cwthf_profile_count")
+        out = {}
+        for i in range(n):
+            nm, ms, k = ctypes.c_char_p(), ctypes.c_double(), ctypes.c_int64()
+            _check(lib().cwthf_profile_read(self._h, i, ctypes.byref(nm), ctypes.byref(ms), ctypes.byref(k)),
+                   "cwthf_profile_read")
+            out[nm.value.decode()] = (ms.value, k.value)
+        return out
 
     def sync(self, stream=None) -> int:
         return int(lib().cwthf_sync(self._h, self._stream(stream)))

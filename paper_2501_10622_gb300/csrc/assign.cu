@@ -221,14 +221,12 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
     int blocks = ctx->sm_count * 8;
     cudaError_t e = cudaMemsetAsync(ctx->d_mtot, 0, 8, s);
     if (e != cudaSuccess) return cuda_status(e);
-    k_count_cells<<<blocks, kThreads, 0, s>>>(label, cells, ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc,
-                                              ctx->d_status);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_count_cells", k_count_cells<<<blocks, kThreads, 0, s>>>(label, cells, ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc,
+                                              ctx->d_status));
     DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
     int pblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kThreads), int64_t(ctx->sm_count) * 16));
-    k_assign<<<pblocks, kThreads, 0, s>>>(a, label, ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc, ctx->part_slot,
-                                          ctx->d_mtot, ctx->d_status);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_assign", k_assign<<<pblocks, kThreads, 0, s>>>(a, label, ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc, ctx->part_slot,
+                                          ctx->d_mtot, ctx->d_status));
     FilterArgs f;
     f.ng = ng;
     f.L = L;
@@ -236,14 +234,11 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
     f.dens_th = p->dens_th;
     f.particle_th = p->particle_th;
     f.cat_cap = cat_cap;
-    k_keep<<<blocks, kThreads, 0, s>>>(ctx->acc, d_nseeds, ctx->d_mtot, f, ctx->keep_off);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_keep", k_keep<<<blocks, kThreads, 0, s>>>(ctx->acc, d_nseeds, ctx->d_mtot, f, ctx->keep_off));
     if ((rc = scan_u32_dev(ctx, ctx->keep_off, ctx->keep_off, d_nseeds, slot_cap, s))) return rc;
-    k_catalogue<<<blocks, kThreads, 0, s>>>(ctx->acc, ctx->seed_list, d_nseeds, ctx->keep_off, cwt, f, cat, n_halo,
-                                            ctx->d_status);
-    count_launch(ctx);
-    k_finalize<<<pblocks, kThreads, 0, s>>>(ctx->part_slot, np, ctx->keep_off, ctx->seed_list, halo_id);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_catalogue", k_catalogue<<<blocks, kThreads, 0, s>>>(ctx->acc, ctx->seed_list, d_nseeds, ctx->keep_off, cwt, f, cat, n_halo,
+                                            ctx->d_status));
+    CWTHF_LAUNCH(ctx, s, "k_finalize", k_finalize<<<pblocks, kThreads, 0, s>>>(ctx->part_slot, np, ctx->keep_off, ctx->seed_list, halo_id));
     return cuda_status(cudaGetLastError());
 }
 

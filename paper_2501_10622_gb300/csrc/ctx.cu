@@ -184,6 +184,9 @@ void cwthf_destroy(cwthf_ctx* ctx) {
     if (!ctx) return;
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
+    cwthf_profile(ctx, 0);
+    for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    ctx->prof_pool.clear();
     release(ctx);
     delete ctx;
 }
@@ -288,5 +291,53 @@ const char* cwthf_error_string(int code) {
 }
 
 int64_t cwthf_launch_count(const cwthf_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
+int cwthf_profile(cwthf_ctx* ctx, int enable) {
+    if (!ctx) return CWTHF_E_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    for (auto& r : ctx->prof_pending) {
+        cudaEventSynchronize(r.b);
+        ctx->prof_pool.push_back(r.a);
+        ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+    ctx->prof_names.clear();
+    ctx->prof_ms.clear();
+    ctx->prof_n.clear();
+    ctx->prof_on = enable != 0;
+    return CWTHF_OK;
+}
+
+int cwthf_profile_count(cwthf_ctx* ctx) {
+    if (!ctx) return -CWTHF_E_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    int rc = CWTHF_OK;
+    for (auto& r : ctx->prof_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+            rc = CWTHF_E_CUDA;
+        size_t k = 0;
+        while (k < ctx->prof_names.size() && std::strcmp(ctx->prof_names[k], r.name) != 0) k++;
+        if (k == ctx->prof_names.size()) {
+            ctx->prof_names.push_back(r.name);
+            ctx->prof_ms.push_back(0.0);
+            ctx->prof_n.push_back(0);
+        }
+        ctx->prof_ms[k] += ms;
+        ctx->prof_n[k] += 1;
+        ctx->prof_pool.push_back(r.a);
+        ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+    return rc ? -rc : int(ctx->prof_names.size());
+}
+
+int cwthf_profile_read(const cwthf_ctx* ctx, int i, const char** name, double* total_ms, int64_t* launches) {
+    if (!ctx || i < 0 || size_t(i) >= ctx->prof_names.size()) return CWTHF_E_INVALID_ARG;
+    if (name) *name = ctx->prof_names[i];
+    if (total_ms) *total_ms = ctx->prof_ms[i];
+    if (launches) *launches = ctx->prof_n[i];
+    return CWTHF_OK;
+}
 
 }  // extern "C"

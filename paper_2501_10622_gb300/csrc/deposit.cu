@@ -195,19 +195,16 @@ int deposit_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mas
     if ((e = cudaMemsetAsync(ctx->dep_count, 0, size_t(nkeys) * 4, s)) != cudaSuccess) return cuda_status(e);
     if ((e = cudaMemsetAsync(ctx->d_mtot, 0, 8, s)) != cudaSuccess) return cuda_status(e);
     int blocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kCountThreads), int64_t(ctx->sm_count) * 16));
-    k_dep_count<<<blocks, kCountThreads, 0, s>>>(a, ctx->dep_count, ctx->d_mtot, ctx->d_status);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_dep_count", k_dep_count<<<blocks, kCountThreads, 0, s>>>(a, ctx->dep_count, ctx->d_mtot, ctx->d_status));
     int rc = scan_u32(ctx, ctx->dep_count, ctx->dep_off, nkeys, s);
     if (rc) return rc;
     if ((e = cudaMemcpyAsync(ctx->dep_cursor, ctx->dep_off, size_t(nkeys) * 4, cudaMemcpyDeviceToDevice, s)) !=
         cudaSuccess)
         return cuda_status(e);
-    k_dep_scatter<<<blocks, kCountThreads, 0, s>>>(a, ctx->dep_cursor, ctx->dep_rec, ctx->dep_mq);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_dep_scatter", k_dep_scatter<<<blocks, kCountThreads, 0, s>>>(a, ctx->dep_cursor, ctx->dep_rec, ctx->dep_mq));
     int tblocks = int(std::min<int64_t>(g.ntiles, int64_t(ctx->sm_count) * 8));
-    k_dep_tile<<<tblocks, kTileThreads, 0, s>>>(a, ctx->dep_off, ctx->dep_rec, ctx->dep_mq, ctx->d_mtot, grid,
-                                                ctx->d_status);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_dep_tile", k_dep_tile<<<tblocks, kTileThreads, 0, s>>>(a, ctx->dep_off, ctx->dep_rec, ctx->dep_mq, ctx->d_mtot, grid,
+                                                ctx->d_status));
     if (mtot && (e = cudaMemcpyAsync(mtot, ctx->d_mtot, 8, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return cuda_status(e);
     return cuda_status(cudaGetLastError());

@@ -797,8 +797,7 @@ int launch_yz(cwthf_ctx* ctx, float2* src, float2* dst, int ng, bool along_z, in
     a.status = ctx->d_status;
     size_t smem = yz_smem(p);
     cudaFuncSetAttribute(k_fft_yz, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    k_fft_yz<<<unsigned(a.ncc) * ng, p.T, smem, s>>>(in_map, out_map, a);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_fft_yz", k_fft_yz<<<unsigned(a.ncc) * ng, p.T, smem, s>>>(in_map, out_map, a));
     return cuda_status(cudaGetLastError());
 }
 
@@ -827,8 +826,7 @@ int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, double mas
     int rc = x_args(ng, mass_unit / double(int64_t(1) << (3 * kFracBits)), t, a);
     if (rc) return rc;
     cudaFuncSetAttribute(k_fft_x_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(x_smem(a.p)));
-    k_fft_x_fwd<<<div_up(a.rows, a.p.C), a.p.T, x_smem(a.p), s>>>(a, grid, spec);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_fft_x_fwd", k_fft_x_fwd<<<div_up(a.rows, a.p.C), a.p.T, x_smem(a.p), s>>>(a, grid, spec));
     if ((rc = cuda_status(cudaGetLastError()))) return rc;
     return launch_yz(ctx, spec, spec, ng, false, kYzForward, t, nullptr, 0.0, s);
 }
@@ -844,8 +842,7 @@ int transform_wavelet_inverse(cwthf_ctx* ctx, float2* src, float2* dst, int ng, 
     XArgs a;
     if ((rc = x_args(ng, 0.0, t, a))) return rc;
     cudaFuncSetAttribute(k_fft_x_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(x_smem(a.p)));
-    k_fft_x_inv<<<div_up(a.rows, a.p.C), a.p.T, x_smem(a.p), s>>>(a, dst, cwt);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_fft_x_inv", k_fft_x_inv<<<div_up(a.rows, a.p.C), a.p.T, x_smem(a.p), s>>>(a, dst, cwt));
     return cuda_status(cudaGetLastError());
 }
 

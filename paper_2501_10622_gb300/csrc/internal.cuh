@@ -109,6 +109,18 @@ struct cwthf_ctx {
 
     std::atomic<int64_t> launches{0};
 
+    // optional per-kernel CUDA-event timing (cwthf_profile)
+    struct ProfRec {
+        const char* name;
+        cudaEvent_t a, b;
+    };
+    bool prof_on = false;
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    std::vector<const char*> prof_names;
+    std::vector<double> prof_ms;
+    std::vector<int64_t> prof_n;
+
     std::mutex table_mu;
     std::map<int, cwthf::Tables*> fft_tables;                                 // per ng
     std::map<std::tuple<int, double, double>, float*> wavelet_tables;        // (ng, L, w) -> device [2*ng]
@@ -149,6 +161,45 @@ __device__ __forceinline__ T group_sum(T v, unsigned peers, int lane, int rank) 
 int check_ng(int ng);
 int cuda_status(cudaError_t e);
 inline void count_launch(cwthf_ctx* c, int n = 1) { c->launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Counts one kernel launch and, when profiling is on, brackets it with CUDA
+// events recorded on the launching stream.
+struct LaunchScope {
+    cwthf_ctx* ctx;
+    cudaStream_t s;
+    const char* name;
+    cudaEvent_t a = nullptr;
+    LaunchScope(cwthf_ctx* c, cudaStream_t st, const char* n) : ctx(c), s(st), name(n) {
+        count_launch(c);
+        if (c->prof_on) {
+            a = prof_event(c);
+            if (a) cudaEventRecord(a, s);
+        }
+    }
+    ~LaunchScope() {
+        if (a) {
+            cudaEvent_t b = prof_event(ctx);
+            if (b) {
+                cudaEventRecord(b, s);
+                ctx->prof_pending.push_back({name, a, b});
+            }
+        }
+    }
+    static cudaEvent_t prof_event(cwthf_ctx* c) {
+        if (!c->prof_pool.empty()) {
+            cudaEvent_t e = c->prof_pool.back();
+            c->prof_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+    }
+};
+#define CWTHF_LAUNCH(ctx, stream, name, ...)               \
+    do {                                                     \
+        ::cwthf::LaunchScope _cwthf_scope(ctx, stream, name); \
+        __VA_ARGS__;                                         \
+    } while (0)
 
 // ---- scan (scan.cu) ----------------------------------------------------------
 // Exclusive scan of n uint32 values (n given on the host): out[i] = sum_{j<i} in[j],

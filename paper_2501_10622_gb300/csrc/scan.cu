@@ -120,10 +120,9 @@ int scan_generic(cwthf_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n_ca
     if (nb < 1) nb = 1;
     if (size_t(nb) + 2 > ctx->scan_tmp_cap) return CWTHF_E_INVALID_ARG;
     uint32_t* sums = ctx->scan_tmp;
-    k_block_sums<<<unsigned(nb), kScanThreads, 0, s>>>(in, n_cap, d_n, sums);
-    k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb, n_cap, d_n);
-    k_scan_add<<<unsigned(nb), kScanThreads, 0, s>>>(in, n_cap, d_n, sums, nb, out);
-    count_launch(ctx, 3);
+    CWTHF_LAUNCH(ctx, s, "k_block_sums", k_block_sums<<<unsigned(nb), kScanThreads, 0, s>>>(in, n_cap, d_n, sums));
+    CWTHF_LAUNCH(ctx, s, "k_scan_sums", k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb, n_cap, d_n));
+    CWTHF_LAUNCH(ctx, s, "k_scan_add", k_scan_add<<<unsigned(nb), kScanThreads, 0, s>>>(in, n_cap, d_n, sums, nb, out));
     return cuda_status(cudaGetLastError());
 }
 

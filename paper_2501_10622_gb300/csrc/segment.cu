@@ -217,13 +217,11 @@ int seeds_rank(cwthf_ctx* ctx, int ng, cudaStream_t s) {
     int64_t cells = int64_t(ng) * ng * ng;
     int64_t nwords = (cells + 31) / 32;
     int blocks = ctx->sm_count * 8;
-    k_popc<<<blocks, 256, 0, s>>>(ctx->seed_bits, nwords, ctx->seed_prefix);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_popc", k_popc<<<blocks, 256, 0, s>>>(ctx->seed_bits, nwords, ctx->seed_prefix));
     int rc = scan_u32(ctx, ctx->seed_prefix, ctx->seed_prefix, nwords, s);
     if (rc) return rc;
-    k_seed_list<<<blocks, 256, 0, s>>>(ctx->seed_bits, ctx->seed_prefix, nwords, cells / 8 + 8, ctx->seed_list,
-                                       ctx->acc, ctx->n_seeds, ctx->d_status);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_seed_list", k_seed_list<<<blocks, 256, 0, s>>>(ctx->seed_bits, ctx->seed_prefix, nwords, cells / 8 + 8, ctx->seed_list,
+                                       ctx->acc, ctx->n_seeds, ctx->d_status));
     return cuda_status(cudaGetLastError());
 }
 
@@ -232,8 +230,7 @@ int seeds_from_labels(cwthf_ctx* ctx, const int32_t* label, int ng, cudaStream_t
     int64_t nwords = (cells + 31) / 32;
     cudaError_t e = cudaMemsetAsync(ctx->seed_bits, 0, size_t(nwords) * 4, s);
     if (e != cudaSuccess) return cuda_status(e);
-    k_seeds_from_labels<<<ctx->sm_count * 8, 256, 0, s>>>(label, cells, ctx->seed_bits, ctx->d_status);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_seeds_from_labels", k_seeds_from_labels<<<ctx->sm_count * 8, 256, 0, s>>>(label, cells, ctx->seed_bits, ctx->d_status));
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     return seeds_rank(ctx, ng, s);
 }
@@ -246,15 +243,12 @@ int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->jump_changed, 0, sizeof(int) * (kMaxJumpRounds + 1), s);
     if (e != cudaSuccess) return cuda_status(e);
     int64_t ntiles = int64_t(div_up(ng, kSegTX)) * div_up(ng, kSegTY) * div_up(ng, kSegTZ);
-    k_seg_tile<<<unsigned(ntiles), kSegThreads, 0, s>>>(cwt, ng, cwt_min, label, ctx->seed_bits, ctx->d_status);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_seg_tile", k_seg_tile<<<unsigned(ntiles), kSegThreads, 0, s>>>(cwt, ng, cwt_min, label, ctx->seed_bits, ctx->d_status));
     int blocks = ctx->sm_count * 8;
     for (int r = 0; r < kMaxJumpRounds; r++) {
-        k_seg_jump<<<blocks, kSegThreads, 0, s>>>(label, cells, ctx->jump_changed, r);
-        count_launch(ctx);
+        CWTHF_LAUNCH(ctx, s, "k_seg_jump", k_seg_jump<<<blocks, kSegThreads, 0, s>>>(label, cells, ctx->jump_changed, r));
     }
-    k_seg_jump_check<<<1, 1, 0, s>>>(ctx->jump_changed, kMaxJumpRounds, ctx->d_status);
-    count_launch(ctx);
+    CWTHF_LAUNCH(ctx, s, "k_seg_jump_check", k_seg_jump_check<<<1, 1, 0, s>>>(ctx->jump_changed, kMaxJumpRounds, ctx->d_status));
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     return seeds_rank(ctx, ng, s);
 }
