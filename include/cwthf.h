@@ -69,7 +69,8 @@ enum {
     CWTHF_E_NOT_CONVERGED = 6,    /* label propagation hit its round limit */
     CWTHF_E_TIMEOUT = 7,          /* a bounded device wait gave up */
     CWTHF_E_CAPACITY = 8,         /* more halos than cat_cap; the count is still reported */
-    CWTHF_E_BAD_INPUT = 9         /* non-finite or out-of-range position / mass / CWT value */
+    CWTHF_E_BAD_INPUT = 9,        /* non-finite or out-of-range position / mass / CWT value */
+    CWTHF_E_SCRATCH_LIMIT = 10    /* too large for cwthf_deposit_noalloc's fixed scratch */
 };
 
 typedef struct cwthf_ctx cwthf_ctx;
@@ -188,6 +189,28 @@ CWTHF_API const char *cwthf_error_string(int code);
 /* Number of kernel launches queued by this context since it was created
  * (instrumentation for launch accounting). */
 CWTHF_API int64_t cwthf_launch_count(const cwthf_ctx *ctx);
+
+/* The CIC deposit of cwthf_deposit without a context and without any device
+ * allocation.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory -- for example code recorded
+ * into a CUDA graph while a stream is being captured (allocation calls are
+ * not capturable), or hosts whose device memory belongs to another allocator
+ * or pool, or loops that must not pay the device synchronisation of
+ * cudaMalloc / cudaFree.  The caller passes inputs and outputs as for
+ * cwthf_deposit (same arguments, same bit-exact grid); the binning scratch is
+ * a fixed array inside the library (about 3.3 MB, held on every GPU that
+ * uses the library until the process exits).
+ *   ng <= 128 and np <= 262144, else CWTHF_E_SCRATCH_LIMIT (nothing queued).
+ *   status  device, int [1] or NULL: receives the device-detected status of
+ *           this call (CWTHF_OK, CWTHF_E_BAD_INPUT, CWTHF_E_OVERFLOW) once the
+ *           stream reaches it.
+ * Runs on the current device.  Every call shares the one scratch array, so
+ * calls whose GPU work overlaps (other streams, other host threads) race and
+ * corrupt each other's result: keep them ordered on one stream.  The first
+ * call on a device looks up the array's device address; make it before any
+ * stream capture. */
+CWTHF_API int cwthf_deposit_noalloc(const float *pos, const float *mass, double mass_unit, int64_t np, double L,
+                                    int ng, int64_t *grid, int64_t *mtot, int *status, void *stream);
 
 /* Per-kernel timing (instrumentation).  With enable != 0 every later kernel
  * launch of this context is bracketed by two CUDA events recorded on its own

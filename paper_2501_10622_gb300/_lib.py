@@ -20,6 +20,7 @@ HEADER = _PKG.parent / "include" / "cwthf.h"
 
 OK = 0
 E_INVALID_ARG, E_UNSUPPORTED_SIZE, E_OVERFLOW, E_OOM, E_CUDA, E_NOT_CONVERGED, E_TIMEOUT, E_CAPACITY, E_BAD_INPUT = range(1, 10)
+E_SCRATCH_LIMIT = 10
 FRAC_BITS = 10
 MIN_NG, MAX_NG = 8, 1024
 
@@ -70,6 +71,7 @@ def lib() -> ctypes.CDLL:
         L.cwthf_error_string.restype = ctypes.c_char_p
         L.cwthf_launch_count.argtypes = [P]
         L.cwthf_launch_count.restype = i64
+        L.cwthf_deposit_noalloc.argtypes = [P, P, d, i64, d, i32, P, P, P, P]
         L.cwthf_profile.argtypes = [P, i32]
         L.cwthf_profile_count.argtypes = [P]
         L.cwthf_profile_read.argtypes = [P, i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(d),

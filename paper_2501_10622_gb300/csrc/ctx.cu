@@ -286,6 +286,7 @@ const char* cwthf_error_string(int code) {
         case CWTHF_E_TIMEOUT: return "a bounded device wait timed out";
         case CWTHF_E_CAPACITY: return "more halos than the catalogue capacity";
         case CWTHF_E_BAD_INPUT: return "non-finite or out-of-range input value";
+        case CWTHF_E_SCRATCH_LIMIT: return "size beyond the fixed scratch of cwthf_deposit_noalloc (ng <= 128, np <= 262144)";
         default: return "unknown status";
     }
 }

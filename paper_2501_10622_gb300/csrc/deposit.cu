@@ -210,4 +210,26 @@ int deposit_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mas
     return cuda_status(cudaGetLastError());
 }
 
+// The same three passes on caller-provided scratch instead of a context's
+// (no allocation, no context; used by the fixed-scratch entry point).
+int deposit_into_scratch(const DepositScratch& sc, const float* pos, const float* mass, double mass_unit, int64_t np,
+                         double L, int ng, int64_t* grid, cudaStream_t s) {
+    DepositGeom g = deposit_geom(ng);
+    DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
+    int64_t nkeys = g.ntiles * kDepClasses;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(sc.count, 0, size_t(nkeys) * 4, s)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaMemsetAsync(sc.mtot, 0, 8, s)) != cudaSuccess) return cuda_status(e);
+    int blocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kCountThreads), int64_t(sc.sm_count) * 16));
+    k_dep_count<<<blocks, kCountThreads, 0, s>>>(a, sc.count, sc.mtot, sc.status);
+    int rc = scan_u32_scratch(sc.count, sc.off, nkeys, sc.scan_tmp, sc.scan_cap, s);
+    if (rc) return rc;
+    if ((e = cudaMemcpyAsync(sc.cursor, sc.off, size_t(nkeys) * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return cuda_status(e);
+    k_dep_scatter<<<blocks, kCountThreads, 0, s>>>(a, sc.cursor, sc.rec, sc.mq);
+    int tblocks = int(std::min<int64_t>(g.ntiles, int64_t(sc.sm_count) * 8));
+    k_dep_tile<<<tblocks, kTileThreads, 0, s>>>(a, sc.off, sc.rec, sc.mq, sc.mtot, grid, sc.status);
+    return cuda_status(cudaGetLastError());
+}
+
 }  // namespace cwthf

@@ -227,4 +227,21 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
                 cwthf_halo* cat, int64_t cat_cap, int64_t* n_halo, bool seeds_ready, cudaStream_t s);
 void free_tables(cwthf_ctx* ctx);
 
+// ---- deposit on caller-provided scratch (used by cwthf_deposit_noalloc) ------
+struct DepositScratch {
+    uint32_t* count;           // [keys + 2]
+    uint32_t* off;             // [keys + 2]
+    uint32_t* cursor;          // [keys + 2]
+    uint32_t* scan_tmp;        // [scan_cap]
+    size_t scan_cap;
+    unsigned long long* rec;   // [np]
+    uint32_t* mq;              // [np]
+    unsigned long long* mtot;  // [1]
+    int* status;               // [1]
+    int sm_count;
+};
+int deposit_into_scratch(const DepositScratch& sc, const float* pos, const float* mass, double mass_unit, int64_t np,
+                         double L, int ng, int64_t* grid, cudaStream_t s);
+int scan_u32_scratch(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, size_t tmp_cap, cudaStream_t s);
+
 }  // namespace cwthf

@@ -1,6 +1,8 @@
 // scan.cu -- exclusive prefix sum of uint32 arrays (reduce, scan block sums,
 // scan + add).  Used for the deposit bins, the seed ranks and the compaction
 // of kept halos.  No spin waits: three plain launches.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace cwthf {
@@ -137,6 +139,16 @@ int scan_u32(cwthf_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n, cudaS
 int scan_u32_dev(cwthf_ctx* ctx, const uint32_t* in, uint32_t* out, const uint32_t* d_n, int64_t n_cap,
                  cudaStream_t s) {
     return scan_generic(ctx, in, out, n_cap, d_n, s);
+}
+
+// The same three launches on caller-provided block-sum storage (no context).
+int scan_u32_scratch(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, size_t tmp_cap, cudaStream_t s) {
+    int64_t nb = std::max<int64_t>((n + kScanChunk - 1) / kScanChunk, 1);
+    if (size_t(nb) + 2 > tmp_cap) return CWTHF_E_INVALID_ARG;
+    k_block_sums<<<unsigned(nb), kScanThreads, 0, s>>>(in, n, nullptr, tmp);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(tmp, nb, n, nullptr);
+    k_scan_add<<<unsigned(nb), kScanThreads, 0, s>>>(in, n, nullptr, tmp, nb, out);
+    return cuda_status(cudaGetLastError());
 }
 
 }  // namespace cwthf
