@@ -53,10 +53,11 @@
 /* Quantisation (reading of Sec. 2.1: positions to F fractional cell bits).  */
 /* ------------------------------------------------------------------------ */
 
-/* Fixed-point coordinate of one float coordinate: floor(x * (N/L) * 2^F),
- * wrapped into [0, N * 2^F).  The scale (N/L)*2^F is one fp64 division
- * followed by an exact power-of-two product; x*scale is one fp64 product.
- * Returns 0 on success, ORC_E_ARG if x is not finite or |x*scale| >= 2^40. */
+/* Fixed-point coordinate of one float coordinate: floor(x * s) wrapped into
+ * [0, N * 2^F), with s the quantisation scale below.  Because s has at most
+ * 29 significant bits and a float has 24, the fp64 product x*s is exact, so
+ * this is the floor of the exact product.  Returns 0 on success, ORC_E_ARG if
+ * x is not finite or |x*s| >= 2^40. */
 static int quantise_coord(float x, double scale, int64_t modulus, int64_t *q) {
     double t = (double)x * scale;
     if (!isfinite(t) || fabs(t) >= 1099511627776.0) return ORC_E_ARG;
@@ -67,7 +68,14 @@ static int quantise_coord(float x, double scale, int64_t modulus, int64_t *q) {
     return ORC_OK;
 }
 
-static double quant_scale(int ng, double L) { return ((double)ng / L) * (double)FRAC_ONE; }
+/* The scale N * 2^F / L: the fp64 quotient N/L times 2^F (exact), rounded to
+ * 29 significant bits (round half to even). */
+static double quant_scale(int ng, double L) {
+    double s = ((double)ng / L) * (double)FRAC_ONE;
+    int e;
+    double f = frexp(s, &e); /* s = f 2^e, 0.5 <= f < 1 */
+    return ldexp(nearbyint(ldexp(f, 29)), e - 29);
+}
 
 int orc_quantise(const float *pos, int64_t np, double L, int ng, int64_t *q) {
     if (ng < 1 || !(L > 0)) return ORC_E_ARG;

@@ -104,6 +104,29 @@ def test_quantise_matches_definition_on_exact_lattice():
     np.testing.assert_array_equal(exact, q)
 
 
+def _scale29(ng, L):
+    """N 2^10 / L in fp64, rounded half-to-even to 29 significant bits."""
+    import math
+    m, e = math.frexp((ng / L) * 1024.0)
+    return round(m * 2 ** 29) * 2.0 ** (e - 29)
+
+
+def test_quantise_is_floor_of_exact_product():
+    # with a 29-bit scale and 24-bit floats the product is exact: the code is
+    # the floor of the rational x*s, wrapped into [0, N 2^10)
+    from fractions import Fraction
+    rng = np.random.default_rng(11)
+    for ng, L in ((64, 50.0), (1024, 500.0), (96, 77.7), (8, 3.0)):
+        s = Fraction(_scale29(ng, L))
+        assert s.denominator & (s.denominator - 1) == 0 and (s.numerator.bit_length() <= 29)
+        x = np.concatenate([rng.random(3000) * L, rng.random(300) * L * 3 - L, [0.0, L, np.nextafter(L, 0)]])
+        x = x.astype(np.float32)
+        got = oracle.quantise(np.stack([x, x, x], 1), L, ng)[:, 0]
+        mod = ng * 1024
+        want = np.array([(int(Fraction(float(v)) * s // 1)) % mod for v in x], np.int64)
+        np.testing.assert_array_equal(got, want)
+
+
 def test_rejects_bad_input():
     with pytest.raises(oracle.OracleError) as e:
         oracle.cic(np.array([[np.nan, 0, 0]], np.float32), 8.0, 8)
