@@ -42,7 +42,90 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-ng", type=int, default=128)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=16, help="jobs in the served Poisson stream (0: skip)")
+    ap.add_argument("--batch-jobs", type=int, default=64, help="uneven subvolumes in the batched graph (0: skip)")
     return ap.parse_args()
+
+
+def run_batched(args, dev):
+    """64 periodic subvolumes, grids uniform over {32,64,96,128,192}^3, particles
+    log-uniform in [1e4, 1e7]: one CUDA-graph launch for the whole batch (jobs on
+    8 concurrent slot streams) against back-to-back single cwthf_find calls."""
+    import torch
+    import paper_2501_10622_gb300 as pkg
+    from paper_2501_10622_gb300 import batch, synth
+    subs = synth.batched_subvolumes(n_jobs=args.batch_jobs, seed=4)
+    jobs = [batch.BatchJob(w.positions(dev), w.box, w.ng, [pkg.default_params(2.0)]) for w in subs]
+    npart = sum(j.np for j in jobs)
+    b = batch.Batch(jobs, n_slots=8, device=dev)
+    try:
+        b.capture()
+        for _ in range(2):
+            b.replay()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(b.main)
+        for _ in range(reps):
+            b.replay()
+        e1.record(b.main)
+        torch.cuda.synchronize(dev)
+        b.check()
+        g_ms = e0.elapsed_time(e1) / reps
+        sums = [int(j.n_halo[0]) for j in jobs]
+        # back to back: one context, one stream, one call per job
+        ctx = b.ctx[0]
+        s = torch.cuda.current_stream(dev)
+        for j in jobs:
+            ctx.find(j.pos, j.box, j.ng, j.params, cat_cap=b.cat_cap, halo_id=j.halo_id, cat=j.cat,
+                     n_halo=j.n_halo, stream=s)
+        torch.cuda.synchronize(dev)
+        e0.record(s)
+        for _ in range(reps):
+            for j in jobs:
+                ctx.find(j.pos, j.box, j.ng, j.params, cat_cap=b.cat_cap, halo_id=j.halo_id, cat=j.cat,
+                         n_halo=j.n_halo, stream=s)
+        e1.record(s)
+        torch.cuda.synchronize(dev)
+        ctx.check()
+        s_ms = e0.elapsed_time(e1) / reps
+        same = sums == [int(j.n_halo[0]) for j in jobs]
+    finally:
+        b.close()
+        del jobs
+        torch.cuda.empty_cache()
+    return {"jobs": args.batch_jobs, "particles": npart, "grids": [32, 64, 96, 128, 192], "slots": 8,
+            "graph_ms": g_ms, "graph_mparticles_per_s": npart / g_ms / 1e3,
+            "single_calls_ms": s_ms, "single_calls_mparticles_per_s": npart / s_ms / 1e3,
+            "identical_halo_counts": same}
+
+
+def run_served(args, dev):
+    """Poisson stream (200 jobs/s) of halo-finding jobs with grids 64^3-512^3
+    (log-uniform, 2^a 3^b), 8 particles per cell, served by continuous batching
+    under a 120 GB HBM budget, against back-to-back single calls."""
+    import torch
+    from paper_2501_10622_gb300 import serve
+    jobs = serve.poisson_jobs(args.serve_jobs, rate=200.0, lo_ng=64, hi_ng=512, per_cell=8.0, seed=5, device=dev)
+    srv = serve.Server(device=dev, budget_bytes=120 * 2 ** 30,
+                       slots_per_class={96: 6, 192: 4, 288: 3, 384: 2, 512: 2})
+    try:
+        srv.run(jobs)  # warm-up pass (tables, caches)
+        for j in jobs:
+            j.done = float("nan")
+        served = srv.run(jobs)
+        ref = {j.jid: (tuple(j.n_halo), j.checksum) for j in jobs}
+        b2b = srv.run_back_to_back(jobs)
+        same = all(ref[j.jid] == (tuple(j.n_halo), j.checksum) for j in jobs)
+        slot_gb = srv.used / 2 ** 30
+    finally:
+        srv.close()
+        del jobs
+        torch.cuda.empty_cache()
+    return {"arrival_rate_per_s": 200.0, "grid_range": [64, 512], "particles_per_cell": 8, "hbm_budget_gb": 120,
+            "slot_memory_gb": slot_gb, **{k: served[k] for k in served},
+            "back_to_back": {k: b2b[k] for k in ("p50_ms", "p99_ms", "mean_ms", "makespan_s", "mparticles_per_s")},
+            "identical_results_alone_vs_mixed": same}
 
 
 # ---------------------------------------------------------------------------
@@ -61,8 +144,10 @@ def algorithmic_bytes(name, u):
         "k_dep_scatter": 12 * npart + 8 * npart,
         "k_seg_tile": 4 * cells + 4 * cells,           # CWT in, labels out
         "k_seg_jump": 4 * cells,
+        "k_seg_resolve": 4 * cells,                    # labels in (flagged ones rewritten)
         "k_count_cells": 4 * cells,
-        "k_assign": 12 * npart + 4 * npart + 4 * npart,
+        "k_assign_ids": 12 * npart + 4 * npart + 4 * npart,  # positions, label gather, slot out
+        "k_halo_sums": 8 * npart + 4 * npart,                # records, label gather
         "k_finalize": 8 * npart,
     }
     return table.get(name)
@@ -203,9 +288,8 @@ def main():
     args = parse()
     from paper_2501_10622_gb300 import synth
     wl = synth.WORKLOADS[args.workload]
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2501_10622_gb300 import replicas
+    world, rank, local = replicas.env_ranks()
     if args.impl == "reference":
         run_reference(args, wl, rank)
         return
@@ -223,7 +307,8 @@ def main():
     torch.cuda.set_device(dev)
 
     # replicas: each rank finds halos in its own synthetic box (weak scaling)
-    pos = synth.clumped_box(wl.n_particles, wl.box, wl.n_clumps, seed=wl.seed + 1000 * rank, device=dev)
+    pos = synth.clumped_box(wl.n_particles, wl.box, wl.n_clumps, seed=replicas.replica_seed(wl.seed, rank),
+                            device=dev)
     npart, ng = pos.shape[0], wl.ng
     params = [pkg.default_params(w) for w in wl.scales]
     ns = len(params)
@@ -264,12 +349,8 @@ def main():
     prof = ctx.profile_read()
     ctx.profile(False)
     ctx.check(what="timed steps")
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t)
-    value = world * npart / (ms / 1e3) / 1e6
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
+    value = replicas.whole_job_throughput(npart, world, ms)
 
     # ---- per-kernel roofline --------------------------------------------------
     peak, peak_kind = measured_peaks()
@@ -289,7 +370,11 @@ def main():
     roofline = {"bound": "hbm", "kernel": dom, "achieved": d["gbs"], "peak": peak, "unit": "GB/s",
                 "frac": d["gbs"] / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                 "traffic": stored_traffic(dom, u), "algorithmic_bytes_per_launch": d["algorithmic_bytes"]}
-    step_bytes = sum(v["algorithmic_bytes"] * v["launches"] for v in kernels.values() if "algorithmic_bytes" in v)
+    # step total: every kernel's algorithmic bytes per launch, except the pointer-jumping
+    # rounds, of which only the first per segmentation must run (later ones exit early)
+    n_seg = kernels.get("k_seg_tile", {}).get("launches", 0)
+    step_bytes = sum(v["algorithmic_bytes"] * (n_seg if k == "k_seg_jump" else v["launches"])
+                     for k, v in kernels.items() if "algorithmic_bytes" in v)
     step_bytes /= args.steps
 
     # ---- end to end through host buffers ---------------------------------------
@@ -316,14 +401,22 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-        ems = f0.elapsed_time(f1) / args.steps
-        if dist:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t)
+        ems = replicas.max_over_ranks(f0.elapsed_time(f1) / args.steps, dev)
         ctx.check(what="e2e steps")
-        e2e = {"value": world * npart / (ems / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ems,
+        e2e = {"value": replicas.whole_job_throughput(npart, world, ems), "unit": UNIT, "ms_per_step": ems,
                "h2d_bytes_per_step": pos.numel() * 4, "d2h_bytes_per_step": hid.numel() * 4 + nh.numel() * 8}
+
+    halos = [int(x) for x in nh.cpu()]
+    ctx.close()
+    del hid, cat
+    torch.cuda.empty_cache()
+
+    # ---- served and batched forms (rank 0, N = 1) --------------------------------------
+    served = batched = None
+    if rank == 0 and world == 1 and args.serve_jobs > 0:
+        served = run_served(args, dev)
+    if rank == 0 and world == 1 and args.batch_jobs > 0:
+        batched = run_batched(args, dev)
 
     # ---- CPU oracle baseline (rank 0, N = 1) ------------------------------------
     cpu = None
@@ -347,10 +440,9 @@ def main():
                 "algorithmic_bytes_per_step": step_bytes,
                 "step_roofline_frac": step_bytes / (ms / 1e3) / 1e9 / peak,
                 "roofline": roofline, "kernels": kernels, "gpu_launches": launches,
-                "halos_per_scale": [int(x) for x in nh.cpu()],
-                "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu}
+                "halos_per_scale": halos,
+                "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "served": served, "batched": batched}
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist:
         dist.destroy_process_group()
 

@@ -1,0 +1,94 @@
+"""Batched halo finding: many uneven periodic subvolumes in one CUDA graph.
+
+The jobs are spread over `n_slots` slots (a library context with its own
+stream), longest job first onto the least-loaded slot.  One pass over all
+jobs -- each job's whole cwthf_find (deposit, FFT, segmentation, assignment)
+on its slot's stream, the slot streams forked from and joined back into one
+capture stream -- is recorded once into a CUDA graph; a batch then costs a
+single graph launch, and jobs on different slots overlap on the GPU.
+
+Before capture every job runs once eagerly, so that the library's per-size
+FFT and wavelet tables exist (their first use allocates, which a capture
+cannot contain).  Results are deterministic: each job's halo ids equal those
+of a single cwthf_find call.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+
+
+class BatchJob:
+    def __init__(self, pos, box, ng, params):
+        self.pos, self.box, self.ng, self.params = pos, box, ng, params
+        self.np = int(pos.shape[0])
+        self.slot = None
+        self.halo_id = None
+        self.cat = None
+        self.n_halo = None
+
+
+class Batch:
+    def __init__(self, jobs, n_slots=8, cat_cap=1 << 16, device="cuda"):
+        self.device = torch.device(device)
+        self.jobs = list(jobs)
+        ns = max(len(j.params) for j in self.jobs)
+        max_ng = max(j.ng for j in self.jobs)
+        max_np = max(j.np for j in self.jobs)
+        self.n_slots = min(n_slots, len(self.jobs))
+        self.ctx = [_lib.Context(self.device.index or 0, max_ng=max_ng, max_np=max_np, max_scales=ns)
+                    for _ in range(self.n_slots)]
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(self.n_slots)]
+        # longest-processing-time assignment (cells + particles as the cost)
+        load = [0.0] * self.n_slots
+        for j in sorted(self.jobs, key=lambda j: -(j.ng ** 3 + j.np)):
+            s = min(range(self.n_slots), key=lambda i: load[i])
+            j.slot = s
+            load[s] += j.ng ** 3 + j.np
+        for j in self.jobs:
+            k = len(j.params)
+            j.halo_id = torch.empty((k, j.np), dtype=torch.int32, device=self.device)
+            j.cat = torch.empty((k, cat_cap, 64), dtype=torch.uint8, device=self.device)
+            j.n_halo = torch.zeros(k, dtype=torch.int64, device=self.device)
+        self.cat_cap = cat_cap
+        self.graph = None
+        self.main = torch.cuda.Stream(self.device)
+
+    def _enqueue(self, main):
+        """All jobs on their slots' streams, forked from / joined into `main`."""
+        for s in self.streams:
+            s.wait_stream(main)
+        for j in self.jobs:
+            s = self.streams[j.slot]
+            with torch.cuda.stream(s):
+                self.ctx[j.slot].find(j.pos, j.box, j.ng, j.params, cat_cap=self.cat_cap, halo_id=j.halo_id,
+                                      cat=j.cat, n_halo=j.n_halo, stream=s)
+        for s in self.streams:
+            main.wait_stream(s)
+
+    def run_eager(self):
+        cur = torch.cuda.current_stream(self.device)
+        self._enqueue(cur)
+        torch.cuda.synchronize(self.device)
+        self.check()
+
+    def capture(self):
+        self.run_eager()  # tables for every (grid, box, scale) exist before capture
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.main):
+            self._enqueue(self.main)
+        torch.cuda.synchronize(self.device)
+
+    def replay(self):
+        self.graph.replay()
+
+    def check(self):
+        for c in self.ctx:
+            c.check()
+
+    def close(self):
+        self.graph = None
+        for c in self.ctx:
+            c.close()
+        self.ctx = []

@@ -21,108 +21,165 @@ constexpr int kThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
 using u64 = unsigned long long;
 
-// Slot of seed cell `lab`; false if lab is not a seed or its slot is beyond
-// the number of slots in use.
-__device__ __forceinline__ bool seed_slot(const uint32_t* bits, const uint32_t* prefix, const uint32_t* n_slots,
-                                          int32_t lab, uint32_t& slot) {
-    uint32_t w = bits[lab >> 5];
-    uint32_t m = 1u << (lab & 31);
-    slot = prefix[lab >> 5] + __popc(w & (m - 1u));
-    return (w & m) != 0 && slot < *n_slots;
-}
-
-// Cells per seed.
+// Cells per seed: four labels per thread and iteration, one atomic per slot
+// per warp.
 __global__ void __launch_bounds__(kThreads) k_count_cells(const int32_t* __restrict__ label, int64_t cells,
                                                          const uint32_t* __restrict__ bits,
                                                          const uint32_t* __restrict__ prefix,
                                                          const uint32_t* __restrict__ n_slots, HaloAcc* acc,
                                                          int* status) {
-    int lane = threadIdx.x & 31;
-    int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < cells; base += stride) {
-        int64_t c = base + lane;
-        uint32_t key = 0xffffffffu;
-        if (c < cells) {
-            int32_t l = label[c];
-            uint32_t slot;
-            if (l >= 0 && l < cells) {
-                if (seed_slot(bits, prefix, n_slots, l, slot)) key = slot;
-                else set_status(status, CWTHF_E_BAD_INPUT);
-            } else if (l != -1) {
-                set_status(status, CWTHF_E_BAD_INPUT);
+    const int lane = threadIdx.x & 31;
+    const int64_t n4 = (cells + 3) / 4;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n4; base += stride) {
+        const int64_t i = base + lane;  // warp-uniform trip count
+        int l[4] = {-1, -1, -1, -1};
+        if (i < n4) {
+            if (4 * i + 3 < cells) {
+                const int4 q = reinterpret_cast<const int4*>(label)[i];
+                l[0] = q.x; l[1] = q.y; l[2] = q.z; l[3] = q.w;
+            } else {
+                for (int j = 0; j < 4 && 4 * i + j < cells; j++) l[j] = label[4 * i + j];
             }
         }
-        unsigned peers = __match_any_sync(kFull, key);
-        if (key != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(&acc[key].n_cells, u64(__popc(peers)));
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            uint32_t key = 0xffffffffu;
+            if (l[j] >= 0 && l[j] < cells) {
+                uint32_t slot;
+                if (seed_slot(bits, prefix, n_slots, l[j], slot)) key = slot;
+                else set_status(status, CWTHF_E_BAD_INPUT);
+            } else if (l[j] != -1) {
+                set_status(status, CWTHF_E_BAD_INPUT);
+            }
+            const unsigned peers = __match_any_sync(kFull, key);
+            if (key != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(&acc[key].n_cells, u64(__popc(peers)));
+        }
     }
 }
 
-// Particles: nearest node, its label, slot; integer sums per slot.
-__global__ void __launch_bounds__(kThreads) k_assign(DepArgs a, const int32_t* __restrict__ label,
-                                                    const uint32_t* __restrict__ bits,
-                                                    const uint32_t* __restrict__ prefix,
-                                                    const uint32_t* __restrict__ n_slots, HaloAcc* acc,
-                                                    int32_t* __restrict__ part_slot, u64* __restrict__ mtot,
-                                                    int* status) {
-    int lane = threadIdx.x & 31;
-    int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    const int64_t N = a.ng, M = a.modulus;
-    u64 msum = 0;
-    for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < a.np; base += stride) {
-        int64_t i = base + lane;
-        uint32_t key = 0xffffffffu;
-        uint32_t mq = 0;
-        long long mom[3] = {0, 0, 0};
-        if (i < a.np) {
+// Nearest node per axis from the fixed-point coordinate q in [0, ng*2^10):
+// (q + 2^9) >> 10, with ng wrapping to 0.
+__device__ __forceinline__ int nearest_node(int64_t q, int ng) {
+    int n = int((q + kFracOne / 2) >> kFracBits);
+    return n == ng ? 0 : n;
+}
+
+// Particles in their own order: nearest node, its label, the label's slot
+// (or -1).  Gathers only; the per-halo sums are formed by k_halo_sums.
+__global__ void __launch_bounds__(kThreads) k_assign_ids(DepArgs a, const int32_t* __restrict__ label,
+                                                        const uint32_t* __restrict__ bits,
+                                                        const uint32_t* __restrict__ prefix,
+                                                        const uint32_t* __restrict__ n_slots,
+                                                        int32_t* __restrict__ part_slot, int* status) {
+    constexpr int kIlp = 4;  // independent particles per thread: several gather chains in flight
+    const size_t N = size_t(a.ng);
+    const int64_t cells = int64_t(N * N * N);
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < a.np; i0 += kIlp * stride) {
+        int32_t lab[kIlp];
+        bool ok[kIlp];
+#pragma unroll
+        for (int u = 0; u < kIlp; u++) {
+            const int64_t i = i0 + u * stride;
+            lab[u] = -1;
+            ok[u] = false;
+            if (i >= a.np) continue;
             int64_t q[3];
             const float* p = a.pos + 3 * i;
-            bool ok = quantise(p[0], a.scale, M, q[0]) && quantise(p[1], a.scale, M, q[1]) &&
-                      quantise(p[2], a.scale, M, q[2]);
-            int ms = ok ? mass_quantum(a, i, mq) : CWTHF_E_BAD_INPUT;
-            int32_t slot_out = -1;
-            if (ms != CWTHF_OK) {
-                set_status(status, ms);
-                mq = 0;
+            if (quantise(p[0], a.scale_m, a.scale_e, a.modulus, q[0]) &&
+                quantise(p[1], a.scale_m, a.scale_e, a.modulus, q[1]) &&
+                quantise(p[2], a.scale_m, a.scale_e, a.modulus, q[2])) {
+                const size_t cell = (size_t(nearest_node(q[2], a.ng)) * N + nearest_node(q[1], a.ng)) * N +
+                                    nearest_node(q[0], a.ng);
+                lab[u] = label[cell];
+                ok[u] = true;
             } else {
-                int64_t n[3];
+                set_status(status, CWTHF_E_BAD_INPUT);
+            }
+        }
 #pragma unroll
-                for (int d = 0; d < 3; d++) n[d] = ((q[d] + kFracOne / 2) >> kFracBits) % N;
-                int32_t lab = label[(n[2] * N + n[1]) * N + n[0]];
+        for (int u = 0; u < kIlp; u++) {
+            const int64_t i = i0 + u * stride;
+            if (i >= a.np) continue;
+            int32_t out = -1;
+            uint32_t slot;
+            if (ok[u] && lab[u] >= 0 && lab[u] < cells && seed_slot(bits, prefix, n_slots, lab[u], slot))
+                out = int32_t(slot);
+            part_slot[i] = out;
+        }
+    }
+}
+
+// Per-halo integer sums over the binned records, one deposit tile at a time:
+// the records of a tile come from a 32 x 8 x 8-cell block, so neighbouring
+// lanes mostly share a halo and the warp folds their contributions into one
+// set of atomics per halo.
+__global__ void __launch_bounds__(kThreads) k_halo_sums(DepArgs a, const uint32_t* __restrict__ off,
+                                                       const unsigned long long* __restrict__ rec,
+                                                       const uint32_t* __restrict__ rec_mq,
+                                                       const int32_t* __restrict__ label,
+                                                       const uint32_t* __restrict__ bits,
+                                                       const uint32_t* __restrict__ prefix,
+                                                       const uint32_t* __restrict__ n_slots, HaloAcc* acc,
+                                                       u64* __restrict__ mtot) {
+    const int lane = threadIdx.x & 31;
+    const int N = a.ng;
+    const int64_t M = a.modulus;
+    const int64_t ntiles = int64_t(a.ntx) * a.nty * a.ntz;
+    const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    u64 msum = 0;
+    for (int64_t t = warp; t < ntiles; t += nwarps) {  // one warp per tile
+        const int tx = int(t % a.ntx), ty = int((t / a.ntx) % a.nty), tz = int(t / (int64_t(a.ntx) * a.nty));
+        const uint32_t beg = off[t * kDepClasses], end = off[t * kDepClasses + kDepClasses];
+        for (uint32_t r0 = beg; r0 < end; r0 += 32) {  // warp-uniform
+            const uint32_t r = r0 + uint32_t(lane);
+            uint32_t key = 0xffffffffu;
+            uint32_t mq = 0;
+            long long mom[3] = {0, 0, 0};
+            if (r < end) {
+                const u64 e = rec[r];
+                mq = a.mass ? rec_mq[r] : 1u;
+                const int64_t q[3] = {int64_t(tx * kDepTX + int(e & 63)) * kFracOne + int64_t((e >> 18) & 1023),
+                                      int64_t(ty * kDepTY + int((e >> 6) & 63)) * kFracOne + int64_t((e >> 28) & 1023),
+                                      int64_t(tz * kDepTZ + int((e >> 12) & 63)) * kFracOne + int64_t((e >> 38) & 1023)};
+                const int nx = nearest_node(q[0], N), ny = nearest_node(q[1], N), nz = nearest_node(q[2], N);
+                const int32_t lab = label[(size_t(nz) * N + ny) * N + nx];
                 uint32_t slot;
-                if (lab >= 0 && lab < N * N * N && seed_slot(bits, prefix, n_slots, lab, slot)) {
+                if (lab >= 0 && int64_t(lab) < int64_t(N) * N * N && seed_slot(bits, prefix, n_slots, lab, slot)) {
                     key = slot;
-                    slot_out = int32_t(slot);
-                    int64_t s[3] = {lab % N, (lab / N) % N, lab / (N * N)};
+                    const int sx = lab % N, sy = (lab / N) % N, sz = lab / (N * N);
+                    const int sc[3] = {sx, sy, sz};
 #pragma unroll
                     for (int d = 0; d < 3; d++) {
-                        int64_t dq = (q[d] - s[d] * kFracOne) % M;
+                        int64_t dq = q[d] - int64_t(sc[d]) * kFracOne;  // in (-M, M)
                         if (dq < 0) dq += M;
-                        if (2 * dq >= M) dq -= M;
+                        if (2 * dq >= M) dq -= M;                      // minimum image in [-M/2, M/2)
                         mom[d] = (long long)mq * dq;
                     }
                 }
             }
-            part_slot[i] = slot_out;
-        }
-        msum += mq;
-        unsigned peers = __match_any_sync(kFull, key);
-        int rank = __popc(peers & ((1u << lane) - 1));
-        u64 cnt = 1, m_sum = mq;
-        long long m0 = mom[0], m1 = mom[1], m2 = mom[2];
-        if (__any_sync(kFull, __popc(peers) > 1)) {  // warp-uniform: aggregate groups first
-            cnt = __popc(peers);
-            m_sum = group_sum<u64>(m_sum, peers, lane, rank);
-            m0 = group_sum<long long>(m0, peers, lane, rank);
-            m1 = group_sum<long long>(m1, peers, lane, rank);
-            m2 = group_sum<long long>(m2, peers, lane, rank);
-        }
-        if (key != 0xffffffffu && rank == 0) {
-            HaloAcc* h = acc + key;
-            atomicAdd(&h->n_part, cnt);
-            atomicAdd(&h->mq, m_sum);
-            atomicAdd(reinterpret_cast<u64*>(&h->mom[0]), u64(m0));
-            atomicAdd(reinterpret_cast<u64*>(&h->mom[1]), u64(m1));
-            atomicAdd(reinterpret_cast<u64*>(&h->mom[2]), u64(m2));
+            msum += mq;
+            // a warp whose records all fall in one halo adds one set of sums; otherwise
+            // every lane adds its own (records of different halos rarely collide)
+            const bool uniform = __all_sync(kFull, key == __shfl_sync(kFull, key, 0)) && key != 0xffffffffu;
+            u64 cnt = 1, m_sum = mq, m0 = u64(mom[0]), m1 = u64(mom[1]), m2 = u64(mom[2]);
+            if (uniform) {
+                cnt = 32;
+                m_sum = warp_sum32(mq);
+                m0 = warp_sum64(m0);
+                m1 = warp_sum64(m1);
+                m2 = warp_sum64(m2);
+            }
+            if (key != 0xffffffffu && (!uniform || lane == 0)) {
+                HaloAcc* h = acc + key;
+                atomicAdd(&h->n_part, cnt);
+                atomicAdd(&h->mq, m_sum);
+                atomicAdd(reinterpret_cast<u64*>(&h->mom[0]), m0);
+                atomicAdd(reinterpret_cast<u64*>(&h->mom[1]), m1);
+                atomicAdd(reinterpret_cast<u64*>(&h->mom[2]), m2);
+            }
         }
     }
 #pragma unroll
@@ -211,22 +268,30 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const int32_t* __restrict
 
 int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L, int ng,
                 const int32_t* label, const float* cwt, const cwthf_params* p, int32_t* halo_id, cwthf_halo* cat,
-                int64_t cat_cap, int64_t* n_halo, bool seeds_ready, cudaStream_t s) {
+                int64_t cat_cap, int64_t* n_halo, bool seeds_ready, bool bins_ready, cudaStream_t s) {
     int rc;
     if (!seeds_ready && (rc = seeds_from_labels(ctx, label, ng, s))) return rc;
+    if (!bins_ready && (rc = bin_particles(ctx, pos, mass, mass_unit, np, L, ng, s))) return rc;
     int64_t cells = int64_t(ng) * ng * ng;
-    int64_t nwords = (cells + 31) / 32;
     const uint32_t* d_nseeds = ctx->n_seeds;  // seeds in use (clamped to slot_cap)
     int64_t slot_cap = cells / 8 + 8;
     int blocks = ctx->sm_count * 8;
     cudaError_t e = cudaMemsetAsync(ctx->d_mtot, 0, 8, s);
     if (e != cudaSuccess) return cuda_status(e);
-    CWTHF_LAUNCH(ctx, s, "k_count_cells", k_count_cells<<<blocks, kThreads, 0, s>>>(label, cells, ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc,
-                                              ctx->d_status));
+    if (!seeds_ready)  // after segment_impl the resolve pass has counted the cells already
+        CWTHF_LAUNCH(ctx, s, "k_count_cells",
+                     k_count_cells<<<blocks, kThreads, 0, s>>>(label, cells, ctx->seed_bits, ctx->seed_prefix,
+                                                               d_nseeds, ctx->acc, ctx->d_status));
     DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
     int pblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kThreads), int64_t(ctx->sm_count) * 16));
-    CWTHF_LAUNCH(ctx, s, "k_assign", k_assign<<<pblocks, kThreads, 0, s>>>(a, label, ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc, ctx->part_slot,
-                                          ctx->d_mtot, ctx->d_status));
+    CWTHF_LAUNCH(ctx, s, "k_assign_ids",
+                 k_assign_ids<<<pblocks, kThreads, 0, s>>>(a, label, ctx->seed_bits, ctx->seed_prefix, d_nseeds,
+                                                           ctx->part_slot, ctx->d_status));
+    int tblocks = int(std::min<int64_t>(deposit_geom(ng).ntiles, int64_t(ctx->sm_count) * 8));
+    CWTHF_LAUNCH(ctx, s, "k_halo_sums",
+                 k_halo_sums<<<tblocks, kThreads, 0, s>>>(a, ctx->dep_off, ctx->dep_rec, ctx->dep_mq, label,
+                                                          ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc,
+                                                          ctx->d_mtot));
     FilterArgs f;
     f.ng = ng;
     f.L = L;
@@ -236,9 +301,11 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
     f.cat_cap = cat_cap;
     CWTHF_LAUNCH(ctx, s, "k_keep", k_keep<<<blocks, kThreads, 0, s>>>(ctx->acc, d_nseeds, ctx->d_mtot, f, ctx->keep_off));
     if ((rc = scan_u32_dev(ctx, ctx->keep_off, ctx->keep_off, d_nseeds, slot_cap, s))) return rc;
-    CWTHF_LAUNCH(ctx, s, "k_catalogue", k_catalogue<<<blocks, kThreads, 0, s>>>(ctx->acc, ctx->seed_list, d_nseeds, ctx->keep_off, cwt, f, cat, n_halo,
-                                            ctx->d_status));
-    CWTHF_LAUNCH(ctx, s, "k_finalize", k_finalize<<<pblocks, kThreads, 0, s>>>(ctx->part_slot, np, ctx->keep_off, ctx->seed_list, halo_id));
+    CWTHF_LAUNCH(ctx, s, "k_catalogue",
+                 k_catalogue<<<blocks, kThreads, 0, s>>>(ctx->acc, ctx->seed_list, d_nseeds, ctx->keep_off, cwt, f,
+                                                         cat, n_halo, ctx->d_status));
+    CWTHF_LAUNCH(ctx, s, "k_finalize",
+                 k_finalize<<<pblocks, kThreads, 0, s>>>(ctx->part_slot, np, ctx->keep_off, ctx->seed_list, halo_id));
     return cuda_status(cudaGetLastError());
 }
 

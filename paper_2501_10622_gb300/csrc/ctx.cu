@@ -208,8 +208,8 @@ int cwthf_transform(cwthf_ctx* ctx, const int64_t* grid, int ng, double L, doubl
     if (!grid || !cwt || !(w > 0) || !std::isfinite(w) || !(mass_unit > 0)) return CWTHF_E_INVALID_ARG;
     DeviceGuard g(ctx->device);
     cudaStream_t s = as_stream(stream);
-    rc = transform_forward_xy(ctx, grid, ng, mass_unit, ctx->spec, s);
-    if (!rc) rc = transform_wavelet_inverse(ctx, ctx->spec, ctx->spec, ng, L, w, cwt, s);
+    rc = transform_forward_xy(ctx, grid, ng, ctx->spec, s);
+    if (!rc) rc = transform_wavelet_inverse(ctx, ctx->spec, ctx->spec, ng, L, w, mass_unit, cwt, s);
     return rc;
 }
 
@@ -232,7 +232,7 @@ int cwthf_assign(cwthf_ctx* ctx, const float* pos, const float* mass, double mas
         return CWTHF_E_INVALID_ARG;
     DeviceGuard g(ctx->device);
     return assign_impl(ctx, pos, mass, mass_unit, np, L, ng, cell_label, cwt, params, halo_id, cat, cat_cap, n_halo,
-                       false, as_stream(stream));
+                       false, false, as_stream(stream));
 }
 
 int cwthf_find(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L, int ng,
@@ -251,14 +251,14 @@ int cwthf_find(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_
     DeviceGuard g(ctx->device);
     cudaStream_t s = as_stream(stream);
     rc = deposit_impl(ctx, pos, mass, mass_unit, np, L, ng, ctx->grid, nullptr, s);
-    if (!rc) rc = transform_forward_xy(ctx, ctx->grid, ng, mass_unit, ctx->spec, s);
+    if (!rc) rc = transform_forward_xy(ctx, ctx->grid, ng, ctx->spec, s);
     for (int i = 0; i < n_scales && !rc; i++) {
         float2* dst = n_scales > 1 ? ctx->spec2 : ctx->spec;
-        rc = transform_wavelet_inverse(ctx, ctx->spec, dst, ng, L, params[i].w, ctx->cwt, s);
+        rc = transform_wavelet_inverse(ctx, ctx->spec, dst, ng, L, params[i].w, mass_unit, ctx->cwt, s);
         if (!rc) rc = segment_impl(ctx, ctx->cwt, ng, params[i].cwt_min, ctx->label, true, s);
         if (!rc)
             rc = assign_impl(ctx, pos, mass, mass_unit, np, L, ng, ctx->label, ctx->cwt, &params[i],
-                             halo_id + int64_t(i) * np, cat + int64_t(i) * cat_cap, cat_cap, n_halo + i, true, s);
+                             halo_id + int64_t(i) * np, cat + int64_t(i) * cat_cap, cat_cap, n_halo + i, true, true, s);
     }
     return rc;
 }

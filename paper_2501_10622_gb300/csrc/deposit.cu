@@ -41,8 +41,8 @@ __device__ __forceinline__ PartBin bin_particle(const DepArgs& a, int64_t i) {
     b.status = CWTHF_OK;
     int64_t q[3];
     const float* p = a.pos + 3 * i;
-    bool ok = quantise(p[0], a.scale, a.modulus, q[0]) && quantise(p[1], a.scale, a.modulus, q[1]) &&
-              quantise(p[2], a.scale, a.modulus, q[2]);
+    bool ok = quantise(p[0], a.scale_m, a.scale_e, a.modulus, q[0]) && quantise(p[1], a.scale_m, a.scale_e, a.modulus, q[1]) &&
+              quantise(p[2], a.scale_m, a.scale_e, a.modulus, q[2]);
     if (!ok) { b.status = CWTHF_E_BAD_INPUT; return b; }
     int ms = mass_quantum(a, i, b.mq);
     if (ms != CWTHF_OK) { b.status = ms; b.mq = 0; return b; }
@@ -111,74 +111,114 @@ __global__ void __launch_bounds__(kCountThreads) k_dep_scatter(DepArgs a, uint32
     }
 }
 
-// Pass 3: one tile at a time per CTA; shared-memory int64 accumulation of the
-// tile's own bin and the reaching-in particles of its 7 lower neighbours.
+// Exact 64-bit accumulation from native 32-bit shared atomics: the low word
+// takes the low half and reports its own wrap-around, which is carried into
+// the high word together with the high half.
+__device__ __forceinline__ void acc_add(uint32_t* lo, uint32_t* hi, int c, u64 v) {
+    uint32_t vl = uint32_t(v), vh = uint32_t(v >> 32);
+    uint32_t old = atomicAdd(&lo[c], vl);
+    vh += (old + vl < old) ? 1u : 0u;
+    if (vh) atomicAdd(&hi[c], vh);
+}
+
+// The 27 (neighbour offset mask m, boundary class) pairs whose particles reach
+// into a tile: a particle of the lower neighbour at offset m reaches in iff
+// its class has every bit of m set.
+constexpr int kReachSegments = 27;
+
+// Pass 3: one tile at a time per CTA.  The record ranges of the 27 reaching-in
+// segments are fetched in parallel, then processed as one flattened list, so
+// every warp works on full batches whatever the segment sizes.
 __global__ void __launch_bounds__(kTileThreads) k_dep_tile(DepArgs a, const uint32_t* __restrict__ off,
                                                           const unsigned long long* __restrict__ rec,
                                                           const uint32_t* __restrict__ rec_mq,
                                                           const unsigned long long* __restrict__ mtot,
                                                           int64_t* __restrict__ grid, int* status) {
-    __shared__ unsigned long long acc[kDepTZ][kDepTY][kDepTX];
     constexpr int kCells = kDepTX * kDepTY * kDepTZ;
-    int lane = threadIdx.x & 31;
+    __shared__ uint32_t acc_lo[kCells], acc_hi[kCells];
+    __shared__ uint32_t seg_beg[kReachSegments], seg_pre[kReachSegments + 1];
+    __shared__ uint8_t seg_m[kReachSegments];
+    const int lane = threadIdx.x & 31;
     if (blockIdx.x == 0 && threadIdx.x == 0 && *mtot >= (1ull << 33)) set_status(status, CWTHF_E_OVERFLOW);
-    int64_t ntiles = int64_t(a.ntx) * a.nty * a.ntz;
+    const int64_t ntiles = int64_t(a.ntx) * a.nty * a.ntz;
     const int64_t ng = a.ng;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        int tx = int(t % a.ntx), ty = int((t / a.ntx) % a.nty), tz = int(t / (int64_t(a.ntx) * a.nty));
-        int x0 = tx * kDepTX, y0 = ty * kDepTY, z0 = tz * kDepTZ;
-        int wx = min(kDepTX, a.ng - x0), wy = min(kDepTY, a.ng - y0), wz = min(kDepTZ, a.ng - z0);
-        for (int c = threadIdx.x; c < kCells; c += kTileThreads) (&acc[0][0][0])[c] = 0ull;
-        __syncthreads();
-#pragma unroll 1
-        for (int m = 0; m < 8; m++) {
-            int dx = m & 1, dy = (m >> 1) & 1, dz = (m >> 2) & 1;
-            int sx = tx - dx < 0 ? a.ntx - 1 : tx - dx;
-            int sy = ty - dy < 0 ? a.nty - 1 : ty - dy;
-            int sz = tz - dz < 0 ? a.ntz - 1 : tz - dz;
-            int64_t src = (int64_t(sz) * a.nty + sy) * a.ntx + sx;
-#pragma unroll 1
-            for (int cls = 0; cls < 8; cls++) {
-                if ((cls & m) != m) continue;
-                uint32_t beg = off[src * kDepClasses + cls], end = off[src * kDepClasses + cls + 1];
-                // warp-uniform trip count so that the warp collectives see all lanes
-                for (uint32_t r0 = beg + (threadIdx.x & ~31u); r0 < end; r0 += kTileThreads) {
-                    uint32_t r = r0 + uint32_t(lane);
-                    bool live = r < end;
-                    unsigned long long e = live ? rec[r] : 0ull;
-                    uint32_t mq = live ? (a.mass ? rec_mq[r] : 1u) : 0u;
-                    int lx = int(e & 63), ly = int((e >> 6) & 63), lz = int((e >> 12) & 63);
-                    int fx = int((e >> 18) & 1023), fy = int((e >> 28) & 1023), fz = int((e >> 38) & 1023);
-                    // a particle from a lower neighbour only reaches in with its upper node
-                    if (dx) lx = -1;
-                    if (dy) ly = -1;
-                    if (dz) lz = -1;
-                    u64 wxv[2] = {u64(kFracOne - fx), u64(fx)};
-                    u64 wyv[2] = {u64(kFracOne - fy), u64(fy)};
-                    u64 wzv[2] = {u64(kFracOne - fz), u64(fz)};
-                    uint32_t key = live ? uint32_t(((lz + 1) * (kDepTY + 2) + (ly + 1)) * (kDepTX + 2) + (lx + 1))
-                                        : kInvalidKey;
-                    unsigned peers = __match_any_sync(kFull, key);
-                    int big = __reduce_max_sync(kFull, unsigned(__popc(peers)));
-                    int rank = __popc(peers & ((1u << lane) - 1));
-                    bool writer = live && (big < 6 || rank == 0);
-#pragma unroll
-                    for (int k = 0; k < 8; k++) {
-                        int ex = k & 1, ey = (k >> 1) & 1, ez = (k >> 2) & 1;
-                        u64 v = u64(mq) * wxv[ex] * wyv[ey] * wzv[ez];
-                        if (big >= 6) v = group_sum<u64>(v, peers, lane, rank);  // warp-uniform branch
-                        int cx = lx + ex, cy = ly + ey, cz = lz + ez;
-                        if (writer && v && cx >= 0 && cx < wx && cy >= 0 && cy < wy && cz >= 0 && cz < wz)
-                            atomicAdd(&acc[cz][cy][cx], v);
+        const int tx = int(t % a.ntx), ty = int((t / a.ntx) % a.nty), tz = int(t / (int64_t(a.ntx) * a.nty));
+        const int x0 = tx * kDepTX, y0 = ty * kDepTY, z0 = tz * kDepTZ;
+        const int wx = min(kDepTX, a.ng - x0), wy = min(kDepTY, a.ng - y0), wz = min(kDepTZ, a.ng - z0);
+        for (int c = threadIdx.x; c < kCells; c += kTileThreads) {
+            acc_lo[c] = 0u;
+            acc_hi[c] = 0u;
+        }
+        if (threadIdx.x < kReachSegments) {
+            // the j-th (m, class) pair in (m, class) order
+            int j = threadIdx.x, m = 0, cls = 0, n = 0;
+            for (int mm = 0; mm < 8; mm++)
+                for (int cc = 0; cc < 8; cc++)
+                    if ((cc & mm) == mm) {
+                        if (n == j) { m = mm; cls = cc; }
+                        n++;
                     }
-                }
+            const int dx = m & 1, dy = (m >> 1) & 1, dz = (m >> 2) & 1;
+            const int sx = tx - dx < 0 ? a.ntx - 1 : tx - dx;
+            const int sy = ty - dy < 0 ? a.nty - 1 : ty - dy;
+            const int sz = tz - dz < 0 ? a.ntz - 1 : tz - dz;
+            const int64_t key = ((int64_t(sz) * a.nty + sy) * a.ntx + sx) * kDepClasses + cls;
+            const uint32_t b = off[key], e = off[key + 1];
+            seg_beg[j] = b;
+            seg_pre[j + 1] = e - b;
+            seg_m[j] = uint8_t(m);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            seg_pre[0] = 0;
+            for (int j = 0; j < kReachSegments; j++) seg_pre[j + 1] += seg_pre[j];
+        }
+        __syncthreads();
+        const uint32_t total = seg_pre[kReachSegments];
+        for (uint32_t k0 = (threadIdx.x & ~31u); k0 < total; k0 += kTileThreads) {  // warp-uniform trip count
+            const uint32_t k = k0 + uint32_t(lane);
+            const bool live = k < total;
+            int sgi = 0;  // segment of k: last j with seg_pre[j] <= k
+#pragma unroll
+            for (int w = 16; w > 0; w >>= 1)
+                if (sgi + w < kReachSegments && seg_pre[sgi + w] <= k) sgi += w;
+            const uint32_t r = seg_beg[sgi] + (k - seg_pre[sgi]);
+            const int m = seg_m[sgi];
+            const u64 e = live ? rec[r] : 0ull;
+            const uint32_t mq = live ? (a.mass ? rec_mq[r] : 1u) : 0u;
+            int lx = int(e & 63), ly = int((e >> 6) & 63), lz = int((e >> 12) & 63);
+            const int fx = int((e >> 18) & 1023), fy = int((e >> 28) & 1023), fz = int((e >> 38) & 1023);
+            // a particle of a lower neighbour only reaches in with its upper node
+            if (m & 1) lx = -1;
+            if (m & 2) ly = -1;
+            if (m & 4) lz = -1;
+            const u64 wxv[2] = {u64(kFracOne - fx), u64(fx)};
+            const u64 wyv[2] = {u64(kFracOne - fy), u64(fy)};
+            const u64 wzv[2] = {u64(kFracOne - fz), u64(fz)};
+            // a warp whose 32 records all share one base cell (dense clumps) folds its
+            // 8 corner sums with full-warp reductions; otherwise every lane adds its own
+            // corners (native 32-bit shared atomics; same-cell lanes serialise briefly)
+            const uint32_t key = live ? uint32_t(((lz + 1) * (kDepTY + 2) + (ly + 1)) * (kDepTX + 2) + (lx + 1))
+                                      : kInvalidKey;
+            const bool uniform = __all_sync(kFull, key == __shfl_sync(kFull, key, 0)) && key != kInvalidKey;
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int ex = q & 1, ey = (q >> 1) & 1, ez = (q >> 2) & 1;
+                u64 v = u64(mq) * wxv[ex] * wyv[ey] * wzv[ez];
+                if (uniform) v = warp_sum64(v);  // warp-uniform branch
+                const int cx = lx + ex, cy = ly + ey, cz = lz + ez;
+                if (live && (!uniform || lane == 0) && v && cx >= 0 && cx < wx && cy >= 0 && cy < wy && cz >= 0 &&
+                    cz < wz)
+                    acc_add(acc_lo, acc_hi, (cz * kDepTY + cy) * kDepTX + cx, v);
             }
         }
         __syncthreads();
         for (int c = threadIdx.x; c < kCells; c += kTileThreads) {
-            int cx = c % kDepTX, cy = (c / kDepTX) % kDepTY, cz = c / (kDepTX * kDepTY);
+            const int cx = c % kDepTX, cy = (c / kDepTX) % kDepTY, cz = c / (kDepTX * kDepTY);
             if (cx < wx && cy < wy && cz < wz)
-                grid[(int64_t(z0 + cz) * ng + (y0 + cy)) * ng + (x0 + cx)] = (int64_t)acc[cz][cy][cx];
+                grid[(int64_t(z0 + cz) * ng + (y0 + cy)) * ng + (x0 + cx)] =
+                    int64_t((u64(acc_hi[c]) << 32) | u64(acc_lo[c]));
         }
         __syncthreads();
     }
@@ -186,8 +226,8 @@ __global__ void __launch_bounds__(kTileThreads) k_dep_tile(DepArgs a, const uint
 
 }  // namespace
 
-int deposit_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L,
-                 int ng, int64_t* grid, int64_t* mtot, cudaStream_t s) {
+int bin_particles(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L, int ng,
+                  cudaStream_t s) {
     DepositGeom g = deposit_geom(ng);
     DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
     int64_t nkeys = g.ntiles * kDepClasses;
@@ -202,9 +242,19 @@ int deposit_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mas
         cudaSuccess)
         return cuda_status(e);
     CWTHF_LAUNCH(ctx, s, "k_dep_scatter", k_dep_scatter<<<blocks, kCountThreads, 0, s>>>(a, ctx->dep_cursor, ctx->dep_rec, ctx->dep_mq));
+    return cuda_status(cudaGetLastError());
+}
+
+int deposit_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L,
+                 int ng, int64_t* grid, int64_t* mtot, cudaStream_t s) {
+    int rc = bin_particles(ctx, pos, mass, mass_unit, np, L, ng, s);
+    if (rc) return rc;
+    DepositGeom g = deposit_geom(ng);
+    DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
     int tblocks = int(std::min<int64_t>(g.ntiles, int64_t(ctx->sm_count) * 8));
     CWTHF_LAUNCH(ctx, s, "k_dep_tile", k_dep_tile<<<tblocks, kTileThreads, 0, s>>>(a, ctx->dep_off, ctx->dep_rec, ctx->dep_mq, ctx->d_mtot, grid,
                                                 ctx->d_status));
+    cudaError_t e;
     if (mtot && (e = cudaMemcpyAsync(mtot, ctx->d_mtot, 8, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return cuda_status(e);
     return cuda_status(cudaGetLastError());

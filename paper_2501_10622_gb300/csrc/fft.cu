@@ -359,14 +359,18 @@ struct YzArgs {
     int nbox;        // boxes per tile (boxr * nbox == L)
     int mode;
     int along_z;     // 1: transform along z (plane index o = y), 0: along y (o = z)
+    int nplanes;     // planes (ng)
     int M;           // ng / 2 (highest valid kx)
     const float2* tw;   // [L]
     const float* ghat;  // [L]  G^(k)   (wavelet mode)
     const float* hhat;  // [L]  H^(k)
-    float scale;        // w^1.5 / ng^3
+    float scale;        // w^1.5 * mass_unit / ng^3
     int* status;
 };
 
+// One CTA per tile: TMA brings the [L][C] pencil tile into shared memory
+// (mbarrier completion), the block transforms it, TMA stores it back.
+// Several CTAs per SM overlap their load, compute and store phases.
 __global__ void __launch_bounds__(512, 1)
     k_fft_yz(const __grid_constant__ CUtensorMap in_map, const __grid_constant__ CUtensorMap out_map, YzArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(512, 1)
     if (threadIdx.x == 0) {
         mbar_expect_tx(bar, uint32_t(L) * C * 8u);
         for (int b = 0; b < a.nbox; b++) {
-            int r = b * a.boxr;
+            const int r = b * a.boxr;
             if (a.along_z) tma_load_3d(tile + r * C, &in_map, bar, 2 * cc * C, o, r);
             else tma_load_3d(tile + r * C, &in_map, bar, 2 * cc * C, r, o);
         }
@@ -401,17 +405,19 @@ __global__ void __launch_bounds__(512, 1)
     Wave wv{0.f, 0.f, gz, hz};
     if (a.mode == kYzWavelet) {
         // column c <-> kx = cc*C + c, this plane <-> ky = o
-        int kx = cc * C + int(threadIdx.x % C);
+        const int kx = cc * C + int(threadIdx.x % C);
         if (kx <= a.M) {
-            float gx = a.ghat[kx], hx = a.hhat[kx], gy = a.ghat[o], hy = a.hhat[o];
+            const float gx = a.ghat[kx], hx = a.hhat[kx], gy = a.ghat[o], hy = a.hhat[o];
             wv.a = a.scale * (6.f * gx * gy - hx * gy - gx * hy);
             wv.b = -a.scale * gx * gy;
         }
     }
     __syncthreads();
-    if (!mbar_wait(bar, 0, kSpinLimit)) {
-        set_status(a.status, CWTHF_E_TIMEOUT);
-        mbar_wait(bar, 0, kSpinLimit);  // give the copy a second bounded chance before leaving
+    // the whole block agrees on the outcome of its bounded wait before leaving together
+    const bool loaded = mbar_wait(bar, 0, kSpinLimit);
+    if (__syncthreads_or(!loaded)) {
+        if (threadIdx.x == 0) set_status(a.status, CWTHF_E_TIMEOUT);
+        mbar_wait(bar, 0, kSpinLimit);  // a second bounded chance for the copy before leaving
         return;
     }
     AddrPlain addr{C};
@@ -446,7 +452,7 @@ __global__ void __launch_bounds__(512, 1)
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int b = 0; b < a.nbox; b++) {
-            int r = b * a.boxr;
+            const int r = b * a.boxr;
             if (a.along_z) tma_store_3d(&out_map, tile + r * C, 2 * cc * C, o, r);
             else tma_store_3d(&out_map, tile + r * C, 2 * cc * C, r, o);
         }
@@ -461,7 +467,6 @@ struct XArgs {
     Plan p;          // complex FFT of length M = ng / 2 over C rows
     int ng, M, P;
     int64_t rows;    // ng * ng
-    double unit;     // physical mass of one grid unit (mass_unit * 2^-30)
     const float2* twM;  // [M]   exp(-2 pi i m / M)
     const float2* twN;  // [ng]  exp(-2 pi i k / ng)
 };
@@ -477,7 +482,11 @@ __global__ void __launch_bounds__(512, 1) k_fft_x_fwd(XArgs a, const int64_t* __
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = a.twM[i];
     AddrSwz addr{C};
-    // load, exact row sum, remove the row mean in fp64, round to fp32
+    // load, exact row sum, remove the row's integer mean exactly, round to fp32.
+    // Dropping the mean's fractional part only shifts the row's DC bin, which is
+    // replaced by the exact row sum below.  The spectrum is in units of 2^-30 of
+    // the grid (mass_unit is applied with the wavelet).
+    constexpr float kUnit = 9.3132257461547852e-10f;  // 2^-30, exact
     for (int r = warp; r < C; r += nwarp) {
         int64_t row = int64_t(blockIdx.x) * C + r;
         longlong2 v[16];
@@ -491,14 +500,14 @@ __global__ void __launch_bounds__(512, 1) k_fft_x_fwd(XArgs a, const int64_t* __
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        double mean = __ddiv_rn(__dmul_rn(double(sum), a.unit), double(a.ng));
-        if (lane == 0) rowdc[r] = __dmul_rn(double(sum), a.unit);
+        const long long q0 = sum / a.ng;  // grid values are >= 0
+        if (lane == 0) rowdc[r] = double(__ll2float_rn(sum) * kUnit);
 #pragma unroll
         for (int i = 0; i < 16; i++) {
             int k = lane + 32 * i;
             if (k < M) {
-                float re = float(__dsub_rn(__dmul_rn(double(v[i].x), a.unit), mean));
-                float im = float(__dsub_rn(__dmul_rn(double(v[i].y), a.unit), mean));
+                float re = __ll2float_rn(v[i].x - q0) * kUnit;
+                float im = __ll2float_rn(v[i].y - q0) * kUnit;
                 tile[addr(k, r)] = make_float2(re, im);
             }
         }
@@ -547,19 +556,33 @@ __global__ void __launch_bounds__(512, 1) k_fft_x_inv(XArgs a, const float2* __r
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = a.twM[i];
     AddrSwz addr{C};
-    // c2r pre-processing: Z'[k] = (X[k] + X*[M-k]) + i W_N^-k (X[k] - X*[M-k]); stored conjugated
+    // c2r pre-processing: Z'[k] = (X[k] + X*[M-k]) + i W_N^-k (X[k] - X*[M-k]); stored conjugated.
+    // All of a row's loads are issued before any is used (memory parallelism).
     for (int r = warp; r < C; r += nwarp) {
         int64_t row = int64_t(blockIdx.x) * C + r;
         const float2* in = spec + (row < a.rows ? row : 0) * a.P;
-        for (int k = lane; k <= M / 2; k += 32) {
-            float2 xk = in[k], xm = in[M - k];
-            if (k == 0) {
-                xk.y = 0.f;
-                xm.y = 0.f;
+        constexpr int kPairs = 9;  // k = lane + 32 i, i < 9 covers k <= M/2 <= 256
+        float2 xk[kPairs], xm[kPairs];
+#pragma unroll
+        for (int i = 0; i < kPairs; i++) {
+            const int k = lane + 32 * i;
+            if (k <= M / 2) {
+                xk[i] = in[k];
+                xm[i] = in[M - k];
             }
-            float2 e = make_float2(xk.x + xm.x, xk.y - xm.y);  // X[k] + conj X[M-k]
-            float2 d = make_float2(xk.x - xm.x, xk.y + xm.y);  // X[k] - conj X[M-k]
-            float2 winv = conjf2(a.twN[k]);                    // W_N^-k
+        }
+#pragma unroll
+        for (int i = 0; i < kPairs; i++) {
+            const int k = lane + 32 * i;
+            if (k > M / 2) continue;
+            float2 a0 = xk[i], a1 = xm[i];
+            if (k == 0) {
+                a0.y = 0.f;
+                a1.y = 0.f;
+            }
+            float2 e = make_float2(a0.x + a1.x, a0.y - a1.y);  // X[k] + conj X[M-k]
+            float2 d = make_float2(a0.x - a1.x, a0.y + a1.y);  // X[k] - conj X[M-k]
+            float2 winv = conjf2(a.twN[k]);                     // W_N^-k
             float2 wd = cmul(winv, d);
             float2 zk = make_float2(e.x - wd.y, e.y + wd.x);   // e + i W^-k d
             tile[addr(k, r)] = conjf2(zk);
@@ -642,24 +665,29 @@ int plan_threads(const Plan& p) {
     return (t + 31) / 32 * 32;
 }
 
-// Columns per y/z tile: <= 64 KB of complex data and <= 512 threads.
+// Columns per y/z tile: <= 64 KB of complex data, preferring <= 256 threads
+// (two CTAs per SM at 128 registers) over <= 512.
 bool yz_plan(int L, Plan& p) {
     if (!make_plan(L, p)) return false;
-    for (int C : {16, 8, 4, 2}) {
-        p.C = C;
-        p.T = plan_threads(p);
-        if (size_t(L) * C * 8 <= 65536 && p.T <= 512) return true;
-    }
+    for (int tmax : {256, 512})
+        for (int C : {16, 8, 4, 2}) {
+            p.C = C;
+            p.T = plan_threads(p);
+            if (size_t(L) * C * 8 <= 65536 && p.T <= tmax) return true;
+        }
     return false;
 }
 
+// Rows per x tile: <= 64 KB of complex data, one warp per row for the loads,
+// preferring <= 256 threads (two CTAs per SM) over <= 512.
 bool x_plan(int M, Plan& p) {
     if (!make_plan(M, p)) return false;
-    for (int C : {16, 8, 4, 2}) {
-        p.C = C;
-        p.T = std::max(plan_threads(p), 32 * std::min(C, 16));  // at least one warp per row for the load
-        if (size_t(M) * C * 8 <= 65536 && p.T <= 512) return true;
-    }
+    for (int tmax : {256, 512})
+        for (int C : {16, 8, 4, 2}) {
+            p.C = C;
+            p.T = std::max(plan_threads(p), 32 * std::min(C, 16));
+            if (size_t(M) * C * 8 <= 65536 && p.T <= tmax) return true;
+        }
     return false;
 }
 
@@ -773,7 +801,7 @@ float* get_wavelet_tables(cwthf_ctx* ctx, int ng, double L, double w) {
 }
 
 int launch_yz(cwthf_ctx* ctx, float2* src, float2* dst, int ng, bool along_z, int mode, const Tables* t,
-              const float* wtab, double w, cudaStream_t s) {
+              const float* wtab, double w, double mass_unit, cudaStream_t s) {
     Plan p;
     if (!yz_plan(ng, p)) return CWTHF_E_UNSUPPORTED_SIZE;
     int boxr = pick_boxr(ng, p.C);
@@ -790,10 +818,13 @@ int launch_yz(cwthf_ctx* ctx, float2* src, float2* dst, int ng, bool along_z, in
     a.nbox = ng / boxr;
     a.mode = mode;
     a.along_z = along_z ? 1 : 0;
+    a.nplanes = ng;
     a.tw = t->twN;
     a.ghat = wtab;
     a.hhat = wtab ? wtab + ng : nullptr;
-    a.scale = float(std::pow(w, 1.5) / (double(ng) * ng * ng));
+    // w^1.5 (Eq. 4), the 1/ng^3 of the inverse DFT, and the mass of one spectrum
+    // unit (the x pass already scaled the int64 grid by 2^-30: units of mass_unit)
+    a.scale = float(std::pow(w, 1.5) * mass_unit / (double(ng) * ng * ng));
     a.status = ctx->d_status;
     size_t smem = yz_smem(p);
     cudaFuncSetAttribute(k_fft_yz, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -801,7 +832,7 @@ int launch_yz(cwthf_ctx* ctx, float2* src, float2* dst, int ng, bool along_z, in
     return cuda_status(cudaGetLastError());
 }
 
-int x_args(int ng, double unit, const Tables* t, XArgs& a) {
+int x_args(int ng, const Tables* t, XArgs& a) {
     Plan p;
     if (!x_plan(ng / 2, p)) return CWTHF_E_UNSUPPORTED_SIZE;
     a.p = p;
@@ -809,7 +840,6 @@ int x_args(int ng, double unit, const Tables* t, XArgs& a) {
     a.M = ng / 2;
     a.P = spec_pitch(ng);
     a.rows = int64_t(ng) * ng;
-    a.unit = unit;
     a.twM = t->twM;
     a.twN = t->twN;
     return CWTHF_OK;
@@ -817,30 +847,29 @@ int x_args(int ng, double unit, const Tables* t, XArgs& a) {
 
 }  // namespace
 
-int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, double mass_unit, float2* spec,
-                         cudaStream_t s) {
+int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, float2* spec, cudaStream_t s) {
     if (ng / 2 > 512) return CWTHF_E_UNSUPPORTED_SIZE;
     Tables* t = get_tables(ctx, ng, s);
     if (!t) return CWTHF_E_CUDA;
     XArgs a;
-    int rc = x_args(ng, mass_unit / double(int64_t(1) << (3 * kFracBits)), t, a);
+    int rc = x_args(ng, t, a);
     if (rc) return rc;
     cudaFuncSetAttribute(k_fft_x_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(x_smem(a.p)));
     CWTHF_LAUNCH(ctx, s, "k_fft_x_fwd", k_fft_x_fwd<<<div_up(a.rows, a.p.C), a.p.T, x_smem(a.p), s>>>(a, grid, spec));
     if ((rc = cuda_status(cudaGetLastError()))) return rc;
-    return launch_yz(ctx, spec, spec, ng, false, kYzForward, t, nullptr, 0.0, s);
+    return launch_yz(ctx, spec, spec, ng, false, kYzForward, t, nullptr, 0.0, 1.0, s);
 }
 
-int transform_wavelet_inverse(cwthf_ctx* ctx, float2* src, float2* dst, int ng, double L, double w, float* cwt,
-                              cudaStream_t s) {
+int transform_wavelet_inverse(cwthf_ctx* ctx, float2* src, float2* dst, int ng, double L, double w,
+                              double mass_unit, float* cwt, cudaStream_t s) {
     Tables* t = get_tables(ctx, ng, s);
     float* wtab = get_wavelet_tables(ctx, ng, L, w);
     if (!t || !wtab) return CWTHF_E_CUDA;
-    int rc = launch_yz(ctx, src, dst, ng, true, kYzWavelet, t, wtab, w, s);
-    if (!rc) rc = launch_yz(ctx, dst, dst, ng, false, kYzInverse, t, nullptr, 0.0, s);
+    int rc = launch_yz(ctx, src, dst, ng, true, kYzWavelet, t, wtab, w, mass_unit, s);
+    if (!rc) rc = launch_yz(ctx, dst, dst, ng, false, kYzInverse, t, nullptr, 0.0, 1.0, s);
     if (rc) return rc;
     XArgs a;
-    if ((rc = x_args(ng, 0.0, t, a))) return rc;
+    if ((rc = x_args(ng, t, a))) return rc;
     cudaFuncSetAttribute(k_fft_x_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(x_smem(a.p)));
     CWTHF_LAUNCH(ctx, s, "k_fft_x_inv", k_fft_x_inv<<<div_up(a.rows, a.p.C), a.p.T, x_smem(a.p), s>>>(a, dst, cwt));
     return cuda_status(cudaGetLastError());

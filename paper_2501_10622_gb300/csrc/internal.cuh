@@ -24,11 +24,11 @@ constexpr int kDepTX = 32, kDepTY = 8, kDepTZ = 8;
 constexpr int kDepClasses = 8;  // boundary class bits (x, y, z) per particle
 
 // Segmentation tiles (owned cells; one halo layer is staged around them).
-constexpr int kSegTX = 32, kSegTY = 8, kSegTZ = 4;
+constexpr int kSegTX = 30, kSegTY = 16, kSegTZ = 32;
 constexpr int kMaxJumpRounds = 40;
 
 // A bounded device wait gives up after this many polls.
-constexpr long long kSpinLimit = 1ll << 26;
+constexpr long long kSpinLimit = 1ll << 20;
 
 struct Tables;  // FFT and wavelet tables for one grid size (fft.cu)
 
@@ -131,6 +131,17 @@ namespace cwthf {
 // ---- status helpers ---------------------------------------------------------
 __device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
 
+// Slot (rank among all seeds, in cell order) of seed cell `lab`, from the seed
+// bitmap and its per-word popcount prefix; false if lab is not a seed or its
+// slot is beyond the number of slots in use.
+__device__ __forceinline__ bool seed_slot(const uint32_t* bits, const uint32_t* prefix, const uint32_t* n_slots,
+                                          int32_t lab, uint32_t& slot) {
+    uint32_t w = bits[lab >> 5];
+    uint32_t m = 1u << (lab & 31);
+    slot = prefix[lab >> 5] + __popc(w & (m - 1u));
+    return (w & m) != 0 && slot < *n_slots;
+}
+
 // ---- warp helpers -------------------------------------------------------------
 // Lane of the n-th (0-based) member of the lane set `group`, or 32 if the
 // group has no more than n members.
@@ -141,6 +152,23 @@ __device__ __forceinline__ int nth_member(unsigned group, int n) {
     for (int w = 16; w > 0; w >>= 1)
         if (__popc(group & ((1u << (pos + w)) - 1u)) <= n) pos += w;
     return pos;
+}
+
+// Sum of v over all 32 lanes of a converged warp, given to every lane.
+// Exact modulo 2^64: 16-bit chunks go through the native 32-bit warp
+// reduction (a chunk sum over 32 lanes fits in 21 bits).
+__device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
+    unsigned long long s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        unsigned c = unsigned((v >> (16 * k)) & 0xffffull);
+        s += (unsigned long long)__reduce_add_sync(0xffffffffu, c) << (16 * k);
+    }
+    return s;
+}
+__device__ __forceinline__ unsigned long long warp_sum32(unsigned v) {
+    return (unsigned long long)__reduce_add_sync(0xffffffffu, v & 0xffffu) +
+           ((unsigned long long)__reduce_add_sync(0xffffffffu, v >> 16) << 16);
 }
 
 // Sum of v over the lanes of `peers` (lanes sharing one key, as returned by
@@ -213,18 +241,25 @@ size_t scan_tmp_words(int64_t n_cap);
 // ---- stages -------------------------------------------------------------------
 int deposit_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L,
                  int ng, int64_t* grid, int64_t* mtot, cudaStream_t s);
+// The binning passes of the deposit alone: packed records per (tile, class)
+// in ctx->dep_rec / dep_mq with offsets ctx->dep_off, and sum m_q in d_mtot.
+int bin_particles(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L, int ng,
+                  cudaStream_t s);
 // Forward half of the transform: x r2c and y c2c -> ctx spectrum `spec`.
-int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, double mass_unit, float2* spec,
-                         cudaStream_t s);
+int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, float2* spec, cudaStream_t s);
 // z forward, wavelet multiply, z inverse (src -> dst, may alias), then
 // y inverse and x c2r into cwt.
-int transform_wavelet_inverse(cwthf_ctx* ctx, float2* src, float2* dst, int ng, double L, double w, float* cwt,
-                              cudaStream_t s);
+int transform_wavelet_inverse(cwthf_ctx* ctx, float2* src, float2* dst, int ng, double L, double w,
+                              double mass_unit, float* cwt, cudaStream_t s);
 int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_t* label, bool seeds_ready,
                  cudaStream_t s);
+// seeds_ready: the seed bitmap / ranks of `label` are already in ctx (after
+// segment_impl); bins_ready: ctx->dep_* hold the binned records of these
+// particles for this grid (after deposit_impl).
 int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L,
                 int ng, const int32_t* label, const float* cwt, const cwthf_params* p, int32_t* halo_id,
-                cwthf_halo* cat, int64_t cat_cap, int64_t* n_halo, bool seeds_ready, cudaStream_t s);
+                cwthf_halo* cat, int64_t cat_cap, int64_t* n_halo, bool seeds_ready, bool bins_ready,
+                cudaStream_t s);
 void free_tables(cwthf_ctx* ctx);
 
 // ---- deposit on caller-provided scratch (used by cwthf_deposit_noalloc) ------

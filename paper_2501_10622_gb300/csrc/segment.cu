@@ -21,125 +21,266 @@
 namespace cwthf {
 namespace {
 
-constexpr int kSegThreads = 256;
-constexpr int kHX = kSegTX + 2, kHY = kSegTY + 2, kHZ = kSegTZ + 2;
+// Tile: kSegTX x kSegTY x kSegTZ owned cells.  A warp covers one grid row of
+// 32 columns: lanes 1..30 own cells, lanes 0 and 31 read the x-halo columns.
+// Warps 0 and 17 read the y-halo rows.
+constexpr int kSegRows = kSegTY + 2;          // warps per CTA
+constexpr int kSegThreads = 32 * kSegRows;    // 576
 constexpr int kOwned = kSegTX * kSegTY * kSegTZ;
 constexpr int32_t kFlag = 1 << 30;
 constexpr int32_t kMask = kFlag - 1;
-constexpr int kLocalRounds = 12;  // > log2(kOwned) + 1
+constexpr int kChaseLimit = 64;  // longest in-tile chain followed before handing over to the global pass
+constexpr int kSegPrefetch = 8;  // planes of a column loaded ahead
 
-__device__ __forceinline__ bool beats(float va, int64_t ia, float vb, int64_t ib) {
-    return va > vb || (va == vb && ia < ib);
+__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Order-preserving map of a float to an unsigned integer (larger float ->
+// larger integer); -0 is folded onto +0 first so that the two compare equal.
+__device__ __forceinline__ uint32_t ord_bits(float v) {
+    const uint32_t u = __float_as_uint(v + 0.0f);
+    return u ^ ((uint32_t)((int32_t)u >> 31) | 0x80000000u);
 }
 
+// Rank (0, 1, 2) of each of the three wrapped coordinates (c-1, c, c+1): the
+// strict cell order breaks value ties by the smaller linear index, i.e. by
+// the smaller wrapped z, then y, then x.
+__device__ __forceinline__ void ranks3(int a, int b, int c, int& ra, int& rb, int& rc) {
+    ra = (a > b) + (a > c);
+    rb = (b > a) + (b > c);
+    rc = (c > a) + (c > b);
+}
+
+// Parents of a 30 x 16 x 32-cell tile and the in-tile part of every chain.
+//
+// Candidates carry a 64-bit key: high word = order-preserving bits of the CWT
+// value, low word = tie-break priority and the candidate's offset.  The
+// maximum of the keys is the best cell under the strict order, so each of the
+// 26 comparisons is one unsigned max, done separably: along x by warp
+// shuffles, along y through a shared row buffer (one barrier per plane),
+// along z in registers over the last three planes.  Parents go to shared
+// memory; every cell then follows its chain there until it reaches a seed, a
+// non-seed maximum, or a cell outside the tile.
 __global__ void __launch_bounds__(kSegThreads) k_seg_tile(const float* __restrict__ C, int ng, float cwt_min,
                                                          int32_t* __restrict__ label, uint32_t* __restrict__ seed_bits,
                                                          int* status) {
-    __shared__ float h[kHZ][kHY][kHX];
-    __shared__ int32_t ptr[kOwned];
+    extern __shared__ int32_t ptr[];  // [kOwned], dynamic
+    __shared__ unsigned long long rowbest[2][kSegRows][32];
     const int ntx = (ng + kSegTX - 1) / kSegTX, nty = (ng + kSegTY - 1) / kSegTY;
-    const int64_t t = blockIdx.x;
-    const int tx = int(t % ntx), ty = int((t / ntx) % nty), tz = int(t / (int64_t(ntx) * nty));
+    const int t = int(blockIdx.x);
+    const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
     const int x0 = tx * kSegTX, y0 = ty * kSegTY, z0 = tz * kSegTZ;
     const int wx = min(kSegTX, ng - x0), wy = min(kSegTY, ng - y0), wz = min(kSegTZ, ng - z0);
-    const int64_t N = ng;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned full = 0xffffffffu;
+    // this lane's column and this warp's row (wrapped; columns past a small grid
+    // need a full modulo)
+    const int lx = lane - 1, ly = w - 1;  // owned local coordinates when in range
+    const int xc = ((x0 + lx) % ng + ng) % ng, yc = ((y0 + ly) % ng + ng) % ng;
+    const int xm = wrap(xc - 1, ng), xp = wrap(xc + 1, ng);
+    const int ym = wrap(yc - 1, ng), yp = wrap(yc + 1, ng);
+    const bool own = lx >= 0 && lx < wx && ly >= 0 && ly < wy;
+    int rxm, rxc, rxp, rym, ryc, ryp;
+    ranks3(xm, xc, xp, rxm, rxc, rxp);
+    ranks3(ym, yc, yp, rym, ryc, ryp);
+    // low-word fields: bits 0-1 x offset code, 2-3 x priority, 8-9 y code,
+    // 10-11 y priority, 16-17 z code, 18-19 z priority (priority 2 - rank)
+    const uint32_t lxm = (0u) | (uint32_t(2 - rxm) << 2), lxc = 1u | (uint32_t(2 - rxc) << 2),
+                   lxp = 2u | (uint32_t(2 - rxp) << 2);
+    const uint32_t lym = (0u << 8) | (uint32_t(2 - rym) << 10), lyc = (1u << 8) | (uint32_t(2 - ryc) << 10),
+                   lyp = (2u << 8) | (uint32_t(2 - ryp) << 10);
+    const size_t N = size_t(ng);
+    const float* colp = C + size_t(yc) * N + xc;
+    const uint32_t ord_min = ord_bits(cwt_min);
+    auto key = [](uint32_t hi, uint32_t lo) { return ((unsigned long long)hi << 32) | lo; };
+    auto kmax = [](unsigned long long a, unsigned long long b) { return a > b ? a : b; };
 
     bool bad = false;
-    for (int i = threadIdx.x; i < kHX * kHY * kHZ; i += kSegThreads) {
-        int hx = i % kHX, hy = (i / kHX) % kHY, hz = i / (kHX * kHY);
-        float v = -INFINITY;
-        if (hx <= wx + 1 && hy <= wy + 1 && hz <= wz + 1) {
-            int gx = x0 - 1 + hx, gy = y0 - 1 + hy, gz = z0 - 1 + hz;
-            gx = gx < 0 ? gx + ng : (gx >= ng ? gx - ng : gx);
-            gy = gy < 0 ? gy + ng : (gy >= ng ? gy - ng : gy);
-            gz = gz < 0 ? gz + ng : (gz >= ng ? gz - ng : gz);
-            v = C[(gz * N + gy) * N + gx];
-            bad |= (v != v);
+    unsigned long long pl[3] = {0ull, 0ull, 0ull};  // in-plane winners of planes p-2, p-1, p
+    // kSegPrefetch planes of this column in flight (a register ring), so that
+    // the per-plane barrier does not expose the load latency
+    const int np_ = wz + 2;
+    const size_t plane = N * N;
+    float ring[kSegPrefetch];
+#pragma unroll
+    for (int d = 0; d < kSegPrefetch; d++)
+        ring[d] = d < np_ ? __ldg(colp + size_t(wrap(z0 - 1 + d, ng)) * plane) : 0.f;
+#pragma unroll 1
+    for (int p0 = 0; p0 < np_; p0 += kSegPrefetch)
+#pragma unroll
+    for (int d = 0; d < kSegPrefetch; d++) {
+        const int p = p0 + d;
+        if (p >= np_) break;  // block-uniform
+        const float vcur = ring[d];
+        if (p + kSegPrefetch < np_) ring[d] = __ldg(colp + size_t(wrap(z0 - 1 + p + kSegPrefetch, ng)) * plane);
+        bad |= (vcur != vcur);
+        const uint32_t o = ord_bits(vcur);
+        const uint32_t ol = __shfl_up_sync(full, o, 1), orr = __shfl_down_sync(full, o, 1);
+        // best along x of this row, at this column
+        const unsigned long long rb = kmax(kmax(key(ol, lxm), key(o, lxc)), key(orr, lxp));
+        rowbest[p & 1][w][lane] = rb;
+        __syncthreads();
+        if (w >= 1 && w <= kSegTY) {
+            const unsigned long long a = rowbest[p & 1][w - 1][lane], b = rowbest[p & 1][w][lane],
+                                     c = rowbest[p & 1][w + 1][lane];
+            pl[0] = pl[1];
+            pl[1] = pl[2];
+            pl[2] = kmax(kmax(a | lym, b | lyc), c | lyp);
         }
-        h[hz][hy][hx] = v;
+        if (p >= 2 && own) {
+            // the cell of plane p-1 (owned z index lz = p-2): winner over planes p-2, p-1, p
+            const int lz = p - 2;
+            const int zc = z0 + lz, zm = wrap(zc - 1, ng), zp = wrap(zc + 1, ng);
+            int rzm, rzc, rzp;
+            ranks3(zm, zc, zp, rzm, rzc, rzp);
+            const unsigned long long best =
+                kmax(kmax(pl[0] | (uint64_t(0u << 16 | uint32_t(2 - rzm) << 18)),
+                          pl[1] | (uint64_t(1u << 16 | uint32_t(2 - rzc) << 18))),
+                     pl[2] | (uint64_t(2u << 16 | uint32_t(2 - rzp) << 18)));
+            const uint32_t lo = uint32_t(best);
+            const int cx = int(lo & 3u), cy = int((lo >> 8) & 3u), cz = int((lo >> 16) & 3u);
+            const int i = (lz * kSegTY + ly) * kSegTX + lx;
+            if (cx == 1 && cy == 1 && cz == 1) {
+                // a local maximum (its own key won): a seed iff its value > cwt_min
+                if (uint32_t(best >> 32) > ord_min) {
+                    ptr[i] = i;
+                    const uint32_t g = uint32_t((size_t(zc) * N + yc) * N + xc);
+                    atomicOr(&seed_bits[g >> 5], 1u << (g & 31));
+                } else {
+                    ptr[i] = -1;
+                }
+            } else {
+                const int px = cx == 0 ? xm : (cx == 2 ? xp : xc);
+                const int py = cy == 0 ? ym : (cy == 2 ? yp : yc);
+                const int pz = cz == 0 ? zm : (cz == 2 ? zp : zc);
+                const int qx = px - x0, qy = py - y0, qz = pz - z0;
+                if (qx >= 0 && qx < wx && qy >= 0 && qy < wy && qz >= 0 && qz < wz)
+                    ptr[i] = (qz * kSegTY + qy) * kSegTX + qx;
+                else
+                    ptr[i] = -2 - int32_t((size_t(pz) * N + py) * N + px);
+            }
+        }
     }
     if (bad) set_status(status, CWTHF_E_BAD_INPUT);
     __syncthreads();
 
-    // parents of the owned cells
-    for (int i = threadIdx.x; i < kOwned; i += kSegThreads) {
-        int lx = i % kSegTX, ly = (i / kSegTX) % kSegTY, lz = i / (kSegTX * kSegTY);
-        if (lx >= wx || ly >= wy || lz >= wz) { ptr[i] = -1; continue; }
-        int bx = 0, by = 0, bz = 0;
-        int gx0 = x0 + lx, gy0 = y0 + ly, gz0 = z0 + lz;
-        float bv = h[lz + 1][ly + 1][lx + 1];
-        int64_t bi = (gz0 * N + gy0) * N + gx0;
-#pragma unroll
-        for (int dz = -1; dz <= 1; dz++)
-#pragma unroll
-            for (int dy = -1; dy <= 1; dy++)
-#pragma unroll
-                for (int dx = -1; dx <= 1; dx++) {
-                    if (dx == 0 && dy == 0 && dz == 0) continue;
-                    float v = h[lz + 1 + dz][ly + 1 + dy][lx + 1 + dx];
-                    if (v < bv) continue;  // cannot beat (fast path; ties fall through)
-                    int gx = gx0 + dx, gy = gy0 + dy, gz = gz0 + dz;
-                    gx = gx < 0 ? gx + ng : (gx >= ng ? gx - ng : gx);
-                    gy = gy < 0 ? gy + ng : (gy >= ng ? gy - ng : gy);
-                    gz = gz < 0 ? gz + ng : (gz >= ng ? gz - ng : gz);
-                    int64_t gi = (gz * N + gy) * N + gx;
-                    if (beats(v, gi, bv, bi)) {
-                        bv = v;
-                        bi = gi;
-                        bx = dx;
-                        by = dy;
-                        bz = dz;
-                    }
-                }
-        if (bx == 0 && by == 0 && bz == 0) {
-            // a local maximum: a seed if above cwt_min, otherwise a root labelled -1
-            if (bv > cwt_min) {
-                ptr[i] = i;
-                atomicOr(&seed_bits[bi >> 5], 1u << (bi & 31));
+    // follow each chain inside the tile (read-only walk over the parents)
+    if (own) {
+        int32_t* out = label + (size_t(z0) * N + yc) * N + xc;
+        for (int lz = 0; lz < wz; lz++, out += N * N) {
+            const int i = (lz * kSegTY + ly) * kSegTX + lx;
+            int32_t cur = ptr[i];
+            int steps = 0;
+            while (cur >= 0 && steps < kChaseLimit) {
+                const int32_t nxt = ptr[cur];
+                if (nxt == cur) break;  // a seed
+                cur = nxt;
+                steps++;
+            }
+            int32_t res;
+            if (cur == -1) {
+                res = -1;
+            } else if (cur <= -2) {
+                res = (-2 - cur) | kFlag;
             } else {
-                ptr[i] = -1;
+                const int px = cur % kSegTX, py = (cur / kSegTX) % kSegTY, pz = cur / (kSegTX * kSegTY);
+                const int32_t g = int32_t((size_t(z0 + pz) * N + (y0 + py)) * N + (x0 + px));
+                res = (ptr[cur] == cur) ? g : (g | kFlag);  // walk stopped at the limit: resume globally
             }
-        } else {
-            int gx = int(bi % N), gy = int((bi / N) % N), gz = int(bi / (N * N));
-            int px = gx - x0, py = gy - y0, pz = gz - z0;
-            if (px >= 0 && px < wx && py >= 0 && py < wy && pz >= 0 && pz < wz)
-                ptr[i] = (pz * kSegTY + py) * kSegTX + px;
+            *out = res;
+        }
+    }
+}
+
+// Finishes every flagged label by following its chain through the label
+// grid (at most kChaseLimit steps per cell) and counts the cells of every
+// seed.  Labels read while other threads update them are always a later point
+// of the same chain, so the result does not depend on timing.  A cell still
+// unfinished at the limit stays flagged (pointing further along) and sets
+// changed[0]: the doubling rounds then finish it and the cells are recounted.
+__global__ void __launch_bounds__(256) k_seg_resolve(int32_t* __restrict__ label, int64_t cells,
+                                                     const uint32_t* __restrict__ bits,
+                                                     const uint32_t* __restrict__ prefix,
+                                                     const uint32_t* __restrict__ n_slots, HaloAcc* acc,
+                                                     int* __restrict__ changed) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    bool left = false;
+    const int64_t n4 = (cells + 3) / 4;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n4; base += stride) {
+        const int64_t i = base + lane;  // warp-uniform trip count
+        int v[4] = {-1, -1, -1, -1};
+        const bool vec = 4 * i + 3 < cells;
+        if (i < n4) {
+            if (vec) {
+                const int4 q = reinterpret_cast<const int4*>(label)[i];
+                v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+            } else {
+                for (int j = 0; j < 4 && 4 * i + j < cells; j++) v[j] = label[4 * i + j];
+            }
+        }
+        bool wrote = false;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            int32_t w = v[j];
+            if (w < 0 || !(w & kFlag)) continue;
+            int steps = 0;
+            while (w >= 0 && (w & kFlag) && steps < kChaseLimit) {
+                w = label[w & kMask];
+                steps++;
+            }
+            v[j] = w;
+            wrote = true;
+            left |= (w >= 0 && (w & kFlag));
+        }
+        if (wrote) {
+            if (vec) reinterpret_cast<int4*>(label)[i] = make_int4(v[0], v[1], v[2], v[3]);
             else
-                ptr[i] = -2 - int32_t(bi);
+                for (int j = 0; j < 4 && 4 * i + j < cells; j++) label[4 * i + j] = v[j];
         }
-    }
-    __syncthreads();
-
-    // pointer jumping inside the tile
-    for (int round = 0; round < kLocalRounds; round++) {
-        bool changed = false;
-        for (int i = threadIdx.x; i < kOwned; i += kSegThreads) {
-            int32_t p = ptr[i];
-            if (p >= 0 && p != i) {
-                int32_t q = ptr[p];
-                if (q != p) {
-                    ptr[i] = q;
-                    changed = true;
-                }
+        // cells per seed: runs of equal labels within the thread, one atomic per run,
+        // or one per warp when all 128 labels of the warp are the same seed
+        // (the shuffle runs on every lane: it must not sit behind a short-circuit)
+        const int lead = __shfl_sync(full, v[3], 0);
+        const bool same = (v[0] == v[3]) & (v[1] == v[3]) & (v[2] == v[3]) & (v[3] == lead);
+        const bool uniform = __all_sync(full, same);
+        if (uniform) {
+            uint32_t slot;
+            if (lane == 0 && v[0] >= 0 && !(v[0] & kFlag) && seed_slot(bits, prefix, n_slots, v[0], slot))
+                atomicAdd(&acc[slot].n_cells, 128ull);  // padding entries are -1, so all 128 are cells
+        } else {
+            int j = 0;
+            while (j < 4) {
+                int k = j + 1;
+                while (k < 4 && v[k] == v[j]) k++;
+                uint32_t slot;
+                if (v[j] >= 0 && !(v[j] & kFlag) && seed_slot(bits, prefix, n_slots, v[j], slot))
+                    atomicAdd(&acc[slot].n_cells, (unsigned long long)(k - j));
+                j = k;
             }
         }
-        if (!__syncthreads_or(changed)) break;
     }
+    if (__any_sync(full, left) && lane == 0) changed[0] = 1;
+}
 
-    for (int i = threadIdx.x; i < kOwned; i += kSegThreads) {
-        int lx = i % kSegTX, ly = (i / kSegTX) % kSegTY, lz = i / (kSegTX * kSegTY);
-        if (lx >= wx || ly >= wy || lz >= wz) continue;
-        int32_t p = ptr[i], out;
-        if (p == -1) {
-            out = -1;
-        } else if (p <= -2) {
-            out = (-2 - p) | kFlag;
-        } else {
-            int px = p % kSegTX, py = (p / kSegTX) % kSegTY, pz = p / (kSegTX * kSegTY);
-            int32_t g = int32_t(((z0 + pz) * N + (y0 + py)) * N + (x0 + px));
-            out = (ptr[p] == p) ? g : (g | kFlag);  // not yet resolved only if the local bound was hit
-        }
-        label[((z0 + lz) * N + (y0 + ly)) * N + (x0 + lx)] = out;
+// Fallback when a chain outlived the bounded walks: after the doubling rounds,
+// clear and recount the cells of every seed (does nothing otherwise).
+__global__ void __launch_bounds__(256) k_seg_recount(const int32_t* __restrict__ label, int64_t cells,
+                                                     const uint32_t* __restrict__ bits,
+                                                     const uint32_t* __restrict__ prefix,
+                                                     const uint32_t* __restrict__ n_slots, HaloAcc* acc,
+                                                     const int* __restrict__ changed, int phase) {
+    if (changed[0] == 0) return;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (phase == 0) {
+        for (int64_t s = gid; s < int64_t(*n_slots); s += stride) acc[s].n_cells = 0;
+        return;
+    }
+    for (int64_t c = gid; c < cells; c += stride) {
+        uint32_t slot;
+        const int32_t l = label[c];
+        if (l >= 0 && seed_slot(bits, prefix, n_slots, l, slot)) atomicAdd(&acc[slot].n_cells, 1ull);
     }
 }
 
@@ -243,14 +384,28 @@ int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->jump_changed, 0, sizeof(int) * (kMaxJumpRounds + 1), s);
     if (e != cudaSuccess) return cuda_status(e);
     int64_t ntiles = int64_t(div_up(ng, kSegTX)) * div_up(ng, kSegTY) * div_up(ng, kSegTZ);
-    CWTHF_LAUNCH(ctx, s, "k_seg_tile", k_seg_tile<<<unsigned(ntiles), kSegThreads, 0, s>>>(cwt, ng, cwt_min, label, ctx->seed_bits, ctx->d_status));
+    cudaFuncSetAttribute(k_seg_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(int32_t) * kOwned));
+    CWTHF_LAUNCH(ctx, s, "k_seg_tile",
+                 k_seg_tile<<<unsigned(ntiles), kSegThreads, sizeof(int32_t) * kOwned, s>>>(cwt, ng, cwt_min, label,
+                                                                                          ctx->seed_bits,
+                                                                                          ctx->d_status));
+    // seed ranks first (the resolve pass counts cells per seed slot)
+    int rc = seeds_rank(ctx, ng, s);
+    if (rc) return rc;
     int blocks = ctx->sm_count * 8;
-    for (int r = 0; r < kMaxJumpRounds; r++) {
-        CWTHF_LAUNCH(ctx, s, "k_seg_jump", k_seg_jump<<<blocks, kSegThreads, 0, s>>>(label, cells, ctx->jump_changed, r));
+    CWTHF_LAUNCH(ctx, s, "k_seg_resolve",
+                 k_seg_resolve<<<blocks, 256, 0, s>>>(label, cells, ctx->seed_bits, ctx->seed_prefix, ctx->n_seeds,
+                                                      ctx->acc, ctx->jump_changed));
+    // pointer doubling for whatever the bounded walks left (normally nothing: every round exits at once)
+    for (int r = 1; r < kMaxJumpRounds; r++) {
+        CWTHF_LAUNCH(ctx, s, "k_seg_jump", k_seg_jump<<<blocks, 256, 0, s>>>(label, cells, ctx->jump_changed, r));
     }
     CWTHF_LAUNCH(ctx, s, "k_seg_jump_check", k_seg_jump_check<<<1, 1, 0, s>>>(ctx->jump_changed, kMaxJumpRounds, ctx->d_status));
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
-    return seeds_rank(ctx, ng, s);
+    for (int phase = 0; phase < 2; phase++)
+        CWTHF_LAUNCH(ctx, s, "k_seg_recount",
+                     k_seg_recount<<<blocks, 256, 0, s>>>(label, cells, ctx->seed_bits, ctx->seed_prefix,
+                                                          ctx->n_seeds, ctx->acc, ctx->jump_changed, phase));
+    return cuda_status(cudaGetLastError());
 }
 
 }  // namespace cwthf

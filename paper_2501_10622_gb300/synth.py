@@ -82,15 +82,24 @@ def clumped_box(n_particles: int, box: float, n_clumps: int | None = None, seed:
     n_uni = int(round(uniform_frac * n_particles))
     n_cl = n_particles - n_uni
     f64 = torch.float64
-    out = torch.empty((n_particles, 3), dtype=f64, device=device)
-    out[:n_uni] = torch.rand((n_uni, 3), generator=gen, device=device, dtype=f64) * box
+    # positions are formed in fp64 chunk by chunk, wrapped, and stored as float32
+    out = torch.empty((n_particles, 3), dtype=torch.float32, device=device)
+    chunk = 1 << 24
+
+    def store(dst0, x):
+        x = torch.remainder(x, box).to(torch.float32)
+        x[x >= box] = 0.0  # float32 rounding of values just below box
+        out[dst0:dst0 + x.shape[0]] = x
+
+    for s in range(0, n_uni, chunk):
+        k = min(chunk, n_uni - s)
+        store(s, torch.rand((k, 3), generator=gen, device=device, dtype=f64) * box)
     if n_cl > 0:
         counts = clump_counts(n_cl, n_clumps, gen, device)
         centres = torch.rand((n_clumps, 3), generator=gen, device=device, dtype=f64) * box
         conc = NFW_C_RANGE[0] + (NFW_C_RANGE[1] - NFW_C_RANGE[0]) * torch.rand(n_clumps, generator=gen, device=device, dtype=f64)
         rvir = RVIR_RANGE[0] + (RVIR_RANGE[1] - RVIR_RANGE[0]) * torch.rand(n_clumps, generator=gen, device=device, dtype=f64)
         owner = torch.repeat_interleave(torch.arange(n_clumps, device=device), counts)
-        chunk = 1 << 24
         for s in range(0, n_cl, chunk):
             o = owner[s:s + chunk]
             k = o.numel()
@@ -99,14 +108,12 @@ def clumped_box(n_particles: int, box: float, n_clumps: int | None = None, seed:
             r = y * (rvir[o] / conc[o])
             d = torch.randn((k, 3), generator=gen, device=device, dtype=f64)
             d = d / d.norm(dim=1, keepdim=True).clamp_min(1e-300)
-            out[n_uni + s:n_uni + s + k] = centres[o] + r[:, None] * d
-    out = torch.remainder(out, box)
-    pos = out.to(torch.float32)
-    pos[pos >= box] = 0.0  # float32 rounding of values just below box
+            store(n_uni + s, centres[o] + r[:, None] * d)
+        del owner
     if shuffle:
         perm = torch.randperm(n_particles, generator=gen, device=device)
-        pos = pos[perm]
-    return pos.contiguous()
+        out = out[perm]
+    return out.contiguous()
 
 
 def smooth_ng(ng: float) -> int:
@@ -145,6 +152,7 @@ class Workload:
 WORKLOADS = {
     "clumped-64cube-L50": Workload("clumped-64cube-L50", 64 ** 3, 50.0, 64, 200, 1),
     "clumped-256cube-L200": Workload("clumped-256cube-L200", 256 ** 3, 200.0, 256, 12800, 2),
+    "clumped-256cube-grid512-L250": Workload("clumped-256cube-grid512-L250", 256 ** 3, 250.0, 512, 12500, 6),
     "clumped-512cube-grid1024-L500": Workload("clumped-512cube-grid1024-L500", 512 ** 3, 500.0, 1024,
                                               100000, 3, scales=(2.0, 3.0, 4.0)),
 }
