@@ -141,14 +141,13 @@ def algorithmic_bytes(name, u):
         "k_fft_x_inv": 8 * half + 4 * cells,           # half spectrum in, fp32 CWT out
         "k_dep_tile": 8 * cells + 8 * npart,           # records in once, int64 grid out
         "k_dep_count": 12 * npart,
-        "k_dep_scatter": 12 * npart + 8 * npart,
+        "k_dep_scatter": 12 * npart + 8 * npart + 4 * npart,  # positions in, record + index out
         "k_seg_tile": 4 * cells + 4 * cells,           # CWT in, labels out
         "k_seg_jump": 4 * cells,
         "k_seg_resolve": 4 * cells,                    # labels in (flagged ones rewritten)
         "k_count_cells": 4 * cells,
-        "k_assign_ids": 12 * npart + 4 * npart + 4 * npart,  # positions, label gather, slot out
-        "k_halo_sums": 8 * npart + 4 * npart,                # records, label gather
-        "k_finalize": 8 * npart,
+        "k_halo_sums": 8 * npart + 4 * npart + 4 * npart,    # records, label gather, slot out
+        "k_finalize": 12 * npart,                            # slot + index in, halo id scattered out
     }
     return table.get(name)
 

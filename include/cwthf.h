@@ -21,7 +21,9 @@
  *     others make the call fail with CWTHF_E_BAD_INPUT (reported by
  *     cwthf_sync, see below).
  *   - Positions are quantised to CWTHF_FRAC_BITS fractional bits of a cell:
- *     q = floor(x * ((ng / L) * 2^10)) mod ng*2^10, with one fp64 product.
+ *     q = floor(x * s) mod ng*2^10, where s = (ng / L) * 2^10 is formed in
+ *     fp64 and rounded to 29 significant bits, so that x * s is exact (the
+ *     device forms it as one 32 x 32 -> 64-bit integer product).
  *   - Masses: mass == NULL means every particle has mass mass_unit.
  *     Otherwise particle i has integer mass m_q = rint(mass[i] / mass_unit)
  *     in units of mass_unit; 0 <= m_q < 2^31 is required per particle and
@@ -159,7 +161,7 @@ CWTHF_API int cwthf_segment(cwthf_ctx *ctx, const float *cwt, int ng, float cwt_
  *   cell_label  device, int32 [ng^3] from cwthf_segment
  *   cwt         device, float [ng^3] or NULL (then cat[].peak = 0)
  *   params      host; w is ignored here
- *   halo_id     device, int32 [np]; overwritten
+ *   halo_id     device, int32 [np]; overwritten (unspecified when the call fails)
  *   cat         device, cwthf_halo [cat_cap]
  *   n_halo      device, int64 [1]: the number of kept halos (even when it
  *               exceeds cat_cap, which also records CWTHF_E_CAPACITY). */

@@ -65,56 +65,13 @@ __device__ __forceinline__ int nearest_node(int64_t q, int ng) {
     return n == ng ? 0 : n;
 }
 
-// Particles in their own order: nearest node, its label, the label's slot
-// (or -1).  Gathers only; the per-halo sums are formed by k_halo_sums.
-__global__ void __launch_bounds__(kThreads) k_assign_ids(DepArgs a, const int32_t* __restrict__ label,
-                                                        const uint32_t* __restrict__ bits,
-                                                        const uint32_t* __restrict__ prefix,
-                                                        const uint32_t* __restrict__ n_slots,
-                                                        int32_t* __restrict__ part_slot, int* status) {
-    constexpr int kIlp = 4;  // independent particles per thread: several gather chains in flight
-    const size_t N = size_t(a.ng);
-    const int64_t cells = int64_t(N * N * N);
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < a.np; i0 += kIlp * stride) {
-        int32_t lab[kIlp];
-        bool ok[kIlp];
-#pragma unroll
-        for (int u = 0; u < kIlp; u++) {
-            const int64_t i = i0 + u * stride;
-            lab[u] = -1;
-            ok[u] = false;
-            if (i >= a.np) continue;
-            int64_t q[3];
-            const float* p = a.pos + 3 * i;
-            if (quantise(p[0], a.scale_m, a.scale_e, a.modulus, q[0]) &&
-                quantise(p[1], a.scale_m, a.scale_e, a.modulus, q[1]) &&
-                quantise(p[2], a.scale_m, a.scale_e, a.modulus, q[2])) {
-                const size_t cell = (size_t(nearest_node(q[2], a.ng)) * N + nearest_node(q[1], a.ng)) * N +
-                                    nearest_node(q[0], a.ng);
-                lab[u] = label[cell];
-                ok[u] = true;
-            } else {
-                set_status(status, CWTHF_E_BAD_INPUT);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kIlp; u++) {
-            const int64_t i = i0 + u * stride;
-            if (i >= a.np) continue;
-            int32_t out = -1;
-            uint32_t slot;
-            if (ok[u] && lab[u] >= 0 && lab[u] < cells && seed_slot(bits, prefix, n_slots, lab[u], slot))
-                out = int32_t(slot);
-            part_slot[i] = out;
-        }
-    }
-}
-
-// Per-halo integer sums over the binned records, one deposit tile at a time:
-// the records of a tile come from a 32 x 8 x 8-cell block, so neighbouring
-// lanes mostly share a halo and the warp folds their contributions into one
-// set of atomics per halo.
+// Per-halo integer sums over the binned records, 32 consecutive records per
+// warp and batch, kIlp batches in flight per warp (independent gather chains:
+// record -> label -> seed bitmap and prefix).  Records are grouped by deposit
+// tile (a 32 x 8 x 8-cell block), so the lanes of a warp often share a halo,
+// and a batch whose records all fall in one halo folds them into one set of
+// atomics.  Each record's halo slot (or -1) is kept, in record order, for the
+// final pass.
 __global__ void __launch_bounds__(kThreads) k_halo_sums(DepArgs a, const uint32_t* __restrict__ off,
                                                        const unsigned long long* __restrict__ rec,
                                                        const uint32_t* __restrict__ rec_mq,
@@ -122,58 +79,80 @@ __global__ void __launch_bounds__(kThreads) k_halo_sums(DepArgs a, const uint32_
                                                        const uint32_t* __restrict__ bits,
                                                        const uint32_t* __restrict__ prefix,
                                                        const uint32_t* __restrict__ n_slots, HaloAcc* acc,
-                                                       u64* __restrict__ mtot) {
+                                                       int32_t* __restrict__ rec_slot, u64* __restrict__ mtot) {
+    constexpr int kIlp = 4;
     const int lane = threadIdx.x & 31;
     const int N = a.ng;
     const int64_t M = a.modulus;
-    const int64_t ntiles = int64_t(a.ntx) * a.nty * a.ntz;
-    const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const int64_t cells = int64_t(N) * N * N;
+    const int64_t total = off[int64_t(a.ntx) * a.nty * a.ntz * kDepClasses];  // records binned
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const uint32_t ns = *n_slots;
     u64 msum = 0;
-    for (int64_t t = warp; t < ntiles; t += nwarps) {  // one warp per tile
-        const int tx = int(t % a.ntx), ty = int((t / a.ntx) % a.nty), tz = int(t / (int64_t(a.ntx) * a.nty));
-        const uint32_t beg = off[t * kDepClasses], end = off[t * kDepClasses + kDepClasses];
-        for (uint32_t r0 = beg; r0 < end; r0 += 32) {  // warp-uniform
-            const uint32_t r = r0 + uint32_t(lane);
-            uint32_t key = 0xffffffffu;
-            uint32_t mq = 0;
-            long long mom[3] = {0, 0, 0};
-            if (r < end) {
+    for (int64_t r0 = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); r0 < total; r0 += kIlp * stride) {
+        int64_t q[kIlp][3];
+        uint32_t mq[kIlp];
+        int32_t lab[kIlp];
+#pragma unroll
+        for (int u = 0; u < kIlp; u++) {  // records, then labels: kIlp independent chains
+            const int64_t r = r0 + u * stride + lane;
+            mq[u] = 0;
+            lab[u] = -1;
+            q[u][0] = q[u][1] = q[u][2] = 0;
+            if (r < total) {
                 const u64 e = rec[r];
-                mq = a.mass ? rec_mq[r] : 1u;
-                const int64_t q[3] = {int64_t(tx * kDepTX + int(e & 63)) * kFracOne + int64_t((e >> 18) & 1023),
-                                      int64_t(ty * kDepTY + int((e >> 6) & 63)) * kFracOne + int64_t((e >> 28) & 1023),
-                                      int64_t(tz * kDepTZ + int((e >> 12) & 63)) * kFracOne + int64_t((e >> 38) & 1023)};
-                const int nx = nearest_node(q[0], N), ny = nearest_node(q[1], N), nz = nearest_node(q[2], N);
-                const int32_t lab = label[(size_t(nz) * N + ny) * N + nx];
-                uint32_t slot;
-                if (lab >= 0 && int64_t(lab) < int64_t(N) * N * N && seed_slot(bits, prefix, n_slots, lab, slot)) {
-                    key = slot;
-                    const int sx = lab % N, sy = (lab / N) % N, sz = lab / (N * N);
-                    const int sc[3] = {sx, sy, sz};
+                mq[u] = a.mass ? rec_mq[r] : 1u;
+                q[u][0] = rec_q(e, 0);
+                q[u][1] = rec_q(e, 1);
+                q[u][2] = rec_q(e, 2);
+                const int nx = nearest_node(q[u][0], N), ny = nearest_node(q[u][1], N),
+                          nz = nearest_node(q[u][2], N);
+                lab[u] = label[(size_t(nz) * N + ny) * N + nx];
+            }
+        }
+        uint32_t key[kIlp], word[kIlp], pre[kIlp];
+#pragma unroll
+        for (int u = 0; u < kIlp; u++) {  // seed bitmap and prefix words
+            const bool in = lab[u] >= 0 && int64_t(lab[u]) < cells;
+            word[u] = in ? bits[lab[u] >> 5] : 0u;
+            pre[u] = in ? prefix[lab[u] >> 5] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kIlp; u++) {
+            const int64_t r = r0 + u * stride + lane;
+            key[u] = 0xffffffffu;
+            long long mom[3] = {0, 0, 0};
+            if (r < total) {
+                const uint32_t bit = 1u << (lab[u] & 31);
+                const uint32_t slot = pre[u] + __popc(word[u] & (bit - 1u));
+                if ((word[u] & bit) && slot < ns) {
+                    key[u] = slot;
+                    const int sc[3] = {lab[u] % N, (lab[u] / N) % N, lab[u] / (N * N)};
 #pragma unroll
                     for (int d = 0; d < 3; d++) {
-                        int64_t dq = q[d] - int64_t(sc[d]) * kFracOne;  // in (-M, M)
+                        int64_t dq = q[u][d] - int64_t(sc[d]) * kFracOne;  // in (-M, M)
                         if (dq < 0) dq += M;
-                        if (2 * dq >= M) dq -= M;                      // minimum image in [-M/2, M/2)
-                        mom[d] = (long long)mq * dq;
+                        if (2 * dq >= M) dq -= M;  // minimum image in [-M/2, M/2)
+                        mom[d] = (long long)mq[u] * dq;
                     }
                 }
+                rec_slot[r] = int32_t(key[u]);  // 0xffffffff reads as -1
             }
-            msum += mq;
-            // a warp whose records all fall in one halo adds one set of sums; otherwise
-            // every lane adds its own (records of different halos rarely collide)
-            const bool uniform = __all_sync(kFull, key == __shfl_sync(kFull, key, 0)) && key != 0xffffffffu;
-            u64 cnt = 1, m_sum = mq, m0 = u64(mom[0]), m1 = u64(mom[1]), m2 = u64(mom[2]);
+            msum += mq[u];
+            // a batch whose records all fall in one halo adds one set of sums; otherwise
+            // every lane adds its own (the shuffle runs on every lane)
+            const uint32_t k0 = __shfl_sync(kFull, key[u], 0);
+            const bool uniform = __all_sync(kFull, key[u] == k0) && key[u] != 0xffffffffu;
+            u64 cnt = 1, m_sum = mq[u], m0 = u64(mom[0]), m1 = u64(mom[1]), m2 = u64(mom[2]);
             if (uniform) {
                 cnt = 32;
-                m_sum = warp_sum32(mq);
+                m_sum = warp_sum32(mq[u]);
                 m0 = warp_sum64(m0);
                 m1 = warp_sum64(m1);
                 m2 = warp_sum64(m2);
             }
-            if (key != 0xffffffffu && (!uniform || lane == 0)) {
-                HaloAcc* h = acc + key;
+            if (key[u] != 0xffffffffu && (!uniform || lane == 0)) {
+                HaloAcc* h = acc + key[u];
                 atomicAdd(&h->n_part, cnt);
                 atomicAdd(&h->mq, m_sum);
                 atomicAdd(reinterpret_cast<u64*>(&h->mom[0]), m0);
@@ -215,6 +194,7 @@ __global__ void __launch_bounds__(kThreads) k_catalogue(const HaloAcc* __restric
                                                        const uint32_t* __restrict__ n_seeds,
                                                        const uint32_t* __restrict__ keep_off, const float* cwt,
                                                        FilterArgs f, cwthf_halo* __restrict__ cat,
+                                                       int32_t* __restrict__ slot_halo,
                                                        int64_t* __restrict__ n_halo, int* status) {
     uint32_t ns = *n_seeds;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -226,8 +206,10 @@ __global__ void __launch_bounds__(kThreads) k_catalogue(const HaloAcc* __restric
     const double cell_q = (f.L / double(f.ng)) / double(kFracOne);
     int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < ns; s += stride) {
-        uint32_t pos = keep_off[s];
-        if (keep_off[s + 1] == pos || int64_t(pos) >= f.cat_cap) continue;
+        const uint32_t pos = keep_off[s];
+        const bool kept = keep_off[s + 1] != pos;
+        slot_halo[s] = kept ? seed_list[s] : -1;
+        if (!kept || int64_t(pos) >= f.cat_cap) continue;
         HaloAcc h = acc[s];
         int64_t seed = seed_list[s];
         int64_t sc[3] = {seed % N, (seed / N) % N, seed / (N * N)};
@@ -251,16 +233,33 @@ __global__ void __launch_bounds__(kThreads) k_catalogue(const HaloAcc* __restric
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_finalize(const int32_t* __restrict__ part_slot, int64_t np,
-                                                      const uint32_t* __restrict__ keep_off,
-                                                      const int32_t* __restrict__ seed_list,
+// halo_id of every particle, in particle order: the record it was binned to,
+// that record's halo slot, and the slot's seed if the halo was kept.  Several
+// particles per thread keep independent gather chains in flight.
+__global__ void __launch_bounds__(kThreads) k_finalize(const uint32_t* __restrict__ part_rec, int64_t np,
+                                                      const uint32_t* __restrict__ total_ptr,
+                                                      const int32_t* __restrict__ rec_slot,
+                                                      const int32_t* __restrict__ slot_halo,
                                                       int32_t* __restrict__ halo_id) {
-    int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np; i += stride) {
-        int32_t s = part_slot[i];
-        int32_t out = -1;
-        if (s >= 0 && keep_off[s + 1] != keep_off[s]) out = seed_list[s];
-        halo_id[i] = out;
+    constexpr int kIlp = 4;
+    const int64_t total = *total_ptr;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < np; i0 += kIlp * stride) {
+        int32_t sl[kIlp];
+#pragma unroll
+        for (int u = 0; u < kIlp; u++) {
+            const int64_t i = i0 + u * stride;
+            sl[u] = -1;
+            if (i < np) {
+                const uint32_t r = part_rec[i];
+                if (int64_t(r) < total) sl[u] = rec_slot[r];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kIlp; u++) {
+            const int64_t i = i0 + u * stride;
+            if (i < np) halo_id[i] = sl[u] >= 0 ? slot_halo[sl[u]] : -1;
+        }
     }
 }
 
@@ -283,15 +282,12 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
                      k_count_cells<<<blocks, kThreads, 0, s>>>(label, cells, ctx->seed_bits, ctx->seed_prefix,
                                                                d_nseeds, ctx->acc, ctx->d_status));
     DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
+    const int64_t total_key = deposit_geom(ng).ntiles * kDepClasses;  // dep_off[total_key] = records binned
     int pblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kThreads), int64_t(ctx->sm_count) * 16));
-    CWTHF_LAUNCH(ctx, s, "k_assign_ids",
-                 k_assign_ids<<<pblocks, kThreads, 0, s>>>(a, label, ctx->seed_bits, ctx->seed_prefix, d_nseeds,
-                                                           ctx->part_slot, ctx->d_status));
-    int tblocks = int(std::min<int64_t>(deposit_geom(ng).ntiles, int64_t(ctx->sm_count) * 8));
     CWTHF_LAUNCH(ctx, s, "k_halo_sums",
-                 k_halo_sums<<<tblocks, kThreads, 0, s>>>(a, ctx->dep_off, ctx->dep_rec, ctx->dep_mq, label,
+                 k_halo_sums<<<pblocks, kThreads, 0, s>>>(a, ctx->dep_off, ctx->dep_rec, ctx->dep_mq, label,
                                                           ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc,
-                                                          ctx->d_mtot));
+                                                          ctx->part_slot, ctx->d_mtot));
     FilterArgs f;
     f.ng = ng;
     f.L = L;
@@ -303,9 +299,10 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
     if ((rc = scan_u32_dev(ctx, ctx->keep_off, ctx->keep_off, d_nseeds, slot_cap, s))) return rc;
     CWTHF_LAUNCH(ctx, s, "k_catalogue",
                  k_catalogue<<<blocks, kThreads, 0, s>>>(ctx->acc, ctx->seed_list, d_nseeds, ctx->keep_off, cwt, f,
-                                                         cat, n_halo, ctx->d_status));
+                                                         cat, ctx->slot_halo, n_halo, ctx->d_status));
     CWTHF_LAUNCH(ctx, s, "k_finalize",
-                 k_finalize<<<pblocks, kThreads, 0, s>>>(ctx->part_slot, np, ctx->keep_off, ctx->seed_list, halo_id));
+                 k_finalize<<<pblocks, kThreads, 0, s>>>(ctx->part_rec, np, ctx->dep_off + total_key,
+                                                         ctx->part_slot, ctx->slot_halo, halo_id));
     return cuda_status(cudaGetLastError());
 }
 

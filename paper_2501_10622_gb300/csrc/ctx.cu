@@ -64,6 +64,7 @@ void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, F
     f(reinterpret_cast<void**>(&c->dep_cursor), size_t(z.keys + 1) * 4);
     f(reinterpret_cast<void**>(&c->dep_rec), size_t(z.np) * 8);
     f(reinterpret_cast<void**>(&c->dep_mq), size_t(z.np) * 4);
+    f(reinterpret_cast<void**>(&c->part_rec), size_t(z.np) * 4);
     f(reinterpret_cast<void**>(&c->d_mtot), 16);
     f(reinterpret_cast<void**>(&c->n_seeds), 16);
     f(reinterpret_cast<void**>(&c->spec), spec_bytes(max_ng));
@@ -73,6 +74,7 @@ void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, F
     f(reinterpret_cast<void**>(&c->seed_list), size_t(z.slots) * 4);
     f(reinterpret_cast<void**>(&c->acc), size_t(z.slots) * sizeof(HaloAcc));
     f(reinterpret_cast<void**>(&c->keep_off), size_t(z.slots + 2) * 4);
+    f(reinterpret_cast<void**>(&c->slot_halo), size_t(z.slots) * 4);
     f(reinterpret_cast<void**>(&c->part_slot), size_t(z.np) * 4);
     f(reinterpret_cast<void**>(&c->jump_changed), sizeof(int) * (kMaxJumpRounds + 2));
     f(reinterpret_cast<void**>(&c->scan_tmp), z.scan_words * 4);

@@ -47,19 +47,16 @@ __device__ __forceinline__ PartBin bin_particle(const DepArgs& a, int64_t i) {
     int ms = mass_quantum(a, i, b.mq);
     if (ms != CWTHF_OK) { b.status = ms; b.mq = 0; return b; }
     const int T[3] = {kDepTX, kDepTY, kDepTZ};
-    int n[3], t[3], l[3], f[3], cls = 0;
+    int n[3], t[3], cls = 0;
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         n[d] = int(q[d] >> kFracBits);
-        f[d] = int(q[d] & (kFracOne - 1));
         t[d] = n[d] / T[d];
-        l[d] = n[d] - t[d] * T[d];
         if (n[d] + 1 == a.ng || (n[d] + 1) % T[d] == 0) cls |= 1 << d;
     }
     uint32_t tile = uint32_t((int64_t(t[2]) * a.nty + t[1]) * a.ntx + t[0]);
     b.key = tile * kDepClasses + uint32_t(cls);
-    b.rec = (unsigned long long)l[0] | ((unsigned long long)l[1] << 6) | ((unsigned long long)l[2] << 12) |
-            ((unsigned long long)f[0] << 18) | ((unsigned long long)f[1] << 28) | ((unsigned long long)f[2] << 38);
+    b.rec = pack_rec(q[0], q[1], q[2]);
     return b;
 }
 
@@ -86,10 +83,13 @@ __global__ void __launch_bounds__(kCountThreads) k_dep_count(DepArgs a, uint32_t
     if (lane == 0 && msum) atomicAdd(mtot, msum);
 }
 
-// Pass 2: write each particle's packed record into its (tile, class) segment.
+// Pass 2: write each particle's packed record into its (tile, class) segment,
+// and (when part_rec is given) the record's position in particle order
+// (0xffffffff for a particle that was not binned).
 __global__ void __launch_bounds__(kCountThreads) k_dep_scatter(DepArgs a, uint32_t* __restrict__ cursor,
                                                               unsigned long long* __restrict__ rec,
-                                                              uint32_t* __restrict__ rec_mq) {
+                                                              uint32_t* __restrict__ rec_mq,
+                                                              uint32_t* __restrict__ part_rec) {
     int lane = threadIdx.x & 31;
     int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < a.np; base += stride) {
@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(kCountThreads) k_dep_scatter(DepArgs a, uint32
             rec[slot] = b.rec;
             if (a.mass) rec_mq[slot] = b.mq;
         }
+        if (part_rec && i < a.np) part_rec[i] = b.key != kInvalidKey ? slot : 0xffffffffu;
     }
 }
 
@@ -187,8 +188,9 @@ __global__ void __launch_bounds__(kTileThreads) k_dep_tile(DepArgs a, const uint
             const int m = seg_m[sgi];
             const u64 e = live ? rec[r] : 0ull;
             const uint32_t mq = live ? (a.mass ? rec_mq[r] : 1u) : 0u;
-            int lx = int(e & 63), ly = int((e >> 6) & 63), lz = int((e >> 12) & 63);
-            const int fx = int((e >> 18) & 1023), fy = int((e >> 28) & 1023), fz = int((e >> 38) & 1023);
+            const int qx = rec_q(e, 0), qy = rec_q(e, 1), qz = rec_q(e, 2);
+            int lx = (qx >> kFracBits) - x0, ly = (qy >> kFracBits) - y0, lz = (qz >> kFracBits) - z0;
+            const int fx = qx & (kFracOne - 1), fy = qy & (kFracOne - 1), fz = qz & (kFracOne - 1);
             // a particle of a lower neighbour only reaches in with its upper node
             if (m & 1) lx = -1;
             if (m & 2) ly = -1;
@@ -241,7 +243,8 @@ int bin_particles(cwthf_ctx* ctx, const float* pos, const float* mass, double ma
     if ((e = cudaMemcpyAsync(ctx->dep_cursor, ctx->dep_off, size_t(nkeys) * 4, cudaMemcpyDeviceToDevice, s)) !=
         cudaSuccess)
         return cuda_status(e);
-    CWTHF_LAUNCH(ctx, s, "k_dep_scatter", k_dep_scatter<<<blocks, kCountThreads, 0, s>>>(a, ctx->dep_cursor, ctx->dep_rec, ctx->dep_mq));
+    CWTHF_LAUNCH(ctx, s, "k_dep_scatter", k_dep_scatter<<<blocks, kCountThreads, 0, s>>>(a, ctx->dep_cursor, ctx->dep_rec, ctx->dep_mq,
+                                                                        ctx->part_rec));
     return cuda_status(cudaGetLastError());
 }
 
@@ -276,7 +279,7 @@ int deposit_into_scratch(const DepositScratch& sc, const float* pos, const float
     if (rc) return rc;
     if ((e = cudaMemcpyAsync(sc.cursor, sc.off, size_t(nkeys) * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return cuda_status(e);
-    k_dep_scatter<<<blocks, kCountThreads, 0, s>>>(a, sc.cursor, sc.rec, sc.mq);
+    k_dep_scatter<<<blocks, kCountThreads, 0, s>>>(a, sc.cursor, sc.rec, sc.mq, nullptr);
     int tblocks = int(std::min<int64_t>(g.ntiles, int64_t(sc.sm_count) * 8));
     k_dep_tile<<<tblocks, kTileThreads, 0, s>>>(a, sc.off, sc.rec, sc.mq, sc.mtot, grid, sc.status);
     return cuda_status(cudaGetLastError());

@@ -23,6 +23,18 @@ constexpr int64_t kFracOne = int64_t(1) << kFracBits;
 constexpr int kDepTX = 32, kDepTY = 8, kDepTZ = 8;
 constexpr int kDepClasses = 8;  // boundary class bits (x, y, z) per particle
 
+// A binned particle record: its three fixed-point coordinates q (each below
+// ng * 2^10 <= 2^20) in 21-bit fields, x lowest.
+constexpr int kRecBits = 21;
+static_assert(int64_t(CWTHF_MAX_NG) * (int64_t(1) << CWTHF_FRAC_BITS) <= (int64_t(1) << kRecBits),
+              "record fields too narrow for the largest grid");
+__host__ __device__ __forceinline__ unsigned long long pack_rec(int64_t qx, int64_t qy, int64_t qz) {
+    return (unsigned long long)qx | ((unsigned long long)qy << kRecBits) | ((unsigned long long)qz << (2 * kRecBits));
+}
+__host__ __device__ __forceinline__ int rec_q(unsigned long long e, int d) {
+    return int((e >> (kRecBits * d)) & ((1ull << kRecBits) - 1));
+}
+
 // Segmentation tiles (owned cells; one halo layer is staged around them).
 constexpr int kSegTX = 30, kSegTY = 16, kSegTZ = 32;
 constexpr int kMaxJumpRounds = 40;
@@ -82,8 +94,9 @@ struct cwthf_ctx {
     uint32_t* dep_count = nullptr;   // [max_tiles * 8 + 1]
     uint32_t* dep_off = nullptr;     // [max_tiles * 8 + 1]
     uint32_t* dep_cursor = nullptr;  // [max_tiles * 8]
-    unsigned long long* dep_rec = nullptr;  // [max_np] packed fixed-point records
+    unsigned long long* dep_rec = nullptr;  // [max_np] packed fixed-point records (pack_rec)
     uint32_t* dep_mq = nullptr;             // [max_np] integer masses of the records
+    uint32_t* part_rec = nullptr;           // [max_np] record position of each particle (~0u: not binned)
     unsigned long long* d_mtot = nullptr;   // [1] sum of m_q of the last deposit / assign
 
     // transform scratch
@@ -97,7 +110,8 @@ struct cwthf_ctx {
     uint32_t* n_seeds = nullptr;      // [1]
     cwthf::HaloAcc* acc = nullptr;    // [ng^3 / 8 + 1]
     uint32_t* keep_off = nullptr;     // [ng^3 / 8 + 2] kept-halo prefix
-    int32_t* part_slot = nullptr;     // [max_np]
+    int32_t* slot_halo = nullptr;     // [ng^3 / 8 + 1] seed of each kept slot, -1 otherwise
+    int32_t* part_slot = nullptr;     // [max_np] halo slot of each binned record (-1: none)
     int* jump_changed = nullptr;      // [kMaxJumpRounds + 1]
     uint32_t* scan_tmp = nullptr;     // block sums of the device scan
     size_t scan_tmp_cap = 0;          // words

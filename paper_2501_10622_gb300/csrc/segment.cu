@@ -34,37 +34,45 @@ constexpr int kSegPrefetch = 8;  // planes of a column loaded ahead
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-// Order-preserving map of a float to an unsigned integer (larger float ->
-// larger integer); -0 is folded onto +0 first so that the two compare equal.
-__device__ __forceinline__ uint32_t ord_bits(float v) {
-    const uint32_t u = __float_as_uint(v + 0.0f);
-    return u ^ ((uint32_t)((int32_t)u >> 31) | 0x80000000u);
+// Search codes of the three candidates (-1, 0, +1) along one axis: rank of
+// the wrapped coordinate (0 = smallest) times 4 plus the candidate's position.
+// The smallest code among the candidates holding the maximum is the winner
+// under the strict order; kNoMatch (only reached when the window holds no
+// comparable value, i.e. NaN input) decodes to the centre.
+constexpr int kNoMatch = 13;
+__device__ __forceinline__ void codes3(int m, int c, int p, int& km, int& kc, int& kp) {
+    km = ((m > c) + (m > p)) * 4 + 0;
+    kc = ((c > m) + (c > p)) * 4 + 1;
+    kp = ((p > m) + (p > c)) * 4 + 2;
 }
 
-// Rank (0, 1, 2) of each of the three wrapped coordinates (c-1, c, c+1): the
-// strict cell order breaks value ties by the smaller linear index, i.e. by
-// the smaller wrapped z, then y, then x.
-__device__ __forceinline__ void ranks3(int a, int b, int c, int& ra, int& rb, int& rc) {
-    ra = (a > b) + (a > c);
-    rb = (b > a) + (b > c);
-    rc = (c > a) + (c > b);
+// Position (0, 1, 2 for -1, 0, +1) of the first candidate, in the strict
+// order, whose value equals M.
+__device__ __forceinline__ int pick3(float a, float b, float c, float M, int ka, int kb, int kc) {
+    const int x = min(min(a == M ? ka : kNoMatch, b == M ? kb : kNoMatch), c == M ? kc : kNoMatch);
+    return x & 3;
 }
 
 // Parents of a 30 x 16 x 32-cell tile and the in-tile part of every chain.
 //
-// Candidates carry a 64-bit key: high word = order-preserving bits of the CWT
-// value, low word = tie-break priority and the candidate's offset.  The
-// maximum of the keys is the best cell under the strict order, so each of the
-// 26 comparisons is one unsigned max, done separably: along x by warp
-// shuffles, along y through a shared row buffer (one barrier per plane),
-// along z in registers over the last three planes.  Parents go to shared
-// memory; every cell then follows its chain there until it reaches a seed, a
-// non-seed maximum, or a cell outside the tile.
-__global__ void __launch_bounds__(kSegThreads) k_seg_tile(const float* __restrict__ C, int ng, float cwt_min,
+// The best of the 27 cells around c is found in two steps.  First the
+// maximum value M, separably: along x by warp shuffles, along y through a
+// shared buffer of x-window maxima, along z in registers over the last three
+// planes.  Then the winner among the cells equal to M, which under the
+// strict order is the one with the smallest wrapped (z, y, x) in
+// lexicographic order: the first plane (in wrapped z order) whose window
+// holds M, then in that plane the first row whose x-window holds M, then in
+// that row the first column holding M.  Two rings of four planes in shared
+// memory (raw values and x-window maxima) serve the search, so one barrier
+// per plane suffices.  Parents go to shared memory; every cell then follows
+// its chain there until it reaches a seed, a non-seed maximum, or a cell
+// outside the tile.
+__global__ void __launch_bounds__(kSegThreads, 2) k_seg_tile(const float* __restrict__ C, int ng, float cwt_min,
                                                          int32_t* __restrict__ label, uint32_t* __restrict__ seed_bits,
                                                          int* status) {
     extern __shared__ int32_t ptr[];  // [kOwned], dynamic
-    __shared__ unsigned long long rowbest[2][kSegRows][32];
+    __shared__ float vals[4][kSegRows][32];  // raw values of planes p-3 .. p (ring)
+    __shared__ float rmax[4][kSegRows][32];  // x-window maxima of the same planes
     const int ntx = (ng + kSegTX - 1) / kSegTX, nty = (ng + kSegTY - 1) / kSegTY;
     const int t = int(blockIdx.x);
     const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
@@ -79,23 +87,14 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_tile(const float* __restric
     const int xm = wrap(xc - 1, ng), xp = wrap(xc + 1, ng);
     const int ym = wrap(yc - 1, ng), yp = wrap(yc + 1, ng);
     const bool own = lx >= 0 && lx < wx && ly >= 0 && ly < wy;
-    int rxm, rxc, rxp, rym, ryc, ryp;
-    ranks3(xm, xc, xp, rxm, rxc, rxp);
-    ranks3(ym, yc, yp, rym, ryc, ryp);
-    // low-word fields: bits 0-1 x offset code, 2-3 x priority, 8-9 y code,
-    // 10-11 y priority, 16-17 z code, 18-19 z priority (priority 2 - rank)
-    const uint32_t lxm = (0u) | (uint32_t(2 - rxm) << 2), lxc = 1u | (uint32_t(2 - rxc) << 2),
-                   lxp = 2u | (uint32_t(2 - rxp) << 2);
-    const uint32_t lym = (0u << 8) | (uint32_t(2 - rym) << 10), lyc = (1u << 8) | (uint32_t(2 - ryc) << 10),
-                   lyp = (2u << 8) | (uint32_t(2 - ryp) << 10);
+    int kxm, kxc, kxp, kym, kyc, kyp;
+    codes3(xm, xc, xp, kxm, kxc, kxp);
+    codes3(ym, yc, yp, kym, kyc, kyp);
     const size_t N = size_t(ng);
     const float* colp = C + size_t(yc) * N + xc;
-    const uint32_t ord_min = ord_bits(cwt_min);
-    auto key = [](uint32_t hi, uint32_t lo) { return ((unsigned long long)hi << 32) | lo; };
-    auto kmax = [](unsigned long long a, unsigned long long b) { return a > b ? a : b; };
 
     bool bad = false;
-    unsigned long long pl[3] = {0ull, 0ull, 0ull};  // in-plane winners of planes p-2, p-1, p
+    float pl0 = 0.f, pl1 = 0.f, pl2 = 0.f;  // window maxima of planes p-2, p-1, p at this row and column
     // kSegPrefetch planes of this column in flight (a register ring), so that
     // the per-plane barrier does not expose the load latency
     const int np_ = wz + 2;
@@ -110,38 +109,35 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_tile(const float* __restric
     for (int d = 0; d < kSegPrefetch; d++) {
         const int p = p0 + d;
         if (p >= np_) break;  // block-uniform
-        const float vcur = ring[d];
+        const float v = ring[d];
         if (p + kSegPrefetch < np_) ring[d] = __ldg(colp + size_t(wrap(z0 - 1 + p + kSegPrefetch, ng)) * plane);
-        bad |= (vcur != vcur);
-        const uint32_t o = ord_bits(vcur);
-        const uint32_t ol = __shfl_up_sync(full, o, 1), orr = __shfl_down_sync(full, o, 1);
-        // best along x of this row, at this column
-        const unsigned long long rb = kmax(kmax(key(ol, lxm), key(o, lxc)), key(orr, lxp));
-        rowbest[p & 1][w][lane] = rb;
+        bad |= (v != v);
+        const float vl = __shfl_up_sync(full, v, 1), vr = __shfl_down_sync(full, v, 1);
+        const int sp = p & 3;
+        vals[sp][w][lane] = v;
+        rmax[sp][w][lane] = fmaxf(fmaxf(vl, v), vr);
         __syncthreads();
         if (w >= 1 && w <= kSegTY) {
-            const unsigned long long a = rowbest[p & 1][w - 1][lane], b = rowbest[p & 1][w][lane],
-                                     c = rowbest[p & 1][w + 1][lane];
-            pl[0] = pl[1];
-            pl[1] = pl[2];
-            pl[2] = kmax(kmax(a | lym, b | lyc), c | lyp);
+            pl0 = pl1;
+            pl1 = pl2;
+            pl2 = fmaxf(fmaxf(rmax[sp][w - 1][lane], rmax[sp][w][lane]), rmax[sp][w + 1][lane]);
         }
         if (p >= 2 && own) {
-            // the cell of plane p-1 (owned z index lz = p-2): winner over planes p-2, p-1, p
+            // the cell of plane p-1 (owned z index lz = p-2)
             const int lz = p - 2;
             const int zc = z0 + lz, zm = wrap(zc - 1, ng), zp = wrap(zc + 1, ng);
-            int rzm, rzc, rzp;
-            ranks3(zm, zc, zp, rzm, rzc, rzp);
-            const unsigned long long best =
-                kmax(kmax(pl[0] | (uint64_t(0u << 16 | uint32_t(2 - rzm) << 18)),
-                          pl[1] | (uint64_t(1u << 16 | uint32_t(2 - rzc) << 18))),
-                     pl[2] | (uint64_t(2u << 16 | uint32_t(2 - rzp) << 18)));
-            const uint32_t lo = uint32_t(best);
-            const int cx = int(lo & 3u), cy = int((lo >> 8) & 3u), cz = int((lo >> 16) & 3u);
+            int kzm, kzc, kzp;
+            codes3(zm, zc, zp, kzm, kzc, kzp);
+            const float M = fmaxf(fmaxf(pl0, pl1), pl2);
+            const int cz = pick3(pl0, pl1, pl2, M, kzm, kzc, kzp);
+            const int sz = (p - 2 + cz) & 3;
+            const int cy = pick3(rmax[sz][w - 1][lane], rmax[sz][w][lane], rmax[sz][w + 1][lane], M, kym, kyc, kyp);
+            const float* row = &vals[sz][w - 1 + cy][lane];
+            const int cx = pick3(row[-1], row[0], row[1], M, kxm, kxc, kxp);
             const int i = (lz * kSegTY + ly) * kSegTX + lx;
             if (cx == 1 && cy == 1 && cz == 1) {
-                // a local maximum (its own key won): a seed iff its value > cwt_min
-                if (uint32_t(best >> 32) > ord_min) {
+                // a local maximum: a seed iff its value > cwt_min
+                if (M > cwt_min) {
                     ptr[i] = i;
                     const uint32_t g = uint32_t((size_t(zc) * N + yc) * N + xc);
                     atomicOr(&seed_bits[g >> 5], 1u << (g & 31));
@@ -149,14 +145,15 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_tile(const float* __restric
                     ptr[i] = -1;
                 }
             } else {
-                const int px = cx == 0 ? xm : (cx == 2 ? xp : xc);
-                const int py = cy == 0 ? ym : (cy == 2 ? yp : yc);
-                const int pz = cz == 0 ? zm : (cz == 2 ? zp : zc);
-                const int qx = px - x0, qy = py - y0, qz = pz - z0;
-                if (qx >= 0 && qx < wx && qy >= 0 && qy < wy && qz >= 0 && qz < wz)
-                    ptr[i] = (qz * kSegTY + qy) * kSegTX + qx;
-                else
+                const int qx = lx + cx - 1, qy = ly + cy - 1, qz = lz + cz - 1;
+                if (unsigned(qx) < unsigned(wx) && unsigned(qy) < unsigned(wy) && unsigned(qz) < unsigned(wz)) {
+                    ptr[i] = i + (cx - 1) + (cy - 1) * kSegTX + (cz - 1) * (kSegTX * kSegTY);
+                } else {
+                    const int px = cx == 0 ? xm : (cx == 2 ? xp : xc);
+                    const int py = cy == 0 ? ym : (cy == 2 ? yp : yc);
+                    const int pz = cz == 0 ? zm : (cz == 2 ? zp : zc);
                     ptr[i] = -2 - int32_t((size_t(pz) * N + py) * N + px);
+                }
             }
         }
     }

@@ -32,6 +32,7 @@ def test_random_fields_with_plateaus(gctx, ng):
     C[rng.random(C.shape) < 0.02] = -0.0
     _check(gctx, C)
     _check(gctx, np.round(C * 4) / 4)  # heavy plateaus
+    _check(gctx, rng.integers(0, 3, C.shape).astype(np.float32))  # three levels: ties everywhere
 
 
 def test_constant_field_single_seed(gctx):
