@@ -147,7 +147,8 @@ def algorithmic_bytes(name, u):
         "k_seg_resolve": 4 * cells,                    # labels in (flagged ones rewritten)
         "k_count_cells": 4 * cells,
         "k_halo_sums": 8 * npart + 4 * npart + 4 * npart,    # records, label gather, slot out
-        "k_finalize": 12 * npart,                            # slot + index in, halo id scattered out
+        # record position in; per scale: record slot gathered, halo id out
+        "k_finalize": 4 * npart + 8 * npart * u.get("scales", 1),
     }
     return table.get(name)
 
@@ -353,7 +354,7 @@ def main():
 
     # ---- per-kernel roofline --------------------------------------------------
     peak, peak_kind = measured_peaks()
-    u = dict(ng=ng, np=npart, cells=ng ** 3, half=ng * ng * (ng // 2 + 1))
+    u = dict(ng=ng, np=npart, cells=ng ** 3, half=ng * ng * (ng // 2 + 1), scales=ns)
     kernels = {}
     for name, (tot, n) in prof.items():
         b = algorithmic_bytes(name, u)

@@ -65,37 +65,69 @@ __device__ __forceinline__ int nearest_node(int64_t q, int ng) {
     return n == ng ? 0 : n;
 }
 
-// Per-halo integer sums over the binned records, 32 consecutive records per
-// warp and batch, kIlp batches in flight per warp (independent gather chains:
-// record -> label -> seed bitmap and prefix).  Records are grouped by deposit
-// tile (a 32 x 8 x 8-cell block), so the lanes of a warp often share a halo,
-// and a batch whose records all fall in one halo folds them into one set of
-// atomics.  Each record's halo slot (or -1) is kept, in record order, for the
-// final pass.
-__global__ void __launch_bounds__(kThreads) k_halo_sums(DepArgs a, const uint32_t* __restrict__ off,
+// Per-halo integer sums over the binned records.  A CTA takes kChunk
+// consecutive records at a time (records are grouped by deposit tile, a
+// 32 x 8 x 8-cell block, so a chunk covers a few neighbouring tiles and a
+// few dozen halos), kRecPerThread per thread with independent gather chains
+// (record -> label -> seed bitmap and prefix).  The chunk is first folded into
+// a small open-addressing table of halo slots in shared memory (exact 64-bit
+// sums from 32-bit atomics), then each table entry is added to the global
+// accumulators once; a record whose slot finds no entry within kProbe probes
+// goes straight to the global atomics.  A warp whose 32 records share one
+// halo is folded with warp reductions first.  Each record's halo slot (or -1)
+// is kept for the final pass, at rec_slot[r * slot_stride].
+constexpr int kTab = 1024;  // table entries per CTA (power of two)
+constexpr int kProbe = 16;
+constexpr int kRecPerThread = 4;
+constexpr int kChunk = kThreads * kRecPerThread;
+constexpr uint32_t kEmpty = 0xffffffffu;
+
+__device__ __forceinline__ void global_halo_add(HaloAcc* h, u64 cnt, u64 mq, u64 m0, u64 m1, u64 m2) {
+    atomicAdd(&h->n_part, cnt);
+    atomicAdd(&h->mq, mq);
+    atomicAdd(reinterpret_cast<u64*>(&h->mom[0]), m0);
+    atomicAdd(reinterpret_cast<u64*>(&h->mom[1]), m1);
+    atomicAdd(reinterpret_cast<u64*>(&h->mom[2]), m2);
+}
+
+__global__ void __launch_bounds__(kThreads) k_halo_sums(DepArgs a, const uint32_t* __restrict__ total_ptr,
                                                        const unsigned long long* __restrict__ rec,
                                                        const uint32_t* __restrict__ rec_mq,
                                                        const int32_t* __restrict__ label,
                                                        const uint32_t* __restrict__ bits,
                                                        const uint32_t* __restrict__ prefix,
                                                        const uint32_t* __restrict__ n_slots, HaloAcc* acc,
-                                                       int32_t* __restrict__ rec_slot, u64* __restrict__ mtot) {
-    constexpr int kIlp = 4;
+                                                       int32_t* __restrict__ rec_slot, int slot_stride,
+                                                       u64* __restrict__ mtot) {
+    __shared__ uint32_t tkey[kTab], tcnt[kTab], tmq_lo[kTab], tmq_hi[kTab];
+    __shared__ uint32_t tm_lo[3][kTab], tm_hi[3][kTab];
+    __shared__ uint32_t tused[kTab];
+    __shared__ uint32_t n_used[2];
     const int lane = threadIdx.x & 31;
     const int N = a.ng;
     const int64_t M = a.modulus;
     const int64_t cells = int64_t(N) * N * N;
-    const int64_t total = off[int64_t(a.ntx) * a.nty * a.ntz * kDepClasses];  // records binned
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const int64_t total = *total_ptr;  // records binned
     const uint32_t ns = *n_slots;
+    for (int e = threadIdx.x; e < kTab; e += blockDim.x) {
+        tkey[e] = kEmpty;
+        tcnt[e] = tmq_lo[e] = tmq_hi[e] = 0u;
+        tm_lo[0][e] = tm_lo[1][e] = tm_lo[2][e] = 0u;
+        tm_hi[0][e] = tm_hi[1][e] = tm_hi[2][e] = 0u;
+    }
+    if (threadIdx.x < 2) n_used[threadIdx.x] = 0;
+    __syncthreads();
     u64 msum = 0;
-    for (int64_t r0 = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); r0 < total; r0 += kIlp * stride) {
-        int64_t q[kIlp][3];
-        uint32_t mq[kIlp];
-        int32_t lab[kIlp];
+    int it = 0;
+    for (int64_t c0 = int64_t(blockIdx.x) * kChunk; c0 < total; c0 += int64_t(gridDim.x) * kChunk, it ^= 1) {
+        uint32_t* used = &n_used[it];
+        // gathers for kRecPerThread records, warp-contiguous runs of 32
+        int64_t q[kRecPerThread][3];
+        uint32_t mq[kRecPerThread];
+        int32_t lab[kRecPerThread];
 #pragma unroll
-        for (int u = 0; u < kIlp; u++) {  // records, then labels: kIlp independent chains
-            const int64_t r = r0 + u * stride + lane;
+        for (int u = 0; u < kRecPerThread; u++) {
+            const int64_t r = c0 + u * kThreads + threadIdx.x;
             mq[u] = 0;
             lab[u] = -1;
             q[u][0] = q[u][1] = q[u][2] = 0;
@@ -105,28 +137,27 @@ __global__ void __launch_bounds__(kThreads) k_halo_sums(DepArgs a, const uint32_
                 q[u][0] = rec_q(e, 0);
                 q[u][1] = rec_q(e, 1);
                 q[u][2] = rec_q(e, 2);
-                const int nx = nearest_node(q[u][0], N), ny = nearest_node(q[u][1], N),
-                          nz = nearest_node(q[u][2], N);
-                lab[u] = label[(size_t(nz) * N + ny) * N + nx];
+                lab[u] = label[(size_t(nearest_node(q[u][2], N)) * N + nearest_node(q[u][1], N)) * N +
+                               nearest_node(q[u][0], N)];
             }
         }
-        uint32_t key[kIlp], word[kIlp], pre[kIlp];
+        uint32_t word[kRecPerThread], pre[kRecPerThread];
 #pragma unroll
-        for (int u = 0; u < kIlp; u++) {  // seed bitmap and prefix words
+        for (int u = 0; u < kRecPerThread; u++) {
             const bool in = lab[u] >= 0 && int64_t(lab[u]) < cells;
             word[u] = in ? bits[lab[u] >> 5] : 0u;
             pre[u] = in ? prefix[lab[u] >> 5] : 0u;
         }
 #pragma unroll
-        for (int u = 0; u < kIlp; u++) {
-            const int64_t r = r0 + u * stride + lane;
-            key[u] = 0xffffffffu;
+        for (int u = 0; u < kRecPerThread; u++) {
+            const int64_t r = c0 + u * kThreads + threadIdx.x;
+            uint32_t key = kEmpty;
             long long mom[3] = {0, 0, 0};
             if (r < total) {
                 const uint32_t bit = 1u << (lab[u] & 31);
                 const uint32_t slot = pre[u] + __popc(word[u] & (bit - 1u));
                 if ((word[u] & bit) && slot < ns) {
-                    key[u] = slot;
+                    key = slot;
                     const int sc[3] = {lab[u] % N, (lab[u] / N) % N, lab[u] / (N * N)};
 #pragma unroll
                     for (int d = 0; d < 3; d++) {
@@ -136,30 +167,68 @@ __global__ void __launch_bounds__(kThreads) k_halo_sums(DepArgs a, const uint32_
                         mom[d] = (long long)mq[u] * dq;
                     }
                 }
-                rec_slot[r] = int32_t(key[u]);  // 0xffffffff reads as -1
+                rec_slot[r * slot_stride] = int32_t(key);  // kEmpty reads as -1
             }
             msum += mq[u];
-            // a batch whose records all fall in one halo adds one set of sums; otherwise
-            // every lane adds its own (the shuffle runs on every lane)
-            const uint32_t k0 = __shfl_sync(kFull, key[u], 0);
-            const bool uniform = __all_sync(kFull, key[u] == k0) && key[u] != 0xffffffffu;
+            // all 32 records in one halo: one lane carries the warp's sums (the
+            // shuffle runs on every lane)
+            const uint32_t k0 = __shfl_sync(kFull, key, 0);
+            const bool uniform = __all_sync(kFull, key == k0) && key != kEmpty;
             u64 cnt = 1, m_sum = mq[u], m0 = u64(mom[0]), m1 = u64(mom[1]), m2 = u64(mom[2]);
             if (uniform) {
                 cnt = 32;
-                m_sum = warp_sum32(mq[u]);
+                m_sum = a.mass ? warp_sum32(mq[u]) : 32u;
                 m0 = warp_sum64(m0);
                 m1 = warp_sum64(m1);
                 m2 = warp_sum64(m2);
             }
-            if (key[u] != 0xffffffffu && (!uniform || lane == 0)) {
-                HaloAcc* h = acc + key[u];
-                atomicAdd(&h->n_part, cnt);
-                atomicAdd(&h->mq, m_sum);
-                atomicAdd(reinterpret_cast<u64*>(&h->mom[0]), m0);
-                atomicAdd(reinterpret_cast<u64*>(&h->mom[1]), m1);
-                atomicAdd(reinterpret_cast<u64*>(&h->mom[2]), m2);
+            if (key != kEmpty && (!uniform || lane == 0)) {
+                // find or claim the table entry of this slot
+                uint32_t h = (key * 2654435761u) >> 22;  // top 10 bits: kTab = 1024
+                int found = -1;
+                for (int pr = 0; pr < kProbe; pr++, h = (h + 1) & (kTab - 1)) {
+                    uint32_t k = tkey[h];
+                    if (k == kEmpty) {
+                        k = atomicCAS(&tkey[h], kEmpty, key);
+                        if (k == kEmpty) {
+                            tused[atomicAdd(used, 1u)] = h;
+                            k = key;
+                        }
+                    }
+                    if (k == key) {
+                        found = int(h);
+                        break;
+                    }
+                }
+                if (found >= 0) {
+                    atomicAdd(&tcnt[found], uint32_t(cnt));
+                    if (a.mass) shared_add64(tmq_lo, tmq_hi, found, m_sum);
+                    shared_add64(tm_lo[0], tm_hi[0], found, m0);
+                    shared_add64(tm_lo[1], tm_hi[1], found, m1);
+                    shared_add64(tm_lo[2], tm_hi[2], found, m2);
+                } else {
+                    global_halo_add(acc + key, cnt, m_sum, m0, m1, m2);
+                }
             }
         }
+        __syncthreads();
+        // one set of global atomics per table entry used by this chunk; the entries are
+        // cleared, and the other counter is reset for the next chunk (its last readers
+        // passed the barrier above)
+        const uint32_t nu = *used;
+        if (threadIdx.x == 0) n_used[it ^ 1] = 0;
+        for (uint32_t j = threadIdx.x; j < nu; j += blockDim.x) {
+            const uint32_t h = tused[j];
+            const u64 c = tcnt[h];
+            const u64 mqs = a.mass ? ((u64(tmq_hi[h]) << 32) | tmq_lo[h]) : c;
+            global_halo_add(acc + tkey[h], c, mqs, (u64(tm_hi[0][h]) << 32) | tm_lo[0][h],
+                            (u64(tm_hi[1][h]) << 32) | tm_lo[1][h], (u64(tm_hi[2][h]) << 32) | tm_lo[2][h]);
+            tkey[h] = kEmpty;
+            tcnt[h] = tmq_lo[h] = tmq_hi[h] = 0u;
+            tm_lo[0][h] = tm_lo[1][h] = tm_lo[2][h] = 0u;
+            tm_hi[0][h] = tm_hi[1][h] = tm_hi[2][h] = 0u;
+        }
+        __syncthreads();
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) msum += __shfl_xor_sync(kFull, msum, o);
@@ -233,32 +302,46 @@ __global__ void __launch_bounds__(kThreads) k_catalogue(const HaloAcc* __restric
     }
 }
 
-// halo_id of every particle, in particle order: the record it was binned to,
-// that record's halo slot, and the slot's seed if the halo was kept.  Several
-// particles per thread keep independent gather chains in flight.
+// halo_id of every particle for every scale, in particle order: the record
+// the particle was binned to, that record's halo slots (one per scale, stored
+// side by side, so one gather serves all scales), and each slot's seed if
+// its halo was kept.  Up to kScalesAtOnce scales are handled per pass, with
+// all gathers of kIlp particles in flight together.
 __global__ void __launch_bounds__(kThreads) k_finalize(const uint32_t* __restrict__ part_rec, int64_t np,
                                                       const uint32_t* __restrict__ total_ptr,
-                                                      const int32_t* __restrict__ rec_slot,
-                                                      const int32_t* __restrict__ slot_halo,
+                                                      const int32_t* __restrict__ rec_slot, int n_scales,
+                                                      const int32_t* __restrict__ slot_halo, int64_t slot_stride,
                                                       int32_t* __restrict__ halo_id) {
-    constexpr int kIlp = 4;
+    constexpr int kIlp = 2, kScalesAtOnce = 4;
     const int64_t total = *total_ptr;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < np; i0 += kIlp * stride) {
-        int32_t sl[kIlp];
+        int64_t r[kIlp];
 #pragma unroll
         for (int u = 0; u < kIlp; u++) {
             const int64_t i = i0 + u * stride;
-            sl[u] = -1;
-            if (i < np) {
-                const uint32_t r = part_rec[i];
-                if (int64_t(r) < total) sl[u] = rec_slot[r];
-            }
+            const uint32_t x = i < np ? part_rec[i] : 0xffffffffu;
+            r[u] = int64_t(x) < total ? int64_t(x) : -1;
         }
+        for (int k0 = 0; k0 < n_scales; k0 += kScalesAtOnce) {
+            int32_t sl[kIlp][kScalesAtOnce];
 #pragma unroll
-        for (int u = 0; u < kIlp; u++) {
-            const int64_t i = i0 + u * stride;
-            if (i < np) halo_id[i] = sl[u] >= 0 ? slot_halo[sl[u]] : -1;
+            for (int u = 0; u < kIlp; u++)
+#pragma unroll
+                for (int j = 0; j < kScalesAtOnce; j++)
+                    sl[u][j] = (r[u] >= 0 && k0 + j < n_scales) ? rec_slot[r[u] * n_scales + k0 + j] : -1;
+#pragma unroll
+            for (int u = 0; u < kIlp; u++)
+#pragma unroll
+                for (int j = 0; j < kScalesAtOnce; j++)
+                    sl[u][j] = sl[u][j] >= 0 ? slot_halo[(k0 + j) * slot_stride + sl[u][j]] : -1;
+#pragma unroll
+            for (int u = 0; u < kIlp; u++) {
+                const int64_t i = i0 + u * stride;
+#pragma unroll
+                for (int j = 0; j < kScalesAtOnce; j++)
+                    if (i < np && k0 + j < n_scales) halo_id[(k0 + j) * np + i] = sl[u][j];
+            }
         }
     }
 }
@@ -266,8 +349,9 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const uint32_t* __restric
 }  // namespace
 
 int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L, int ng,
-                const int32_t* label, const float* cwt, const cwthf_params* p, int32_t* halo_id, cwthf_halo* cat,
-                int64_t cat_cap, int64_t* n_halo, bool seeds_ready, bool bins_ready, cudaStream_t s) {
+                const int32_t* label, const float* cwt, const cwthf_params* p, int scale, int n_scales,
+                int32_t* halo_id, cwthf_halo* cat, int64_t cat_cap, int64_t* n_halo, bool seeds_ready,
+                bool bins_ready, cudaStream_t s) {
     int rc;
     if (!seeds_ready && (rc = seeds_from_labels(ctx, label, ng, s))) return rc;
     if (!bins_ready && (rc = bin_particles(ctx, pos, mass, mass_unit, np, L, ng, s))) return rc;
@@ -284,10 +368,11 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
     DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
     const int64_t total_key = deposit_geom(ng).ntiles * kDepClasses;  // dep_off[total_key] = records binned
     int pblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kThreads), int64_t(ctx->sm_count) * 16));
+    int cblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kChunk), int64_t(ctx->sm_count) * 4));
     CWTHF_LAUNCH(ctx, s, "k_halo_sums",
-                 k_halo_sums<<<pblocks, kThreads, 0, s>>>(a, ctx->dep_off, ctx->dep_rec, ctx->dep_mq, label,
-                                                          ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc,
-                                                          ctx->part_slot, ctx->d_mtot));
+                 k_halo_sums<<<cblocks, kThreads, 0, s>>>(a, ctx->dep_off + total_key, ctx->dep_rec, ctx->dep_mq,
+                                                          label, ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc,
+                                                          ctx->part_slot + scale, n_scales, ctx->d_mtot));
     FilterArgs f;
     f.ng = ng;
     f.L = L;
@@ -299,10 +384,13 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
     if ((rc = scan_u32_dev(ctx, ctx->keep_off, ctx->keep_off, d_nseeds, slot_cap, s))) return rc;
     CWTHF_LAUNCH(ctx, s, "k_catalogue",
                  k_catalogue<<<blocks, kThreads, 0, s>>>(ctx->acc, ctx->seed_list, d_nseeds, ctx->keep_off, cwt, f,
-                                                         cat, ctx->slot_halo, n_halo, ctx->d_status));
-    CWTHF_LAUNCH(ctx, s, "k_finalize",
-                 k_finalize<<<pblocks, kThreads, 0, s>>>(ctx->part_rec, np, ctx->dep_off + total_key,
-                                                         ctx->part_slot, ctx->slot_halo, halo_id));
+                                                         cat, ctx->slot_halo + int64_t(scale) * slot_cap, n_halo,
+                                                         ctx->d_status));
+    if (scale == n_scales - 1)  // halo ids of all scales at once
+        CWTHF_LAUNCH(ctx, s, "k_finalize",
+                     k_finalize<<<pblocks, kThreads, 0, s>>>(ctx->part_rec, np, ctx->dep_off + total_key,
+                                                             ctx->part_slot, n_scales, ctx->slot_halo, slot_cap,
+                                                             halo_id));
     return cuda_status(cudaGetLastError());
 }
 

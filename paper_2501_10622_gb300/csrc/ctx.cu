@@ -71,11 +71,12 @@ void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, F
     if (max_scales > 1) f(reinterpret_cast<void**>(&c->spec2), spec_bytes(max_ng));
     f(reinterpret_cast<void**>(&c->seed_bits), size_t(z.nwords + 1) * 4);
     f(reinterpret_cast<void**>(&c->seed_prefix), size_t(z.nwords + 2) * 4);
+    f(reinterpret_cast<void**>(&c->seed_cells), size_t(z.cells) * 2);
     f(reinterpret_cast<void**>(&c->seed_list), size_t(z.slots) * 4);
     f(reinterpret_cast<void**>(&c->acc), size_t(z.slots) * sizeof(HaloAcc));
     f(reinterpret_cast<void**>(&c->keep_off), size_t(z.slots + 2) * 4);
-    f(reinterpret_cast<void**>(&c->slot_halo), size_t(z.slots) * 4);
-    f(reinterpret_cast<void**>(&c->part_slot), size_t(z.np) * 4);
+    f(reinterpret_cast<void**>(&c->slot_halo), size_t(z.slots) * 4 * size_t(std::max(max_scales, 1)));
+    f(reinterpret_cast<void**>(&c->part_slot), size_t(z.np) * 4 * size_t(std::max(max_scales, 1)));
     f(reinterpret_cast<void**>(&c->jump_changed), sizeof(int) * (kMaxJumpRounds + 2));
     f(reinterpret_cast<void**>(&c->scan_tmp), z.scan_words * 4);
     f(reinterpret_cast<void**>(&c->grid), size_t(z.cells) * 8);
@@ -233,8 +234,8 @@ int cwthf_assign(cwthf_ctx* ctx, const float* pos, const float* mass, double mas
         std::isnan(params->dens_th))
         return CWTHF_E_INVALID_ARG;
     DeviceGuard g(ctx->device);
-    return assign_impl(ctx, pos, mass, mass_unit, np, L, ng, cell_label, cwt, params, halo_id, cat, cat_cap, n_halo,
-                       false, false, as_stream(stream));
+    return assign_impl(ctx, pos, mass, mass_unit, np, L, ng, cell_label, cwt, params, 0, 1, halo_id, cat, cat_cap,
+                       n_halo, false, false, as_stream(stream));
 }
 
 int cwthf_find(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L, int ng,
@@ -259,8 +260,8 @@ int cwthf_find(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_
         rc = transform_wavelet_inverse(ctx, ctx->spec, dst, ng, L, params[i].w, mass_unit, ctx->cwt, s);
         if (!rc) rc = segment_impl(ctx, ctx->cwt, ng, params[i].cwt_min, ctx->label, true, s);
         if (!rc)
-            rc = assign_impl(ctx, pos, mass, mass_unit, np, L, ng, ctx->label, ctx->cwt, &params[i],
-                             halo_id + int64_t(i) * np, cat + int64_t(i) * cat_cap, cat_cap, n_halo + i, true, true, s);
+            rc = assign_impl(ctx, pos, mass, mass_unit, np, L, ng, ctx->label, ctx->cwt, &params[i], i, n_scales,
+                             halo_id, cat + int64_t(i) * cat_cap, cat_cap, n_halo + i, true, true, s);
     }
     return rc;
 }

@@ -112,16 +112,6 @@ __global__ void __launch_bounds__(kCountThreads) k_dep_scatter(DepArgs a, uint32
     }
 }
 
-// Exact 64-bit accumulation from native 32-bit shared atomics: the low word
-// takes the low half and reports its own wrap-around, which is carried into
-// the high word together with the high half.
-__device__ __forceinline__ void acc_add(uint32_t* lo, uint32_t* hi, int c, u64 v) {
-    uint32_t vl = uint32_t(v), vh = uint32_t(v >> 32);
-    uint32_t old = atomicAdd(&lo[c], vl);
-    vh += (old + vl < old) ? 1u : 0u;
-    if (vh) atomicAdd(&hi[c], vh);
-}
-
 // The 27 (neighbour offset mask m, boundary class) pairs whose particles reach
 // into a tile: a particle of the lower neighbour at offset m reaches in iff
 // its class has every bit of m set.
@@ -212,7 +202,7 @@ __global__ void __launch_bounds__(kTileThreads) k_dep_tile(DepArgs a, const uint
                 const int cx = lx + ex, cy = ly + ey, cz = lz + ez;
                 if (live && (!uniform || lane == 0) && v && cx >= 0 && cx < wx && cy >= 0 && cy < wy && cz >= 0 &&
                     cz < wz)
-                    acc_add(acc_lo, acc_hi, (cz * kDepTY + cy) * kDepTX + cx, v);
+                    shared_add64(acc_lo, acc_hi, (cz * kDepTY + cy) * kDepTX + cx, v);
             }
         }
         __syncthreads();

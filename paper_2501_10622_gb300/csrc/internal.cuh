@@ -106,12 +106,13 @@ struct cwthf_ctx {
     // segmentation / assignment scratch
     uint32_t* seed_bits = nullptr;    // [ng^3 / 32 + 1] seed bitmap
     uint32_t* seed_prefix = nullptr;  // [ng^3 / 32 + 1] exclusive popcount prefix
+    uint16_t* seed_cells = nullptr;   // [ng^3] in-tile cell count, valid at seed cells only
     int32_t* seed_list = nullptr;     // [ng^3 / 8 + 1] seed cell of each slot
     uint32_t* n_seeds = nullptr;      // [1]
     cwthf::HaloAcc* acc = nullptr;    // [ng^3 / 8 + 1]
     uint32_t* keep_off = nullptr;     // [ng^3 / 8 + 2] kept-halo prefix
-    int32_t* slot_halo = nullptr;     // [ng^3 / 8 + 1] seed of each kept slot, -1 otherwise
-    int32_t* part_slot = nullptr;     // [max_np] halo slot of each binned record (-1: none)
+    int32_t* slot_halo = nullptr;     // [max_scales][ng^3 / 8 + 8] seed of each kept slot, -1 otherwise
+    int32_t* part_slot = nullptr;     // [max_np][max_scales] halo slot of each binned record per scale (-1: none)
     int* jump_changed = nullptr;      // [kMaxJumpRounds + 1]
     uint32_t* scan_tmp = nullptr;     // block sums of the device scan
     size_t scan_tmp_cap = 0;          // words
@@ -154,6 +155,17 @@ __device__ __forceinline__ bool seed_slot(const uint32_t* bits, const uint32_t* 
     uint32_t m = 1u << (lab & 31);
     slot = prefix[lab >> 5] + __popc(w & (m - 1u));
     return (w & m) != 0 && slot < *n_slots;
+}
+
+// Exact 64-bit accumulation (mod 2^64) in shared memory from native 32-bit
+// atomics: the low word takes the low half and reports its own wrap-around,
+// which is carried into the high word together with the high half.
+__device__ __forceinline__ void shared_add64(uint32_t* lo, uint32_t* hi, int c, unsigned long long v) {
+    const uint32_t vl = uint32_t(v);
+    uint32_t vh = uint32_t(v >> 32);
+    const uint32_t old = atomicAdd(&lo[c], vl);
+    vh += (old + vl < old) ? 1u : 0u;
+    if (vh) atomicAdd(&hi[c], vh);
 }
 
 // ---- warp helpers -------------------------------------------------------------
@@ -270,10 +282,12 @@ int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_
 // seeds_ready: the seed bitmap / ranks of `label` are already in ctx (after
 // segment_impl); bins_ready: ctx->dep_* hold the binned records of these
 // particles for this grid (after deposit_impl).
+// scale / n_scales: this call's scale among those of one find; the halo ids
+// of all scales are written (halo_id[k * np + i]) once the last one is done.
 int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L,
-                int ng, const int32_t* label, const float* cwt, const cwthf_params* p, int32_t* halo_id,
-                cwthf_halo* cat, int64_t cat_cap, int64_t* n_halo, bool seeds_ready, bool bins_ready,
-                cudaStream_t s);
+                int ng, const int32_t* label, const float* cwt, const cwthf_params* p, int scale, int n_scales,
+                int32_t* halo_id, cwthf_halo* cat, int64_t cat_cap, int64_t* n_halo, bool seeds_ready,
+                bool bins_ready, cudaStream_t s);
 void free_tables(cwthf_ctx* ctx);
 
 // ---- deposit on caller-provided scratch (used by cwthf_deposit_noalloc) ------

@@ -26,11 +26,21 @@ namespace {
 // Warps 0 and 17 read the y-halo rows.
 constexpr int kSegRows = kSegTY + 2;          // warps per CTA
 constexpr int kSegThreads = 32 * kSegRows;    // 576
-constexpr int kOwned = kSegTX * kSegTY * kSegTZ;
+// Shared-memory parent pointers use a padded local index (lz * 16 + ly) * 32 + lx,
+// so that local coordinates come back with shifts and masks.
+constexpr int kPX = 32, kPXBits = 5;
+constexpr int kPlaneL = kPX * kSegTY, kPlaneBits = 9;
+constexpr int kLocal = kPlaneL * kSegTZ;  // 16384 entries
+static_assert(kSegTX <= kPX && kPlaneL == (1 << kPlaneBits) && kSegTY == 16, "padded layout");
 constexpr int32_t kFlag = 1 << 30;
 constexpr int32_t kMask = kFlag - 1;
 constexpr int kChaseLimit = 64;  // longest in-tile chain followed before handing over to the global pass
-constexpr int kSegPrefetch = 8;  // planes of a column loaded ahead
+constexpr int kSegPrefetch = 4;  // planes of a column loaded ahead
+// Seeds of one tile: at most one local maximum per 2 x 2 x 2 block of cells
+// (any two cells of such a block are neighbours), so 15 * 8 * 16 per tile.
+constexpr int kTileSeedCap = ((kSegTX + 1) / 2) * ((kSegTY + 1) / 2) * ((kSegTZ + 1) / 2);
+constexpr int32_t kLocalMask = 0xffff;  // local index bits of a shared-memory pointer
+constexpr int kCountShift = 16;         // a seed's in-tile cell count rides above them
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
@@ -64,15 +74,18 @@ __device__ __forceinline__ int pick3(float a, float b, float c, float M, int ka,
 // holds M, then in that plane the first row whose x-window holds M, then in
 // that row the first column holding M.  Two rings of four planes in shared
 // memory (raw values and x-window maxima) serve the search, so one barrier
-// per plane suffices.  Parents go to shared memory; every cell then follows
-// its chain there until it reaches a seed, a non-seed maximum, or a cell
-// outside the tile.
+// per plane suffices.  The parent is then formed without branches.  Parents
+// go to shared memory; every cell then follows its chain there until it
+// reaches a seed, a non-seed maximum, or a cell outside the tile.
 __global__ void __launch_bounds__(kSegThreads, 2) k_seg_tile(const float* __restrict__ C, int ng, float cwt_min,
                                                          int32_t* __restrict__ label, uint32_t* __restrict__ seed_bits,
-                                                         int* status) {
-    extern __shared__ int32_t ptr[];  // [kOwned], dynamic
-    __shared__ float vals[4][kSegRows][32];  // raw values of planes p-3 .. p (ring)
-    __shared__ float rmax[4][kSegRows][32];  // x-window maxima of the same planes
+                                                         uint16_t* __restrict__ seed_cells, int* status) {
+    extern __shared__ int32_t ptr[];  // [kLocal], dynamic
+    __shared__ uint16_t tile_seeds[kTileSeedCap];
+    __shared__ uint32_t n_tile_seeds;
+    constexpr int kSlot = kSegRows * 32;          // floats per ring slot
+    __shared__ float vals[4 * kSlot];             // raw values of planes p-3 .. p (ring)
+    __shared__ float rmax[4 * kSlot];             // x-window maxima of the same planes
     const int ntx = (ng + kSegTX - 1) / kSegTX, nty = (ng + kSegTY - 1) / kSegTY;
     const int t = int(blockIdx.x);
     const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
@@ -87,18 +100,26 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_tile(const float* __rest
     const int xm = wrap(xc - 1, ng), xp = wrap(xc + 1, ng);
     const int ym = wrap(yc - 1, ng), yp = wrap(yc + 1, ng);
     const bool own = lx >= 0 && lx < wx && ly >= 0 && ly < wy;
+    const bool row_warp = w >= 1 && w <= kSegTY;  // warps of owned rows (warp-uniform)
     int kxm, kxc, kxp, kym, kyc, kyp;
     codes3(xm, xc, xp, kxm, kxc, kxp);
     codes3(ym, yc, yp, kym, kyc, kyp);
-    const size_t N = size_t(ng);
+    const int N = ng;
     const float* colp = C + size_t(yc) * N + xc;
+    // search addresses stay inside the rows even for the two halo lanes
+    const int lanec = min(max(lane, 1), 30);
+    const float* rsrc = rmax + (w - 1) * 32 + lanec;
+    const float* vsrc = vals + (w - 1) * 32 + lanec;
+    const int i0 = ly * kPX + lx;
 
     bool bad = false;
+    if (threadIdx.x == 0) n_tile_seeds = 0;  // ordered before its first use by the plane barriers
     float pl0 = 0.f, pl1 = 0.f, pl2 = 0.f;  // window maxima of planes p-2, p-1, p at this row and column
     // kSegPrefetch planes of this column in flight (a register ring), so that
     // the per-plane barrier does not expose the load latency
+    static_assert(kSegPrefetch % 4 == 0, "ring slots follow the prefetch slot");
     const int np_ = wz + 2;
-    const size_t plane = N * N;
+    const size_t plane = size_t(N) * N;
     float ring[kSegPrefetch];
 #pragma unroll
     for (int d = 0; d < kSegPrefetch; d++)
@@ -113,62 +134,69 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_tile(const float* __rest
         if (p + kSegPrefetch < np_) ring[d] = __ldg(colp + size_t(wrap(z0 - 1 + p + kSegPrefetch, ng)) * plane);
         bad |= (v != v);
         const float vl = __shfl_up_sync(full, v, 1), vr = __shfl_down_sync(full, v, 1);
-        const int sp = p & 3;
-        vals[sp][w][lane] = v;
-        rmax[sp][w][lane] = fmaxf(fmaxf(vl, v), vr);
+        const int sp = d & 3;  // p & 3, since p0 is a multiple of 4 (folded once unrolled)
+        vals[sp * kSlot + w * 32 + lane] = v;
+        rmax[sp * kSlot + w * 32 + lane] = fmaxf(fmaxf(vl, v), vr);
         __syncthreads();
-        if (w >= 1 && w <= kSegTY) {
-            pl0 = pl1;
-            pl1 = pl2;
-            pl2 = fmaxf(fmaxf(rmax[sp][w - 1][lane], rmax[sp][w][lane]), rmax[sp][w + 1][lane]);
-        }
-        if (p >= 2 && own) {
-            // the cell of plane p-1 (owned z index lz = p-2)
-            const int lz = p - 2;
-            const int zc = z0 + lz, zm = wrap(zc - 1, ng), zp = wrap(zc + 1, ng);
-            int kzm, kzc, kzp;
-            codes3(zm, zc, zp, kzm, kzc, kzp);
-            const float M = fmaxf(fmaxf(pl0, pl1), pl2);
-            const int cz = pick3(pl0, pl1, pl2, M, kzm, kzc, kzp);
-            const int sz = (p - 2 + cz) & 3;
-            const int cy = pick3(rmax[sz][w - 1][lane], rmax[sz][w][lane], rmax[sz][w + 1][lane], M, kym, kyc, kyp);
-            const float* row = &vals[sz][w - 1 + cy][lane];
-            const int cx = pick3(row[-1], row[0], row[1], M, kxm, kxc, kxp);
-            const int i = (lz * kSegTY + ly) * kSegTX + lx;
-            if (cx == 1 && cy == 1 && cz == 1) {
-                // a local maximum: a seed iff its value > cwt_min
-                if (M > cwt_min) {
-                    ptr[i] = i;
-                    const uint32_t g = uint32_t((size_t(zc) * N + yc) * N + xc);
-                    atomicOr(&seed_bits[g >> 5], 1u << (g & 31));
-                } else {
-                    ptr[i] = -1;
-                }
-            } else {
-                const int qx = lx + cx - 1, qy = ly + cy - 1, qz = lz + cz - 1;
-                if (unsigned(qx) < unsigned(wx) && unsigned(qy) < unsigned(wy) && unsigned(qz) < unsigned(wz)) {
-                    ptr[i] = i + (cx - 1) + (cy - 1) * kSegTX + (cz - 1) * (kSegTX * kSegTY);
-                } else {
-                    const int px = cx == 0 ? xm : (cx == 2 ? xp : xc);
-                    const int py = cy == 0 ? ym : (cy == 2 ? yp : yc);
-                    const int pz = cz == 0 ? zm : (cz == 2 ? zp : zc);
-                    ptr[i] = -2 - int32_t((size_t(pz) * N + py) * N + px);
-                }
+        if (!row_warp) continue;  // warp-uniform: halo-row warps only feed the buffers
+        pl0 = pl1;
+        pl1 = pl2;
+        pl2 = fmaxf(fmaxf(rmax[sp * kSlot + (w - 1) * 32 + lane], rmax[sp * kSlot + w * 32 + lane]),
+                    rmax[sp * kSlot + (w + 1) * 32 + lane]);
+        if (p < 2) continue;  // block-uniform
+        // the cell of plane p-1 (owned z index lz = p-2); z codes are uniform and
+        // differ from the interior ones only on the two wrapped planes
+        const int lz = p - 2;
+        const int zc = z0 + lz;
+        const bool zlo = zc == 0, zhi = zc == N - 1;
+        const int kzm = zlo ? 8 : (zhi ? 4 : 0), kzc = zlo ? 1 : (zhi ? 9 : 5), kzp = zlo ? 6 : (zhi ? 2 : 10);
+        const float M = fmaxf(fmaxf(pl0, pl1), pl2);
+        const int cz = pick3(pl0, pl1, pl2, M, kzm, kzc, kzp);
+        const int so = ((d + 2 + cz) & 3) * kSlot;  // ring slot of plane p-2+cz
+        const int cy = pick3(rsrc[so], rsrc[so + 32], rsrc[so + 64], M, kym, kyc, kyp);
+        const float* row = vsrc + so + cy * 32;
+        const int cx = pick3(row[-1], row[0], row[1], M, kxm, kxc, kxp);
+        const int i = i0 + lz * kPlaneL;
+        const int dx = cx - 1, dy = cy - 1, dz = cz - 1;
+        const bool is_max = (dx | dy | dz) == 0;
+        const bool in_tile = unsigned(lx + dx) < unsigned(wx) && unsigned(ly + dy) < unsigned(wy) &&
+                             unsigned(lz + dz) < unsigned(wz);
+        const int gx = dx < 0 ? xm : (dx > 0 ? xp : xc);
+        const int gy = dy < 0 ? ym : (dy > 0 ? yp : yc);
+        const int gz = wrap(zc + dz, N);
+        const int32_t outside = -2 - ((gz * N + gy) * N + gx);
+        const bool seed = is_max && M > cwt_min;
+        const int32_t val = is_max ? (seed ? i : -1) : (in_tile ? i + dx + dy * kPX + dz * kPlaneL : outside);
+        if (own) {
+            ptr[i] = val;
+            if (seed) {
+                const uint32_t g = uint32_t((zc * N + yc) * N + xc);
+                atomicOr(&seed_bits[g >> 5], 1u << (g & 31));
+                const uint32_t j = atomicAdd(&n_tile_seeds, 1u);
+                if (j < uint32_t(kTileSeedCap)) tile_seeds[j] = uint16_t(i);
             }
         }
     }
     if (bad) set_status(status, CWTHF_E_BAD_INPUT);
     __syncthreads();
 
-    // follow each chain inside the tile (read-only walk over the parents)
+    // Follow each chain inside the tile.  A chain that ends at a seed of this
+    // tile adds one to the seed's cell count, kept in the upper half of the
+    // seed's own entry (its lower half stays its own index, so that every walk
+    // still recognises it); the walked cell then points straight at the seed.
+    // Every value read or written is a later point of the same chain, so
+    // concurrent walks do not change any result.
+    const int32_t gbase = (z0 * N + y0) * N + x0;
     if (own) {
         int32_t* out = label + (size_t(z0) * N + yc) * N + xc;
-        for (int lz = 0; lz < wz; lz++, out += N * N) {
-            const int i = (lz * kSegTY + ly) * kSegTX + lx;
-            int32_t cur = ptr[i];
+        for (int lz = 0; lz < wz; lz++, out += plane) {
+            const int i = i0 + lz * kPlaneL;
+            const int32_t v = ptr[i];
+            int32_t cur = v >= 0 ? (v & kLocalMask) : v;
             int steps = 0;
             while (cur >= 0 && steps < kChaseLimit) {
-                const int32_t nxt = ptr[cur];
+                const int32_t nv = ptr[cur];
+                const int32_t nxt = nv >= 0 ? (nv & kLocalMask) : nv;
                 if (nxt == cur) break;  // a seed
                 cur = nxt;
                 steps++;
@@ -179,28 +207,53 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_tile(const float* __rest
             } else if (cur <= -2) {
                 res = (-2 - cur) | kFlag;
             } else {
-                const int px = cur % kSegTX, py = (cur / kSegTX) % kSegTY, pz = cur / (kSegTX * kSegTY);
-                const int32_t g = int32_t((size_t(z0 + pz) * N + (y0 + py)) * N + (x0 + px));
-                res = (ptr[cur] == cur) ? g : (g | kFlag);  // walk stopped at the limit: resume globally
+                const int px = cur & (kPX - 1), py = (cur >> kPXBits) & (kSegTY - 1), pz = cur >> kPlaneBits;
+                const int32_t g = gbase + (pz * N + py) * N + px;
+                const int32_t nv = ptr[cur];
+                if (nv >= 0 && (nv & kLocalMask) == cur) {
+                    res = g;
+                    atomicAdd(&ptr[cur], 1 << kCountShift);
+                } else {
+                    res = g | kFlag;  // walk stopped at the limit: resume globally
+                }
+                if (steps > 1) ptr[i] = cur;  // i is not a seed here: its entry holds no count
             }
             *out = res;
         }
     }
+    __syncthreads();
+    // in-tile cell counts of this tile's seeds (cells reaching them from other
+    // tiles are added by the global pass)
+    const uint32_t nts = n_tile_seeds;
+    if (threadIdx.x == 0 && nts > uint32_t(kTileSeedCap)) set_status(status, CWTHF_E_BAD_INPUT);
+    for (uint32_t j = threadIdx.x; j < min(nts, uint32_t(kTileSeedCap)); j += blockDim.x) {
+        const int i = tile_seeds[j];
+        const int px = i & (kPX - 1), py = (i >> kPXBits) & (kSegTY - 1), pz = i >> kPlaneBits;
+        seed_cells[size_t(gbase + (pz * N + py) * N + px)] = uint16_t(uint32_t(ptr[i]) >> kCountShift);
+    }
 }
 
 // Finishes every flagged label by following its chain through the label
-// grid (at most kChaseLimit steps per cell) and counts the cells of every
-// seed.  Labels read while other threads update them are always a later point
-// of the same chain, so the result does not depend on timing.  A cell still
-// unfinished at the limit stays flagged (pointing further along) and sets
-// changed[0]: the doubling rounds then finish it and the cells are recounted.
-__global__ void __launch_bounds__(256) k_seg_resolve(int32_t* __restrict__ label, int64_t cells,
-                                                     const uint32_t* __restrict__ bits,
-                                                     const uint32_t* __restrict__ prefix,
-                                                     const uint32_t* __restrict__ n_slots, HaloAcc* acc,
-                                                     int* __restrict__ changed) {
+// grid (at most kChaseLimit steps per cell) and adds the cells of every seed
+// that the tile pass could not count (those that arrived flagged).  Each warp
+// takes 128 consecutive labels, queues its flagged ones in shared memory and
+// chases them with all lanes at once, then counts the finished ones with one
+// atomic per distinct seed among them.  Labels read while other threads update
+// them are always a later point of the same chain, so the result does not
+// depend on timing.  A cell still unfinished at the limit stays flagged
+// (pointing further along) and sets changed[0]: the doubling rounds then
+// finish it and the cells are recounted.
+constexpr int kResolveThreads = 256;
+__global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __restrict__ label, int64_t cells,
+                                                                 const uint32_t* __restrict__ bits,
+                                                                 const uint32_t* __restrict__ prefix,
+                                                                 const uint32_t* __restrict__ n_slots, HaloAcc* acc,
+                                                                 int* __restrict__ changed) {
+    __shared__ int32_t queue[kResolveThreads / 32][128];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    int32_t* wq = queue[threadIdx.x >> 5];
     bool left = false;
     const int64_t n4 = (cells + 3) / 4;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -216,46 +269,54 @@ __global__ void __launch_bounds__(256) k_seg_resolve(int32_t* __restrict__ label
                 for (int j = 0; j < 4 && 4 * i + j < cells; j++) v[j] = label[4 * i + j];
             }
         }
-        bool wrote = false;
+        // queue the flagged labels of the warp, in (j, lane) order
+        bool fl[4];
+        int pos[4];
+        int total = 0;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            int32_t w = v[j];
-            if (w < 0 || !(w & kFlag)) continue;
+            fl[j] = v[j] >= 0 && (v[j] & kFlag);
+            const unsigned b = __ballot_sync(full, fl[j]);
+            pos[j] = total + __popc(b & below);
+            total += __popc(b);
+            if (fl[j]) wq[pos[j]] = v[j];
+        }
+        if (total == 0) continue;  // warp-uniform
+        __syncwarp();
+        for (int e = lane; e < total; e += 32) {
+            int32_t w = wq[e];
             int steps = 0;
             while (w >= 0 && (w & kFlag) && steps < kChaseLimit) {
                 w = label[w & kMask];
                 steps++;
             }
-            v[j] = w;
-            wrote = true;
+            wq[e] = w;
             left |= (w >= 0 && (w & kFlag));
         }
-        if (wrote) {
+        __syncwarp();
+        bool mine = false;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            if (fl[j]) {
+                v[j] = wq[pos[j]];
+                mine = true;
+            }
+        if (mine) {
             if (vec) reinterpret_cast<int4*>(label)[i] = make_int4(v[0], v[1], v[2], v[3]);
             else
                 for (int j = 0; j < 4 && 4 * i + j < cells; j++) label[4 * i + j] = v[j];
         }
-        // cells per seed: runs of equal labels within the thread, one atomic per run,
-        // or one per warp when all 128 labels of the warp are the same seed
-        // (the shuffle runs on every lane: it must not sit behind a short-circuit)
-        const int lead = __shfl_sync(full, v[3], 0);
-        const bool same = (v[0] == v[3]) & (v[1] == v[3]) & (v[2] == v[3]) & (v[3] == lead);
-        const bool uniform = __all_sync(full, same);
-        if (uniform) {
+        // cells per seed among the finished queue entries: one atomic per distinct seed
+        for (int e0 = 0; e0 < total; e0 += 32) {  // warp-uniform
+            const int e = e0 + lane;
+            int32_t lab = e < total ? wq[e] : -1;
+            if (lab < 0 || (lab & kFlag)) lab = -1;
+            const unsigned peers = __match_any_sync(full, lab);
             uint32_t slot;
-            if (lane == 0 && v[0] >= 0 && !(v[0] & kFlag) && seed_slot(bits, prefix, n_slots, v[0], slot))
-                atomicAdd(&acc[slot].n_cells, 128ull);  // padding entries are -1, so all 128 are cells
-        } else {
-            int j = 0;
-            while (j < 4) {
-                int k = j + 1;
-                while (k < 4 && v[k] == v[j]) k++;
-                uint32_t slot;
-                if (v[j] >= 0 && !(v[j] & kFlag) && seed_slot(bits, prefix, n_slots, v[j], slot))
-                    atomicAdd(&acc[slot].n_cells, (unsigned long long)(k - j));
-                j = k;
-            }
+            if (lab >= 0 && lane == __ffs(peers) - 1 && seed_slot(bits, prefix, n_slots, lab, slot))
+                atomicAdd(&acc[slot].n_cells, (unsigned long long)__popc(peers));
         }
+        __syncwarp();  // the queue is refilled next
     }
     if (__any_sync(full, left) && lane == 0) changed[0] = 1;
 }
@@ -308,12 +369,13 @@ __global__ void k_popc(const uint32_t* __restrict__ bits, int64_t nwords, uint32
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nwords; i += stride) out[i] = __popc(bits[i]);
 }
 
-// slot -> seed cell, in increasing cell order; clears the slot's accumulators.
+// slot -> seed cell, in increasing cell order; clears the slot's accumulators
+// (the cell count starts from the tile pass's in-tile count when given).
 // *n_slots = number of seeds, clamped to slot_cap (more seeds than that can
 // only come from an inconsistent label grid, reported as bad input).
 __global__ void k_seed_list(const uint32_t* __restrict__ bits, const uint32_t* __restrict__ prefix, int64_t nwords,
-                            int64_t slot_cap, int32_t* __restrict__ seed_list, HaloAcc* __restrict__ acc,
-                            uint32_t* __restrict__ n_slots, int* status) {
+                            int64_t slot_cap, int32_t* __restrict__ seed_list, const uint16_t* __restrict__ seed_cells,
+                            HaloAcc* __restrict__ acc, uint32_t* __restrict__ n_slots, int* status) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         uint32_t total = prefix[nwords];
         if (int64_t(total) > slot_cap) set_status(status, CWTHF_E_BAD_INPUT);
@@ -331,7 +393,7 @@ __global__ void k_seed_list(const uint32_t* __restrict__ bits, const uint32_t* _
             z.n_part = 0;
             z.mq = 0;
             z.mom[0] = z.mom[1] = z.mom[2] = 0;
-            z.n_cells = 0;
+            z.n_cells = seed_cells ? seed_cells[i * 32 + bit] : 0;
             acc[s] = z;
             s++;
         }
@@ -351,7 +413,7 @@ __global__ void k_seeds_from_labels(const int32_t* __restrict__ label, int64_t c
 
 }  // namespace
 
-int seeds_rank(cwthf_ctx* ctx, int ng, cudaStream_t s) {
+int seeds_rank(cwthf_ctx* ctx, int ng, const uint16_t* seed_cells, cudaStream_t s) {
     int64_t cells = int64_t(ng) * ng * ng;
     int64_t nwords = (cells + 31) / 32;
     int blocks = ctx->sm_count * 8;
@@ -359,7 +421,7 @@ int seeds_rank(cwthf_ctx* ctx, int ng, cudaStream_t s) {
     int rc = scan_u32(ctx, ctx->seed_prefix, ctx->seed_prefix, nwords, s);
     if (rc) return rc;
     CWTHF_LAUNCH(ctx, s, "k_seed_list", k_seed_list<<<blocks, 256, 0, s>>>(ctx->seed_bits, ctx->seed_prefix, nwords, cells / 8 + 8, ctx->seed_list,
-                                       ctx->acc, ctx->n_seeds, ctx->d_status));
+                                       seed_cells, ctx->acc, ctx->n_seeds, ctx->d_status));
     return cuda_status(cudaGetLastError());
 }
 
@@ -370,7 +432,7 @@ int seeds_from_labels(cwthf_ctx* ctx, const int32_t* label, int ng, cudaStream_t
     if (e != cudaSuccess) return cuda_status(e);
     CWTHF_LAUNCH(ctx, s, "k_seeds_from_labels", k_seeds_from_labels<<<ctx->sm_count * 8, 256, 0, s>>>(label, cells, ctx->seed_bits, ctx->d_status));
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
-    return seeds_rank(ctx, ng, s);
+    return seeds_rank(ctx, ng, nullptr, s);
 }
 
 int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_t* label, bool,
@@ -381,17 +443,18 @@ int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->jump_changed, 0, sizeof(int) * (kMaxJumpRounds + 1), s);
     if (e != cudaSuccess) return cuda_status(e);
     int64_t ntiles = int64_t(div_up(ng, kSegTX)) * div_up(ng, kSegTY) * div_up(ng, kSegTZ);
-    cudaFuncSetAttribute(k_seg_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(int32_t) * kOwned));
+    cudaFuncSetAttribute(k_seg_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(int32_t) * kLocal));
     CWTHF_LAUNCH(ctx, s, "k_seg_tile",
-                 k_seg_tile<<<unsigned(ntiles), kSegThreads, sizeof(int32_t) * kOwned, s>>>(cwt, ng, cwt_min, label,
+                 k_seg_tile<<<unsigned(ntiles), kSegThreads, sizeof(int32_t) * kLocal, s>>>(cwt, ng, cwt_min, label,
                                                                                           ctx->seed_bits,
+                                                                                          ctx->seed_cells,
                                                                                           ctx->d_status));
     // seed ranks first (the resolve pass counts cells per seed slot)
-    int rc = seeds_rank(ctx, ng, s);
+    int rc = seeds_rank(ctx, ng, ctx->seed_cells, s);
     if (rc) return rc;
     int blocks = ctx->sm_count * 8;
     CWTHF_LAUNCH(ctx, s, "k_seg_resolve",
-                 k_seg_resolve<<<blocks, 256, 0, s>>>(label, cells, ctx->seed_bits, ctx->seed_prefix, ctx->n_seeds,
+                 k_seg_resolve<<<blocks, kResolveThreads, 0, s>>>(label, cells, ctx->seed_bits, ctx->seed_prefix, ctx->n_seeds,
                                                       ctx->acc, ctx->jump_changed));
     // pointer doubling for whatever the bounded walks left (normally nothing: every round exits at once)
     for (int r = 1; r < kMaxJumpRounds; r++) {
