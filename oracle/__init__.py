@@ -60,6 +60,7 @@ def lib() -> ctypes.CDLL:
         L.orc_dft3d.argtypes = [P, P, i32, i32]
         L.orc_cwt.argtypes = [P, i32, d, d, d, P]
         L.orc_cwt_direct.argtypes = [P, i32, d, d, d, P]
+        L.orc_cwt_at.argtypes = [P, i32, d, d, d, P, i64, P]
         L.orc_parent.argtypes = [P, i32, P]
         L.orc_segment.argtypes = [P, i32, f, P]
         L.orc_assign.argtypes = [P, P, d, i64, d, i32, P, P, d, i64, P, i64, P, P, P, P, P, P, P]
@@ -149,6 +150,18 @@ def cwt_direct(grid, L: float, w: float, mass_unit: float = 1.0) -> np.ndarray:
     C = np.empty(grid.shape, dtype=np.float64)
     _check(lib().orc_cwt_direct(_ptr(grid), ng, float(L), float(mass_unit), float(w), _ptr(C)), "cwt_direct")
     return C
+
+
+def cwt_at(grid, L: float, w: float, nodes, mass_unit: float = 1.0) -> np.ndarray:
+    """Eq. 2 summed literally at the given linear node indices (the wavelet's
+    fp64 support only, which is the full sum): full-size spot checks."""
+    grid = np.ascontiguousarray(grid, dtype=np.int64)
+    ng = grid.shape[0]
+    nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+    out = np.empty(nodes.shape[0], dtype=np.float64)
+    _check(lib().orc_cwt_at(_ptr(grid), ng, float(L), float(mass_unit), float(w), _ptr(nodes), nodes.shape[0],
+                            _ptr(out)), "cwt_at")
+    return out
 
 
 def parent(C) -> np.ndarray:

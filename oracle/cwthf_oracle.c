@@ -342,6 +342,46 @@ int orc_cwt_direct(const int64_t *grid, int ng, double L, double mass_unit, doub
     return ORC_OK;
 }
 
+/* Eq. 2 evaluated literally at chosen nodes only: for each requested node x,
+ * the sum over every node g of m_g Psi(w, x - g) (minimum-image separation).
+ * Terms whose separation has w^2 r^2 > 3000 are exactly zero in fp64 (the
+ * factor exp(-w^2 r^2 / 4) underflows to 0), so the loops visit only the
+ * offsets within that support (every offset once, also on small grids);
+ * the result is the full sum up to the order of the additions.  Cost per
+ * node: the support, not N^3. */
+int orc_cwt_at(const int64_t *grid, int ng, double L, double mass_unit, double w, const int64_t *nodes,
+               int64_t n_nodes, double *out) {
+    if (ng < 1 || !(L > 0) || !(w > 0) || !(mass_unit > 0) || n_nodes < 0) return ORC_E_ARG;
+    const double dx = L / ng;
+    const int64_t cells = (int64_t)ng * ng * ng;
+    /* offsets d in [-R, R] per axis, capped so that no node is visited twice */
+    int64_t R = (int64_t)ceil(sqrt(3000.0) / (w * dx));
+    int64_t lo = -(int64_t)(ng / 2) + (ng % 2 == 0 ? 1 : 0), hi = ng / 2; /* ng consecutive offsets */
+    int64_t dlo = -R < lo ? lo : -R, dhi = R > hi ? hi : R;
+    for (int64_t i = 0; i < n_nodes; i++) {
+        int64_t c = nodes[i];
+        if (c < 0 || c >= cells) return ORC_E_ARG;
+        int64_t x = c % ng, y = (c / ng) % ng, z = c / ((int64_t)ng * ng);
+        double s = 0.0;
+        for (int64_t dz = dlo; dz <= dhi; dz++)
+            for (int64_t dy = dlo; dy <= dhi; dy++)
+                for (int64_t dxo = dlo; dxo <= dhi; dxo++) {
+                    /* node g = x - d; its minimum-image separation from x is d itself
+                       (d lies in the minimum-image range) */
+                    int64_t gx = ((x - dxo) % ng + ng) % ng, gy = ((y - dy) % ng + ng) % ng,
+                            gz = ((z - dz) % ng + ng) % ng;
+                    int64_t g = (gz * ng + gy) * ng + gx;
+                    if (grid[g] == 0) continue;
+                    double ox = dx * (double)min_image((dxo % ng + ng) % ng, ng);
+                    double oy = dx * (double)min_image((dy % ng + ng) % ng, ng);
+                    double oz = dx * (double)min_image((dz % ng + ng) % ng, ng);
+                    s += node_mass(grid, g, mass_unit) * orc_wavelet(w, ox * ox + oy * oy + oz * oz);
+                }
+        out[i] = s;
+    }
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Sec. 2 step 4 and Sec. 2.3: local maxima and steepest-ascent segments.    */
 /* ------------------------------------------------------------------------ */

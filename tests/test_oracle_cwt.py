@@ -131,3 +131,27 @@ def test_isolated_clump_peaks_at_its_centre():
     lab = oracle.segment(C.astype(np.float32), 0.0)
     seeds = np.flatnonzero(lab.ravel() == np.arange(lab.size))
     assert seeds.tolist() == [(4 * n + 5) * n + 6]
+
+
+@pytest.mark.parametrize("n,L,w", [(12, 9.0, 1.0), (16, 40.0, 3.0), (10, 50.0, 4.0), (9, 7.0, 2.0)])
+def test_cwt_at_nodes_equals_direct_eq2_sum(n, L, w):
+    # the support-limited sum at chosen nodes is the literal Eq. 2 sum (only the
+    # order of the additions differs); large w*dx exercises the truncated support
+    rng = np.random.default_rng(n)
+    grid = (rng.random((n, n, n)) < 0.3) * rng.integers(1, 1 << 31, (n, n, n))
+    full = oracle.cwt_direct(grid, L, w)
+    nodes = np.concatenate([[0, n ** 3 - 1], rng.integers(0, n ** 3, 40)])
+    got = oracle.cwt_at(grid, L, w, nodes)
+    np.testing.assert_allclose(got, full.ravel()[nodes], rtol=1e-12, atol=1e-12 * np.abs(full).max())
+
+
+def test_cwt_at_far_nodes_see_only_the_support():
+    # a single particle mass on a 96^3 grid: nodes far beyond the fp64 support get exactly 0
+    n, L, w = 96, 96.0, 4.0
+    grid = np.zeros((n, n, n), np.int64)
+    grid[10, 20, 30] = 1 << 30
+    near = (10 * n + 20) * n + 31
+    far = (58 * n + 68) * n + 78
+    v = oracle.cwt_at(grid, L, w, [near, far])
+    assert v[0] == pytest.approx(oracle.wavelet(w, 1.0))
+    assert v[1] == 0.0
