@@ -303,6 +303,175 @@ __device__ __forceinline__ void stage_fused(int R, float2* tile, A addr, const f
 }
 
 // ---------------------------------------------------------------------------
+// Compile-time stages for the sizes the large grids use: length, columns and
+// radices are constants, so index arithmetic folds to shifts and constants,
+// everything inlines into the kernel (one register allocation, no calls), and
+// the conjugations of the inverse transforms ride on the first load and the
+// last store instead of separate passes over the tile.
+// ---------------------------------------------------------------------------
+template <int L, int C, int R, int Ns, bool kConjIn, bool kConjOut, class A>
+__device__ __forceinline__ void stage_ct(float2* tile, A addr, const float2* tw) {
+    constexpr int NB = L / R;  // butterflies per sequence
+    const int c = int(threadIdx.x) % C, j = int(threadIdx.x) / C;
+    const bool on = j < NB;
+    float2 v[R];
+    if (on) {
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            v[r] = tile[addr(j + r * NB, c)];
+            if (kConjIn) v[r].y = -v[r].y;
+        }
+        if constexpr (Ns > 1) {
+            const int k = j % Ns;
+            constexpr int step = L / (Ns * R);
+#pragma unroll
+            for (int r = 1; r < R; r++) v[r] = cmul(v[r], tw[r * k * step]);
+        }
+        RegDif<R>::template run<0>(v);
+    }
+    __syncthreads();
+    if (on) {
+        const int k = j % Ns;
+        const int base = (j / Ns) * Ns * R + k;
+        static_for<0, R>([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            float2 x = v[dig_rev(R, r)];
+            if (kConjOut) x.y = -x.y;
+            tile[addr(base + r * Ns, c)] = x;
+        });
+    }
+    __syncthreads();
+}
+
+// The fused stage of the wavelet transform with constant sizes: last forward
+// stage (Ns * R == L), multiply by Psi^ and conjugate, first inverse stage.
+template <int L, int C, int R, int Ns, class A>
+__device__ __forceinline__ void stage_fused_ct(float2* tile, A addr, const float2* tw, const Wave& wv) {
+    static_assert(Ns * R == L, "the fused stage is the last forward stage");
+    const int c = int(threadIdx.x) % C, j = int(threadIdx.x) / C;
+    const bool on = j < L / R;
+    float2 v[R];
+    if (on) {
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = tile[addr(j + r * Ns, c)];
+        if constexpr (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; r++) v[r] = cmul(v[r], tw[r * j]);  // k = j, step = 1
+        }
+        RegDif<R>::template run<0>(v);
+        float2 u[R];
+        static_for<0, R>([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            const int kz = j + r * Ns;
+            const float psi = wv.a * wv.gz[kz] + wv.b * wv.hz[kz];
+            const float2 x = v[dig_rev(R, r)];
+            u[r] = make_float2(x.x * psi, -(x.y * psi));
+        });
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = u[r];
+        RegDif<R>::template run<0>(v);
+    }
+    __syncthreads();
+    if (on) {
+        static_for<0, R>([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            tile[addr(j * R + r, c)] = v[dig_rev(R, r)];
+        });
+    }
+    __syncthreads();
+}
+
+// A transform policy: the tile FFTs a kernel runs, and its tile width.
+// DynFft follows the run-time plan; CtFft<...> is one compile-time plan of at
+// most three radices (R2 = 1 for two stages).
+struct DynFft {
+    static constexpr int kThreads = 512, kMinBlocks = 1;
+    static constexpr bool kGlobalTables = false;
+    static __device__ __forceinline__ int cols(const Plan& p) { return p.C; }
+    static __device__ __forceinline__ int len(const Plan& p) { return p.L; }
+    template <class A>
+    static __device__ __forceinline__ void fwd(const Plan& p, float2* t, A addr, const float2* tw) {
+        fft_tile(p, t, addr, tw);
+    }
+    // inverse of conjugated input: conj(DFT(conj(x))) with the conjugations as passes
+    template <class A>
+    static __device__ __forceinline__ void inv(const Plan& p, float2* t, A addr, const float2* tw) {
+        const int n = p.L * p.C;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) t[i] = conjf2(t[i]);
+        __syncthreads();
+        fft_tile(p, t, addr, tw);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) t[i] = conjf2(t[i]);
+    }
+    template <class A>
+    static __device__ __forceinline__ void wave(const Plan& p, float2* t, A addr, const float2* tw, const Wave& wv) {
+        const int L = p.L, C = p.C, r0 = p.rad[0], r1 = p.rad[1], r2 = p.rad[2];
+        if (p.nst == 1) {
+            stage_fused(r0, t, addr, tw, L, 1, C, wv);
+        } else if (p.nst == 2) {
+            stage(r0, t, addr, tw, L, 1, C);
+            stage_fused(r1, t, addr, tw, L, r0, C, wv);
+            stage(r0, t, addr, tw, L, r1, C);
+        } else {
+            stage(r0, t, addr, tw, L, 1, C);
+            stage(r1, t, addr, tw, L, r0, C);
+            stage_fused(r2, t, addr, tw, L, r0 * r1, C, wv);
+            stage(r1, t, addr, tw, L, r2, C);
+            stage(r0, t, addr, tw, L, r2 * r1, C);
+        }
+        const int n = L * C;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) t[i] = conjf2(t[i]);
+    }
+};
+
+template <int L_, int C_, int R0, int R1, int R2, int MinBlocks>
+struct CtFft {
+    static constexpr int kRmin = R2 > 1 ? (R0 < R1 ? (R0 < R2 ? R0 : R2) : (R1 < R2 ? R1 : R2))
+                                        : (R1 > 1 ? (R0 < R1 ? R0 : R1) : R0);
+    static constexpr int kThreads = C_ * (L_ / kRmin), kMinBlocks = MinBlocks;
+    static constexpr bool kGlobalTables = true;  // y/z pass: tables through the cache
+    static_assert(R0 * R1 * R2 == L_, "radices multiply to the length");
+    static __device__ __forceinline__ int cols(const Plan&) { return C_; }
+    static __device__ __forceinline__ int len(const Plan&) { return L_; }
+    template <bool kCI, bool kCO, class A>
+    static __device__ __forceinline__ void run(float2* t, A addr, const float2* tw) {
+        if constexpr (R1 == 1) {
+            stage_ct<L_, C_, R0, 1, kCI, kCO>(t, addr, tw);
+        } else if constexpr (R2 == 1) {
+            stage_ct<L_, C_, R0, 1, kCI, false>(t, addr, tw);
+            stage_ct<L_, C_, R1, R0, false, kCO>(t, addr, tw);
+        } else {
+            stage_ct<L_, C_, R0, 1, kCI, false>(t, addr, tw);
+            stage_ct<L_, C_, R1, R0, false, false>(t, addr, tw);
+            stage_ct<L_, C_, R2, R0 * R1, false, kCO>(t, addr, tw);
+        }
+    }
+    template <class A>
+    static __device__ __forceinline__ void fwd(const Plan&, float2* t, A addr, const float2* tw) {
+        run<false, false>(t, addr, tw);
+    }
+    template <class A>
+    static __device__ __forceinline__ void inv(const Plan&, float2* t, A addr, const float2* tw) {
+        run<true, true>(t, addr, tw);
+    }
+    template <class A>
+    static __device__ __forceinline__ void wave(const Plan&, float2* t, A addr, const float2* tw, const Wave& wv) {
+        if constexpr (R1 == 1) {
+            static_assert(R1 != 1, "single-stage wavelet plans use the run-time path");
+        } else if constexpr (R2 == 1) {
+            stage_ct<L_, C_, R0, 1, false, false>(t, addr, tw);
+            stage_fused_ct<L_, C_, R1, R0>(t, addr, tw, wv);
+            stage_ct<L_, C_, R0, R1, false, true>(t, addr, tw);
+        } else {
+            stage_ct<L_, C_, R0, 1, false, false>(t, addr, tw);
+            stage_ct<L_, C_, R1, R0, false, false>(t, addr, tw);
+            stage_fused_ct<L_, C_, R2, R0 * R1>(t, addr, tw, wv);
+            stage_ct<L_, C_, R1, R2, false, false>(t, addr, tw);
+            stage_ct<L_, C_, R0, R2 * R1, false, true>(t, addr, tw);
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
 // TMA and mbarrier helpers (inline PTX).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -371,18 +540,37 @@ struct YzArgs {
 // One CTA per tile: TMA brings the [L][C] pencil tile into shared memory
 // (mbarrier completion), the block transforms it, TMA stores it back.
 // Several CTAs per SM overlap their load, compute and store phases.
-__global__ void __launch_bounds__(512, 1)
+template <class F>
+__global__ void __launch_bounds__(F::kThreads, F::kMinBlocks)
     k_fft_yz(const __grid_constant__ CUtensorMap in_map, const __grid_constant__ CUtensorMap out_map, YzArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const Plan& p = a.p;
-    const int L = p.L, C = p.C;
+    const int L = F::len(p), C = F::cols(p);
     // TMA boxes land at 128-byte aligned offsets of the tile
     unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     float2* tile = reinterpret_cast<float2*>(base);
-    float2* tw = tile + L * C;
-    float* gz = reinterpret_cast<float*>(tw + L);
-    float* hz = gz + L;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(hz + L);  // 8-byte aligned: 8 * (L*C + 2L) bytes in
+    // twiddle and wavelet tables: read through the cache (compile-time plans, so
+    // that three CTAs fit an SM) or staged in shared memory (run-time plans)
+    const float2* tw = a.tw;
+    const float* gz = a.ghat;
+    const float* hz = a.hhat;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tile + L * C);
+    if constexpr (!F::kGlobalTables) {
+        float2* tws = tile + L * C;
+        float* gzs = reinterpret_cast<float*>(tws + L);
+        float* hzs = gzs + L;
+        bar = reinterpret_cast<uint64_t*>(hzs + L);  // 8-byte aligned: 8 * (L*C + 2L) bytes in
+        for (int i = threadIdx.x; i < L; i += blockDim.x) {
+            tws[i] = a.tw[i];
+            if (a.mode == kYzWavelet) {
+                gzs[i] = a.ghat[i];
+                hzs[i] = a.hhat[i];
+            }
+        }
+        tw = tws;
+        gz = gzs;
+        hz = hzs;
+    }
     const int cc = blockIdx.x % a.ncc, o = blockIdx.x / a.ncc;
 
     if (threadIdx.x == 0) mbar_init(bar, 1);
@@ -393,13 +581,6 @@ __global__ void __launch_bounds__(512, 1)
             const int r = b * a.boxr;
             if (a.along_z) tma_load_3d(tile + r * C, &in_map, bar, 2 * cc * C, o, r);
             else tma_load_3d(tile + r * C, &in_map, bar, 2 * cc * C, r, o);
-        }
-    }
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        tw[i] = a.tw[i];
-        if (a.mode == kYzWavelet) {
-            gz[i] = a.ghat[i];
-            hz[i] = a.hhat[i];
         }
     }
     Wave wv{0.f, 0.f, gz, hz};
@@ -421,33 +602,9 @@ __global__ void __launch_bounds__(512, 1)
         return;
     }
     AddrPlain addr{C};
-    const int n = L * C;
-    if (a.mode == kYzInverse) {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) tile[i] = conjf2(tile[i]);
-        __syncthreads();
-        fft_tile(p, tile, addr, tw);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) tile[i] = conjf2(tile[i]);
-    } else if (a.mode == kYzForward) {
-        fft_tile(p, tile, addr, tw);
-    } else {
-        // forward stages, the last fused with the multiply and the first inverse
-        // stage, then the remaining inverse stages with the radices reversed
-        const int r0 = p.rad[0], r1 = p.rad[1], r2 = p.rad[2];
-        if (p.nst == 1) {
-            stage_fused(r0, tile, addr, tw, L, 1, C, wv);
-        } else if (p.nst == 2) {
-            stage(r0, tile, addr, tw, L, 1, C);
-            stage_fused(r1, tile, addr, tw, L, r0, C, wv);
-            stage(r0, tile, addr, tw, L, r1, C);
-        } else {
-            stage(r0, tile, addr, tw, L, 1, C);
-            stage(r1, tile, addr, tw, L, r0, C);
-            stage_fused(r2, tile, addr, tw, L, r0 * r1, C, wv);
-            stage(r1, tile, addr, tw, L, r2, C);
-            stage(r0, tile, addr, tw, L, r2 * r1, C);
-        }
-        for (int i = threadIdx.x; i < n; i += blockDim.x) tile[i] = conjf2(tile[i]);
-    }
+    if (a.mode == kYzInverse) F::inv(p, tile, addr, tw);
+    else if (a.mode == kYzForward) F::fwd(p, tile, addr, tw);
+    else F::wave(p, tile, addr, tw, wv);  // forward, multiply, inverse (last stage conjugates)
     fence_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -471,11 +628,12 @@ struct XArgs {
     const float2* twN;  // [ng]  exp(-2 pi i k / ng)
 };
 
-__global__ void __launch_bounds__(512, 1) k_fft_x_fwd(XArgs a, const int64_t* __restrict__ grid,
-                                                      float2* __restrict__ spec) {
+template <class F>
+__global__ void __launch_bounds__(F::kThreads, F::kMinBlocks) k_fft_x_fwd(XArgs a, const int64_t* __restrict__ grid,
+                                                                          float2* __restrict__ spec) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const Plan& p = a.p;
-    const int M = a.M, C = p.C;
+    const int M = F::len(p), C = F::cols(p);
     float2* tile = reinterpret_cast<float2*>(smem_raw);
     float2* tw = tile + M * C;
     double* rowdc = reinterpret_cast<double*>(tw + M);
@@ -513,7 +671,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_x_fwd(XArgs a, const int64_t* __
         }
     }
     __syncthreads();
-    fft_tile(p, tile, addr, tw);
+    F::fwd(p, tile, addr, tw);
     // r2c post-processing: X[k] = (Z[k] + Z*[M-k])/2 - (i/2) W_N^k (Z[k] - Z*[M-k])
     for (int r = warp; r < C; r += nwarp) {
         int64_t row = int64_t(blockIdx.x) * C + r;
@@ -546,11 +704,12 @@ __global__ void __launch_bounds__(512, 1) k_fft_x_fwd(XArgs a, const int64_t* __
     }
 }
 
-__global__ void __launch_bounds__(512, 1) k_fft_x_inv(XArgs a, const float2* __restrict__ spec,
-                                                      float* __restrict__ cwt) {
+template <class F>
+__global__ void __launch_bounds__(F::kThreads, F::kMinBlocks) k_fft_x_inv(XArgs a, const float2* __restrict__ spec,
+                                                                          float* __restrict__ cwt) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const Plan& p = a.p;
-    const int M = a.M, C = p.C;
+    const int M = F::len(p), C = F::cols(p);
     float2* tile = reinterpret_cast<float2*>(smem_raw);
     float2* tw = tile + M * C;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -597,7 +756,7 @@ __global__ void __launch_bounds__(512, 1) k_fft_x_inv(XArgs a, const float2* __r
         }
     }
     __syncthreads();
-    fft_tile(p, tile, addr, tw);
+    F::fwd(p, tile, addr, tw);
     for (int r = warp; r < C; r += nwarp) {
         int64_t row = int64_t(blockIdx.x) * C + r;
         if (row >= a.rows) continue;
@@ -730,7 +889,9 @@ int pick_boxr(int L, int C) {
     return -1;
 }
 
-size_t yz_smem(const Plan& p) { return 128 + size_t(p.L) * p.C * 8 + size_t(p.L) * 8 + size_t(p.L) * 8 + 16; }
+size_t yz_smem(const Plan& p, bool global_tables) {
+    return 128 + size_t(p.L) * p.C * 8 + (global_tables ? 0 : size_t(p.L) * 16) + 16;
+}
 size_t x_smem(const Plan& p) { return size_t(p.L) * p.C * 8 + size_t(p.L) * 8 + size_t(p.C) * 8; }
 
 void host_twiddles(int n, std::vector<float2>& out) {
@@ -800,6 +961,41 @@ float* get_wavelet_tables(cwthf_ctx* ctx, int ng, double L, double w) {
     return d;
 }
 
+// Compile-time instances for the plans of the large power-of-two grids; any
+// other plan runs the run-time kernels.  An instance is used only when the
+// run-time plan picks exactly its length, tile width and radices.
+template <class F>
+bool plan_is(const Plan& p, int L, int C, int r0, int r1, int r2) {
+    const int nst = r2 > 1 ? 3 : (r1 > 1 ? 2 : 1);
+    return p.L == L && p.C == C && p.nst == nst && p.rad[0] == r0 && (nst < 2 || p.rad[1] == r1) &&
+           (nst < 3 || p.rad[2] == r2) && p.T == F::kThreads;
+}
+using Yz1024 = CtFft<1024, 8, 32, 32, 1, 3>;
+using Yz512 = CtFft<512, 8, 16, 32, 1, 3>;
+using X512 = CtFft<512, 8, 16, 32, 1, 3>;
+using X256 = CtFft<256, 8, 16, 16, 1, 3>;
+
+using YzKernel = void (*)(const CUtensorMap, const CUtensorMap, YzArgs);
+YzKernel pick_yz(const Plan& p, bool& global_tables) {
+    global_tables = true;
+    if (plan_is<Yz1024>(p, 1024, 8, 32, 32, 1)) return k_fft_yz<Yz1024>;
+    if (plan_is<Yz512>(p, 512, 8, 16, 32, 1)) return k_fft_yz<Yz512>;
+    global_tables = false;
+    return k_fft_yz<DynFft>;
+}
+using XFwdKernel = void (*)(XArgs, const int64_t*, float2*);
+using XInvKernel = void (*)(XArgs, const float2*, float*);
+XFwdKernel pick_x_fwd(const Plan& p) {
+    if (plan_is<X512>(p, 512, 8, 16, 32, 1)) return k_fft_x_fwd<X512>;
+    if (plan_is<X256>(p, 256, 8, 16, 16, 1)) return k_fft_x_fwd<X256>;
+    return k_fft_x_fwd<DynFft>;
+}
+XInvKernel pick_x_inv(const Plan& p) {
+    if (plan_is<X512>(p, 512, 8, 16, 32, 1)) return k_fft_x_inv<X512>;
+    if (plan_is<X256>(p, 256, 8, 16, 16, 1)) return k_fft_x_inv<X256>;
+    return k_fft_x_inv<DynFft>;
+}
+
 int launch_yz(cwthf_ctx* ctx, float2* src, float2* dst, int ng, bool along_z, int mode, const Tables* t,
               const float* wtab, double w, double mass_unit, cudaStream_t s) {
     Plan p;
@@ -826,9 +1022,11 @@ int launch_yz(cwthf_ctx* ctx, float2* src, float2* dst, int ng, bool along_z, in
     // unit (the x pass already scaled the int64 grid by 2^-30: units of mass_unit)
     a.scale = float(std::pow(w, 1.5) * mass_unit / (double(ng) * ng * ng));
     a.status = ctx->d_status;
-    size_t smem = yz_smem(p);
-    cudaFuncSetAttribute(k_fft_yz, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    CWTHF_LAUNCH(ctx, s, "k_fft_yz", k_fft_yz<<<unsigned(a.ncc) * ng, p.T, smem, s>>>(in_map, out_map, a));
+    bool global_tables = false;
+    YzKernel k = pick_yz(p, global_tables);
+    size_t smem = yz_smem(p, global_tables);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    CWTHF_LAUNCH(ctx, s, "k_fft_yz", k<<<unsigned(a.ncc) * ng, p.T, smem, s>>>(in_map, out_map, a));
     return cuda_status(cudaGetLastError());
 }
 
@@ -854,8 +1052,9 @@ int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, float2* sp
     XArgs a;
     int rc = x_args(ng, t, a);
     if (rc) return rc;
-    cudaFuncSetAttribute(k_fft_x_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(x_smem(a.p)));
-    CWTHF_LAUNCH(ctx, s, "k_fft_x_fwd", k_fft_x_fwd<<<div_up(a.rows, a.p.C), a.p.T, x_smem(a.p), s>>>(a, grid, spec));
+    XFwdKernel k = pick_x_fwd(a.p);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(x_smem(a.p)));
+    CWTHF_LAUNCH(ctx, s, "k_fft_x_fwd", k<<<div_up(a.rows, a.p.C), a.p.T, x_smem(a.p), s>>>(a, grid, spec));
     if ((rc = cuda_status(cudaGetLastError()))) return rc;
     return launch_yz(ctx, spec, spec, ng, false, kYzForward, t, nullptr, 0.0, 1.0, s);
 }
@@ -870,8 +1069,9 @@ int transform_wavelet_inverse(cwthf_ctx* ctx, float2* src, float2* dst, int ng, 
     if (rc) return rc;
     XArgs a;
     if ((rc = x_args(ng, t, a))) return rc;
-    cudaFuncSetAttribute(k_fft_x_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, int(x_smem(a.p)));
-    CWTHF_LAUNCH(ctx, s, "k_fft_x_inv", k_fft_x_inv<<<div_up(a.rows, a.p.C), a.p.T, x_smem(a.p), s>>>(a, dst, cwt));
+    XInvKernel k = pick_x_inv(a.p);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(x_smem(a.p)));
+    CWTHF_LAUNCH(ctx, s, "k_fft_x_inv", k<<<div_up(a.rows, a.p.C), a.p.T, x_smem(a.p), s>>>(a, dst, cwt));
     return cuda_status(cudaGetLastError());
 }
 

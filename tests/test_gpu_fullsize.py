@@ -1,0 +1,158 @@
+"""The full-size workload in the launch configuration the benchmark times
+(2^27 clumped particles, a 1024^3 grid, L = 500 Mpc/h, scales w = 2, 3, 4).
+
+The oracle cannot run this size end to end, so the checks are:
+* deposit: the whole int64 grid, bit for bit, against the oracle's CIC;
+* CWT: spot values against Eq. 2 summed by the oracle at chosen nodes (the
+  field maximum, the highest-density nodes and random nodes);
+* segmentation and assignment: properties that hold at any size, checked on
+  large samples (every label equals its parent's label, seeds are exactly the
+  maxima above cwt_min, every assigned particle's nearest node carries its
+  halo's label, catalogue counts match the particle ids).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2501_10622_gb300 as pkg
+from paper_2501_10622_gb300 import synth
+from tests.gpu_util import CWT_MAX_REL
+
+pytestmark = pytest.mark.gpu
+
+WL = synth.WORKLOADS["clumped-512cube-grid1024-L500"]
+
+
+@pytest.fixture(scope="module")
+def big():
+    pos = WL.positions("cuda")  # the box the benchmark's first replica times
+    ctx = pkg.Context(0, max_ng=WL.ng, max_np=pos.shape[0], max_scales=len(WL.scales))
+    grid_ref, _ = oracle.cic(pos.cpu().numpy(), WL.box, WL.ng)
+    yield ctx, pos, grid_ref
+    ctx.close()
+    torch.cuda.empty_cache()
+
+
+def _strict_parent(C, nodes):
+    """Best of each node and its 26 periodic neighbours: larger value, then the
+    smaller linear index (written out here for sampled nodes)."""
+    n = C.shape[0]
+    z, y, x = nodes // (n * n), (nodes // n) % n, nodes % n
+    best_v = np.full(nodes.shape, -np.inf)
+    best_i = np.full(nodes.shape, np.iinfo(np.int64).max)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                j = (((z + dz) % n) * n + (y + dy) % n) * n + (x + dx) % n
+                v = C.reshape(-1)[j].astype(np.float64)
+                take = (v > best_v) | ((v == best_v) & (j < best_i))
+                best_v = np.where(take, v, best_v)
+                best_i = np.where(take, j, best_i)
+    return best_i
+
+
+def test_deposit_bit_exact(big):
+    ctx, pos, grid_ref = big
+    g = ctx.deposit(pos, WL.box, WL.ng)
+    ctx.check()
+    assert np.array_equal(g.cpu().numpy(), grid_ref)
+
+
+@pytest.mark.parametrize("w", WL.scales)
+def test_cwt_spot_values(big, w):
+    ctx, pos, grid_ref = big
+    g = torch.from_numpy(grid_ref).cuda()
+    c = ctx.transform(g, WL.box, w)
+    ctx.check()
+    ch = c.cpu().numpy().reshape(-1)
+    del g
+    rng = np.random.default_rng(int(w * 10))
+    dens = grid_ref.reshape(-1)
+    nodes = np.unique(np.concatenate([
+        [int(np.argmax(ch)), int(np.argmin(ch))],
+        np.argpartition(dens, -12)[-12:],          # densest nodes
+        rng.integers(0, WL.ng ** 3, 16),           # anywhere
+    ]))
+    ref = oracle.cwt_at(grid_ref, WL.box, w, nodes)
+    err = np.abs(ch[nodes].astype(np.float64) - ref)
+    scale = np.max(np.abs(ref))  # includes the field's extremes
+    assert np.max(err) <= CWT_MAX_REL * scale, (w, np.max(err) / scale)
+
+
+def test_segmentation_properties(big):
+    ctx, pos, grid_ref = big
+    g = torch.from_numpy(grid_ref).cuda()
+    c = ctx.transform(g, WL.box, WL.scales[0])
+    del g
+    lab = ctx.segment(c, 0.0)
+    ctx.check()
+    C = c.cpu().numpy()
+    L = lab.cpu().numpy().reshape(-1)
+    rng = np.random.default_rng(5)
+    nodes = rng.integers(0, WL.ng ** 3, 400_000)
+    par = _strict_parent(C, nodes)
+    is_max = par == nodes
+    val = C.reshape(-1)[nodes]
+    # maxima: seeds above cwt_min label themselves, the others are unassigned
+    assert np.all(L[nodes[is_max]] == np.where(val[is_max] > 0.0, nodes[is_max], -1))
+    # every other node carries its parent's label
+    assert np.all(L[nodes[~is_max]] == L[par[~is_max]])
+    # every label is -1 or a seed: a maximum above cwt_min that labels itself
+    seeds = np.unique(L[nodes][L[nodes] >= 0])
+    assert np.all(L[seeds] == seeds)
+    assert np.all(_strict_parent(C, seeds) == seeds) and np.all(C.reshape(-1)[seeds] > 0.0)
+
+
+def test_grid512_deposit_and_cwt_spots(gctx):
+    # the 512^3 grid takes the other compile-time FFT instances
+    wl = synth.WORKLOADS["clumped-256cube-grid512-L250"]
+    pos = wl.positions("cuda")
+    ctx = pkg.Context(0, max_ng=wl.ng, max_np=pos.shape[0], max_scales=1)
+    try:
+        grid_ref, _ = oracle.cic(pos.cpu().numpy(), wl.box, wl.ng)
+        g = ctx.deposit(pos, wl.box, wl.ng)
+        c = ctx.transform(g, wl.box, 2.0)
+        ctx.check()
+        assert np.array_equal(g.cpu().numpy(), grid_ref)
+        ch = c.cpu().numpy().reshape(-1)
+        rng = np.random.default_rng(7)
+        nodes = np.unique(np.concatenate([[int(np.argmax(ch)), int(np.argmin(ch))],
+                                          np.argpartition(grid_ref.reshape(-1), -8)[-8:],
+                                          rng.integers(0, wl.ng ** 3, 16)]))
+        ref = oracle.cwt_at(grid_ref, wl.box, 2.0, nodes)
+        assert np.max(np.abs(ch[nodes] - ref)) <= CWT_MAX_REL * np.max(np.abs(ref))
+    finally:
+        ctx.close()
+
+
+def test_find_properties(big):
+    ctx, pos, grid_ref = big
+    params = [pkg.default_params(w) for w in WL.scales]
+    hid, cat, nh = ctx.find(pos, WL.box, WL.ng, params, cat_cap=1 << 22)
+    ctx.check()
+    q = oracle.quantise(pos.cpu().numpy(), WL.box, WL.ng)
+    node = (q + 512) >> 10
+    node[node == WL.ng] = 0
+    cell = (node[:, 2] * WL.ng + node[:, 1]) * WL.ng + node[:, 0]
+    g = torch.from_numpy(grid_ref).cuda()
+    for k, w in enumerate(WL.scales):
+        cats = pkg.catalogue_to_numpy(cat[k], nh[k])
+        ids = hid[k].cpu().numpy()
+        assert np.all(np.diff(cats["seed"]) > 0)                       # seed order
+        assert np.all(cats["n_part"] >= 15)                            # Table 1 particle threshold
+        # halo ids are kept seeds or -1, and the counts match the catalogue
+        seeds, counts = np.unique(ids[ids >= 0], return_counts=True)
+        assert np.array_equal(seeds, cats["seed"][cats["n_part"] > 0])
+        assert np.array_equal(counts, cats["n_part"][cats["n_part"] > 0])
+        # an assigned particle's nearest node carries its halo's label
+        c = ctx.transform(g, WL.box, w)
+        lab_t = ctx.segment(c, 0.0).reshape(-1)
+        ctx.check()
+        lab = lab_t.cpu().numpy()
+        sel = np.flatnonzero(ids >= 0)[:: 97]
+        assert np.all(lab[cell[sel]] == ids[sel])
+        # and the cells of a halo are those labelled with its seed
+        n_cells = torch.bincount(lab_t[lab_t >= 0].long(), minlength=WL.ng ** 3)
+        assert np.array_equal(cats["n_cells"], n_cells[torch.from_numpy(cats["seed"]).cuda()].cpu().numpy())
+        del c, lab_t, n_cells
