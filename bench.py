@@ -147,8 +147,8 @@ def algorithmic_bytes(name, u):
         "k_seg_resolve": 4 * cells,                    # labels in (flagged ones rewritten)
         "k_count_cells": 4 * cells,
         "k_halo_sums": 8 * npart + 4 * npart + 4 * npart,    # records, label gather, slot out
-        # record position in; per scale: record slot gathered, halo id out
-        "k_finalize": 4 * npart + 8 * npart * u.get("scales", 1),
+        "k_rec_halo": 8 * npart * u.get("scales", 1),               # record slots in, halo ids out
+        "k_finalize": 4 * npart + 8 * npart * u.get("scales", 1),   # record position; per scale id in and out
     }
     return table.get(name)
 

@@ -302,17 +302,31 @@ __global__ void __launch_bounds__(kThreads) k_catalogue(const HaloAcc* __restric
     }
 }
 
-// halo_id of every particle for every scale, in particle order: the record
-// the particle was binned to, that record's halo slots (one per scale, stored
-// side by side, so one gather serves all scales), and each slot's seed if
-// its halo was kept.  Up to kScalesAtOnce scales are handled per pass, with
-// all gathers of kIlp particles in flight together.
+// Record order, after the last scale: each stored record slot becomes its
+// halo id (the slot's seed if the halo was kept, else -1), in place.  Records
+// are grouped by tile, so the slot lookups are coherent.
+__global__ void __launch_bounds__(kThreads) k_rec_halo(int32_t* __restrict__ rec_slot,
+                                                      const uint32_t* __restrict__ total_ptr, int n_scales,
+                                                      const int32_t* __restrict__ slot_halo, int64_t slot_stride) {
+    const int64_t total = *total_ptr;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < total; r += stride) {
+        int32_t* e = rec_slot + r * n_scales;
+        for (int k = 0; k < n_scales; k++) {
+            const int32_t sl = e[k];
+            e[k] = sl >= 0 ? slot_halo[k * slot_stride + sl] : -1;
+        }
+    }
+}
+
+// halo_id of every particle for every scale, in particle order: one gather of
+// its record's halo ids (all scales side by side).  Several particles per
+// thread keep independent gathers in flight.
 __global__ void __launch_bounds__(kThreads) k_finalize(const uint32_t* __restrict__ part_rec, int64_t np,
                                                       const uint32_t* __restrict__ total_ptr,
-                                                      const int32_t* __restrict__ rec_slot, int n_scales,
-                                                      const int32_t* __restrict__ slot_halo, int64_t slot_stride,
+                                                      const int32_t* __restrict__ rec_halo, int n_scales,
                                                       int32_t* __restrict__ halo_id) {
-    constexpr int kIlp = 2, kScalesAtOnce = 4;
+    constexpr int kIlp = 4, kScalesAtOnce = 4;
     const int64_t total = *total_ptr;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < np; i0 += kIlp * stride) {
@@ -324,23 +338,18 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const uint32_t* __restric
             r[u] = int64_t(x) < total ? int64_t(x) : -1;
         }
         for (int k0 = 0; k0 < n_scales; k0 += kScalesAtOnce) {
-            int32_t sl[kIlp][kScalesAtOnce];
+            int32_t h[kIlp][kScalesAtOnce];
 #pragma unroll
             for (int u = 0; u < kIlp; u++)
 #pragma unroll
                 for (int j = 0; j < kScalesAtOnce; j++)
-                    sl[u][j] = (r[u] >= 0 && k0 + j < n_scales) ? rec_slot[r[u] * n_scales + k0 + j] : -1;
-#pragma unroll
-            for (int u = 0; u < kIlp; u++)
-#pragma unroll
-                for (int j = 0; j < kScalesAtOnce; j++)
-                    sl[u][j] = sl[u][j] >= 0 ? slot_halo[(k0 + j) * slot_stride + sl[u][j]] : -1;
+                    h[u][j] = (r[u] >= 0 && k0 + j < n_scales) ? rec_halo[r[u] * n_scales + k0 + j] : -1;
 #pragma unroll
             for (int u = 0; u < kIlp; u++) {
                 const int64_t i = i0 + u * stride;
 #pragma unroll
                 for (int j = 0; j < kScalesAtOnce; j++)
-                    if (i < np && k0 + j < n_scales) halo_id[(k0 + j) * np + i] = sl[u][j];
+                    if (i < np && k0 + j < n_scales) halo_id[(k0 + j) * np + i] = h[u][j];
             }
         }
     }
@@ -386,11 +395,14 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
                  k_catalogue<<<blocks, kThreads, 0, s>>>(ctx->acc, ctx->seed_list, d_nseeds, ctx->keep_off, cwt, f,
                                                          cat, ctx->slot_halo + int64_t(scale) * slot_cap, n_halo,
                                                          ctx->d_status));
-    if (scale == n_scales - 1)  // halo ids of all scales at once
+    if (scale == n_scales - 1) {  // halo ids of all scales at once
+        CWTHF_LAUNCH(ctx, s, "k_rec_halo",
+                     k_rec_halo<<<blocks, kThreads, 0, s>>>(ctx->part_slot, ctx->dep_off + total_key, n_scales,
+                                                            ctx->slot_halo, slot_cap));
         CWTHF_LAUNCH(ctx, s, "k_finalize",
                      k_finalize<<<pblocks, kThreads, 0, s>>>(ctx->part_rec, np, ctx->dep_off + total_key,
-                                                             ctx->part_slot, n_scales, ctx->slot_halo, slot_cap,
-                                                             halo_id));
+                                                             ctx->part_slot, n_scales, halo_id));
+    }
     return cuda_status(cudaGetLastError());
 }
 

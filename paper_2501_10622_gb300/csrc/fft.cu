@@ -427,7 +427,10 @@ template <int L_, int C_, int R0, int R1, int R2, int MinBlocks>
 struct CtFft {
     static constexpr int kRmin = R2 > 1 ? (R0 < R1 ? (R0 < R2 ? R0 : R2) : (R1 < R2 ? R1 : R2))
                                         : (R1 > 1 ? (R0 < R1 ? R0 : R1) : R0);
-    static constexpr int kThreads = C_ * (L_ / kRmin), kMinBlocks = MinBlocks;
+    // one butterfly per thread in the smallest-radix stage, and at least one
+    // warp per row for the x passes' row loads
+    static constexpr int kThreads = C_ * (L_ / kRmin) > 32 * C_ ? C_ * (L_ / kRmin) : 32 * C_;
+    static constexpr int kMinBlocks = MinBlocks;
     static constexpr bool kGlobalTables = true;  // y/z pass: tables through the cache
     static_assert(R0 * R1 * R2 == L_, "radices multiply to the length");
     static __device__ __forceinline__ int cols(const Plan&) { return C_; }
