@@ -161,17 +161,28 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def sources_sha(names):
+    """Short hash of the kernel sources a stored capture was taken from."""
+    h = hashlib.sha256()
+    for n in names:
+        h.update((ROOT / "paper_2501_10622_gb300" / "csrc" / n).read_bytes())
+    return h.hexdigest()[:16]
+
+
 def stored_traffic(name, u):
-    """DRAM bytes per launch from a committed ncu capture, scaled to this
-    workload, if the kernel's source is unchanged since the capture."""
+    """DRAM bytes per launch from a committed ncu capture (profiles/traffic.json),
+    scaled to this workload by its cells, if the kernel's sources are unchanged
+    since the capture; else None."""
     f = ROOT / "profiles" / "traffic.json"
     if not f.exists():
         return None
     d = json.loads(f.read_text()).get(name)
     if not d:
         return None
-    src = ROOT / "paper_2501_10622_gb300" / "csrc" / d["source"]
-    if not src.exists() or hashlib.sha256(src.read_bytes()).hexdigest()[:16] != d["source_sha"]:
+    try:
+        if sources_sha(d["sources"]) != d["sources_sha"]:
+            return None
+    except OSError:
         return None
     return d["dram_bytes_per_launch"] * (u["ng"] / d["ng"]) ** 3
 

@@ -76,10 +76,11 @@ __device__ __forceinline__ int nearest_node(int64_t q, int ng) {
 // goes straight to the global atomics.  A warp whose 32 records share one
 // halo is folded with warp reductions first.  Each record's halo slot (or -1)
 // is kept for the final pass, at rec_slot[r * slot_stride].
-constexpr int kTab = 1024;  // table entries per CTA (power of two)
+constexpr int kHsThreads = 256, kHsCtasPerSm = 4;
+constexpr int kTabBits = 10, kTab = 1 << kTabBits;  // table entries per CTA
 constexpr int kProbe = 16;
 constexpr int kRecPerThread = 4;
-constexpr int kChunk = kThreads * kRecPerThread;
+constexpr int kChunk = kHsThreads * kRecPerThread;
 constexpr uint32_t kEmpty = 0xffffffffu;
 
 __device__ __forceinline__ void global_halo_add(HaloAcc* h, u64 cnt, u64 mq, u64 m0, u64 m1, u64 m2) {
@@ -90,7 +91,7 @@ __device__ __forceinline__ void global_halo_add(HaloAcc* h, u64 cnt, u64 mq, u64
     atomicAdd(reinterpret_cast<u64*>(&h->mom[2]), m2);
 }
 
-__global__ void __launch_bounds__(kThreads) k_halo_sums(DepArgs a, const uint32_t* __restrict__ total_ptr,
+__global__ void __launch_bounds__(kHsThreads) k_halo_sums(DepArgs a, const uint32_t* __restrict__ total_ptr,
                                                        const unsigned long long* __restrict__ rec,
                                                        const uint32_t* __restrict__ rec_mq,
                                                        const int32_t* __restrict__ label,
@@ -127,7 +128,7 @@ __global__ void __launch_bounds__(kThreads) k_halo_sums(DepArgs a, const uint32_
         int32_t lab[kRecPerThread];
 #pragma unroll
         for (int u = 0; u < kRecPerThread; u++) {
-            const int64_t r = c0 + u * kThreads + threadIdx.x;
+            const int64_t r = c0 + u * kHsThreads + threadIdx.x;
             mq[u] = 0;
             lab[u] = -1;
             q[u][0] = q[u][1] = q[u][2] = 0;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kThreads) k_halo_sums(DepArgs a, const uint32_
         }
 #pragma unroll
         for (int u = 0; u < kRecPerThread; u++) {
-            const int64_t r = c0 + u * kThreads + threadIdx.x;
+            const int64_t r = c0 + u * kHsThreads + threadIdx.x;
             uint32_t key = kEmpty;
             long long mom[3] = {0, 0, 0};
             if (r < total) {
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_halo_sums(DepArgs a, const uint32_
             }
             if (key != kEmpty && (!uniform || lane == 0)) {
                 // find or claim the table entry of this slot
-                uint32_t h = (key * 2654435761u) >> 22;  // top 10 bits: kTab = 1024
+                uint32_t h = (key * 2654435761u) >> (32 - kTabBits);  // multiplicative hash
                 int found = -1;
                 for (int pr = 0; pr < kProbe; pr++, h = (h + 1) & (kTab - 1)) {
                     uint32_t k = tkey[h];
@@ -377,9 +378,9 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
     DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
     const int64_t total_key = deposit_geom(ng).ntiles * kDepClasses;  // dep_off[total_key] = records binned
     int pblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kThreads), int64_t(ctx->sm_count) * 16));
-    int cblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kChunk), int64_t(ctx->sm_count) * 4));
+    int cblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kChunk), int64_t(ctx->sm_count) * kHsCtasPerSm));
     CWTHF_LAUNCH(ctx, s, "k_halo_sums",
-                 k_halo_sums<<<cblocks, kThreads, 0, s>>>(a, ctx->dep_off + total_key, ctx->dep_rec, ctx->dep_mq,
+                 k_halo_sums<<<cblocks, kHsThreads, 0, s>>>(a, ctx->dep_off + total_key, ctx->dep_rec, ctx->dep_mq,
                                                           label, ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc,
                                                           ctx->part_slot + scale, n_scales, ctx->d_mtot));
     FilterArgs f;

@@ -21,7 +21,11 @@ namespace cwthf {
 namespace {
 
 constexpr int kCountThreads = 256;
-constexpr int kTileThreads = 256;
+// Four warps per tile CTA: a tile's phases are separated by barriers, so
+// several mid-sized CTAs per SM keep more tiles in flight than a few large
+// ones (two warps per CTA measured slower: too few threads for the write-out).
+constexpr int kTileThreads = 128;
+constexpr int kTileCtasPerSm = 8;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kInvalidKey = 0xffffffffu;
 using u64 = unsigned long long;
@@ -117,9 +121,25 @@ __global__ void __launch_bounds__(kCountThreads) k_dep_scatter(DepArgs a, uint32
 // its class has every bit of m set.
 constexpr int kReachSegments = 27;
 
-// Pass 3: one tile at a time per CTA.  The record ranges of the 27 reaching-in
-// segments are fetched in parallel, then processed as one flattened list, so
-// every warp works on full batches whatever the segment sizes.
+// The j-th (neighbour offset mask m, boundary class) pair in (m, class) order.
+__device__ __forceinline__ void reach_pair(int j, int& m, int& cls) {
+    int n = 0;
+    m = 0;
+    cls = 0;
+    for (int mm = 0; mm < 8; mm++)
+        for (int cc = 0; cc < 8; cc++)
+            if ((cc & mm) == mm) {
+                if (n == j) { m = mm; cls = cc; }
+                n++;
+            }
+}
+
+// Pass 3: one tile at a time per CTA.  Warp 0 fetches the record ranges of
+// the 27 reaching-in segments (those of the next tile while the current one is
+// written out) and scans them with shuffles; the CTA processes them as one
+// flattened list, so every warp works on full batches whatever the segment
+// sizes; the write-out also clears the shared accumulators for the next tile.
+// Three barriers per tile.
 __global__ void __launch_bounds__(kTileThreads) k_dep_tile(DepArgs a, const uint32_t* __restrict__ off,
                                                           const unsigned long long* __restrict__ rec,
                                                           const uint32_t* __restrict__ rec_mq,
@@ -129,41 +149,50 @@ __global__ void __launch_bounds__(kTileThreads) k_dep_tile(DepArgs a, const uint
     __shared__ uint32_t acc_lo[kCells], acc_hi[kCells];
     __shared__ uint32_t seg_beg[kReachSegments], seg_pre[kReachSegments + 1];
     __shared__ uint8_t seg_m[kReachSegments];
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x == 0 && *mtot >= (1ull << 33)) set_status(status, CWTHF_E_OVERFLOW);
     const int64_t ntiles = int64_t(a.ntx) * a.nty * a.ntz;
     const int64_t ng = a.ng;
+    for (int c = threadIdx.x; c < kCells; c += kTileThreads) {
+        acc_lo[c] = 0u;
+        acc_hi[c] = 0u;
+    }
+    // this lane's (m, class) pair, fixed for all tiles
+    int my_m = 0, my_cls = 0;
+    if (warp == 0 && lane < kReachSegments) reach_pair(lane, my_m, my_cls);
+    // record range of this lane's segment of tile t (warp 0 only)
+    auto fetch = [&](int64_t t, uint32_t& b, uint32_t& e) {
+        b = e = 0;
+        if (t < ntiles && lane < kReachSegments) {
+            const int tx = int(t % a.ntx), ty = int((t / a.ntx) % a.nty), tz = int(t / (int64_t(a.ntx) * a.nty));
+            const int sx = tx - (my_m & 1) < 0 ? a.ntx - 1 : tx - (my_m & 1);
+            const int sy = ty - ((my_m >> 1) & 1) < 0 ? a.nty - 1 : ty - ((my_m >> 1) & 1);
+            const int sz = tz - ((my_m >> 2) & 1) < 0 ? a.ntz - 1 : tz - ((my_m >> 2) & 1);
+            const int64_t key = ((int64_t(sz) * a.nty + sy) * a.ntx + sx) * kDepClasses + my_cls;
+            b = off[key];
+            e = off[key + 1];
+        }
+    };
+    uint32_t nb = 0, ne = 0;
+    if (warp == 0) fetch(blockIdx.x, nb, ne);
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int tx = int(t % a.ntx), ty = int((t / a.ntx) % a.nty), tz = int(t / (int64_t(a.ntx) * a.nty));
         const int x0 = tx * kDepTX, y0 = ty * kDepTY, z0 = tz * kDepTZ;
         const int wx = min(kDepTX, a.ng - x0), wy = min(kDepTY, a.ng - y0), wz = min(kDepTZ, a.ng - z0);
-        for (int c = threadIdx.x; c < kCells; c += kTileThreads) {
-            acc_lo[c] = 0u;
-            acc_hi[c] = 0u;
-        }
-        if (threadIdx.x < kReachSegments) {
-            // the j-th (m, class) pair in (m, class) order
-            int j = threadIdx.x, m = 0, cls = 0, n = 0;
-            for (int mm = 0; mm < 8; mm++)
-                for (int cc = 0; cc < 8; cc++)
-                    if ((cc & mm) == mm) {
-                        if (n == j) { m = mm; cls = cc; }
-                        n++;
-                    }
-            const int dx = m & 1, dy = (m >> 1) & 1, dz = (m >> 2) & 1;
-            const int sx = tx - dx < 0 ? a.ntx - 1 : tx - dx;
-            const int sy = ty - dy < 0 ? a.nty - 1 : ty - dy;
-            const int sz = tz - dz < 0 ? a.ntz - 1 : tz - dz;
-            const int64_t key = ((int64_t(sz) * a.nty + sy) * a.ntx + sx) * kDepClasses + cls;
-            const uint32_t b = off[key], e = off[key + 1];
-            seg_beg[j] = b;
-            seg_pre[j + 1] = e - b;
-            seg_m[j] = uint8_t(m);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            seg_pre[0] = 0;
-            for (int j = 0; j < kReachSegments; j++) seg_pre[j + 1] += seg_pre[j];
+        if (warp == 0) {
+            // inclusive scan of the 27 segment sizes
+            uint32_t n = ne - nb, incl = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane < kReachSegments) {
+                seg_beg[lane] = nb;
+                seg_pre[lane + 1] = incl;
+                seg_m[lane] = uint8_t(my_m);
+            }
+            if (lane == 0) seg_pre[0] = 0;
         }
         __syncthreads();
         const uint32_t total = seg_pre[kReachSegments];
@@ -206,11 +235,14 @@ __global__ void __launch_bounds__(kTileThreads) k_dep_tile(DepArgs a, const uint
             }
         }
         __syncthreads();
+        if (warp == 0) fetch(t + gridDim.x, nb, ne);  // the next tile's ranges, in flight during the write-out
         for (int c = threadIdx.x; c < kCells; c += kTileThreads) {
             const int cx = c % kDepTX, cy = (c / kDepTX) % kDepTY, cz = c / (kDepTX * kDepTY);
             if (cx < wx && cy < wy && cz < wz)
                 grid[(int64_t(z0 + cz) * ng + (y0 + cy)) * ng + (x0 + cx)] =
                     int64_t((u64(acc_hi[c]) << 32) | u64(acc_lo[c]));
+            acc_lo[c] = 0u;
+            acc_hi[c] = 0u;
         }
         __syncthreads();
     }
@@ -244,7 +276,7 @@ int deposit_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mas
     if (rc) return rc;
     DepositGeom g = deposit_geom(ng);
     DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
-    int tblocks = int(std::min<int64_t>(g.ntiles, int64_t(ctx->sm_count) * 8));
+    int tblocks = int(std::min<int64_t>(g.ntiles, int64_t(ctx->sm_count) * kTileCtasPerSm));
     CWTHF_LAUNCH(ctx, s, "k_dep_tile", k_dep_tile<<<tblocks, kTileThreads, 0, s>>>(a, ctx->dep_off, ctx->dep_rec, ctx->dep_mq, ctx->d_mtot, grid,
                                                 ctx->d_status));
     cudaError_t e;
@@ -270,7 +302,7 @@ int deposit_into_scratch(const DepositScratch& sc, const float* pos, const float
     if ((e = cudaMemcpyAsync(sc.cursor, sc.off, size_t(nkeys) * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return cuda_status(e);
     k_dep_scatter<<<blocks, kCountThreads, 0, s>>>(a, sc.cursor, sc.rec, sc.mq, nullptr);
-    int tblocks = int(std::min<int64_t>(g.ntiles, int64_t(sc.sm_count) * 8));
+    int tblocks = int(std::min<int64_t>(g.ntiles, int64_t(sc.sm_count) * kTileCtasPerSm));
     k_dep_tile<<<tblocks, kTileThreads, 0, s>>>(a, sc.off, sc.rec, sc.mq, sc.mtot, grid, sc.status);
     return cuda_status(cudaGetLastError());
 }
