@@ -142,7 +142,8 @@ def algorithmic_bytes(name, u):
         "k_dep_tile": 8 * cells + 8 * npart,           # records in once, int64 grid out
         "k_dep_count": 12 * npart,
         "k_dep_scatter": 12 * npart + 8 * npart + 4 * npart,  # positions in, record + index out
-        "k_seg_tile": 4 * cells + 4 * cells,           # CWT in, labels out
+        "k_seg_parent": 4 * cells + 1 * cells,         # CWT in, parent codes out
+        "k_seg_chase": 1 * cells + 4 * cells,          # parent codes in, labels out
         "k_seg_jump": 4 * cells,
         "k_seg_resolve": 4 * cells,                    # labels in (flagged ones rewritten)
         "k_count_cells": 4 * cells,
@@ -383,7 +384,7 @@ def main():
                 "traffic": stored_traffic(dom, u), "algorithmic_bytes_per_launch": d["algorithmic_bytes"]}
     # step total: every kernel's algorithmic bytes per launch, except the pointer-jumping
     # rounds, of which only the first per segmentation must run (later ones exit early)
-    n_seg = kernels.get("k_seg_tile", {}).get("launches", 0)
+    n_seg = kernels.get("k_seg_chase", {}).get("launches", 0)
     step_bytes = sum(v["algorithmic_bytes"] * (n_seg if k == "k_seg_jump" else v["launches"])
                      for k, v in kernels.items() if "algorithmic_bytes" in v)
     step_bytes /= args.steps

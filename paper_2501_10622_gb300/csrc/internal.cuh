@@ -35,8 +35,6 @@ __host__ __device__ __forceinline__ int rec_q(unsigned long long e, int d) {
     return int((e >> (kRecBits * d)) & ((1ull << kRecBits) - 1));
 }
 
-// Segmentation tiles (owned cells; one halo layer is staged around them).
-constexpr int kSegTX = 30, kSegTY = 16, kSegTZ = 32;
 constexpr int kMaxJumpRounds = 40;
 
 // A bounded device wait gives up after this many polls.

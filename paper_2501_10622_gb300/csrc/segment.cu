@@ -7,40 +7,50 @@
 // C > cwt_min is a seed; the label of a cell is the seed its parent chain
 // reaches, or -1 when the chain ends at a maximum that is not a seed.
 //
-// k_seg_tile stages one tile plus a one-cell halo of C in shared memory,
-// computes the parents of the tile's cells, and resolves every chain that
-// stays inside the tile by pointer jumping in shared memory.  A chain that
-// leaves the tile is written as a flagged pointer (bit 30) to the first cell
-// outside; k_seg_jump then replaces flagged pointers by the label of their
-// target, round after round (pointer doubling), until no flagged pointer is
-// left.  The number of rounds is bounded; hitting the bound is reported as
-// CWTHF_E_NOT_CONVERGED.  The result does not depend on update order: every
+// k_seg_parent finds every cell's parent and writes it as a one-byte code
+// (the offset along each axis, a maximum flag, a seed flag): each thread keeps
+// a column of rows in registers and walks along z, so the 27-cell search needs
+// no shared memory and no barrier.  k_seg_chase loads a tile's codes into
+// shared memory as parent pointers and resolves every chain that stays inside
+// the tile.  A chain that leaves the tile is written as a flagged pointer
+// (bit 30) to the first cell outside; the global pass then replaces flagged
+// pointers by the label of their target (bounded walks, then pointer doubling
+// rounds if ever needed; hitting the round bound is reported as
+// CWTHF_E_NOT_CONVERGED).  The result does not depend on update order: every
 // update moves a pointer further along the (unique) chain.
 #include "internal.cuh"
 
 namespace cwthf {
 namespace {
 
-// Tile: kSegTX x kSegTY x kSegTZ owned cells.  A warp covers one grid row of
-// 32 columns: lanes 1..30 own cells, lanes 0 and 31 read the x-halo columns.
-// Warps 0 and 17 read the y-halo rows.
-constexpr int kSegRows = kSegTY + 2;          // warps per CTA
-constexpr int kSegThreads = 32 * kSegRows;    // 576
-// Shared-memory parent pointers use a padded local index (lz * 16 + ly) * 32 + lx,
-// so that local coordinates come back with shifts and masks.
+// Chain tiles: 32 x 16 x 32 cells, one warp per row of 32 columns.  Shared
+// parent pointers use the local index (lz * 16 + ly) * 32 + lx, so local
+// coordinates come back with shifts and masks.
+constexpr int kChTX = 32, kChTY = 16, kChTZ = 32;
+constexpr int kChThreads = 32 * kChTY;  // 512
 constexpr int kPX = 32, kPXBits = 5;
-constexpr int kPlaneL = kPX * kSegTY, kPlaneBits = 9;
-constexpr int kLocal = kPlaneL * kSegTZ;  // 16384 entries
-static_assert(kSegTX <= kPX && kPlaneL == (1 << kPlaneBits) && kSegTY == 16, "padded layout");
+constexpr int kPlaneL = kPX * kChTY, kPlaneBits = 9;
+constexpr int kLocal = kPlaneL * kChTZ;  // 16384 entries
+static_assert(kChTX == kPX && kPlaneL == (1 << kPlaneBits), "local index layout");
 constexpr int32_t kFlag = 1 << 30;
 constexpr int32_t kMask = kFlag - 1;
-constexpr int kChaseLimit = 64;  // longest in-tile chain followed before handing over to the global pass
-constexpr int kSegPrefetch = 4;  // planes of a column loaded ahead
+constexpr int kChaseLimit = 64;  // longest chain the global pass follows per cell before doubling rounds
+constexpr int kJumpRoundsInTile = 16;  // in-place doubling rounds: 2^14 >= cells of a tile
 // Seeds of one tile: at most one local maximum per 2 x 2 x 2 block of cells
-// (any two cells of such a block are neighbours), so 15 * 8 * 16 per tile.
-constexpr int kTileSeedCap = ((kSegTX + 1) / 2) * ((kSegTY + 1) / 2) * ((kSegTZ + 1) / 2);
+// (any two cells of such a block are neighbours).
+constexpr int kTileSeedCap = (kChTX / 2) * (kChTY / 2) * (kChTZ / 2);
 constexpr int32_t kLocalMask = 0xffff;  // local index bits of a shared-memory pointer
 constexpr int kCountShift = 16;         // a seed's in-tile cell count rides above them
+
+// Parent codes: bits 0-1 / 2-3 / 4-5 the offset + 1 along x / y / z; a local
+// maximum has offsets (0, 0, 0); bit 6 marks a maximum that seeds a halo.
+constexpr uint8_t kCodeMax = 0x15, kCodeSeed = 0x40;
+
+// Parent-code blocks: a warp owns 30 columns (lanes 1-30; lanes 0 and 31 hold
+// the x-halo columns) x kParR rows (plus the two y-halo rows, all in each
+// thread's registers) x kParZ planes (plus one halo plane at each end).
+constexpr int kParR = 8, kParZ = 128, kParWarps = 4;
+constexpr int kParThreads = 32 * kParWarps;
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
@@ -63,160 +73,238 @@ __device__ __forceinline__ int pick3(float a, float b, float c, float M, int ka,
     return x & 3;
 }
 
-// Parents of a 30 x 16 x 32-cell tile and the in-tile part of every chain.
-//
-// The best of the 27 cells around c is found in two steps.  First the
-// maximum value M, separably: along x by warp shuffles, along y through a
-// shared buffer of x-window maxima, along z in registers over the last three
-// planes.  Then the winner among the cells equal to M, which under the
-// strict order is the one with the smallest wrapped (z, y, x) in
-// lexicographic order: the first plane (in wrapped z order) whose window
-// holds M, then in that plane the first row whose x-window holds M, then in
-// that row the first column holding M.  Two rings of four planes in shared
-// memory (raw values and x-window maxima) serve the search, so one barrier
-// per plane suffices.  The parent is then formed without branches.  Parents
-// go to shared memory; every cell then follows its chain there until it
-// reaches a seed, a non-seed maximum, or a cell outside the tile.
-__global__ void __launch_bounds__(kSegThreads, 2) k_seg_tile(const float* __restrict__ C, int ng, float cwt_min,
-                                                         int32_t* __restrict__ label, uint32_t* __restrict__ seed_bits,
-                                                         uint16_t* __restrict__ seed_cells, int* status) {
+// Parent code of every cell.  The best of the 27 cells around c is found in
+// two steps: first the maximum value M, separably (x by warp shuffles, y
+// across the thread's registers, z over the last three planes, also in
+// registers); then the winner among the cells equal to M, which under the
+// strict order is the one with the smallest wrapped (z, y, x) in lexicographic
+// order: the first plane (in wrapped z order) whose window holds M, then in
+// that plane the first row whose x-window holds M, then in that row the first
+// column holding M.  The row and column choices of every plane are kept as
+// 2-bit codes per row (x: 10 rows in one word, y + x: 8 rows in one word), so
+// a cell's search ends with a z choice and a few bit extractions.
+__global__ void __launch_bounds__(kParThreads, 4) k_seg_parent(const float* __restrict__ C, int ng, float cwt_min,
+                                                            uint8_t* __restrict__ code_out,
+                                                            uint32_t* __restrict__ seed_bits, int* status) {
+    constexpr int R = kParR, NR = kParR + 2;
+    const int N = ng;
+    const int nbx = (N + 29) / 30, nby = (N + R - 1) / R;
+    const int64_t warp = (int64_t(blockIdx.x) * kParThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = int64_t(nbx) * nby * ((N + kParZ - 1) / kParZ);
+    if (warp >= nwarps) return;  // warp-uniform
+    const int by = int(warp % nby), bx = int((warp / nby) % nbx), bz = int(warp / (int64_t(nby) * nbx));
+    const int x0 = bx * 30, y0 = by * R, z0 = bz * kParZ;
+    const int wzc = min(kParZ, N - z0);
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const int xc = ((x0 + lane - 1) % N + N) % N;
+    const bool own_x = lane >= 1 && lane <= 30 && x0 + lane - 1 < N;
+    int kxm, kxc, kxp;
+    codes3(wrap(xc - 1, N), xc, wrap(xc + 1, N), kxm, kxc, kxp);
+    // rows y0-1 .. y0+R (wrapped) and the y codes of the owned rows, packed
+    // km | kc << 4 | kp << 8 per row (they differ from the interior only at y = 0, N-1)
+    int yrow[NR];
+#pragma unroll
+    for (int j = 0; j < NR; j++) yrow[j] = ((y0 - 1 + j) % N + N) % N;
+    int ykc[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        int a, b, c;
+        codes3(yrow[r], yrow[r + 1], yrow[r + 2], a, b, c);
+        ykc[r] = a | (b << 4) | (c << 8);
+    }
+    const size_t plane = size_t(N) * N;
+    // column pointer of each row
+    const float* colp = C + xc;
+    float v[NR], vn[NR];
+    auto load_plane = [&](int p, float (&dst)[NR]) {
+        const int z = ((z0 - 1 + p) % N + N) % N;
+        const float* base = colp + size_t(z) * plane;
+#pragma unroll
+        for (int j = 0; j < NR; j++) dst[j] = __ldg(base + size_t(yrow[j]) * N);
+    };
+    load_plane(0, v);
+    float pm0[R], pm1[R], pm2[R];  // y-window maxima of planes p-2, p-1, p (per owned row)
+    uint32_t yx0 = 0, yx1 = 0, yx2 = 0;  // their packed (y code, x code) per row
+#pragma unroll
+    for (int r = 0; r < R; r++) pm0[r] = pm1[r] = pm2[r] = 0.f;
+    bool bad = false;
+    const int np_ = wzc + 2;
+#pragma unroll 1
+    for (int p = 0; p < np_; p++) {
+        if (p + 1 < np_) load_plane(p + 1, vn);
+        // x windows of all rows, and each row's x choice
+        float rm[NR];
+        uint32_t xcp = 0;
+#pragma unroll
+        for (int j = 0; j < NR; j++) {
+            bad |= (v[j] != v[j]);
+            const float vl = __shfl_up_sync(full, v[j], 1), vr = __shfl_down_sync(full, v[j], 1);
+            rm[j] = fmaxf(fmaxf(vl, v[j]), vr);
+            xcp |= uint32_t(pick3(vl, v[j], vr, rm[j], kxm, kxc, kxp)) << (2 * j);
+        }
+        // y windows of the owned rows and their (y, x) choices
+        uint32_t yxp = 0;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const float m = fmaxf(fmaxf(rm[r], rm[r + 1]), rm[r + 2]);
+            const int cy = pick3(rm[r], rm[r + 1], rm[r + 2], m, ykc[r] & 15, (ykc[r] >> 4) & 15, ykc[r] >> 8);
+            const uint32_t cx = (xcp >> (2 * (r + cy))) & 3u;
+            yxp |= (uint32_t(cy) | (cx << 2)) << (4 * r);
+            pm0[r] = pm1[r];
+            pm1[r] = pm2[r];
+            pm2[r] = m;
+        }
+        yx0 = yx1;
+        yx1 = yx2;
+        yx2 = yxp;
+        if (p >= 2) {
+            // the cells of plane p-1 (z = z0 + p - 2); z codes differ from the
+            // interior ones only on the two wrapped planes
+            const int zc = z0 + p - 2;
+            const bool zlo = zc == 0, zhi = zc == N - 1;
+            const int kzm = zlo ? 8 : (zhi ? 4 : 0), kzc = zlo ? 1 : (zhi ? 9 : 5), kzp = zlo ? 6 : (zhi ? 2 : 10);
+            uint8_t* out = code_out + size_t(zc) * plane + xc;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const float M = fmaxf(fmaxf(pm0[r], pm1[r]), pm2[r]);
+                const int cz = pick3(pm0[r], pm1[r], pm2[r], M, kzm, kzc, kzp);
+                const uint32_t yx = cz == 0 ? yx0 : (cz == 1 ? yx1 : yx2);
+                const uint32_t f = (yx >> (4 * r)) & 15u;
+                uint32_t code = (f >> 2) | ((f & 3u) << 2) | (uint32_t(cz) << 4);
+                const bool seed = code == kCodeMax && M > cwt_min;
+                code |= seed ? kCodeSeed : 0u;
+                if (own_x && y0 + r < N) {
+                    const size_t y = size_t(yrow[r + 1]);
+                    out[y * N] = uint8_t(code);
+                    if (seed) {
+                        const uint32_t g = uint32_t((size_t(zc) * N + y) * N + xc);
+                        atomicOr(&seed_bits[g >> 5], 1u << (g & 31));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NR; j++) v[j] = vn[j];
+    }
+    if (bad) set_status(status, CWTHF_E_BAD_INPUT);
+}
+
+// In-tile chains of a 32 x 16 x 32-cell tile from the parent codes.  Every
+// cell's code becomes a shared-memory pointer (a local index, a seed's own
+// index, -1 for a maximum that is not a seed, or -2 - g for a parent g outside
+// the tile); pointer-jumping rounds over the whole tile then bring every
+// pointer to the end of its chain inside the tile: a seed, a non-seed maximum,
+// or a cell outside the tile.  A cell whose chain ends at a seed of this tile
+// adds one to the seed's cell count, kept in the upper half of the seed's own
+// entry.
+__global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __restrict__ codes, int ng,
+                                                           int32_t* __restrict__ label,
+                                                           uint16_t* __restrict__ seed_cells, int* status) {
     extern __shared__ int32_t ptr[];  // [kLocal], dynamic
     __shared__ uint16_t tile_seeds[kTileSeedCap];
     __shared__ uint32_t n_tile_seeds;
-    constexpr int kSlot = kSegRows * 32;          // floats per ring slot
-    __shared__ float vals[4 * kSlot];             // raw values of planes p-3 .. p (ring)
-    __shared__ float rmax[4 * kSlot];             // x-window maxima of the same planes
-    const int ntx = (ng + kSegTX - 1) / kSegTX, nty = (ng + kSegTY - 1) / kSegTY;
+    const int N = ng;
+    const int ntx = (N + kChTX - 1) / kChTX, nty = (N + kChTY - 1) / kChTY;
     const int t = int(blockIdx.x);
     const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
-    const int x0 = tx * kSegTX, y0 = ty * kSegTY, z0 = tz * kSegTZ;
-    const int wx = min(kSegTX, ng - x0), wy = min(kSegTY, ng - y0), wz = min(kSegTZ, ng - z0);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned full = 0xffffffffu;
-    // this lane's column and this warp's row (wrapped; columns past a small grid
-    // need a full modulo)
-    const int lx = lane - 1, ly = w - 1;  // owned local coordinates when in range
-    const int xc = ((x0 + lx) % ng + ng) % ng, yc = ((y0 + ly) % ng + ng) % ng;
-    const int xm = wrap(xc - 1, ng), xp = wrap(xc + 1, ng);
-    const int ym = wrap(yc - 1, ng), yp = wrap(yc + 1, ng);
-    const bool own = lx >= 0 && lx < wx && ly >= 0 && ly < wy;
-    const bool row_warp = w >= 1 && w <= kSegTY;  // warps of owned rows (warp-uniform)
-    int kxm, kxc, kxp, kym, kyc, kyp;
-    codes3(xm, xc, xp, kxm, kxc, kxp);
-    codes3(ym, yc, yp, kym, kyc, kyp);
-    const int N = ng;
-    const float* colp = C + size_t(yc) * N + xc;
-    // search addresses stay inside the rows even for the two halo lanes
-    const int lanec = min(max(lane, 1), 30);
-    const float* rsrc = rmax + (w - 1) * 32 + lanec;
-    const float* vsrc = vals + (w - 1) * 32 + lanec;
+    const int x0 = tx * kChTX, y0 = ty * kChTY, z0 = tz * kChTZ;
+    const int wx = min(kChTX, N - x0), wy = min(kChTY, N - y0), wz = min(kChTZ, N - z0);
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    const bool own = lx < wx && ly < wy;
+    const int xc = x0 + lx, yc = y0 + ly;
+    const int32_t plane32 = N * N;
+    // global index pieces of the neighbours (one step, or across the periodic boundary)
+    const int32_t oxm = xc == 0 ? N - 1 : -1, oxp = xc == N - 1 ? -(N - 1) : 1;
+    const int32_t oym = yc == 0 ? (N - 1) * N : -N, oyp = yc == N - 1 ? -(N - 1) * N : N;
+    if (threadIdx.x == 0) n_tile_seeds = 0;
+    __syncthreads();
     const int i0 = ly * kPX + lx;
-
-    bool bad = false;
-    if (threadIdx.x == 0) n_tile_seeds = 0;  // ordered before its first use by the plane barriers
-    float pl0 = 0.f, pl1 = 0.f, pl2 = 0.f;  // window maxima of planes p-2, p-1, p at this row and column
-    // kSegPrefetch planes of this column in flight (a register ring), so that
-    // the per-plane barrier does not expose the load latency
-    static_assert(kSegPrefetch % 4 == 0, "ring slots follow the prefetch slot");
-    const int np_ = wz + 2;
-    const size_t plane = size_t(N) * N;
-    float ring[kSegPrefetch];
+    if (own) {
+        const int32_t grow = yc * N + xc;
+        constexpr int kBatch = 8;  // planes whose codes are loaded together (independent loads in flight)
+        for (int lb = 0; lb < wz; lb += kBatch) {
+        uint32_t cb[kBatch];
 #pragma unroll
-    for (int d = 0; d < kSegPrefetch; d++)
-        ring[d] = d < np_ ? __ldg(colp + size_t(wrap(z0 - 1 + d, ng)) * plane) : 0.f;
-#pragma unroll 1
-    for (int p0 = 0; p0 < np_; p0 += kSegPrefetch)
+        for (int u = 0; u < kBatch; u++) cb[u] = lb + u < wz ? codes[(z0 + lb + u) * plane32 + grow] : 0u;
 #pragma unroll
-    for (int d = 0; d < kSegPrefetch; d++) {
-        const int p = p0 + d;
-        if (p >= np_) break;  // block-uniform
-        const float v = ring[d];
-        if (p + kSegPrefetch < np_) ring[d] = __ldg(colp + size_t(wrap(z0 - 1 + p + kSegPrefetch, ng)) * plane);
-        bad |= (v != v);
-        const float vl = __shfl_up_sync(full, v, 1), vr = __shfl_down_sync(full, v, 1);
-        const int sp = d & 3;  // p & 3, since p0 is a multiple of 4 (folded once unrolled)
-        vals[sp * kSlot + w * 32 + lane] = v;
-        rmax[sp * kSlot + w * 32 + lane] = fmaxf(fmaxf(vl, v), vr);
-        __syncthreads();
-        if (!row_warp) continue;  // warp-uniform: halo-row warps only feed the buffers
-        pl0 = pl1;
-        pl1 = pl2;
-        pl2 = fmaxf(fmaxf(rmax[sp * kSlot + (w - 1) * 32 + lane], rmax[sp * kSlot + w * 32 + lane]),
-                    rmax[sp * kSlot + (w + 1) * 32 + lane]);
-        if (p < 2) continue;  // block-uniform
-        // the cell of plane p-1 (owned z index lz = p-2); z codes are uniform and
-        // differ from the interior ones only on the two wrapped planes
-        const int lz = p - 2;
-        const int zc = z0 + lz;
-        const bool zlo = zc == 0, zhi = zc == N - 1;
-        const int kzm = zlo ? 8 : (zhi ? 4 : 0), kzc = zlo ? 1 : (zhi ? 9 : 5), kzp = zlo ? 6 : (zhi ? 2 : 10);
-        const float M = fmaxf(fmaxf(pl0, pl1), pl2);
-        const int cz = pick3(pl0, pl1, pl2, M, kzm, kzc, kzp);
-        const int so = ((d + 2 + cz) & 3) * kSlot;  // ring slot of plane p-2+cz
-        const int cy = pick3(rsrc[so], rsrc[so + 32], rsrc[so + 64], M, kym, kyc, kyp);
-        const float* row = vsrc + so + cy * 32;
-        const int cx = pick3(row[-1], row[0], row[1], M, kxm, kxc, kxp);
-        const int i = i0 + lz * kPlaneL;
-        const int dx = cx - 1, dy = cy - 1, dz = cz - 1;
-        const bool is_max = (dx | dy | dz) == 0;
-        const bool in_tile = unsigned(lx + dx) < unsigned(wx) && unsigned(ly + dy) < unsigned(wy) &&
-                             unsigned(lz + dz) < unsigned(wz);
-        const int gx = dx < 0 ? xm : (dx > 0 ? xp : xc);
-        const int gy = dy < 0 ? ym : (dy > 0 ? yp : yc);
-        const int gz = wrap(zc + dz, N);
-        const int32_t outside = -2 - ((gz * N + gy) * N + gx);
-        const bool seed = is_max && M > cwt_min;
-        const int32_t val = is_max ? (seed ? i : -1) : (in_tile ? i + dx + dy * kPX + dz * kPlaneL : outside);
-        if (own) {
-            ptr[i] = val;
-            if (seed) {
-                const uint32_t g = uint32_t((zc * N + yc) * N + xc);
-                atomicOr(&seed_bits[g >> 5], 1u << (g & 31));
-                const uint32_t j = atomicAdd(&n_tile_seeds, 1u);
-                if (j < uint32_t(kTileSeedCap)) tile_seeds[j] = uint16_t(i);
+        for (int u = 0; u < kBatch; u++) {
+            const int lz = lb + u;
+            if (lz >= wz) break;
+            const int zc = z0 + lz;
+            const int32_t g = zc * plane32 + grow;
+            const uint32_t code = cb[u];
+            const int i = i0 + lz * kPlaneL;
+            int32_t val;
+            if ((code & 0x3fu) == kCodeMax) {
+                val = (code & kCodeSeed) ? i : -1;
+                if (code & kCodeSeed) {
+                    const uint32_t j = atomicAdd(&n_tile_seeds, 1u);
+                    if (j < uint32_t(kTileSeedCap)) tile_seeds[j] = uint16_t(i);
+                }
+            } else {
+                const int dx = int(code & 3u) - 1, dy = int((code >> 2) & 3u) - 1, dz = int((code >> 4) & 3u) - 1;
+                if (unsigned(lx + dx) < unsigned(wx) && unsigned(ly + dy) < unsigned(wy) &&
+                    unsigned(lz + dz) < unsigned(wz)) {
+                    val = i + dx + dy * kPX + dz * kPlaneL;
+                } else {
+                    const int32_t ozm = zc == 0 ? (N - 1) * plane32 : -plane32;
+                    const int32_t ozp = zc == N - 1 ? -(N - 1) * plane32 : plane32;
+                    val = -2 - (g + (dx < 0 ? oxm : (dx > 0 ? oxp : 0)) + (dy < 0 ? oym : (dy > 0 ? oyp : 0)) +
+                                (dz < 0 ? ozm : (dz > 0 ? ozp : 0)));
+                }
             }
+            ptr[i] = val;
+        }
         }
     }
-    if (bad) set_status(status, CWTHF_E_BAD_INPUT);
     __syncthreads();
-
-    // Follow each chain inside the tile.  A chain that ends at a seed of this
-    // tile adds one to the seed's cell count, kept in the upper half of the
-    // seed's own entry (its lower half stays its own index, so that every walk
-    // still recognises it); the walked cell then points straight at the seed.
-    // Every value read or written is a later point of the same chain, so
-    // concurrent walks do not change any result.
+    // Pointer jumping in place, every cell of the tile in lockstep (no divergent
+    // walks): a pointer to a non-root cell takes that cell's pointer, until no
+    // pointer changes.  A value read while another thread rewrites it is either
+    // the old or the new pointer, both points of the same chain.
+    for (int round = 0; round < kJumpRoundsInTile; round++) {
+        bool changed = false;
+        if (own) {
+            for (int lz = 0; lz < wz; lz++) {
+                const int i = i0 + lz * kPlaneL;
+                const int32_t v = ptr[i];
+                if (v >= 0 && v != i) {
+                    const int32_t w = ptr[v];
+                    if (w != v) {
+                        ptr[i] = w;
+                        changed = true;
+                    }
+                }
+            }
+        }
+        if (!__syncthreads_or(changed)) break;
+    }
+    // every pointer now names a root (its cell's seed), -1, or -2 - g (a cell
+    // outside): labels, and one count per cell for the tile's seeds, kept in
+    // the upper half of the seed's own entry (readers mask it off)
     const int32_t gbase = (z0 * N + y0) * N + x0;
     if (own) {
         int32_t* out = label + (size_t(z0) * N + yc) * N + xc;
-        for (int lz = 0; lz < wz; lz++, out += plane) {
+        for (int lz = 0; lz < wz; lz++, out += size_t(plane32)) {
             const int i = i0 + lz * kPlaneL;
             const int32_t v = ptr[i];
-            int32_t cur = v >= 0 ? (v & kLocalMask) : v;
-            int steps = 0;
-            while (cur >= 0 && steps < kChaseLimit) {
-                const int32_t nv = ptr[cur];
-                const int32_t nxt = nv >= 0 ? (nv & kLocalMask) : nv;
-                if (nxt == cur) break;  // a seed
-                cur = nxt;
-                steps++;
-            }
+            const int32_t cur = v >= 0 ? (v & kLocalMask) : v;
             int32_t res;
             if (cur == -1) {
                 res = -1;
             } else if (cur <= -2) {
                 res = (-2 - cur) | kFlag;
             } else {
-                const int px = cur & (kPX - 1), py = (cur >> kPXBits) & (kSegTY - 1), pz = cur >> kPlaneBits;
+                const int px = cur & (kPX - 1), py = (cur >> kPXBits) & (kChTY - 1), pz = cur >> kPlaneBits;
                 const int32_t g = gbase + (pz * N + py) * N + px;
                 const int32_t nv = ptr[cur];
                 if (nv >= 0 && (nv & kLocalMask) == cur) {
                     res = g;
                     atomicAdd(&ptr[cur], 1 << kCountShift);
                 } else {
-                    res = g | kFlag;  // walk stopped at the limit: resume globally
+                    res = g | kFlag;  // not finished within the round bound: resume globally
                 }
-                if (steps > 1) ptr[i] = cur;  // i is not a seed here: its entry holds no count
             }
             *out = res;
         }
@@ -228,7 +316,7 @@ __global__ void __launch_bounds__(kSegThreads, 2) k_seg_tile(const float* __rest
     if (threadIdx.x == 0 && nts > uint32_t(kTileSeedCap)) set_status(status, CWTHF_E_BAD_INPUT);
     for (uint32_t j = threadIdx.x; j < min(nts, uint32_t(kTileSeedCap)); j += blockDim.x) {
         const int i = tile_seeds[j];
-        const int px = i & (kPX - 1), py = (i >> kPXBits) & (kSegTY - 1), pz = i >> kPlaneBits;
+        const int px = i & (kPX - 1), py = (i >> kPXBits) & (kChTY - 1), pz = i >> kPlaneBits;
         seed_cells[size_t(gbase + (pz * N + py) * N + px)] = uint16_t(uint32_t(ptr[i]) >> kCountShift);
     }
 }
@@ -344,7 +432,7 @@ __global__ void __launch_bounds__(256) k_seg_recount(const int32_t* __restrict__
 
 // One global round: replace every flagged pointer by its target's label;
 // changed[round] records whether any pointer is still flagged afterwards.
-__global__ void __launch_bounds__(kSegThreads) k_seg_jump(int32_t* __restrict__ label, int64_t cells,
+__global__ void __launch_bounds__(256) k_seg_jump(int32_t* __restrict__ label, int64_t cells,
                                                          int* __restrict__ changed, int round) {
     if (round > 0 && changed[round - 1] == 0) return;  // converged earlier
     bool any = false;
@@ -442,13 +530,18 @@ int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_
     cudaError_t e = cudaMemsetAsync(ctx->seed_bits, 0, size_t(nwords) * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->jump_changed, 0, sizeof(int) * (kMaxJumpRounds + 1), s);
     if (e != cudaSuccess) return cuda_status(e);
-    int64_t ntiles = int64_t(div_up(ng, kSegTX)) * div_up(ng, kSegTY) * div_up(ng, kSegTZ);
-    cudaFuncSetAttribute(k_seg_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(int32_t) * kLocal));
-    CWTHF_LAUNCH(ctx, s, "k_seg_tile",
-                 k_seg_tile<<<unsigned(ntiles), kSegThreads, sizeof(int32_t) * kLocal, s>>>(cwt, ng, cwt_min, label,
-                                                                                          ctx->seed_bits,
-                                                                                          ctx->seed_cells,
-                                                                                          ctx->d_status));
+    // parent codes into the context's grid buffer (free once the forward
+    // transform has read it), then the in-tile chains
+    uint8_t* codes = reinterpret_cast<uint8_t*>(ctx->grid);
+    const int64_t pwarps = int64_t(div_up(ng, 30)) * div_up(ng, kParR) * div_up(ng, kParZ);
+    CWTHF_LAUNCH(ctx, s, "k_seg_parent",
+                 k_seg_parent<<<unsigned(div_up(pwarps, int64_t(kParWarps))), kParThreads, 0, s>>>(
+                     cwt, ng, cwt_min, codes, ctx->seed_bits, ctx->d_status));
+    const int64_t ntiles = int64_t(div_up(ng, kChTX)) * div_up(ng, kChTY) * div_up(ng, kChTZ);
+    cudaFuncSetAttribute(k_seg_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(int32_t) * kLocal));
+    CWTHF_LAUNCH(ctx, s, "k_seg_chase",
+                 k_seg_chase<<<unsigned(ntiles), kChThreads, sizeof(int32_t) * kLocal, s>>>(
+                     codes, ng, label, ctx->seed_cells, ctx->d_status));
     // seed ranks first (the resolve pass counts cells per seed slot)
     int rc = seeds_rank(ctx, ng, ctx->seed_cells, s);
     if (rc) return rc;
