@@ -145,7 +145,8 @@ def algorithmic_bytes(name, u):
         "k_seg_parent": 4 * cells + 1 * cells,         # CWT in, parent codes out
         "k_seg_chase": 1 * cells + 4 * cells,          # parent codes in, labels out
         "k_seg_jump": 4 * cells,
-        "k_seg_resolve": 4 * cells,                    # labels in (flagged ones rewritten)
+        # k_seg_resolve: 12 B per cell whose chain left its tile (a data-dependent
+        # count the bench does not see), so no algorithmic figure
         "k_count_cells": 4 * cells,
         "k_halo_sums": 8 * npart + 4 * npart + 4 * npart,    # records, label gather, slot out
         "k_rec_halo": 8 * npart * u.get("scales", 1),               # record slots in, halo ids out

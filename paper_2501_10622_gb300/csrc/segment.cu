@@ -200,7 +200,9 @@ __global__ void __launch_bounds__(kParThreads, 4) k_seg_parent(const float* __re
 // entry.
 __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __restrict__ codes, int ng,
                                                            int32_t* __restrict__ label,
-                                                           uint16_t* __restrict__ seed_cells, int* status) {
+                                                           uint16_t* __restrict__ seed_cells,
+                                                           uint32_t* __restrict__ queue, uint32_t* __restrict__ qcount,
+                                                           int* status) {
     extern __shared__ int32_t ptr[];  // [kLocal], dynamic
     __shared__ uint16_t tile_seeds[kTileSeedCap];
     __shared__ uint32_t n_tile_seeds;
@@ -283,10 +285,19 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
     // every pointer now names a root (its cell's seed), -1, or -2 - g (a cell
     // outside): labels, and one count per cell for the tile's seeds, kept in
     // the upper half of the seed's own entry (readers mask it off)
+    // Cells whose chain leaves the tile (flagged) are queued for the global
+    // pass: each warp keeps its per-plane ballots, the CTA reserves one range
+    // of the queue with a single atomic, and each warp then writes its cells.
+    __shared__ uint32_t fl_ballot[kChTY][kChTZ];
+    __shared__ uint32_t fl_base[kChTY];
     const int32_t gbase = (z0 * N + y0) * N + x0;
-    if (own) {
-        int32_t* out = label + (size_t(z0) * N + yc) * N + xc;
-        for (int lz = 0; lz < wz; lz++, out += size_t(plane32)) {
+    const unsigned full = 0xffffffffu;
+    const uint32_t gcell0 = uint32_t((z0 * N + yc) * N + xc);
+    int32_t* out = label + (size_t(z0) * N + yc) * N + xc;
+    uint32_t nfl = 0;  // flagged cells of this warp (the same in every lane)
+    for (int lz = 0; lz < wz; lz++, out += size_t(plane32)) {  // block-uniform trip count
+        bool fl = false;
+        if (own) {
             const int i = i0 + lz * kPlaneL;
             const int32_t v = ptr[i];
             const int32_t cur = v >= 0 ? (v & kLocalMask) : v;
@@ -295,6 +306,7 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
                 res = -1;
             } else if (cur <= -2) {
                 res = (-2 - cur) | kFlag;
+                fl = true;
             } else {
                 const int px = cur & (kPX - 1), py = (cur >> kPXBits) & (kChTY - 1), pz = cur >> kPlaneBits;
                 const int32_t g = gbase + (pz * N + py) * N + px;
@@ -304,9 +316,34 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
                     atomicAdd(&ptr[cur], 1 << kCountShift);
                 } else {
                     res = g | kFlag;  // not finished within the round bound: resume globally
+                    fl = true;
                 }
             }
             *out = res;
+        }
+        const unsigned b = __ballot_sync(full, fl);
+        if (lx == 0) fl_ballot[ly][lz] = b;
+        nfl += __popc(b);
+    }
+    if (lx == 0) fl_base[ly] = nfl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t tot = 0;
+        for (int k = 0; k < kChTY; k++) {
+            const uint32_t c = fl_base[k];
+            fl_base[k] = tot;
+            tot += c;
+        }
+        const uint32_t base = tot ? atomicAdd(qcount, tot) : 0u;
+        for (int k = 0; k < kChTY; k++) fl_base[k] += base;
+    }
+    __syncthreads();
+    if (nfl) {  // warp-uniform
+        uint32_t at = fl_base[ly];
+        for (int lz = 0; lz < wz; lz++) {
+            const uint32_t b = fl_ballot[ly][lz];
+            if (b & (1u << lx)) queue[at + __popc(b & ((1u << lx) - 1u))] = gcell0 + uint32_t(lz) * uint32_t(plane32);
+            at += __popc(b);
         }
     }
     __syncthreads();
@@ -321,90 +358,47 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
     }
 }
 
-// Finishes every flagged label by following its chain through the label
-// grid (at most kChaseLimit steps per cell) and adds the cells of every seed
-// that the tile pass could not count (those that arrived flagged).  Each warp
-// takes 128 consecutive labels, queues its flagged ones in shared memory and
-// chases them with all lanes at once, then counts the finished ones with one
-// atomic per distinct seed among them.  Labels read while other threads update
-// them are always a later point of the same chain, so the result does not
-// depend on timing.  A cell still unfinished at the limit stays flagged
-// (pointing further along) and sets changed[0]: the doubling rounds then
-// finish it and the cells are recounted.
 constexpr int kResolveThreads = 256;
-__global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __restrict__ label, int64_t cells,
+
+// The global pass over the cells the tile pass queued (those whose chain left
+// their tile): each follows its chain through the label grid (at most
+// kChaseLimit steps), takes the label it reaches, and is counted for that
+// seed, one atomic per distinct seed among a warp's 32 cells.  A cell still
+// unfinished at the limit stays flagged and sets changed[0]; the doubling
+// rounds then finish it and the cells are recounted.  Labels read while other
+// threads update them are always a later point of the same chain, so the
+// result does not depend on timing.
+__global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __restrict__ label,
+                                                                 const uint32_t* __restrict__ queue,
+                                                                 const uint32_t* __restrict__ qcount,
                                                                  const uint32_t* __restrict__ bits,
                                                                  const uint32_t* __restrict__ prefix,
-                                                                 const uint32_t* __restrict__ n_slots, HaloAcc* acc,
-                                                                 int* __restrict__ changed) {
-    __shared__ int32_t queue[kResolveThreads / 32][128];
+                                                                 const uint32_t* __restrict__ n_slots,
+                                                                 HaloAcc* acc, int* __restrict__ changed) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const unsigned below = (1u << lane) - 1u;
-    int32_t* wq = queue[threadIdx.x >> 5];
+    const int64_t n = *qcount;
     bool left = false;
-    const int64_t n4 = (cells + 3) / 4;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n4; base += stride) {
-        const int64_t i = base + lane;  // warp-uniform trip count
-        int v[4] = {-1, -1, -1, -1};
-        const bool vec = 4 * i + 3 < cells;
-        if (i < n4) {
-            if (vec) {
-                const int4 q = reinterpret_cast<const int4*>(label)[i];
-                v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-            } else {
-                for (int j = 0; j < 4 && 4 * i + j < cells; j++) v[j] = label[4 * i + j];
-            }
-        }
-        // queue the flagged labels of the warp, in (j, lane) order
-        bool fl[4];
-        int pos[4];
-        int total = 0;
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            fl[j] = v[j] >= 0 && (v[j] & kFlag);
-            const unsigned b = __ballot_sync(full, fl[j]);
-            pos[j] = total + __popc(b & below);
-            total += __popc(b);
-            if (fl[j]) wq[pos[j]] = v[j];
-        }
-        if (total == 0) continue;  // warp-uniform
-        __syncwarp();
-        for (int e = lane; e < total; e += 32) {
-            int32_t w = wq[e];
+    for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t e = base + lane;  // warp-uniform trip count
+        int32_t lab = -1;
+        if (e < n) {
+            const uint32_t c = queue[e];
+            int32_t w = label[c];
             int steps = 0;
             while (w >= 0 && (w & kFlag) && steps < kChaseLimit) {
                 w = label[w & kMask];
                 steps++;
             }
-            wq[e] = w;
-            left |= (w >= 0 && (w & kFlag));
+            label[c] = w;
+            if (w >= 0 && (w & kFlag)) left = true;
+            else lab = w;
         }
-        __syncwarp();
-        bool mine = false;
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-            if (fl[j]) {
-                v[j] = wq[pos[j]];
-                mine = true;
-            }
-        if (mine) {
-            if (vec) reinterpret_cast<int4*>(label)[i] = make_int4(v[0], v[1], v[2], v[3]);
-            else
-                for (int j = 0; j < 4 && 4 * i + j < cells; j++) label[4 * i + j] = v[j];
-        }
-        // cells per seed among the finished queue entries: one atomic per distinct seed
-        for (int e0 = 0; e0 < total; e0 += 32) {  // warp-uniform
-            const int e = e0 + lane;
-            int32_t lab = e < total ? wq[e] : -1;
-            if (lab < 0 || (lab & kFlag)) lab = -1;
-            const unsigned peers = __match_any_sync(full, lab);
-            uint32_t slot;
-            if (lab >= 0 && lane == __ffs(peers) - 1 && seed_slot(bits, prefix, n_slots, lab, slot))
-                atomicAdd(&acc[slot].n_cells, (unsigned long long)__popc(peers));
-        }
-        __syncwarp();  // the queue is refilled next
+        const unsigned peers = __match_any_sync(full, lab);  // every lane, every iteration
+        uint32_t slot;
+        if (lab >= 0 && lane == __ffs(peers) - 1 && seed_slot(bits, prefix, n_slots, lab, slot))
+            atomicAdd(&acc[slot].n_cells, (unsigned long long)__popc(peers));
     }
     if (__any_sync(full, left) && lane == 0) changed[0] = 1;
 }
@@ -528,11 +522,15 @@ int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_
     int64_t cells = int64_t(ng) * ng * ng;
     int64_t nwords = (cells + 31) / 32;
     cudaError_t e = cudaMemsetAsync(ctx->seed_bits, 0, size_t(nwords) * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->jump_changed, 0, sizeof(int) * (kMaxJumpRounds + 1), s);
+    // jump_changed[0 .. kMaxJumpRounds]: round flags; [kMaxJumpRounds + 1]: queued cells
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->jump_changed, 0, sizeof(int) * (kMaxJumpRounds + 2), s);
     if (e != cudaSuccess) return cuda_status(e);
-    // parent codes into the context's grid buffer (free once the forward
-    // transform has read it), then the in-tile chains
+    // parent codes (1 byte per cell) and the queue of flagged cells (4 bytes per
+    // cell at most) in the context's int64 grid buffer (8 bytes per cell, free
+    // once the forward transform has read it), then the in-tile chains
     uint8_t* codes = reinterpret_cast<uint8_t*>(ctx->grid);
+    uint32_t* queue = reinterpret_cast<uint32_t*>(codes + (size_t(cells) + 255) / 256 * 256);
+    uint32_t* qcount = reinterpret_cast<uint32_t*>(ctx->jump_changed + kMaxJumpRounds + 1);
     const int64_t pwarps = int64_t(div_up(ng, 30)) * div_up(ng, kParR) * div_up(ng, kParZ);
     CWTHF_LAUNCH(ctx, s, "k_seg_parent",
                  k_seg_parent<<<unsigned(div_up(pwarps, int64_t(kParWarps))), kParThreads, 0, s>>>(
@@ -541,14 +539,15 @@ int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_
     cudaFuncSetAttribute(k_seg_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(int32_t) * kLocal));
     CWTHF_LAUNCH(ctx, s, "k_seg_chase",
                  k_seg_chase<<<unsigned(ntiles), kChThreads, sizeof(int32_t) * kLocal, s>>>(
-                     codes, ng, label, ctx->seed_cells, ctx->d_status));
+                     codes, ng, label, ctx->seed_cells, queue, qcount, ctx->d_status));
     // seed ranks first (the resolve pass counts cells per seed slot)
     int rc = seeds_rank(ctx, ng, ctx->seed_cells, s);
     if (rc) return rc;
     int blocks = ctx->sm_count * 8;
     CWTHF_LAUNCH(ctx, s, "k_seg_resolve",
-                 k_seg_resolve<<<blocks, kResolveThreads, 0, s>>>(label, cells, ctx->seed_bits, ctx->seed_prefix, ctx->n_seeds,
-                                                      ctx->acc, ctx->jump_changed));
+                 k_seg_resolve<<<blocks, kResolveThreads, 0, s>>>(label, queue, qcount, ctx->seed_bits,
+                                                                   ctx->seed_prefix, ctx->n_seeds, ctx->acc,
+                                                                   ctx->jump_changed));
     // pointer doubling for whatever the bounded walks left (normally nothing: every round exits at once)
     for (int r = 1; r < kMaxJumpRounds; r++) {
         CWTHF_LAUNCH(ctx, s, "k_seg_jump", k_seg_jump<<<blocks, 256, 0, s>>>(label, cells, ctx->jump_changed, r));
