@@ -303,6 +303,11 @@ __global__ void __launch_bounds__(kThreads) k_catalogue(const HaloAcc* __restric
     }
 }
 
+// Per-record slots are stored in groups of four scales (16 bytes, aligned),
+// so that the final pass reads a particle's ids for four scales with one
+// vector gather.
+__host__ __device__ __forceinline__ int slot_group_stride(int n_scales) { return (n_scales + 3) & ~3; }
+
 // Record order, after the last scale: each stored record slot becomes its
 // halo id (the slot's seed if the halo was kept, else -1), in place.  Records
 // are grouped by tile, so the slot lookups are coherent.
@@ -310,9 +315,10 @@ __global__ void __launch_bounds__(kThreads) k_rec_halo(int32_t* __restrict__ rec
                                                       const uint32_t* __restrict__ total_ptr, int n_scales,
                                                       const int32_t* __restrict__ slot_halo, int64_t slot_stride) {
     const int64_t total = *total_ptr;
+    const int rs = slot_group_stride(n_scales);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < total; r += stride) {
-        int32_t* e = rec_slot + r * n_scales;
+        int32_t* e = rec_slot + r * rs;
         for (int k = 0; k < n_scales; k++) {
             const int32_t sl = e[k];
             e[k] = sl >= 0 ? slot_halo[k * slot_stride + sl] : -1;
@@ -320,15 +326,17 @@ __global__ void __launch_bounds__(kThreads) k_rec_halo(int32_t* __restrict__ rec
     }
 }
 
-// halo_id of every particle for every scale, in particle order: one gather of
-// its record's halo ids (all scales side by side).  Several particles per
-// thread keep independent gathers in flight.
+// halo_id of every particle for every scale, in particle order: one 16-byte
+// gather per particle and group of four scales from its record's ids.
+// Several particles per thread keep independent gathers in flight.
 __global__ void __launch_bounds__(kThreads) k_finalize(const uint32_t* __restrict__ part_rec, int64_t np,
                                                       const uint32_t* __restrict__ total_ptr,
                                                       const int32_t* __restrict__ rec_halo, int n_scales,
                                                       int32_t* __restrict__ halo_id) {
-    constexpr int kIlp = 4, kScalesAtOnce = 4;
+    constexpr int kIlp = 4;
     const int64_t total = *total_ptr;
+    const int rs = slot_group_stride(n_scales);
+    const int4* rec4 = reinterpret_cast<const int4*>(rec_halo);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < np; i0 += kIlp * stride) {
         int64_t r[kIlp];
@@ -338,19 +346,19 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const uint32_t* __restric
             const uint32_t x = i < np ? part_rec[i] : 0xffffffffu;
             r[u] = int64_t(x) < total ? int64_t(x) : -1;
         }
-        for (int k0 = 0; k0 < n_scales; k0 += kScalesAtOnce) {
-            int32_t h[kIlp][kScalesAtOnce];
+        for (int k0 = 0; k0 < n_scales; k0 += 4) {
+            int4 h[kIlp];
 #pragma unroll
             for (int u = 0; u < kIlp; u++)
-#pragma unroll
-                for (int j = 0; j < kScalesAtOnce; j++)
-                    h[u][j] = (r[u] >= 0 && k0 + j < n_scales) ? rec_halo[r[u] * n_scales + k0 + j] : -1;
+                h[u] = r[u] >= 0 ? rec4[(r[u] * rs + k0) >> 2] : make_int4(-1, -1, -1, -1);
 #pragma unroll
             for (int u = 0; u < kIlp; u++) {
                 const int64_t i = i0 + u * stride;
+                if (i >= np) continue;
+                const int32_t v[4] = {h[u].x, h[u].y, h[u].z, h[u].w};
 #pragma unroll
-                for (int j = 0; j < kScalesAtOnce; j++)
-                    if (i < np && k0 + j < n_scales) halo_id[(k0 + j) * np + i] = h[u][j];
+                for (int j = 0; j < 4; j++)
+                    if (k0 + j < n_scales) halo_id[(k0 + j) * np + i] = v[j];
             }
         }
     }
@@ -382,7 +390,8 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
     CWTHF_LAUNCH(ctx, s, "k_halo_sums",
                  k_halo_sums<<<cblocks, kHsThreads, 0, s>>>(a, ctx->dep_off + total_key, ctx->dep_rec, ctx->dep_mq,
                                                           label, ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc,
-                                                          ctx->part_slot + scale, n_scales, ctx->d_mtot));
+                                                          ctx->part_slot + scale, slot_group_stride(n_scales),
+                                                          ctx->d_mtot));
     FilterArgs f;
     f.ng = ng;
     f.L = L;
