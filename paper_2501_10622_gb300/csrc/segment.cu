@@ -18,6 +18,8 @@
 // rounds if ever needed; hitting the round bound is reported as
 // CWTHF_E_NOT_CONVERGED).  The result does not depend on update order: every
 // update moves a pointer further along the (unique) chain.
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace cwthf {
@@ -72,6 +74,9 @@ __device__ __forceinline__ int pick3(float a, float b, float c, float M, int ka,
     const int x = min(min(a == M ? ka : kNoMatch, b == M ? kb : kNoMatch), c == M ? kc : kNoMatch);
     return x & 3;
 }
+// The same away from the periodic boundary, where the strict order ranks the
+// three candidates in position order.
+__device__ __forceinline__ int pick3i(float a, float b, float M) { return a == M ? 0 : (b == M ? 1 : 2); }
 
 // Parent code of every cell.  The best of the 27 cells around c is found in
 // two steps: first the maximum value M, separably (x by warp shuffles, y
@@ -83,45 +88,43 @@ __device__ __forceinline__ int pick3(float a, float b, float c, float M, int ka,
 // column holding M.  The row and column choices of every plane are kept as
 // 2-bit codes per row (x: 10 rows in one word, y + x: 8 rows in one word), so
 // a cell's search ends with a z choice and a few bit extractions.
-__global__ void __launch_bounds__(kParThreads, 4) k_seg_parent(const float* __restrict__ C, int ng, float cwt_min,
-                                                            uint8_t* __restrict__ code_out,
-                                                            uint32_t* __restrict__ seed_bits, int* status) {
+// One warp's block.  XI / YI: the block's owned columns / rows are away from
+// the periodic boundary, where the x / y choices reduce to position order;
+// the z choice takes the same shortcut on every plane but the two wrapped ones.
+template <bool XI, bool YI>
+__device__ __forceinline__ void parent_block(const float* __restrict__ C, int N, float cwt_min,
+                                             uint8_t* __restrict__ code_out, uint32_t* __restrict__ seed_bits,
+                                             int* status, int x0, int y0, int z0, int wzc) {
     constexpr int R = kParR, NR = kParR + 2;
-    const int N = ng;
-    const int nbx = (N + 29) / 30, nby = (N + R - 1) / R;
-    const int64_t warp = (int64_t(blockIdx.x) * kParThreads + threadIdx.x) >> 5;
-    const int64_t nwarps = int64_t(nbx) * nby * ((N + kParZ - 1) / kParZ);
-    if (warp >= nwarps) return;  // warp-uniform
-    const int by = int(warp % nby), bx = int((warp / nby) % nbx), bz = int(warp / (int64_t(nby) * nbx));
-    const int x0 = bx * 30, y0 = by * R, z0 = bz * kParZ;
-    const int wzc = min(kParZ, N - z0);
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
     const int xc = ((x0 + lane - 1) % N + N) % N;
     const bool own_x = lane >= 1 && lane <= 30 && x0 + lane - 1 < N;
-    int kxm, kxc, kxp;
-    codes3(wrap(xc - 1, N), xc, wrap(xc + 1, N), kxm, kxc, kxp);
-    // rows y0-1 .. y0+R (wrapped) and the y codes of the owned rows, packed
-    // km | kc << 4 | kp << 8 per row (they differ from the interior only at y = 0, N-1)
-    int yrow[NR];
+    int kxm = 0, kxc = 5, kxp = 10;
+    if (!XI) codes3(wrap(xc - 1, N), xc, wrap(xc + 1, N), kxm, kxc, kxp);
+    // offsets of the rows y0-1 .. y0+R (wrapped) and the y codes of the owned
+    // rows, packed km | kc << 4 | kp << 8 per row
+    int32_t yoff[NR];
 #pragma unroll
-    for (int j = 0; j < NR; j++) yrow[j] = ((y0 - 1 + j) % N + N) % N;
+    for (int j = 0; j < NR; j++) yoff[j] = (((y0 - 1 + j) % N + N) % N) * N;
     int ykc[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
-        int a, b, c;
-        codes3(yrow[r], yrow[r + 1], yrow[r + 2], a, b, c);
-        ykc[r] = a | (b << 4) | (c << 8);
+        ykc[r] = 0 | (5 << 4) | (10 << 8);
+        if (!YI) {
+            int a, b, c;
+            codes3(yoff[r] / N, yoff[r + 1] / N, yoff[r + 2] / N, a, b, c);
+            ykc[r] = a | (b << 4) | (c << 8);
+        }
     }
-    const size_t plane = size_t(N) * N;
-    // column pointer of each row
+    const int32_t plane = N * N;
     const float* colp = C + xc;
     float v[NR], vn[NR];
     auto load_plane = [&](int p, float (&dst)[NR]) {
         const int z = ((z0 - 1 + p) % N + N) % N;
-        const float* base = colp + size_t(z) * plane;
+        const float* base = colp + size_t(z) * size_t(plane);
 #pragma unroll
-        for (int j = 0; j < NR; j++) dst[j] = __ldg(base + size_t(yrow[j]) * N);
+        for (int j = 0; j < NR; j++) dst[j] = __ldg(base + yoff[j]);
     };
     load_plane(0, v);
     float pm0[R], pm1[R], pm2[R];  // y-window maxima of planes p-2, p-1, p (per owned row)
@@ -141,14 +144,16 @@ __global__ void __launch_bounds__(kParThreads, 4) k_seg_parent(const float* __re
             bad |= (v[j] != v[j]);
             const float vl = __shfl_up_sync(full, v[j], 1), vr = __shfl_down_sync(full, v[j], 1);
             rm[j] = fmaxf(fmaxf(vl, v[j]), vr);
-            xcp |= uint32_t(pick3(vl, v[j], vr, rm[j], kxm, kxc, kxp)) << (2 * j);
+            const int cx = XI ? pick3i(vl, v[j], rm[j]) : pick3(vl, v[j], vr, rm[j], kxm, kxc, kxp);
+            xcp |= uint32_t(cx) << (2 * j);
         }
         // y windows of the owned rows and their (y, x) choices
         uint32_t yxp = 0;
 #pragma unroll
         for (int r = 0; r < R; r++) {
             const float m = fmaxf(fmaxf(rm[r], rm[r + 1]), rm[r + 2]);
-            const int cy = pick3(rm[r], rm[r + 1], rm[r + 2], m, ykc[r] & 15, (ykc[r] >> 4) & 15, ykc[r] >> 8);
+            const int cy = YI ? pick3i(rm[r], rm[r + 1], m)
+                              : pick3(rm[r], rm[r + 1], rm[r + 2], m, ykc[r] & 15, (ykc[r] >> 4) & 15, ykc[r] >> 8);
             const uint32_t cx = (xcp >> (2 * (r + cy))) & 3u;
             yxp |= (uint32_t(cy) | (cx << 2)) << (4 * r);
             pm0[r] = pm1[r];
@@ -159,35 +164,58 @@ __global__ void __launch_bounds__(kParThreads, 4) k_seg_parent(const float* __re
         yx1 = yx2;
         yx2 = yxp;
         if (p >= 2) {
-            // the cells of plane p-1 (z = z0 + p - 2); z codes differ from the
-            // interior ones only on the two wrapped planes
+            // the cells of plane p-1 (z = z0 + p - 2)
             const int zc = z0 + p - 2;
             const bool zlo = zc == 0, zhi = zc == N - 1;
             const int kzm = zlo ? 8 : (zhi ? 4 : 0), kzc = zlo ? 1 : (zhi ? 9 : 5), kzp = zlo ? 6 : (zhi ? 2 : 10);
-            uint8_t* out = code_out + size_t(zc) * plane + xc;
+            uint8_t* out = code_out + size_t(zc) * size_t(plane) + xc;
+            const int32_t gz = zc * plane + xc;
+            auto emit = [&](auto zi) {
 #pragma unroll
-            for (int r = 0; r < R; r++) {
-                const float M = fmaxf(fmaxf(pm0[r], pm1[r]), pm2[r]);
-                const int cz = pick3(pm0[r], pm1[r], pm2[r], M, kzm, kzc, kzp);
-                const uint32_t yx = cz == 0 ? yx0 : (cz == 1 ? yx1 : yx2);
-                const uint32_t f = (yx >> (4 * r)) & 15u;
-                uint32_t code = (f >> 2) | ((f & 3u) << 2) | (uint32_t(cz) << 4);
-                const bool seed = code == kCodeMax && M > cwt_min;
-                code |= seed ? kCodeSeed : 0u;
-                if (own_x && y0 + r < N) {
-                    const size_t y = size_t(yrow[r + 1]);
-                    out[y * N] = uint8_t(code);
-                    if (seed) {
-                        const uint32_t g = uint32_t((size_t(zc) * N + y) * N + xc);
-                        atomicOr(&seed_bits[g >> 5], 1u << (g & 31));
+                for (int r = 0; r < R; r++) {
+                    const float M = fmaxf(fmaxf(pm0[r], pm1[r]), pm2[r]);
+                    const int cz = decltype(zi)::value ? pick3i(pm0[r], pm1[r], M)
+                                                       : pick3(pm0[r], pm1[r], pm2[r], M, kzm, kzc, kzp);
+                    const uint32_t yx = cz == 0 ? yx0 : (cz == 1 ? yx1 : yx2);
+                    const uint32_t f = (yx >> (4 * r)) & 15u;
+                    uint32_t code = (f >> 2) | ((f & 3u) << 2) | (uint32_t(cz) << 4);
+                    const bool seed = code == kCodeMax && M > cwt_min;
+                    code |= seed ? kCodeSeed : 0u;
+                    if (own_x && y0 + r < N) {
+                        out[yoff[r + 1]] = uint8_t(code);
+                        if (seed) {
+                            const uint32_t g = uint32_t(gz + yoff[r + 1]);
+                            atomicOr(&seed_bits[g >> 5], 1u << (g & 31));
+                        }
                     }
                 }
-            }
+            };
+            if (!zlo && !zhi) emit(std::integral_constant<bool, true>{});  // uniform: once per plane
+            else emit(std::integral_constant<bool, false>{});
         }
 #pragma unroll
         for (int j = 0; j < NR; j++) v[j] = vn[j];
     }
     if (bad) set_status(status, CWTHF_E_BAD_INPUT);
+}
+
+__global__ void __launch_bounds__(kParThreads, 4) k_seg_parent(const float* __restrict__ C, int ng, float cwt_min,
+                                                            uint8_t* __restrict__ code_out,
+                                                            uint32_t* __restrict__ seed_bits, int* status) {
+    constexpr int R = kParR;
+    const int N = ng;
+    const int nbx = (N + 29) / 30, nby = (N + R - 1) / R;
+    const int64_t warp = (int64_t(blockIdx.x) * kParThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = int64_t(nbx) * nby * ((N + kParZ - 1) / kParZ);
+    if (warp >= nwarps) return;  // warp-uniform
+    const int by = int(warp % nby), bx = int((warp / nby) % nbx), bz = int(warp / (int64_t(nby) * nbx));
+    const int x0 = bx * 30, y0 = by * R, z0 = bz * kParZ;
+    const int wzc = min(kParZ, N - z0);
+    // warp-uniform: owned columns x0 .. x0+29 and rows y0 .. y0+R-1 clear of 0 and N-1
+    if (x0 > 0 && x0 + 30 < N && y0 > 0 && y0 + R < N)
+        parent_block<true, true>(C, N, cwt_min, code_out, seed_bits, status, x0, y0, z0, wzc);
+    else
+        parent_block<false, false>(C, N, cwt_min, code_out, seed_bits, status, x0, y0, z0, wzc);
 }
 
 // In-tile chains of a 32 x 16 x 32-cell tile from the parent codes.  Every
