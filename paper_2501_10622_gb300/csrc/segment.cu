@@ -229,8 +229,7 @@ __global__ void __launch_bounds__(kParThreads, 4) k_seg_parent(const float* __re
 __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __restrict__ codes, int ng,
                                                            int32_t* __restrict__ label,
                                                            uint16_t* __restrict__ seed_cells,
-                                                           uint32_t* __restrict__ queue, uint32_t* __restrict__ qcount,
-                                                           int* status) {
+                                                           uint32_t* __restrict__ ballots, int* status) {
     extern __shared__ int32_t ptr[];  // [kLocal], dynamic
     __shared__ uint16_t tile_seeds[kTileSeedCap];
     __shared__ uint32_t n_tile_seeds;
@@ -313,19 +312,16 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
     // every pointer now names a root (its cell's seed), -1, or -2 - g (a cell
     // outside): labels, and one count per cell for the tile's seeds, kept in
     // the upper half of the seed's own entry (readers mask it off)
-    // Cells whose chain leaves the tile (flagged) are queued for the global
-    // pass: each warp keeps its per-plane ballots, the CTA reserves one range
-    // of the queue with a single atomic, and each warp then writes its cells.
-    __shared__ uint32_t fl_ballot[kChTY][kChTZ];
-    __shared__ uint32_t fl_base[kChTY];
+    // Cells whose chain leaves the tile (flagged) are handed to the global pass
+    // as one 32-bit mask per row and plane of the tile (bit = column), written
+    // as the tile's [16 rows][32 planes] block of masks.
     const int32_t gbase = (z0 * N + y0) * N + x0;
     const unsigned full = 0xffffffffu;
-    const uint32_t gcell0 = uint32_t((z0 * N + yc) * N + xc);
     int32_t* out = label + (size_t(z0) * N + yc) * N + xc;
-    uint32_t nfl = 0;  // flagged cells of this warp (the same in every lane)
-    for (int lz = 0; lz < wz; lz++, out += size_t(plane32)) {  // block-uniform trip count
+    uint32_t* my_ballots = ballots + (size_t(t) * kChTY + ly) * kChTZ;
+    for (int lz = 0; lz < kChTZ; lz++, out += size_t(plane32)) {  // block-uniform trip count
         bool fl = false;
-        if (own) {
+        if (own && lz < wz) {
             const int i = i0 + lz * kPlaneL;
             const int32_t v = ptr[i];
             const int32_t cur = v >= 0 ? (v & kLocalMask) : v;
@@ -350,29 +346,7 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
             *out = res;
         }
         const unsigned b = __ballot_sync(full, fl);
-        if (lx == 0) fl_ballot[ly][lz] = b;
-        nfl += __popc(b);
-    }
-    if (lx == 0) fl_base[ly] = nfl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t tot = 0;
-        for (int k = 0; k < kChTY; k++) {
-            const uint32_t c = fl_base[k];
-            fl_base[k] = tot;
-            tot += c;
-        }
-        const uint32_t base = tot ? atomicAdd(qcount, tot) : 0u;
-        for (int k = 0; k < kChTY; k++) fl_base[k] += base;
-    }
-    __syncthreads();
-    if (nfl) {  // warp-uniform
-        uint32_t at = fl_base[ly];
-        for (int lz = 0; lz < wz; lz++) {
-            const uint32_t b = fl_ballot[ly][lz];
-            if (b & (1u << lx)) queue[at + __popc(b & ((1u << lx) - 1u))] = gcell0 + uint32_t(lz) * uint32_t(plane32);
-            at += __popc(b);
-        }
+        if (lx == lz) my_ballots[lz] = b;  // lane lz stores plane lz's mask (coalesced per warp)
     }
     __syncthreads();
     // in-tile cell counts of this tile's seeds (cells reaching them from other
@@ -387,47 +361,95 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
 }
 
 constexpr int kResolveThreads = 256;
+constexpr int kResolveRows = 4;  // tile rows a warp takes at a time
 
-// The global pass over the cells the tile pass queued (those whose chain left
-// their tile): each follows its chain through the label grid (at most
-// kChaseLimit steps), takes the label it reaches, and is counted for that
-// seed, one atomic per distinct seed among a warp's 32 cells.  A cell still
-// unfinished at the limit stays flagged and sets changed[0]; the doubling
-// rounds then finish it and the cells are recounted.  Labels read while other
-// threads update them are always a later point of the same chain, so the
-// result does not depend on timing.
-__global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __restrict__ label,
-                                                                 const uint32_t* __restrict__ queue,
-                                                                 const uint32_t* __restrict__ qcount,
+// The global pass over the cells whose chain left their tile.  Each warp
+// takes kResolveRows tile rows at a time from a shared counter (the flagged
+// cells crowd where the field is clumped, so a fixed split of the rows leaves
+// some warps far more work than others) and gathers the flagged cells of their non-empty
+// plane masks into a shared batch; every full batch of 32 cells (and the last,
+// partial one) is resolved by the whole warp: each lane follows its cell's
+// chain through the label grid (at most kChaseLimit steps), takes the label it
+// reaches and the cells are counted with one atomic per distinct seed.  A cell
+// still unfinished at the limit stays flagged and sets changed[0]; the
+// doubling rounds then finish it and the cells are recounted.  Labels read
+// while other threads update them are always a later point of the same chain,
+// so the result does not depend on timing.
+__device__ __forceinline__ void resolve_batch(int32_t* __restrict__ label, bool valid, uint32_t c,
+                                              const uint32_t* __restrict__ bits,
+                                              const uint32_t* __restrict__ prefix,
+                                              const uint32_t* __restrict__ n_slots, HaloAcc* acc, bool& left) {
+    int32_t lab = -1;
+    if (valid) {
+        int32_t w = label[c];
+        int steps = 0;
+        while (w >= 0 && (w & kFlag) && steps < kChaseLimit) {
+            w = label[w & kMask];
+            steps++;
+        }
+        label[c] = w;
+        if (w >= 0 && (w & kFlag)) left = true;
+        else lab = w;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, lab);  // every lane
+    uint32_t slot;
+    if (lab >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1 && seed_slot(bits, prefix, n_slots, lab, slot))
+        atomicAdd(&acc[slot].n_cells, (unsigned long long)__popc(peers));
+}
+
+__global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __restrict__ label, int ng,
+                                                                 const uint32_t* __restrict__ ballots,
                                                                  const uint32_t* __restrict__ bits,
                                                                  const uint32_t* __restrict__ prefix,
                                                                  const uint32_t* __restrict__ n_slots,
-                                                                 HaloAcc* acc, int* __restrict__ changed) {
+                                                                 HaloAcc* acc, int* __restrict__ changed,
+                                                                 unsigned* __restrict__ next_row) {
+    __shared__ uint32_t batch[kResolveThreads / 32][64];  // pending cells (fewer than 32 between batches)
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int64_t n = *qcount;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t* wl = batch[threadIdx.x >> 5];
+    const int N = ng;
+    const int ntx = (N + kChTX - 1) / kChTX, nty = (N + kChTY - 1) / kChTY, ntz = (N + kChTZ - 1) / kChTZ;
+    const int64_t rows = int64_t(ntx) * nty * ntz * kChTY;
+    const uint32_t plane32 = uint32_t(N) * uint32_t(N);
     bool left = false;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-        const int64_t e = base + lane;  // warp-uniform trip count
-        int32_t lab = -1;
-        if (e < n) {
-            const uint32_t c = queue[e];
-            int32_t w = label[c];
-            int steps = 0;
-            while (w >= 0 && (w & kFlag) && steps < kChaseLimit) {
-                w = label[w & kMask];
-                steps++;
+    uint32_t k = 0;  // warp-uniform
+    for (;;) {
+        unsigned r0 = 0;
+        if (lane == 0) r0 = atomicAdd(next_row, unsigned(kResolveRows));
+        r0 = __shfl_sync(full, r0, 0);
+        if (int64_t(r0) >= rows) break;  // warp-uniform (rows < 2^21 for ng <= 1024)
+        const int64_t rend = min(int64_t(r0) + kResolveRows, rows);
+        for (int64_t rw = int64_t(r0); rw < rend; rw++) {
+            const int64_t t = rw / kChTY;
+            const int ly = int(rw % kChTY);
+            const int tx = int(t % ntx), ty = int((t / ntx) % nty), tz = int(t / (int64_t(ntx) * nty));
+            const int yc = ty * kChTY + ly;
+            if (yc >= N) continue;  // warp-uniform
+            const uint32_t mine = ballots[rw * kChTZ + lane];  // plane `lane`'s mask
+            uint32_t planes = __ballot_sync(full, mine != 0u);
+            const uint32_t cell0 = uint32_t((int64_t(tz) * kChTZ * N + yc) * N + int64_t(tx) * kChTX) + uint32_t(lane);
+            while (planes) {
+                const int lz = __ffs(planes) - 1;
+                planes &= planes - 1u;
+                const uint32_t b = __shfl_sync(full, mine, lz);
+                if (b & (1u << lane)) wl[k + __popc(b & lt)] = cell0 + uint32_t(lz) * plane32;
+                k += __popc(b);
+                if (k >= 32) {
+                    __syncwarp();
+                    resolve_batch(label, true, wl[lane], bits, prefix, n_slots, acc, left);
+                    const uint32_t rest = wl[32 + lane];
+                    __syncwarp();
+                    if (uint32_t(lane) + 32 < k) wl[lane] = rest;
+                    k -= 32;
+                    __syncwarp();
+                }
             }
-            label[c] = w;
-            if (w >= 0 && (w & kFlag)) left = true;
-            else lab = w;
         }
-        const unsigned peers = __match_any_sync(full, lab);  // every lane, every iteration
-        uint32_t slot;
-        if (lab >= 0 && lane == __ffs(peers) - 1 && seed_slot(bits, prefix, n_slots, lab, slot))
-            atomicAdd(&acc[slot].n_cells, (unsigned long long)__popc(peers));
     }
+    __syncwarp();
+    if (k) resolve_batch(label, uint32_t(lane) < k, uint32_t(lane) < k ? wl[lane] : 0u, bits, prefix, n_slots, acc, left);
     if (__any_sync(full, left) && lane == 0) changed[0] = 1;
 }
 
@@ -550,32 +572,35 @@ int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_
     int64_t cells = int64_t(ng) * ng * ng;
     int64_t nwords = (cells + 31) / 32;
     cudaError_t e = cudaMemsetAsync(ctx->seed_bits, 0, size_t(nwords) * 4, s);
-    // jump_changed[0 .. kMaxJumpRounds]: round flags; [kMaxJumpRounds + 1]: queued cells
+    // jump_changed[0 .. kMaxJumpRounds]: round flags; [kMaxJumpRounds + 1]: the
+    // resolve pass's row counter
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->jump_changed, 0, sizeof(int) * (kMaxJumpRounds + 2), s);
     if (e != cudaSuccess) return cuda_status(e);
-    // parent codes (1 byte per cell) and the queue of flagged cells (4 bytes per
-    // cell at most) in the context's int64 grid buffer (8 bytes per cell, free
-    // once the forward transform has read it), then the in-tile chains
+    // parent codes (1 byte per cell) and the flagged-cell masks of every chain
+    // tile (one bit per cell) in the context's int64 grid buffer (8 bytes per
+    // cell, free once the forward transform has read it), then the in-tile chains
     uint8_t* codes = reinterpret_cast<uint8_t*>(ctx->grid);
-    uint32_t* queue = reinterpret_cast<uint32_t*>(codes + (size_t(cells) + 255) / 256 * 256);
-    uint32_t* qcount = reinterpret_cast<uint32_t*>(ctx->jump_changed + kMaxJumpRounds + 1);
+    uint32_t* ballots = reinterpret_cast<uint32_t*>(codes + (size_t(cells) + 255) / 256 * 256);
+    const int64_t ntiles = int64_t(div_up(ng, kChTX)) * div_up(ng, kChTY) * div_up(ng, kChTZ);
+    if ((cells + 255) / 256 * 256 + ntiles * (kChTY * kChTZ * 4) > cells * 8) return CWTHF_E_UNSUPPORTED_SIZE;
     const int64_t pwarps = int64_t(div_up(ng, 30)) * div_up(ng, kParR) * div_up(ng, kParZ);
     CWTHF_LAUNCH(ctx, s, "k_seg_parent",
                  k_seg_parent<<<unsigned(div_up(pwarps, int64_t(kParWarps))), kParThreads, 0, s>>>(
                      cwt, ng, cwt_min, codes, ctx->seed_bits, ctx->d_status));
-    const int64_t ntiles = int64_t(div_up(ng, kChTX)) * div_up(ng, kChTY) * div_up(ng, kChTZ);
     cudaFuncSetAttribute(k_seg_chase, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sizeof(int32_t) * kLocal));
     CWTHF_LAUNCH(ctx, s, "k_seg_chase",
                  k_seg_chase<<<unsigned(ntiles), kChThreads, sizeof(int32_t) * kLocal, s>>>(
-                     codes, ng, label, ctx->seed_cells, queue, qcount, ctx->d_status));
+                     codes, ng, label, ctx->seed_cells, ballots, ctx->d_status));
     // seed ranks first (the resolve pass counts cells per seed slot)
     int rc = seeds_rank(ctx, ng, ctx->seed_cells, s);
     if (rc) return rc;
     int blocks = ctx->sm_count * 8;
     CWTHF_LAUNCH(ctx, s, "k_seg_resolve",
-                 k_seg_resolve<<<blocks, kResolveThreads, 0, s>>>(label, queue, qcount, ctx->seed_bits,
+                 k_seg_resolve<<<blocks, kResolveThreads, 0, s>>>(label, ng, ballots, ctx->seed_bits,
                                                                    ctx->seed_prefix, ctx->n_seeds, ctx->acc,
-                                                                   ctx->jump_changed));
+                                                                   ctx->jump_changed,
+                                                                   reinterpret_cast<unsigned*>(
+                                                                       ctx->jump_changed + kMaxJumpRounds + 1)));
     // pointer doubling for whatever the bounded walks left (normally nothing: every round exits at once)
     for (int r = 1; r < kMaxJumpRounds; r++) {
         CWTHF_LAUNCH(ctx, s, "k_seg_jump", k_seg_jump<<<blocks, 256, 0, s>>>(label, cells, ctx->jump_changed, r));
