@@ -150,7 +150,7 @@ def algorithmic_bytes(name, u):
         # count the bench does not see), so no algorithmic figure
         "k_count_cells": 4 * cells,
         "k_halo_sums": 8 * npart + 4 * npart + 4 * npart,    # records, label gather, slot out
-        "k_rec_halo": 8 * npart * u.get("scales", 1),               # record slots in, halo ids out
+        "k_rec_halo": 4 * npart * u.get("scales", 1) + 16 * npart * ((u.get("scales", 1) + 3) // 4),  # slots in, id groups out
         "k_finalize": 4 * npart + 8 * npart * u.get("scales", 1),   # record position; per scale id in and out
     }
     return table.get(name)

@@ -303,25 +303,37 @@ __global__ void __launch_bounds__(kThreads) k_catalogue(const HaloAcc* __restric
     }
 }
 
-// Per-record slots are stored in groups of four scales (16 bytes, aligned),
+// Each scale's pass stores its record slots contiguously (rec_slot[scale * np
+// + r]: whole sectors written, none read back).  After the last scale the halo
+// ids are regrouped per record in groups of four scales (16 bytes, aligned),
 // so that the final pass reads a particle's ids for four scales with one
 // vector gather.
 __host__ __device__ __forceinline__ int slot_group_stride(int n_scales) { return (n_scales + 3) & ~3; }
+__host__ __device__ __forceinline__ int64_t slot_groups_offset(int n_scales, int64_t np) {
+    return (int64_t(n_scales) * np + 3) & ~int64_t(3);
+}
 
-// Record order, after the last scale: each stored record slot becomes its
-// halo id (the slot's seed if the halo was kept, else -1), in place.  Records
-// are grouped by tile, so the slot lookups are coherent.
-__global__ void __launch_bounds__(kThreads) k_rec_halo(int32_t* __restrict__ rec_slot,
+// Record order, after the last scale: each record's slot of every scale becomes
+// its halo id (the slot's seed if the halo was kept, else -1), written to the
+// record's group.  Records are grouped by tile, so the slot lookups are
+// coherent.
+__global__ void __launch_bounds__(kThreads) k_rec_halo(const int32_t* __restrict__ rec_slot, int64_t np,
                                                       const uint32_t* __restrict__ total_ptr, int n_scales,
-                                                      const int32_t* __restrict__ slot_halo, int64_t slot_stride) {
+                                                      const int32_t* __restrict__ slot_halo, int64_t slot_stride,
+                                                      int4* __restrict__ groups) {
     const int64_t total = *total_ptr;
-    const int rs = slot_group_stride(n_scales);
+    const int ng4 = slot_group_stride(n_scales) / 4;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < total; r += stride) {
-        int32_t* e = rec_slot + r * rs;
-        for (int k = 0; k < n_scales; k++) {
-            const int32_t sl = e[k];
-            e[k] = sl >= 0 ? slot_halo[k * slot_stride + sl] : -1;
+        for (int g = 0; g < ng4; g++) {
+            int32_t v[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int k = 4 * g + j;
+                const int32_t sl = k < n_scales ? rec_slot[k * np + r] : -1;
+                v[j] = sl >= 0 ? slot_halo[k * slot_stride + sl] : -1;
+            }
+            groups[r * ng4 + g] = make_int4(v[0], v[1], v[2], v[3]);
         }
     }
 }
@@ -390,8 +402,7 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
     CWTHF_LAUNCH(ctx, s, "k_halo_sums",
                  k_halo_sums<<<cblocks, kHsThreads, 0, s>>>(a, ctx->dep_off + total_key, ctx->dep_rec, ctx->dep_mq,
                                                           label, ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc,
-                                                          ctx->part_slot + scale, slot_group_stride(n_scales),
-                                                          ctx->d_mtot));
+                                                          ctx->part_slot + int64_t(scale) * np, 1, ctx->d_mtot));
     FilterArgs f;
     f.ng = ng;
     f.L = L;
@@ -406,12 +417,14 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
                                                          cat, ctx->slot_halo + int64_t(scale) * slot_cap, n_halo,
                                                          ctx->d_status));
     if (scale == n_scales - 1) {  // halo ids of all scales at once
+        int4* groups = reinterpret_cast<int4*>(ctx->part_slot + slot_groups_offset(n_scales, np));
         CWTHF_LAUNCH(ctx, s, "k_rec_halo",
-                     k_rec_halo<<<blocks, kThreads, 0, s>>>(ctx->part_slot, ctx->dep_off + total_key, n_scales,
-                                                            ctx->slot_halo, slot_cap));
+                     k_rec_halo<<<blocks, kThreads, 0, s>>>(ctx->part_slot, np, ctx->dep_off + total_key, n_scales,
+                                                            ctx->slot_halo, slot_cap, groups));
         CWTHF_LAUNCH(ctx, s, "k_finalize",
                      k_finalize<<<pblocks, kThreads, 0, s>>>(ctx->part_rec, np, ctx->dep_off + total_key,
-                                                             ctx->part_slot, n_scales, halo_id));
+                                                             reinterpret_cast<const int32_t*>(groups), n_scales,
+                                                             halo_id));
     }
     return cuda_status(cudaGetLastError());
 }
