@@ -146,13 +146,15 @@ __global__ void __launch_bounds__(kTileThreads) k_dep_tile(DepArgs a, const uint
                                                           const unsigned long long* __restrict__ mtot,
                                                           int64_t* __restrict__ grid, int* status) {
     constexpr int kCells = kDepTX * kDepTY * kDepTZ;
-    __shared__ uint32_t acc_lo[kCells], acc_hi[kCells];
+    __shared__ __align__(16) uint32_t acc_lo[kCells];
+    __shared__ __align__(16) uint32_t acc_hi[kCells];
     __shared__ uint32_t seg_beg[kReachSegments], seg_pre[kReachSegments + 1];
     __shared__ uint8_t seg_m[kReachSegments];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x == 0 && *mtot >= (1ull << 33)) set_status(status, CWTHF_E_OVERFLOW);
     const int64_t ntiles = int64_t(a.ntx) * a.nty * a.ntz;
     const int64_t ng = a.ng;
+    const bool vec = (reinterpret_cast<uintptr_t>(grid) & 15u) == 0 && (ng & 1) == 0;  // 16-byte cell pairs
     for (int c = threadIdx.x; c < kCells; c += kTileThreads) {
         acc_lo[c] = 0u;
         acc_hi[c] = 0u;
@@ -214,9 +216,11 @@ __global__ void __launch_bounds__(kTileThreads) k_dep_tile(DepArgs a, const uint
             if (m & 1) lx = -1;
             if (m & 2) ly = -1;
             if (m & 4) lz = -1;
-            const u64 wxv[2] = {u64(kFracOne - fx), u64(fx)};
-            const u64 wyv[2] = {u64(kFracOne - fy), u64(fy)};
-            const u64 wzv[2] = {u64(kFracOne - fz), u64(fz)};
+            // corner weights: products of three factors <= 2^kFracBits fit 32 bits
+            static_assert(3 * kFracBits <= 32, "corner weight product");
+            const uint32_t wxv[2] = {uint32_t(kFracOne - fx), uint32_t(fx)};
+            const uint32_t wyv[2] = {uint32_t(kFracOne - fy), uint32_t(fy)};
+            const uint32_t wzv[2] = {uint32_t(kFracOne - fz), uint32_t(fz)};
             // a warp whose 32 records all share one base cell (dense clumps) folds its
             // 8 corner sums with full-warp reductions; otherwise every lane adds its own
             // corners (native 32-bit shared atomics; same-cell lanes serialise briefly)
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(kTileThreads) k_dep_tile(DepArgs a, const uint
 #pragma unroll
             for (int q = 0; q < 8; q++) {
                 const int ex = q & 1, ey = (q >> 1) & 1, ez = (q >> 2) & 1;
-                u64 v = u64(mq) * wxv[ex] * wyv[ey] * wzv[ez];
+                u64 v = u64(mq) * (wxv[ex] * wyv[ey] * wzv[ez]);
                 if (uniform) v = warp_sum64(v);  // warp-uniform branch
                 const int cx = lx + ex, cy = ly + ey, cz = lz + ez;
                 if (live && (!uniform || lane == 0) && v && cx >= 0 && cx < wx && cy >= 0 && cy < wy && cz >= 0 &&
@@ -236,13 +240,28 @@ __global__ void __launch_bounds__(kTileThreads) k_dep_tile(DepArgs a, const uint
         }
         __syncthreads();
         if (warp == 0) fetch(t + gridDim.x, nb, ne);  // the next tile's ranges, in flight during the write-out
-        for (int c = threadIdx.x; c < kCells; c += kTileThreads) {
-            const int cx = c % kDepTX, cy = (c / kDepTX) % kDepTY, cz = c / (kDepTX * kDepTY);
-            if (cx < wx && cy < wy && cz < wz)
-                grid[(int64_t(z0 + cz) * ng + (y0 + cy)) * ng + (x0 + cx)] =
-                    int64_t((u64(acc_hi[c]) << 32) | u64(acc_lo[c]));
-            acc_lo[c] = 0u;
-            acc_hi[c] = 0u;
+        if (vec && wx == kDepTX && wy == kDepTY && wz == kDepTZ) {
+            // a whole tile: two cells per thread and step, one 16-byte store each
+            // (a warp writes two 256-byte row segments)
+            int64_t* tg = grid + (int64_t(z0) * ng + y0) * ng + x0;
+            const int32_t plane = int32_t(ng) * int32_t(ng);
+            for (int c = 2 * threadIdx.x; c < kCells; c += 2 * kTileThreads) {
+                const int cx = c & (kDepTX - 1), cy = (c / kDepTX) & (kDepTY - 1), cz = c / (kDepTX * kDepTY);
+                const uint2 lo = *reinterpret_cast<const uint2*>(&acc_lo[c]);
+                const uint2 hi = *reinterpret_cast<const uint2*>(&acc_hi[c]);
+                *reinterpret_cast<uint4*>(tg + (cz * plane + cy * int32_t(ng) + cx)) = make_uint4(lo.x, hi.x, lo.y, hi.y);
+                *reinterpret_cast<uint2*>(&acc_lo[c]) = make_uint2(0u, 0u);
+                *reinterpret_cast<uint2*>(&acc_hi[c]) = make_uint2(0u, 0u);
+            }
+        } else {
+            for (int c = threadIdx.x; c < kCells; c += kTileThreads) {
+                const int cx = c % kDepTX, cy = (c / kDepTX) % kDepTY, cz = c / (kDepTX * kDepTY);
+                if (cx < wx && cy < wy && cz < wz)
+                    grid[(int64_t(z0 + cz) * ng + (y0 + cy)) * ng + (x0 + cx)] =
+                        int64_t((u64(acc_hi[c]) << 32) | u64(acc_lo[c]));
+                acc_lo[c] = 0u;
+                acc_hi[c] = 0u;
+            }
         }
         __syncthreads();
     }
