@@ -446,7 +446,11 @@ def main():
             stream.wait_stream(down)
 
         def timed(fn):
-            fn(1)
+            # warm-up: at least two steps, so that both halves of every double
+            # buffer (pinned host and device) have been through a copy before
+            # the timed steps (the first copy through a pinned buffer runs at
+            # about half speed)
+            fn(max(2, args.warmup))
             torch.cuda.synchronize(dev)
             barrier()
             f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

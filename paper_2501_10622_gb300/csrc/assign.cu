@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const uint32_t* __restric
                                                       const uint32_t* __restrict__ total_ptr,
                                                       const int32_t* __restrict__ rec_halo, int n_scales,
                                                       int32_t* __restrict__ halo_id) {
-    constexpr int kIlp = 4;
+    constexpr int kIlp = 8;
     const int64_t total = *total_ptr;
     const int rs = slot_group_stride(n_scales);
     const int4* rec4 = reinterpret_cast<const int4*>(rec_halo);

@@ -25,7 +25,7 @@ constexpr int kCountThreads = 256;
 // several mid-sized CTAs per SM keep more tiles in flight than a few large
 // ones (two warps per CTA measured slower: too few threads for the write-out).
 constexpr int kTileThreads = 128;
-constexpr int kTileCtasPerSm = 8;
+constexpr int kTileCtasPerSm = 10;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kInvalidKey = 0xffffffffu;
 using u64 = unsigned long long;
@@ -140,7 +140,7 @@ __device__ __forceinline__ void reach_pair(int j, int& m, int& cls) {
 // flattened list, so every warp works on full batches whatever the segment
 // sizes; the write-out also clears the shared accumulators for the next tile.
 // Three barriers per tile.
-__global__ void __launch_bounds__(kTileThreads) k_dep_tile(DepArgs a, const uint32_t* __restrict__ off,
+__global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_dep_tile(DepArgs a, const uint32_t* __restrict__ off,
                                                           const unsigned long long* __restrict__ rec,
                                                           const uint32_t* __restrict__ rec_mq,
                                                           const unsigned long long* __restrict__ mtot,
