@@ -35,7 +35,10 @@ __host__ __device__ __forceinline__ int rec_q(unsigned long long e, int d) {
     return int((e >> (kRecBits * d)) & ((1ull << kRecBits) - 1));
 }
 
-constexpr int kMaxJumpRounds = 40;
+// Pointer-doubling rounds of the segmentation's fallback: round r moves every
+// unfinished pointer 2^r links further, so 31 rounds end any chain of a grid
+// of at most 2^30 cells.
+constexpr int kMaxJumpRounds = 32;
 
 // A bounded device wait gives up after this many polls.
 constexpr long long kSpinLimit = 1ll << 20;
