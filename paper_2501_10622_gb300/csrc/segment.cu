@@ -37,7 +37,7 @@ static_assert(kChTX == kPX && kPlaneL == (1 << kPlaneBits), "local index layout"
 constexpr int32_t kFlag = 1 << 30;
 constexpr int32_t kMask = kFlag - 1;
 constexpr int kChaseLimit = 64;  // longest chain the global pass follows per cell before doubling rounds
-constexpr int kJumpRoundsInTile = 16;  // in-place doubling rounds: 2^14 >= cells of a tile
+constexpr int kJumpRoundsInTile = 16;  // in-place jumping rounds (each at least doubles the distance): 2^14 >= cells of a tile
 // Seeds of one tile: at most one local maximum per 2 x 2 x 2 block of cells
 // (any two cells of such a block are neighbours).
 constexpr int kTileSeedCap = (kChTX / 2) * (kChTY / 2) * (kChTZ / 2);
@@ -289,7 +289,8 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
     }
     __syncthreads();
     // Pointer jumping in place, every cell of the tile in lockstep (no divergent
-    // walks): a pointer to a non-root cell takes that cell's pointer, until no
+    // walks): a pointer to a non-root cell moves two links further (the target's
+    // target's pointer, so a round triples the distance covered), until no
     // pointer changes.  A value read while another thread rewrites it is either
     // the old or the new pointer, both points of the same chain.
     for (int round = 0; round < kJumpRoundsInTile; round++) {
@@ -299,8 +300,9 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
                 const int i = i0 + lz * kPlaneL;
                 const int32_t v = ptr[i];
                 if (v >= 0 && v != i) {
-                    const int32_t w = ptr[v];
+                    int32_t w = ptr[v];
                     if (w != v) {
+                        if (w >= 0) w = ptr[w];
                         ptr[i] = w;
                         changed = true;
                     }
