@@ -101,6 +101,11 @@ def run_batched(args, dev):
             "identical_halo_counts": same}
 
 
+# the served stream's slots per grid class and their HBM budget
+SERVED_SLOTS = {96: 6, 192: 4, 288: 3, 384: 2, 512: 2}
+SERVED_BUDGET = 120 * 2 ** 30
+
+
 def run_served(args, dev):
     """Poisson stream (200 jobs/s) of halo-finding jobs with grids 64^3-512^3
     (log-uniform, 2^a 3^b), 8 particles per cell, served by continuous batching
@@ -108,8 +113,7 @@ def run_served(args, dev):
     import torch
     from paper_2501_10622_gb300 import serve
     jobs = serve.poisson_jobs(args.serve_jobs, rate=200.0, lo_ng=64, hi_ng=512, per_cell=8.0, seed=5, device=dev)
-    srv = serve.Server(device=dev, budget_bytes=120 * 2 ** 30,
-                       slots_per_class={96: 6, 192: 4, 288: 3, 384: 2, 512: 2})
+    srv = serve.Server(device=dev, budget_bytes=SERVED_BUDGET, slots_per_class=SERVED_SLOTS)
     try:
         srv.run(jobs)  # warm-up pass (tables, caches)
         for j in jobs:

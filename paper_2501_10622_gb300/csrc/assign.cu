@@ -305,50 +305,81 @@ __global__ void __launch_bounds__(kThreads) k_catalogue(const HaloAcc* __restric
 
 // Each scale's pass stores its record slots contiguously (rec_slot[scale * np
 // + r]: whole sectors written, none read back).  After the last scale the halo
-// ids are regrouped per record in groups of four scales (16 bytes, aligned),
-// so that the final pass reads a particle's ids for four scales with one
-// vector gather.
-__host__ __device__ __forceinline__ int slot_group_stride(int n_scales) { return (n_scales + 3) & ~3; }
-__host__ __device__ __forceinline__ int64_t slot_groups_offset(int n_scales, int64_t np) {
-    return (int64_t(n_scales) * np + 3) & ~int64_t(3);
+// ids are regrouped per record, RS ids per record (one scale: in place; two:
+// 8-byte groups; more: 16-byte groups of four scales), so that the final pass
+// reads a particle's ids with one vector gather per four scales.
+__host__ __device__ __forceinline__ int slot_group_stride(int n_scales) {
+    return n_scales <= 2 ? n_scales : (n_scales + 3) & ~3;
 }
+__host__ __device__ __forceinline__ int64_t slot_groups_offset(int n_scales, int64_t np) {
+    return n_scales == 1 ? 0 : (int64_t(n_scales) * np + 3) & ~int64_t(3);
+}
+
+template <int RS>
+struct IdGroup;
+template <>
+struct IdGroup<1> {
+    using T = int32_t;
+    __device__ static T make(const int32_t* v) { return v[0]; }
+    __device__ static int32_t get(const T& g, int j) { return g; }
+    __device__ static T none() { return -1; }
+};
+template <>
+struct IdGroup<2> {
+    using T = int2;
+    __device__ static T make(const int32_t* v) { return make_int2(v[0], v[1]); }
+    __device__ static int32_t get(const T& g, int j) { return j == 0 ? g.x : g.y; }
+    __device__ static T none() { return make_int2(-1, -1); }
+};
+template <>
+struct IdGroup<4> {
+    using T = int4;
+    __device__ static T make(const int32_t* v) { return make_int4(v[0], v[1], v[2], v[3]); }
+    __device__ static int32_t get(const T& g, int j) { return j == 0 ? g.x : (j == 1 ? g.y : (j == 2 ? g.z : g.w)); }
+    __device__ static T none() { return make_int4(-1, -1, -1, -1); }
+};
 
 // Record order, after the last scale: each record's slot of every scale becomes
 // its halo id (the slot's seed if the halo was kept, else -1), written to the
-// record's group.  Records are grouped by tile, so the slot lookups are
-// coherent.
-__global__ void __launch_bounds__(kThreads) k_rec_halo(const int32_t* __restrict__ rec_slot, int64_t np,
+// record's group (RS = 4: one group per four scales).  Records are grouped by
+// tile, so the slot lookups are coherent.  With one scale the groups are the
+// slots themselves (each thread rewrites its own entry).
+template <int RS>
+__global__ void __launch_bounds__(kThreads) k_rec_halo(const int32_t* rec_slot, int64_t np,
                                                       const uint32_t* __restrict__ total_ptr, int n_scales,
                                                       const int32_t* __restrict__ slot_halo, int64_t slot_stride,
-                                                      int4* __restrict__ groups) {
+                                                      typename IdGroup<RS>::T* groups) {
+    constexpr int G = RS < 4 ? RS : 4;  // ids per stored group
     const int64_t total = *total_ptr;
-    const int ng4 = slot_group_stride(n_scales) / 4;
+    const int ngr = (n_scales + G - 1) / G;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < total; r += stride) {
-        for (int g = 0; g < ng4; g++) {
-            int32_t v[4];
+        for (int g = 0; g < ngr; g++) {
+            int32_t v[G];
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int k = 4 * g + j;
+            for (int j = 0; j < G; j++) {
+                const int k = G * g + j;
                 const int32_t sl = k < n_scales ? rec_slot[k * np + r] : -1;
                 v[j] = sl >= 0 ? slot_halo[k * slot_stride + sl] : -1;
             }
-            groups[r * ng4 + g] = make_int4(v[0], v[1], v[2], v[3]);
+            groups[r * ngr + g] = IdGroup<RS>::make(v);
         }
     }
 }
 
-// halo_id of every particle for every scale, in particle order: one 16-byte
-// gather per particle and group of four scales from its record's ids.
-// Several particles per thread keep independent gathers in flight.
+// halo_id of every particle for every scale, in particle order: one gather
+// per particle and group of its record's ids.  Several particles per thread
+// keep independent gathers in flight.
+template <int RS>
 __global__ void __launch_bounds__(kThreads) k_finalize(const uint32_t* __restrict__ part_rec, int64_t np,
                                                       const uint32_t* __restrict__ total_ptr,
-                                                      const int32_t* __restrict__ rec_halo, int n_scales,
-                                                      int32_t* __restrict__ halo_id) {
+                                                      const typename IdGroup<RS>::T* __restrict__ groups,
+                                                      int n_scales, int32_t* __restrict__ halo_id) {
     constexpr int kIlp = 8;
+    constexpr int G = RS < 4 ? RS : 4;
+    using T = typename IdGroup<RS>::T;
     const int64_t total = *total_ptr;
-    const int rs = slot_group_stride(n_scales);
-    const int4* rec4 = reinterpret_cast<const int4*>(rec_halo);
+    const int ngr = (n_scales + G - 1) / G;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i0 < np; i0 += kIlp * stride) {
         int64_t r[kIlp];
@@ -358,22 +389,32 @@ __global__ void __launch_bounds__(kThreads) k_finalize(const uint32_t* __restric
             const uint32_t x = i < np ? part_rec[i] : 0xffffffffu;
             r[u] = int64_t(x) < total ? int64_t(x) : -1;
         }
-        for (int k0 = 0; k0 < n_scales; k0 += 4) {
-            int4 h[kIlp];
+        for (int g = 0; g < ngr; g++) {
+            T h[kIlp];
 #pragma unroll
-            for (int u = 0; u < kIlp; u++)
-                h[u] = r[u] >= 0 ? rec4[(r[u] * rs + k0) >> 2] : make_int4(-1, -1, -1, -1);
+            for (int u = 0; u < kIlp; u++) h[u] = r[u] >= 0 ? groups[r[u] * ngr + g] : IdGroup<RS>::none();
 #pragma unroll
             for (int u = 0; u < kIlp; u++) {
                 const int64_t i = i0 + u * stride;
                 if (i >= np) continue;
-                const int32_t v[4] = {h[u].x, h[u].y, h[u].z, h[u].w};
 #pragma unroll
-                for (int j = 0; j < 4; j++)
-                    if (k0 + j < n_scales) halo_id[(k0 + j) * np + i] = v[j];
+                for (int j = 0; j < G; j++)
+                    if (G * g + j < n_scales) halo_id[(G * g + j) * np + i] = IdGroup<RS>::get(h[u], j);
             }
         }
     }
+}
+
+template <int RS>
+void launch_ids(cwthf_ctx* ctx, cudaStream_t s, int blocks, int pblocks, int64_t np, const uint32_t* total,
+                int n_scales, int64_t slot_cap, int32_t* halo_id) {
+    using T = typename IdGroup<RS>::T;
+    T* groups = reinterpret_cast<T*>(ctx->part_slot + slot_groups_offset(n_scales, np));
+    CWTHF_LAUNCH(ctx, s, "k_rec_halo",
+                 k_rec_halo<RS><<<blocks, kThreads, 0, s>>>(ctx->part_slot, np, total, n_scales, ctx->slot_halo,
+                                                            slot_cap, groups));
+    CWTHF_LAUNCH(ctx, s, "k_finalize",
+                 k_finalize<RS><<<pblocks, kThreads, 0, s>>>(ctx->part_rec, np, total, groups, n_scales, halo_id));
 }
 
 }  // namespace
@@ -417,14 +458,11 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
                                                          cat, ctx->slot_halo + int64_t(scale) * slot_cap, n_halo,
                                                          ctx->d_status));
     if (scale == n_scales - 1) {  // halo ids of all scales at once
-        int4* groups = reinterpret_cast<int4*>(ctx->part_slot + slot_groups_offset(n_scales, np));
-        CWTHF_LAUNCH(ctx, s, "k_rec_halo",
-                     k_rec_halo<<<blocks, kThreads, 0, s>>>(ctx->part_slot, np, ctx->dep_off + total_key, n_scales,
-                                                            ctx->slot_halo, slot_cap, groups));
-        CWTHF_LAUNCH(ctx, s, "k_finalize",
-                     k_finalize<<<pblocks, kThreads, 0, s>>>(ctx->part_rec, np, ctx->dep_off + total_key,
-                                                             reinterpret_cast<const int32_t*>(groups), n_scales,
-                                                             halo_id));
+        const int rs = slot_group_stride(n_scales);
+        const uint32_t* total = ctx->dep_off + total_key;
+        if (rs == 1) launch_ids<1>(ctx, s, blocks, pblocks, np, total, n_scales, slot_cap, halo_id);
+        else if (rs == 2) launch_ids<2>(ctx, s, blocks, pblocks, np, total, n_scales, slot_cap, halo_id);
+        else launch_ids<4>(ctx, s, blocks, pblocks, np, total, n_scales, slot_cap, halo_id);
     }
     return cuda_status(cudaGetLastError());
 }

@@ -76,10 +76,12 @@ void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, F
     f(reinterpret_cast<void**>(&c->acc), size_t(z.slots) * sizeof(HaloAcc));
     f(reinterpret_cast<void**>(&c->keep_off), size_t(z.slots + 2) * 4);
     f(reinterpret_cast<void**>(&c->slot_halo), size_t(z.slots) * 4 * size_t(std::max(max_scales, 1)));
-    // record slots of every scale (scale-major), then the records' halo ids in
-    // 16-byte groups of four scales
+    // record slots of every scale (scale-major), then (several scales) the
+    // records' halo ids in groups of 2 or 4k scales; one scale's ids replace
+    // its slots in place
     const size_t ms = size_t(std::max(max_scales, 1));
-    f(reinterpret_cast<void**>(&c->part_slot), (size_t(z.np) * ms + 4) * 4 + size_t(z.np) * 4 * ((ms + 3) & ~size_t(3)));
+    const size_t groups = ms == 1 ? 0 : (ms == 2 ? 2 : (ms + 3) & ~size_t(3));
+    f(reinterpret_cast<void**>(&c->part_slot), (size_t(z.np) * ms + 4) * 4 + size_t(z.np) * 4 * groups);
     f(reinterpret_cast<void**>(&c->jump_changed), sizeof(int) * (kMaxJumpRounds + 2));
     f(reinterpret_cast<void**>(&c->scan_tmp), z.scan_words * 4);
     f(reinterpret_cast<void**>(&c->grid), size_t(z.cells) * 8);

@@ -113,7 +113,7 @@ struct cwthf_ctx {
     cwthf::HaloAcc* acc = nullptr;    // [ng^3 / 8 + 1]
     uint32_t* keep_off = nullptr;     // [ng^3 / 8 + 2] kept-halo prefix
     int32_t* slot_halo = nullptr;     // [max_scales][ng^3 / 8 + 8] seed of each kept slot, -1 otherwise
-    int32_t* part_slot = nullptr;     // [max_scales][max_np] record slots (-1: none), then [max_np][4k] halo ids
+    int32_t* part_slot = nullptr;     // [max_scales][max_np] record slots (-1: none), then [max_np][1|2|4k] halo ids
     int* jump_changed = nullptr;      // [kMaxJumpRounds + 1]
     uint32_t* scan_tmp = nullptr;     // block sums of the device scan
     size_t scan_tmp_cap = 0;          // words

@@ -88,8 +88,7 @@ class Slot:
         self.n_halo = torch.zeros(n_scales, dtype=torch.int64, device=device)
         self.event = torch.cuda.Event()
         self.job = None
-        self.bytes = (_lib.workspace_bytes(ng, np_max, n_scales) + self.halo_id.numel() * 4 + self.cat.numel()
-                      + 64)
+        self.bytes = slot_bytes(ng, np_max, n_scales, cat_cap)
 
     def fits(self, job: Job) -> bool:
         return job.ng <= self.ng and job.np <= self.np_max and len(job.params) <= self.n_scales
@@ -112,6 +111,18 @@ class Slot:
         hid = self.halo_id[:ns, :job.np]
         job.checksum = int((hid.to(torch.int64) * torch.arange(1, job.np + 1, device=hid.device)).sum().item())
         self.job = None
+
+
+def slot_bytes(ng, np_max, n_scales, cat_cap):
+    """Device bytes one slot holds: the context's workspace, the halo ids and
+    the catalogue."""
+    return _lib.workspace_bytes(ng, np_max, n_scales) + n_scales * np_max * 4 + n_scales * cat_cap * 64 + 64
+
+
+def plan_bytes(slots_per_class, n_scales=1, per_cell=8.0, classes=SIZE_CLASSES, cat_cap=1 << 18):
+    """Device bytes of a server's slots (the sizes Server allocates), without a GPU."""
+    return sum(k * slot_bytes(ng, int(round(per_cell * ng ** 3)) + 1024, n_scales, cat_cap)
+               for ng in classes for k in [slots_per_class.get(ng, 0)])
 
 
 class Server:
