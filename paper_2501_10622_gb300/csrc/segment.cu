@@ -293,20 +293,26 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
     // target's pointer, so a round triples the distance covered), until no
     // pointer changes.  A value read while another thread rewrites it is either
     // the old or the new pointer, both points of the same chain.
+    auto jump = [&](int lz, bool& changed) {
+        const int i = i0 + lz * kPlaneL;
+        const int32_t v = ptr[i];
+        if (v >= 0 && v != i) {
+            int32_t w = ptr[v];
+            if (w != v) {
+                if (w >= 0) w = ptr[w];
+                ptr[i] = w;
+                changed = true;
+            }
+        }
+    };
     for (int round = 0; round < kJumpRoundsInTile; round++) {
         bool changed = false;
         if (own) {
-            for (int lz = 0; lz < wz; lz++) {
-                const int i = i0 + lz * kPlaneL;
-                const int32_t v = ptr[i];
-                if (v >= 0 && v != i) {
-                    int32_t w = ptr[v];
-                    if (w != v) {
-                        if (w >= 0) w = ptr[w];
-                        ptr[i] = w;
-                        changed = true;
-                    }
-                }
+            if (wz == kChTZ) {  // every tile but a ragged last one along z
+#pragma unroll 8
+                for (int lz = 0; lz < kChTZ; lz++) jump(lz, changed);
+            } else {
+                for (int lz = 0; lz < wz; lz++) jump(lz, changed);
             }
         }
         if (!__syncthreads_or(changed)) break;
