@@ -21,18 +21,33 @@ def test_workload64_agreement(gctx, work64):
     assert abs(n - len(ref["cat"]["seed"])) <= max(2, n // 50)
 
 
-def test_multi_scale_equals_single_scale(gctx, work64):
-    wl, pos, ref = work64
-    p = dev(pos)
-    scales = [pkg.default_params(w) for w in (2.0, 3.0, 4.0)]
-    hid, cat, nh = gctx.find(p, wl.box, wl.ng, scales)
-    gctx.check()
+def _multi_equals_single(ctx, wl, p, ws):
+    scales = [pkg.default_params(w) for w in ws]
+    hid, cat, nh = ctx.find(p, wl.box, wl.ng, scales)
+    ctx.check()
     for i, sp in enumerate(scales):
-        h1, c1, n1 = gctx.find(p, wl.box, wl.ng, [sp])
-        gctx.check()
-        assert torch.equal(hid[i], h1[0])
+        h1, c1, n1 = ctx.find(p, wl.box, wl.ng, [sp])
+        ctx.check()
+        assert torch.equal(hid[i], h1[0]), (ws, i)
         assert int(nh[i]) == int(n1[0])
         assert torch.equal(cat[i, :int(n1[0])], c1[0, :int(n1[0])])
+
+
+# two scales: halo ids regrouped in pairs; three: one group of four
+@pytest.mark.parametrize("ws", [(2.0, 3.0), (2.0, 3.0, 4.0)])
+def test_multi_scale_equals_single_scale(gctx, work64, ws):
+    wl, pos, ref = work64
+    _multi_equals_single(gctx, wl, dev(pos), ws)
+
+
+def test_five_scales_equal_single_scales(work64):
+    # five scales: two groups of four ids per record, the second partly filled
+    wl, pos, ref = work64
+    ctx = pkg.Context(0, max_ng=wl.ng, max_np=pos.shape[0], max_scales=5)
+    try:
+        _multi_equals_single(ctx, wl, dev(pos), (2.0, 2.5, 3.0, 3.5, 4.0))
+    finally:
+        ctx.close()
 
 
 def test_find_equals_stage_by_stage(gctx, work64):
