@@ -277,6 +277,20 @@ def cpu_model():
     return os.uname().machine
 
 
+def cpu_baseline_leg(wl, sample_ng, min_seconds=10.0, max_runs=8):
+    """The oracle on one host core, on a bounded sample of the workload: the
+    same sample repeated until at least min_seconds of CPU work (at most
+    max_runs runs)."""
+    spos, sbox, desc = oracle_sample(wl, sample_ng)
+    reps, t0 = 0, time.perf_counter()
+    while reps < max_runs and (reps == 0 or time.perf_counter() - t0 < min_seconds):
+        oracle_step(spos, sbox, sample_ng, wl.scales)
+        reps += 1
+    t = time.perf_counter() - t0
+    return {"value": reps * spos.shape[0] / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{desc}; {reps} runs", "seconds": t, "cpu": cpu_model()}
+
+
 def run_reference(args, wl, rank):
     if rank != 0:
         return
@@ -522,12 +536,7 @@ def main():
     # ---- CPU oracle baseline (rank 0, N = 1) ------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        spos, sbox, desc = oracle_sample(wl, args.cpu_sample_ng)
-        t0 = time.perf_counter()
-        oracle_step(spos, sbox, args.cpu_sample_ng, wl.scales)
-        t = time.perf_counter() - t0
-        cpu = {"value": spos.shape[0] / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-               "seconds": t, "cpu": cpu_model()}
+        cpu = cpu_baseline_leg(wl, args.cpu_sample_ng)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
