@@ -71,3 +71,27 @@ def test_workload256_agreement(gctx):
     agree = float(np.mean(hid[0].cpu().numpy() == ref["halo_id"]))
     print(f"256^3 particle agreement {agree:.6f}, halos {int(nh[0])} vs {len(ref['cat']['seed'])}")
     assert agree >= 0.999
+
+
+def test_ragged_grid_agreement(gctx):
+    # 48^3: the chain tiles (32 x 16 x 32) and the deposit tiles (32 x 8 x 8) end
+    # part-filled along x and z; same cell size and density as the 64^3 case
+    ng = 48
+    box = ng * 0.78125
+    pos = synth.clumped_box(ng ** 3, box, 84, seed=11)
+    ref = oracle.find(pos.numpy(), box, ng, 2.0)
+    hid, cat, nh = gctx.find(dev(pos), box, ng, [pkg.default_params(2.0)])
+    gctx.check()
+    agree = float(np.mean(hid[0].cpu().numpy() == ref["halo_id"]))
+    assert agree >= 0.999, agree
+    n = int(nh[0])
+    assert abs(n - len(ref["cat"]["seed"])) <= max(2, n // 50)
+
+
+def test_empty_particle_set_find(gctx):
+    # no particles: a zero field has no maximum above cwt_min, so no halos at any scale
+    pos = torch.empty((0, 3), dtype=torch.float32, device="cuda")
+    hid, cat, nh = gctx.find(pos, 25.0, 32, [pkg.default_params(2.0), pkg.default_params(3.0)])
+    gctx.check()
+    assert tuple(hid.shape) == (2, 0)
+    assert nh.cpu().tolist() == [0, 0]
