@@ -29,6 +29,19 @@ class BatchJob:
         self.n_halo = None
 
 
+def assign_slots(sizes, n_slots):
+    """Longest-processing-time placement: jobs (ng, np), costed as cells +
+    particles, longest first onto the least-loaded slot (the lowest index on
+    ties).  Returns each job's slot, in the jobs' order."""
+    load = [0] * n_slots
+    slot = [0] * len(sizes)
+    for i in sorted(range(len(sizes)), key=lambda i: -(sizes[i][0] ** 3 + sizes[i][1])):
+        s = min(range(n_slots), key=lambda k: load[k])
+        slot[i] = s
+        load[s] += sizes[i][0] ** 3 + sizes[i][1]
+    return slot
+
+
 class Batch:
     def __init__(self, jobs, n_slots=8, cat_cap=1 << 16, device="cuda"):
         self.device = torch.device(device)
@@ -40,12 +53,8 @@ class Batch:
         self.ctx = [_lib.Context(self.device.index or 0, max_ng=max_ng, max_np=max_np, max_scales=ns)
                     for _ in range(self.n_slots)]
         self.streams = [torch.cuda.Stream(self.device) for _ in range(self.n_slots)]
-        # longest-processing-time assignment (cells + particles as the cost)
-        load = [0.0] * self.n_slots
-        for j in sorted(self.jobs, key=lambda j: -(j.ng ** 3 + j.np)):
-            s = min(range(self.n_slots), key=lambda i: load[i])
+        for j, s in zip(self.jobs, assign_slots([(j.ng, j.np) for j in self.jobs], self.n_slots)):
             j.slot = s
-            load[s] += j.ng ** 3 + j.np
         for j in self.jobs:
             k = len(j.params)
             j.halo_id = torch.empty((k, j.np), dtype=torch.int32, device=self.device)
