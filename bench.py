@@ -134,28 +134,52 @@ def run_served(args, dev):
 
 
 # ---------------------------------------------------------------------------
-# Algorithmic bytes per launch of each kernel (what the method itself must
-# move; see the design notes).  u = dict(ng, np, cells, half) with half =
-# ng * ng * (ng/2 + 1) complex values of the half spectrum.
+# Algorithmic bytes: what the method itself must move, with u = cells, h = half-spectrum complex values
+# ng * ng * (ng/2 + 1), p = particles, k = scales:
+#   S1 deposit              12p + 8u        positions in, int64 grid out
+#   S2-S4 transform         44u + 24u(k-1)  five passes over the spectrum; each
+#                                           extra scale repeats the last three
+#   S5-S6 segmentation      8u per scale    CWT in, labels out
+#   S7-S8 assignment        20p per scale   positions in, label gather, ids out
+# Each kernel is charged its share of those bytes; kernels that move only the
+# build's own intermediates (bins, parent codes, slots) are charged nothing.
 # ---------------------------------------------------------------------------
+STAGES = {
+    "S1 deposit": ("k_dep_",),
+    "S2-S4 transform": ("k_fft_",),
+    "S5-S6 segmentation": ("k_seg_", "k_popc", "k_seed_list"),
+    "S7-S8 assignment": ("k_halo_sums", "k_keep", "k_catalogue", "k_rec_halo", "k_finalize", "k_count_cells"),
+}
+
+
+def stage_of(kernel):
+    for st, prefixes in STAGES.items():
+        if kernel.startswith(prefixes):
+            return st
+    return "shared (scans)"
+
+
+def stage_bytes(u):
+    cells, npart, k = u["cells"], u["np"], u["scales"]
+    return {"S1 deposit": 12 * npart + 8 * cells,
+            "S2-S4 transform": 44 * cells + 24 * cells * (k - 1),
+            "S5-S6 segmentation": 8 * cells * k,
+            "S7-S8 assignment": 20 * npart * k}
+
+
 def algorithmic_bytes(name, u):
+    """The kernel's share of its stage's algorithmic bytes, per launch."""
     cells, half, npart = u["cells"], u["half"], u["np"]
     table = {
-        "k_fft_yz": 2 * 8 * half,                      # read + write the half spectrum
-        "k_fft_x_fwd": 8 * cells + 8 * half,           # int64 grid in, half spectrum out
-        "k_fft_x_inv": 8 * half + 4 * cells,           # half spectrum in, fp32 CWT out
-        "k_dep_tile": 8 * cells + 8 * npart,           # records in once, int64 grid out
-        "k_dep_count": 12 * npart,
-        "k_dep_scatter": 12 * npart + 8 * npart + 4 * npart,  # positions in, record + index out
-        "k_seg_parent": 4 * cells + 1 * cells,         # CWT in, parent codes out
-        "k_seg_chase": 1 * cells + 4 * cells,          # parent codes in, labels out
-        "k_seg_jump": 4 * cells,
-        # k_seg_resolve: 12 B per cell whose chain left its tile (a data-dependent
-        # count the bench does not see), so no algorithmic figure
-        "k_count_cells": 4 * cells,
-        "k_halo_sums": 8 * npart + 4 * npart + 4 * npart,    # records, label gather, slot out
-        "k_rec_halo": 4 * npart * u.get("scales", 1) + 16 * npart * ((u.get("scales", 1) + 3) // 4),  # slots in, id groups out
-        "k_finalize": 4 * npart + 8 * npart * u.get("scales", 1),   # record position; per scale id in and out
+        "k_dep_count": 12 * npart,                # positions in
+        "k_dep_tile": 8 * cells,                  # int64 grid out
+        "k_fft_x_fwd": 8 * cells + 8 * half,      # int64 grid in, half spectrum out
+        "k_fft_yz": 2 * 8 * half,                 # half spectrum in and out
+        "k_fft_x_inv": 8 * half + 4 * cells,      # half spectrum in, fp32 CWT out
+        "k_seg_parent": 4 * cells,                # CWT in
+        "k_seg_chase": 4 * cells,                 # labels out
+        "k_halo_sums": 12 * npart + 4 * npart,    # positions (as binned records), label gather
+        "k_finalize": 4 * npart * u["scales"],    # halo ids out, every scale
     }
     return table.get(name)
 
@@ -362,11 +386,10 @@ def main():
         if dist:
             dist.barrier()
 
-    # ---- device-resident timed region --------------------------------------
+    # ---- device-resident timed region (no per-kernel events inside) ----------
     sampler = ClockSampler(local)
     barrier()
     torch.cuda.synchronize(dev)
-    ctx.profile(True)
     launches0 = ctx.launch_count()
     sampler.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -378,36 +401,51 @@ def main():
     barrier()
     clocks = sampler.stop()
     launches = ctx.launch_count() - launches0
-    prof = ctx.profile_read()
-    ctx.profile(False)
     ctx.check(what="timed steps")
     ms = replicas.max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
     value = replicas.whole_job_throughput(npart, world, ms)
 
-    # ---- per-kernel roofline --------------------------------------------------
+    # ---- per-kernel times: a separate pass with CUDA events around every launch
+    prof_steps = max(2, min(args.steps, 5))
+    ctx.profile(True)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(prof_steps):
+        step(pos)
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ctx.check(what="profiled steps")
+    prof_ms = p0.elapsed_time(p1) / prof_steps
+
+    # ---- per-kernel and per-stage roofline --------------------------------------
     peak, peak_kind = measured_peaks()
     u = dict(ng=ng, np=npart, cells=ng ** 3, half=ng * ng * (ng // 2 + 1), scales=ns)
-    kernels = {}
+    kernels, stage_ms = {}, {}
     for name, (tot, n) in prof.items():
         b = algorithmic_bytes(name, u)
         avg = tot / n
-        ent = {"launches": n, "avg_ms": avg, "share": tot / (ms * args.steps)}
+        ent = {"launches_per_step": n / prof_steps, "avg_ms": avg, "ms_per_step": tot / prof_steps,
+               "share": tot / prof_steps / prof_ms, "stage": stage_of(name)}
         if b:
             ent["algorithmic_bytes"] = b
             ent["gbs"] = b / (avg / 1e3) / 1e9
             ent["frac"] = ent["gbs"] / peak
         kernels[name] = ent
-    dom = max((k for k in kernels if "gbs" in kernels[k]), key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
+        stage_ms[ent["stage"]] = stage_ms.get(ent["stage"], 0.0) + tot / prof_steps
+    dom = max((k for k in kernels if "gbs" in kernels[k]), key=lambda k: kernels[k]["ms_per_step"])
     d = kernels[dom]
     roofline = {"bound": "hbm", "kernel": dom, "achieved": d["gbs"], "peak": peak, "unit": "GB/s",
-                "frac": d["gbs"] / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "frac": d["gbs"] / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, copy burst)",
                 "traffic": stored_traffic(dom, u), "algorithmic_bytes_per_launch": d["algorithmic_bytes"]}
-    # step total: every kernel's algorithmic bytes per launch, except the pointer-jumping
-    # rounds, of which only the first per segmentation must run (later ones exit early)
-    n_seg = kernels.get("k_seg_chase", {}).get("launches", 0)
-    step_bytes = sum(v["algorithmic_bytes"] * (n_seg if k == "k_seg_jump" else v["launches"])
-                     for k, v in kernels.items() if "algorithmic_bytes" in v)
-    step_bytes /= args.steps
+    sb = stage_bytes(u)
+    stages = {st: {"algorithmic_bytes": b, "ms_per_step": stage_ms.get(st, 0.0),
+                   "gbs": b / (stage_ms[st] / 1e3) / 1e9 if stage_ms.get(st) else None,
+                   "frac": b / (stage_ms[st] / 1e3) / 1e9 / peak if stage_ms.get(st) else None}
+              for st, b in sb.items()}
+    stages["shared (scans)"] = {"ms_per_step": stage_ms.get("shared (scans)", 0.0)}
+    step_bytes = sum(sb.values())
 
     # ---- end to end through host buffers ---------------------------------------
     # Every step copies its positions host -> device and its halo ids and counts
@@ -490,22 +528,25 @@ def main():
 
     # ---- the transform beside cuFFT (rank 0, N = 1) ------------------------------
     # torch.fft (cuFFT) r2c of the fp32 grid once, then per scale a multiply by a
-    # precomputed full kernel spectrum and a c2r: the library route to the same
-    # convolutions, timed against this path's own FFT kernels in the timed steps.
+    # precomputed full kernel spectrum and a c2r, all into preallocated outputs:
+    # the library route to the same convolutions, timed against this path's own
+    # FFT kernels (from the profiled pass).
     cufft = None
     if rank == 0 and world == 1 and not args.no_cufft:
-        ours = sum(v["avg_ms"] * v["launches"] for k, v in kernels.items() if k.startswith("k_fft")) / args.steps
+        ours = sum(v["ms_per_step"] for k, v in kernels.items() if k.startswith("k_fft"))
         g = ctx.deposit(pos, wl.box, ng)
         x = g.to(torch.float32)
         del g
         kspec = torch.randn((ng, ng, ng // 2 + 1), dtype=torch.complex64, device=dev)
+        X = torch.empty_like(kspec)
+        Y = torch.empty_like(kspec)
         out = torch.empty((ng, ng, ng), dtype=torch.float32, device=dev)
 
         def cufft_step():
-            X = torch.fft.rfftn(x)
+            torch.fft.rfftn(x, out=X)
             for _ in wl.scales:
-                out.copy_(torch.fft.irfftn(X * kspec, s=(ng, ng, ng)))
-            return X
+                torch.mul(X, kspec, out=Y)
+                torch.fft.irfftn(Y, s=(ng, ng, ng), out=out)
 
         cufft_step()
         torch.cuda.synchronize(dev)
@@ -516,9 +557,10 @@ def main():
         c1.record()
         torch.cuda.synchronize(dev)
         cufft = {"ms_per_step": c0.elapsed_time(c1) / args.steps, "ours_ms_per_step": ours,
-                 "what": f"torch.fft rfftn of the fp32 {ng}^3 grid, then per scale ({len(wl.scales)}) multiply by "
-                         "a full precomputed spectrum and irfftn; ours: the k_fft_* kernels of one find step"}
-        del x, kspec, out
+                 "what": f"torch.fft rfftn of the fp32 {ng}^3 grid, then per scale ({len(wl.scales)}) a multiply "
+                         "by a full precomputed spectrum and irfftn, all into preallocated outputs; ours: the k_fft_* "
+                         "kernels of one find step"}
+        del x, kspec, X, Y, out
         torch.cuda.empty_cache()
 
     halos = [int(x) for x in nh.cpu()]
@@ -549,7 +591,10 @@ def main():
                 "grid_cells_per_s": world * ng ** 3 / (ms / 1e3),
                 "algorithmic_bytes_per_step": step_bytes,
                 "step_roofline_frac": step_bytes / (ms / 1e3) / 1e9 / peak,
-                "roofline": roofline, "kernels": kernels, "gpu_launches": launches,
+                "roofline": roofline, "stages": stages, "kernels": kernels,
+                "kernel_table_from": f"{prof_steps} separate steps with CUDA events around every launch "
+                                     f"({prof_ms:.2f} ms per step there)",
+                "gpu_launches": launches,
                 "halos_per_scale": halos,
                 "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "served": served, "batched": batched,
                 "cufft": cufft}

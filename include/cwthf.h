@@ -149,6 +149,17 @@ CWTHF_API int cwthf_transform(cwthf_ctx *ctx, const int64_t *grid, int ng, doubl
 CWTHF_API int cwthf_segment(cwthf_ctx *ctx, const float *cwt, int ng, float cwt_min, int32_t *cell_label,
                   void *stream);
 
+/* Sec. 2.4 (the "grid volume" of a segment).  The seeds found by the last
+ * cwthf_segment call on this context, in increasing cell order, and the
+ * number of cells labelled with each.  Valid until the next call on the
+ * context; queue it on the segmentation's stream.
+ *   seeds    device, int32 [cap]: linear index of each seed
+ *   n_cells  device, int64 [cap]: cells of its segment
+ *   n_seeds  device, int64 [1]: the number of seeds (may exceed cap; only
+ *            the first cap are written). */
+CWTHF_API int cwthf_segment_sizes(cwthf_ctx *ctx, int32_t *seeds, int64_t *n_cells, int64_t cap, int64_t *n_seeds,
+                                  void *stream);
+
 /* Sec. 2 steps 6-7, Sec. 2.3-2.4, Table 1.  Each particle takes the label of
  * its nearest node ((q + 2^9) >> 10 per axis, wrapped).  Per seed: particle
  * count, integer mass, integer first moment about the seed node (minimum
@@ -182,7 +193,9 @@ CWTHF_API int cwthf_find(cwthf_ctx *ctx, const float *pos, const float *mass, do
                int64_t cat_cap, int64_t *n_halo, void *stream);
 
 /* Waits for `stream`, then returns (and clears) the first error the device
- * recorded since the last cwthf_sync, or CWTHF_E_CUDA if the stream failed. */
+ * recorded since the last cwthf_sync, or CWTHF_E_CUDA if the stream failed.
+ * After CWTHF_E_TIMEOUT or CWTHF_E_NOT_CONVERGED every output of the calls
+ * since the previous cwthf_sync is unspecified. */
 CWTHF_API int cwthf_sync(cwthf_ctx *ctx, void *stream);
 
 /* Static English text for a status code. */
@@ -208,11 +221,36 @@ CWTHF_API int64_t cwthf_launch_count(const cwthf_ctx *ctx);
  *           stream reaches it.
  * Runs on the current device.  Every call shares the one scratch array, so
  * calls whose GPU work overlaps (other streams, other host threads) race and
- * corrupt each other's result: keep them ordered on one stream.  The first
- * call on a device looks up the array's device address; make it before any
- * stream capture. */
+ * corrupt each other's result: keep them ordered on one stream.  A call made
+ * outside a stream capture looks up the array's device address; a call made
+ * while its stream is being captured reuses the last address found on that
+ * device, so make one call on each device before any stream capture. */
 CWTHF_API int cwthf_deposit_noalloc(const float *pos, const float *mass, double mass_unit, int64_t np, double L,
                                     int ng, int64_t *grid, int64_t *mtot, int *status, void *stream);
+
+/* Test and fault-injection settings of a context (instrumentation; the paper
+ * has no counterpart).  They let a test reach the library's error paths
+ * without faulting the GPU.  Keys and values:
+ *   CWTHF_DEBUG_JUMP_ROUNDS  0..31 (default 31): pointer-doubling rounds the
+ *       segmentation may run after its bounded chain walks; a chain still
+ *       unfinished after them is reported as CWTHF_E_NOT_CONVERGED.
+ *   CWTHF_DEBUG_CHASE_LIMIT  1..64 (default 64): steps of the bounded chain
+ *       walks across segmentation tiles before the doubling rounds take over.
+ *   CWTHF_DEBUG_TMA_NO_COPY  nonzero: in the next y/z FFT pass of this
+ *       context, one CTA arms its transfer barrier but issues no copy, so its
+ *       bounded wait runs out (nothing is in flight) and the call reports
+ *       CWTHF_E_TIMEOUT.  One-shot.
+ *   CWTHF_DEBUG_FALLBACK_RAN (get only): 1 if the last segmentation needed
+ *       the doubling rounds (a chain outlived the bounded walks), else 0;
+ *       waits for `stream`.
+ * cwthf_debug_set returns CWTHF_E_INVALID_ARG for an unknown key or a value
+ * out of range; settings persist for the context's lifetime. */
+#define CWTHF_DEBUG_JUMP_ROUNDS 1
+#define CWTHF_DEBUG_CHASE_LIMIT 2
+#define CWTHF_DEBUG_TMA_NO_COPY 3
+#define CWTHF_DEBUG_FALLBACK_RAN 4
+CWTHF_API int cwthf_debug_set(cwthf_ctx *ctx, int key, int64_t value);
+CWTHF_API int cwthf_debug_get(cwthf_ctx *ctx, int key, int64_t *value, void *stream);
 
 /* Per-kernel timing (instrumentation).  With enable != 0 every later kernel
  * launch of this context is bracketed by two CUDA events recorded on its own

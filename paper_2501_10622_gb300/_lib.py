@@ -23,6 +23,8 @@ E_INVALID_ARG, E_UNSUPPORTED_SIZE, E_OVERFLOW, E_OOM, E_CUDA, E_NOT_CONVERGED, E
 E_SCRATCH_LIMIT = 10
 FRAC_BITS = 10
 MIN_NG, MAX_NG = 8, 1024
+# cwthf_debug_set / cwthf_debug_get keys
+DEBUG_JUMP_ROUNDS, DEBUG_CHASE_LIMIT, DEBUG_TMA_NO_COPY, DEBUG_FALLBACK_RAN = 1, 2, 3, 4
 
 HALO_DTYPE = np.dtype([("seed", "<i8"), ("n_part", "<i8"), ("n_cells", "<i8"), ("mass", "<f8"),
                        ("centre", "<f8", (3,)), ("peak", "<f4"), ("reserved", "<i4")])
@@ -64,6 +66,9 @@ def lib() -> ctypes.CDLL:
         L.cwthf_deposit.argtypes = [P, P, P, d, i64, d, i32, P, P, P]
         L.cwthf_transform.argtypes = [P, P, i32, d, d, d, P, P]
         L.cwthf_segment.argtypes = [P, P, i32, f, P, P]
+        L.cwthf_segment_sizes.argtypes = [P, P, P, i64, P, P]
+        L.cwthf_debug_set.argtypes = [P, i32, i64]
+        L.cwthf_debug_get.argtypes = [P, i32, ctypes.POINTER(i64), P]
         L.cwthf_assign.argtypes = [P, P, P, d, i64, d, i32, P, P, ctypes.POINTER(Params), P, P, i64, P, P]
         L.cwthf_find.argtypes = [P, P, P, d, i64, d, i32, ctypes.POINTER(Params), i32, P, P, i64, P, P]
         L.cwthf_sync.argtypes = [P, P]
@@ -207,6 +212,26 @@ class Context:
         _check(lib().cwthf_segment(self._h, _ptr(cwt.contiguous()), int(ng), float(cwt_min), _ptr(label),
                                    self._stream(stream)), "cwthf_segment")
         return label
+
+    def segment_sizes(self, cap, stream=None):
+        """Seeds of the last segmentation and their segments' cell counts:
+        (seeds int32 [min(n, cap)], n_cells int64 [min(n, cap)], n) on device / host."""
+        t = self.torch
+        seeds = t.empty(max(cap, 1), dtype=t.int32, device=self.device)
+        n_cells = t.empty(max(cap, 1), dtype=t.int64, device=self.device)
+        n = t.zeros(1, dtype=t.int64, device=self.device)
+        _check(lib().cwthf_segment_sizes(self._h, _ptr(seeds), _ptr(n_cells), int(cap), _ptr(n),
+                                         self._stream(stream)), "cwthf_segment_sizes")
+        k = int(n)
+        return seeds[:min(k, cap)], n_cells[:min(k, cap)], k
+
+    def debug_set(self, key: int, value: int):
+        _check(lib().cwthf_debug_set(self._h, int(key), int(value)), "cwthf_debug_set")
+
+    def debug_get(self, key: int, stream=None) -> int:
+        v = ctypes.c_int64(0)
+        _check(lib().cwthf_debug_get(self._h, int(key), ctypes.byref(v), self._stream(stream)), "cwthf_debug_get")
+        return int(v.value)
 
     def assign(self, pos, L, label, cwt=None, mass=None, mass_unit=1.0, dens_th=4.0, particle_th=15,
                cat_cap=None, stream=None):

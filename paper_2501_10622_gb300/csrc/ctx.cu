@@ -82,7 +82,7 @@ void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, F
     const size_t ms = size_t(std::max(max_scales, 1));
     const size_t groups = ms == 1 ? 0 : (ms == 2 ? 2 : (ms + 3) & ~size_t(3));
     f(reinterpret_cast<void**>(&c->part_slot), (size_t(z.np) * ms + 4) * 4 + size_t(z.np) * 4 * groups);
-    f(reinterpret_cast<void**>(&c->jump_changed), sizeof(int) * (kMaxJumpRounds + 2));
+    f(reinterpret_cast<void**>(&c->jump_changed), sizeof(int) * kJumpWords);
     f(reinterpret_cast<void**>(&c->scan_tmp), z.scan_words * 4);
     f(reinterpret_cast<void**>(&c->grid), size_t(z.cells) * 8);
     f(reinterpret_cast<void**>(&c->cwt), size_t(z.cells) * 4);
@@ -160,7 +160,8 @@ int cwthf_create(int device, int max_ng, int64_t max_np, int max_scales, cwthf_c
     c->max_ng = max_ng;
     c->max_np = max_np;
     c->max_scales = max_scales;
-    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        (c->fallback_blocks = fallback_blocks(c->sm_count)) <= 0) {
         delete c;
         return CWTHF_E_CUDA;
     }
@@ -172,7 +173,7 @@ int cwthf_create(int device, int max_ng, int64_t max_np, int max_scales, cwthf_c
             failed = true;
         }
     });
-    if (!failed && cudaMallocHost(&c->h_status, sizeof(int)) != cudaSuccess) failed = true;
+    if (!failed && cudaMallocHost(&c->h_status, sizeof(int) * 2) != cudaSuccess) failed = true;
     if (!failed) {
         Sizes z = sizes_for(max_ng, max_np);
         c->scan_tmp_cap = z.scan_words;
@@ -227,6 +228,13 @@ int cwthf_segment(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32
     if (!cwt || !cell_label || std::isnan(cwt_min)) return CWTHF_E_INVALID_ARG;
     DeviceGuard g(ctx->device);
     return segment_impl(ctx, cwt, ng, cwt_min, cell_label, false, as_stream(stream));
+}
+
+int cwthf_segment_sizes(cwthf_ctx* ctx, int32_t* seeds, int64_t* n_cells, int64_t cap, int64_t* n_seeds,
+                        void* stream) {
+    if (!ctx || cap < 0 || (cap > 0 && (!seeds || !n_cells)) || !n_seeds) return CWTHF_E_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    return segment_sizes_impl(ctx, seeds, n_cells, cap, n_seeds, as_stream(stream));
 }
 
 int cwthf_assign(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L, int ng,
@@ -300,6 +308,48 @@ const char* cwthf_error_string(int code) {
 }
 
 int64_t cwthf_launch_count(const cwthf_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
+int cwthf_debug_set(cwthf_ctx* ctx, int key, int64_t value) {
+    if (!ctx) return CWTHF_E_INVALID_ARG;
+    switch (key) {
+        case CWTHF_DEBUG_JUMP_ROUNDS:
+            if (value < 0 || value > kMaxJumpRounds) return CWTHF_E_INVALID_ARG;
+            ctx->dbg_jump_rounds = int(value);
+            return CWTHF_OK;
+        case CWTHF_DEBUG_CHASE_LIMIT:
+            if (value < 1 || value > kDefaultChaseLimit) return CWTHF_E_INVALID_ARG;
+            ctx->dbg_chase_limit = int(value);
+            return CWTHF_OK;
+        case CWTHF_DEBUG_TMA_NO_COPY:
+            ctx->dbg_tma_no_copy = value != 0;
+            return CWTHF_OK;
+        default:
+            return CWTHF_E_INVALID_ARG;
+    }
+}
+
+int cwthf_debug_get(cwthf_ctx* ctx, int key, int64_t* value, void* stream) {
+    if (!ctx || !value) return CWTHF_E_INVALID_ARG;
+    switch (key) {
+        case CWTHF_DEBUG_JUMP_ROUNDS: *value = ctx->dbg_jump_rounds; return CWTHF_OK;
+        case CWTHF_DEBUG_CHASE_LIMIT: *value = ctx->dbg_chase_limit; return CWTHF_OK;
+        case CWTHF_DEBUG_TMA_NO_COPY: *value = ctx->dbg_tma_no_copy; return CWTHF_OK;
+        case CWTHF_DEBUG_FALLBACK_RAN: {
+            DeviceGuard g(ctx->device);
+            cudaStream_t s = as_stream(stream);
+            int v = 0;
+            if (cudaMemcpyAsync(ctx->h_status + 1, ctx->jump_changed, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return CWTHF_E_CUDA;
+            v = ctx->h_status[1];
+            *value = v != 0;
+            return CWTHF_OK;
+        }
+        default:
+            return CWTHF_E_INVALID_ARG;
+    }
+}
 
 int cwthf_profile(cwthf_ctx* ctx, int enable) {
     if (!ctx) return CWTHF_E_INVALID_ARG;

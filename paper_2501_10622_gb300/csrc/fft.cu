@@ -538,6 +538,11 @@ struct YzArgs {
     const float* hhat;  // [L]  H^(k)
     float scale;        // w^1.5 * mass_unit / ng^3
     int* status;
+    // fault injection (tests): CTA no_copy_block arms its barrier for the tile
+    // but issues no copy, so its bounded wait (no_copy_spin polls) runs out
+    // with nothing in flight; -1: off
+    int no_copy_block;
+    long long no_copy_spin;
 };
 
 // One CTA per tile: TMA brings the [L][C] pencil tile into shared memory
@@ -576,11 +581,12 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks)
     }
     const int cc = blockIdx.x % a.ncc, o = blockIdx.x / a.ncc;
 
+    const bool no_copy = int(blockIdx.x) == a.no_copy_block;
     if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_expect_tx(bar, uint32_t(L) * C * 8u);
-        for (int b = 0; b < a.nbox; b++) {
+        for (int b = 0; b < a.nbox && !no_copy; b++) {
             const int r = b * a.boxr;
             if (a.along_z) tma_load_3d(tile + r * C, &in_map, bar, 2 * cc * C, o, r);
             else tma_load_3d(tile + r * C, &in_map, bar, 2 * cc * C, r, o);
@@ -597,11 +603,13 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks)
         }
     }
     __syncthreads();
-    // the whole block agrees on the outcome of its bounded wait before leaving together
-    const bool loaded = mbar_wait(bar, 0, kSpinLimit);
+    // the whole block agrees on the outcome of its bounded wait before leaving
+    // together.  After a timeout the call's results are unspecified (the status
+    // word says so); a copy that is still outstanding gets a second bounded wait.
+    const bool loaded = mbar_wait(bar, 0, no_copy ? a.no_copy_spin : kSpinLimit);
     if (__syncthreads_or(!loaded)) {
         if (threadIdx.x == 0) set_status(a.status, CWTHF_E_TIMEOUT);
-        mbar_wait(bar, 0, kSpinLimit);  // a second bounded chance for the copy before leaving
+        if (!no_copy) mbar_wait(bar, 0, kSpinLimit);
         return;
     }
     AddrPlain addr{C};
@@ -1025,6 +1033,13 @@ int launch_yz(cwthf_ctx* ctx, float2* src, float2* dst, int ng, bool along_z, in
     // unit (the x pass already scaled the int64 grid by 2^-30: units of mass_unit)
     a.scale = float(std::pow(w, 1.5) * mass_unit / (double(ng) * ng * ng));
     a.status = ctx->d_status;
+    a.no_copy_block = -1;
+    a.no_copy_spin = 0;
+    if (ctx->dbg_tma_no_copy) {  // one-shot fault injection (cwthf_debug_set)
+        ctx->dbg_tma_no_copy = 0;
+        a.no_copy_block = 0;
+        a.no_copy_spin = 1 << 12;
+    }
     bool global_tables = false;
     YzKernel k = pick_yz(p, global_tables);
     size_t smem = yz_smem(p, global_tables);

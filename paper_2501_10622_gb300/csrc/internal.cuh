@@ -36,9 +36,18 @@ __host__ __device__ __forceinline__ int rec_q(unsigned long long e, int d) {
 }
 
 // Pointer-doubling rounds of the segmentation's fallback: round r moves every
-// unfinished pointer 2^r links further, so 31 rounds end any chain of a grid
-// of at most 2^30 cells.
-constexpr int kMaxJumpRounds = 32;
+// unfinished pointer 2^(r-1) or more links further, so 31 rounds end any chain
+// of a grid of at most 2^30 cells.
+constexpr int kMaxJumpRounds = 31;
+// The segmentation's control words (ctx->jump_changed, cleared per call):
+// [0 .. kMaxJumpRounds] "a pointer is still flagged" after the resolve pass
+// (0) and after each doubling round, then the resolve pass's row counter and
+// the fallback's grid-barrier state (arrivals, generation).
+constexpr int kJumpRowCounter = kMaxJumpRounds + 1;
+constexpr int kJumpBarrier = kMaxJumpRounds + 2;
+constexpr int kJumpWords = kMaxJumpRounds + 4;
+// Default length of the resolve pass's bounded chain walks.
+constexpr int kDefaultChaseLimit = 64;
 
 // A bounded device wait gives up after this many polls.
 constexpr long long kSpinLimit = 1ll << 20;
@@ -114,7 +123,7 @@ struct cwthf_ctx {
     uint32_t* keep_off = nullptr;     // [ng^3 / 8 + 2] kept-halo prefix
     int32_t* slot_halo = nullptr;     // [max_scales][ng^3 / 8 + 8] seed of each kept slot, -1 otherwise
     int32_t* part_slot = nullptr;     // [max_scales][max_np] record slots (-1: none), then [max_np][1|2|4k] halo ids
-    int* jump_changed = nullptr;      // [kMaxJumpRounds + 1]
+    int* jump_changed = nullptr;      // [kJumpWords] segmentation control words
     uint32_t* scan_tmp = nullptr;     // block sums of the device scan
     size_t scan_tmp_cap = 0;          // words
 
@@ -122,6 +131,13 @@ struct cwthf_ctx {
     int64_t* grid = nullptr;
     float* cwt = nullptr;
     int32_t* label = nullptr;
+
+    int fallback_blocks = 0;          // CTAs of the cooperative segmentation fallback
+
+    // test and fault-injection settings (cwthf_debug_set)
+    int dbg_jump_rounds = cwthf::kMaxJumpRounds;
+    int dbg_chase_limit = cwthf::kDefaultChaseLimit;
+    int dbg_tma_no_copy = 0;  // one-shot: the next y/z FFT pass runs one CTA without its copy
 
     std::atomic<int64_t> launches{0};
 
@@ -280,6 +296,11 @@ int transform_wavelet_inverse(cwthf_ctx* ctx, float2* src, float2* dst, int ng, 
                               double mass_unit, float* cwt, cudaStream_t s);
 int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_t* label, bool seeds_ready,
                  cudaStream_t s);
+// CTAs of the segmentation fallback's cooperative launch (-1 on failure).
+int fallback_blocks(int sm_count);
+// Seeds of the last segmentation and the cell count of each segment.
+int segment_sizes_impl(cwthf_ctx* ctx, int32_t* seeds, int64_t* n_cells, int64_t cap, int64_t* n_seeds,
+                       cudaStream_t s);
 // seeds_ready: the seed bitmap / ranks of `label` are already in ctx (after
 // segment_impl); bins_ready: ctx->dep_* hold the binned records of these
 // particles for this grid (after deposit_impl).

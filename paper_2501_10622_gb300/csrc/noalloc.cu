@@ -22,9 +22,10 @@
 // threads on one device) race on the array and give wrong results: order
 // them on one stream.
 //
-// Set-up: the first call on a device looks the array's device address up
-// with cudaGetSymbolAddress (with that device current) and caches it; make
-// that first call before any stream capture.
+// Set-up: every call made outside a stream capture looks the array's device
+// address up with cudaGetSymbolAddress (with the device current); a call made
+// during a capture reuses the address of the last such call on its device, so
+// make one call on each device before capturing.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -63,22 +64,22 @@ std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 int g_sms[kMaxDevices] = {};
 
-// Device address of the scratch on the current device (looked up once per
-// device), or nullptr on failure.
-void* scratch_address(int dev, int* sms) {
+// Device address of the scratch on the current device, or nullptr on failure.
+// Looked up on every call made outside a stream capture (so a module reloaded
+// after cudaDeviceReset is seen); a call made while `s` is being captured
+// uses the address of the last uncaptured call on this device.  Failures are
+// not cleared from the runtime's error state, so the caller still sees them.
+void* scratch_address(int dev, cudaStream_t s, int* sms) {
     if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return nullptr;
     std::lock_guard<std::mutex> g(g_mu);
-    if (!g_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_deposit_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return nullptr;
-        }
         int n = 0;
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
-            cudaGetLastError();
+        if (cudaGetSymbolAddress(&p, g_deposit_scratch) != cudaSuccess || !p ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
             return nullptr;
-        }
         g_sms[dev] = n;
         g_addr[dev] = p;
     }
@@ -100,9 +101,9 @@ extern "C" int cwthf_deposit_noalloc(const float* pos, const float* mass, double
         return CWTHF_E_INVALID_ARG;
     int dev = -1, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CWTHF_E_CUDA;
-    unsigned char* base = static_cast<unsigned char*>(scratch_address(dev, &sms));
-    if (!base) return CWTHF_E_CUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char* base = static_cast<unsigned char*>(scratch_address(dev, s, &sms));
+    if (!base) return CWTHF_E_CUDA;
     DepositScratch sc;
     sc.status = reinterpret_cast<int*>(base + kOffStatus);
     sc.mtot = reinterpret_cast<unsigned long long*>(base + kOffMtot);

@@ -14,10 +14,12 @@
 // shared memory as parent pointers and resolves every chain that stays inside
 // the tile.  A chain that leaves the tile is written as a flagged pointer
 // (bit 30) to the first cell outside; the global pass then replaces flagged
-// pointers by the label of their target (bounded walks, then pointer doubling
-// rounds if ever needed; hitting the round bound is reported as
-// CWTHF_E_NOT_CONVERGED).  The result does not depend on update order: every
-// update moves a pointer further along the (unique) chain.
+// pointers by the label of their target (bounded walks, then, only if a chain
+// outlived them, pointer-doubling rounds in one cooperative launch; hitting the
+// round bound is reported as CWTHF_E_NOT_CONVERGED).  The result does not
+// depend on update order: every update moves a pointer further along the
+// (unique) chain.
+#include <cuda/atomic>
 #include <type_traits>
 
 #include "internal.cuh"
@@ -36,7 +38,7 @@ constexpr int kLocal = kPlaneL * kChTZ;  // 16384 entries
 static_assert(kChTX == kPX && kPlaneL == (1 << kPlaneBits), "local index layout");
 constexpr int32_t kFlag = 1 << 30;
 constexpr int32_t kMask = kFlag - 1;
-constexpr int kChaseLimit = 64;  // longest chain the global pass follows per cell before doubling rounds
+constexpr int kChaseLimit = 64;  // default: longest chain the global pass follows per cell before doubling rounds
 constexpr int kJumpRoundsInTile = 16;  // in-place jumping rounds (each at least doubles the distance): 2^14 >= cells of a tile
 // Seeds of one tile: at most one local maximum per 2 x 2 x 2 block of cells
 // (any two cells of such a block are neighbours).
@@ -377,7 +379,7 @@ constexpr int kResolveRows = 4;  // tile rows a warp takes at a time
 // some warps far more work than others) and gathers the flagged cells of their non-empty
 // plane masks into a shared batch; every full batch of 32 cells (and the last,
 // partial one) is resolved by the whole warp: each lane follows its cell's
-// chain through the label grid (at most kChaseLimit steps), takes the label it
+// chain through the label grid (at most `limit` steps, kChaseLimit by default), takes the label it
 // reaches and the cells are counted with one atomic per distinct seed.  A cell
 // still unfinished at the limit stays flagged and sets changed[0]; the
 // doubling rounds then finish it and the cells are recounted.  Labels read
@@ -386,12 +388,13 @@ constexpr int kResolveRows = 4;  // tile rows a warp takes at a time
 __device__ __forceinline__ void resolve_batch(int32_t* __restrict__ label, bool valid, uint32_t c,
                                               const uint32_t* __restrict__ bits,
                                               const uint32_t* __restrict__ prefix,
-                                              const uint32_t* __restrict__ n_slots, HaloAcc* acc, bool& left) {
+                                              const uint32_t* __restrict__ n_slots, HaloAcc* acc, int limit,
+                                              bool& left) {
     int32_t lab = -1;
     if (valid) {
         int32_t w = label[c];
         int steps = 0;
-        while (w >= 0 && (w & kFlag) && steps < kChaseLimit) {
+        while (w >= 0 && (w & kFlag) && steps < limit) {
             w = label[w & kMask];
             steps++;
         }
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __rest
                                                                  const uint32_t* __restrict__ prefix,
                                                                  const uint32_t* __restrict__ n_slots,
                                                                  HaloAcc* acc, int* __restrict__ changed,
-                                                                 unsigned* __restrict__ next_row) {
+                                                                 unsigned* __restrict__ next_row, int limit) {
     __shared__ uint32_t batch[kResolveThreads / 32][64];  // pending cells (fewer than 32 between batches)
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -446,7 +449,7 @@ __global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __rest
                 k += __popc(b);
                 if (k >= 32) {
                     __syncwarp();
-                    resolve_batch(label, true, wl[lane], bits, prefix, n_slots, acc, left);
+                    resolve_batch(label, true, wl[lane], bits, prefix, n_slots, acc, limit, left);
                     const uint32_t rest = wl[32 + lane];
                     __syncwarp();
                     if (uint32_t(lane) + 32 < k) wl[lane] = rest;
@@ -457,51 +460,88 @@ __global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __rest
         }
     }
     __syncwarp();
-    if (k) resolve_batch(label, uint32_t(lane) < k, uint32_t(lane) < k ? wl[lane] : 0u, bits, prefix, n_slots, acc, left);
+    if (k) resolve_batch(label, uint32_t(lane) < k, uint32_t(lane) < k ? wl[lane] : 0u, bits, prefix, n_slots, acc, limit,
+                         left);
     if (__any_sync(full, left) && lane == 0) changed[0] = 1;
 }
 
-// Fallback when a chain outlived the bounded walks: after the doubling rounds,
-// clear and recount the cells of every seed (does nothing otherwise).
-__global__ void __launch_bounds__(256) k_seg_recount(const int32_t* __restrict__ label, int64_t cells,
-                                                     const uint32_t* __restrict__ bits,
-                                                     const uint32_t* __restrict__ prefix,
-                                                     const uint32_t* __restrict__ n_slots, HaloAcc* acc,
-                                                     const int* __restrict__ changed, int phase) {
-    if (changed[0] == 0) return;
+// Bounded grid-wide barrier of the fallback kernel, which is launched
+// cooperatively (every CTA resident).  bar[0] counts arrivals, bar[1] is the
+// generation.  The wait gives up after kSpinLimit polls, records
+// CWTHF_E_TIMEOUT and returns false; the CTA then leaves the kernel.
+__device__ bool grid_sync(unsigned* bar, int* status) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(bar[0]), gen(bar[1]);
+        const unsigned g = gen.load(cuda::memory_order_acquire);
+        __threadfence();
+        if (cnt.fetch_add(1u, cuda::memory_order_acq_rel) == gridDim.x - 1) {
+            cnt.store(0u, cuda::memory_order_relaxed);
+            gen.store(g + 1u, cuda::memory_order_release);
+        } else {
+            long long it = 0;
+            while (gen.load(cuda::memory_order_acquire) == g) {
+                if (++it > kSpinLimit) {
+                    ok = 0;
+                    set_status(status, CWTHF_E_TIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Fallback for chains that outlived the bounded walks (changed[0] set by the
+// resolve pass); returns at once otherwise.  Round r (1 <= r <= rounds)
+// replaces every flagged pointer by its target's label, which moves it 2^(r-1)
+// or more links further, so 31 rounds finish any chain of a grid of at most
+// 2^30 cells; changed[r] records whether a pointer is still flagged after it.
+// Rounds are separated by grid barriers.  Then the cell counts of every seed
+// are cleared and recounted from the finished labels.  A flag still set after
+// the last round is reported as CWTHF_E_NOT_CONVERGED (the labels are then
+// unspecified, and flagged values are skipped by the recount).
+__global__ void __launch_bounds__(256) k_seg_fallback(int32_t* __restrict__ label, int64_t cells, int* changed,
+                                                      int rounds, const uint32_t* __restrict__ bits,
+                                                      const uint32_t* __restrict__ prefix,
+                                                      const uint32_t* __restrict__ n_slots, HaloAcc* acc,
+                                                      unsigned* bar, int* status) {
+    if (*reinterpret_cast<volatile int*>(&changed[0]) == 0) return;  // the same answer in every CTA
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (phase == 0) {
-        for (int64_t s = gid; s < int64_t(*n_slots); s += stride) acc[s].n_cells = 0;
-        return;
+    bool done = false;
+    for (int r = 1; r <= rounds; r++) {
+        bool any = false;
+        for (int64_t c = gid; c < cells; c += stride) {
+            const int32_t v = label[c];
+            if (v >= 0 && (v & kFlag)) {
+                const int32_t w = label[v & kMask];
+                label[c] = w;
+                any |= (w >= 0 && (w & kFlag));  // still a pointer: another round is needed
+            }
+        }
+        if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(&changed[r], 1);
+        if (!grid_sync(bar, status)) return;
+        if (*reinterpret_cast<volatile int*>(&changed[r]) == 0) {
+            done = true;
+            break;
+        }
     }
+    if (!done && gid == 0) set_status(status, CWTHF_E_NOT_CONVERGED);
+    const int64_t ns = *n_slots;
+    for (int64_t s = gid; s < ns; s += stride) acc[s].n_cells = 0;
+    if (!grid_sync(bar, status)) return;
     for (int64_t c = gid; c < cells; c += stride) {
         uint32_t slot;
         const int32_t l = label[c];
-        if (l >= 0 && seed_slot(bits, prefix, n_slots, l, slot)) atomicAdd(&acc[slot].n_cells, 1ull);
+        if (l >= 0 && int64_t(l) < cells && seed_slot(bits, prefix, n_slots, l, slot))
+            atomicAdd(&acc[slot].n_cells, 1ull);
     }
-}
-
-// One global round: replace every flagged pointer by its target's label;
-// changed[round] records whether any pointer is still flagged afterwards.
-__global__ void __launch_bounds__(256) k_seg_jump(int32_t* __restrict__ label, int64_t cells,
-                                                         int* __restrict__ changed, int round) {
-    if (round > 0 && changed[round - 1] == 0) return;  // converged earlier
-    bool any = false;
-    int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < cells; c += stride) {
-        int32_t v = label[c];
-        if (v >= 0 && (v & kFlag)) {
-            int32_t w = label[v & kMask];
-            label[c] = w;
-            any |= (w >= 0 && (w & kFlag));  // still a pointer: another round is needed
-        }
-    }
-    if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) changed[round] = 1;
-}
-
-__global__ void k_seg_jump_check(const int* changed, int rounds, int* status) {
-    if (changed[rounds - 1]) set_status(status, CWTHF_E_NOT_CONVERGED);
 }
 
 __global__ void k_popc(const uint32_t* __restrict__ bits, int64_t nwords, uint32_t* __restrict__ out) {
@@ -551,7 +591,28 @@ __global__ void k_seeds_from_labels(const int32_t* __restrict__ label, int64_t c
     }
 }
 
+// Seeds of the last segmentation and their segments' cell counts.
+__global__ void k_segment_sizes(const int32_t* __restrict__ seed_list, const HaloAcc* __restrict__ acc,
+                                const uint32_t* __restrict__ n_slots, int64_t cap, int32_t* __restrict__ seeds,
+                                int64_t* __restrict__ n_cells, int64_t* __restrict__ n_out) {
+    const int64_t ns = *n_slots;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_out = ns;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < min(ns, cap); i += stride) {
+        seeds[i] = seed_list[i];
+        n_cells[i] = int64_t(acc[i].n_cells);
+    }
+}
+
 }  // namespace
+
+int segment_sizes_impl(cwthf_ctx* ctx, int32_t* seeds, int64_t* n_cells, int64_t cap, int64_t* n_seeds,
+                       cudaStream_t s) {
+    CWTHF_LAUNCH(ctx, s, "k_segment_sizes",
+                 k_segment_sizes<<<ctx->sm_count, 256, 0, s>>>(ctx->seed_list, ctx->acc, ctx->n_seeds, cap, seeds,
+                                                               n_cells, n_seeds));
+    return cuda_status(cudaGetLastError());
+}
 
 int seeds_rank(cwthf_ctx* ctx, int ng, const uint16_t* seed_cells, cudaStream_t s) {
     int64_t cells = int64_t(ng) * ng * ng;
@@ -575,14 +636,35 @@ int seeds_from_labels(cwthf_ctx* ctx, const int32_t* label, int ng, cudaStream_t
     return seeds_rank(ctx, ng, nullptr, s);
 }
 
+// CTAs of the cooperative fallback launch: all resident at once (its grid
+// barriers need that), at most four per SM.
+int fallback_blocks(int sm_count) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seg_fallback, 256, 0) != cudaSuccess || per_sm < 1)
+        return -1;
+    return std::min(per_sm, 4) * sm_count;
+}
+
+int launch_fallback(cwthf_ctx* ctx, int32_t* label, int64_t cells, cudaStream_t s) {
+    if (ctx->fallback_blocks <= 0) return CWTHF_E_CUDA;
+    int* changed = ctx->jump_changed;
+    unsigned* bar = reinterpret_cast<unsigned*>(changed + kJumpBarrier);
+    int rounds = ctx->dbg_jump_rounds;
+    void* args[] = {&label, &cells, &changed, &rounds, &ctx->seed_bits, &ctx->seed_prefix,
+                    &ctx->n_seeds, &ctx->acc, &bar, &ctx->d_status};
+    cudaError_t e;
+    CWTHF_LAUNCH(ctx, s, "k_seg_fallback",
+                 e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_seg_fallback),
+                                                 dim3(unsigned(ctx->fallback_blocks)), dim3(256), args, 0, s));
+    return cuda_status(e);
+}
+
 int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_t* label, bool,
                  cudaStream_t s) {
     int64_t cells = int64_t(ng) * ng * ng;
     int64_t nwords = (cells + 31) / 32;
     cudaError_t e = cudaMemsetAsync(ctx->seed_bits, 0, size_t(nwords) * 4, s);
-    // jump_changed[0 .. kMaxJumpRounds]: round flags; [kMaxJumpRounds + 1]: the
-    // resolve pass's row counter
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->jump_changed, 0, sizeof(int) * (kMaxJumpRounds + 2), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->jump_changed, 0, sizeof(int) * kJumpWords, s);
     if (e != cudaSuccess) return cuda_status(e);
     // parent codes (1 byte per cell) and the flagged-cell masks of every chain
     // tile (one bit per cell) in the context's int64 grid buffer (8 bytes per
@@ -603,21 +685,16 @@ int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_
     int rc = seeds_rank(ctx, ng, ctx->seed_cells, s);
     if (rc) return rc;
     int blocks = ctx->sm_count * 8;
+    int* changed = ctx->jump_changed;  // see kJumpWords
     CWTHF_LAUNCH(ctx, s, "k_seg_resolve",
                  k_seg_resolve<<<blocks, kResolveThreads, 0, s>>>(label, ng, ballots, ctx->seed_bits,
-                                                                   ctx->seed_prefix, ctx->n_seeds, ctx->acc,
-                                                                   ctx->jump_changed,
-                                                                   reinterpret_cast<unsigned*>(
-                                                                       ctx->jump_changed + kMaxJumpRounds + 1)));
-    // pointer doubling for whatever the bounded walks left (normally nothing: every round exits at once)
-    for (int r = 1; r < kMaxJumpRounds; r++) {
-        CWTHF_LAUNCH(ctx, s, "k_seg_jump", k_seg_jump<<<blocks, 256, 0, s>>>(label, cells, ctx->jump_changed, r));
-    }
-    CWTHF_LAUNCH(ctx, s, "k_seg_jump_check", k_seg_jump_check<<<1, 1, 0, s>>>(ctx->jump_changed, kMaxJumpRounds, ctx->d_status));
-    for (int phase = 0; phase < 2; phase++)
-        CWTHF_LAUNCH(ctx, s, "k_seg_recount",
-                     k_seg_recount<<<blocks, 256, 0, s>>>(label, cells, ctx->seed_bits, ctx->seed_prefix,
-                                                          ctx->n_seeds, ctx->acc, ctx->jump_changed, phase));
+                                                                   ctx->seed_prefix, ctx->n_seeds, ctx->acc, changed,
+                                                                   reinterpret_cast<unsigned*>(changed + kJumpRowCounter),
+                                                                   ctx->dbg_chase_limit));
+    // pointer doubling and a recount for whatever the bounded walks left
+    // (normally nothing: the kernel then returns at once)
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    return launch_fallback(ctx, label, cells, s);
     return cuda_status(cudaGetLastError());
 }
 

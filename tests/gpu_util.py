@@ -1,4 +1,7 @@
 """Helpers shared by the GPU parity tests (no method arithmetic here)."""
+import json
+import os
+
 import numpy as np
 import torch
 
@@ -26,3 +29,12 @@ def random_box(n, L, seed, frac_out=0.02):
     pos[:k] += rng.choice([-L, L], size=(k, 3))
     pos[k:2 * k] = np.floor(pos[k:2 * k] / L * 8) * (L / 8)
     return pos.astype(np.float32)
+
+
+def record(entry: dict):
+    """Appends one JSON line of measured parity figures to the file named by
+    the CWTHF_PRECISION_LOG environment variable (nothing when it is unset)."""
+    path = os.environ.get("CWTHF_PRECISION_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(entry, default=float) + "\n")

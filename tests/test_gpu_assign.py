@@ -59,3 +59,24 @@ def test_capacity_reported(gctx, work64):
     wl, pos, ref = work64
     rc, n = _compare(gctx, pos.numpy(), wl.box, ref["label"], ref["cwt32"], dens_th=0.0, pth=0, cap=7)
     assert rc == pkg._lib.E_CAPACITY and n > 7
+
+
+def test_workload256_on_the_gpu_field(gctx):
+    # at the 256^3 workload the oracle segments the GPU's own fp32 CWT field:
+    # labels bit for bit, then the assignment and catalogue element by element
+    from paper_2501_10622_gb300 import synth
+    wl = synth.WORKLOADS["clumped-256cube-L200"]
+    pos = wl.positions().numpy()
+    c = gctx.transform(gctx.deposit(dev(pos), wl.box, wl.ng), wl.box, 2.0)
+    lab = gctx.segment(c)
+    gctx.check()
+    C = c.cpu().numpy()
+    ref_lab = oracle.segment(C)
+    np.testing.assert_array_equal(lab.cpu().numpy(), ref_lab)
+    seeds, n_cells, ns = gctx.segment_sizes(1 << 22)
+    want_seeds, want_cells = np.unique(ref_lab[ref_lab >= 0], return_counts=True)
+    assert ns == len(want_seeds)
+    np.testing.assert_array_equal(seeds.cpu().numpy(), want_seeds)
+    np.testing.assert_array_equal(n_cells.cpu().numpy(), want_cells)
+    rc, n = _compare(gctx, pos, wl.box, ref_lab, C, cap=1 << 20)
+    assert rc == 0 and n > 1000

@@ -1,4 +1,11 @@
-"""The whole path through cwthf_find against the oracle run end to end."""
+"""The whole path through cwthf_find against the oracle run end to end.
+
+Acceptance: at least 99.9 % of particles get the oracle's halo id, and every
+particle that does not is explained as a near tie (tests/near_tie.py): a
+steepest-ascent choice or a seed threshold that fp32 rounding can flip, or a
+halo whose members differ by such cells and whose threshold decision flips.
+Halos kept on one side only must be explained the same way, and halos with
+identical members on both sides must have identical catalogue entries."""
 import numpy as np
 import pytest
 import torch
@@ -6,19 +13,59 @@ import torch
 import oracle
 import paper_2501_10622_gb300 as pkg
 from paper_2501_10622_gb300 import synth
-from tests.gpu_util import dev
+from tests import near_tie
+from tests.gpu_util import cwt_errors, dev, record
 
 pytestmark = pytest.mark.gpu
 
 
+def _nodes(pos, L, ng):
+    q = oracle.quantise(pos, L, ng)
+    n = (q + 512) >> 10
+    n[n == ng] = 0
+    return (n[:, 2] * ng + n[:, 1]) * ng + n[:, 0]
+
+
+def classified_find(ctx, name, pos, L, ng, w, ref, mass=None, mass_unit=1.0):
+    """cwthf_find against oracle.find with every disagreement classified."""
+    p = dev(pos)
+    m = None if mass is None else dev(mass)
+    hid, cat, nh = ctx.find(p, L, ng, [pkg.default_params(w)], mass=m, mass_unit=mass_unit)
+    # the find's field and labels, through the stage entry points (same kernels)
+    c = ctx.transform(ctx.deposit(p, L, ng, mass=m, mass_unit=mass_unit), L, w, mass_unit=mass_unit)
+    lab = ctx.segment(c)
+    ctx.check()
+    C32g, lab_g, hid_g = c.cpu().numpy(), lab.cpu().numpy().reshape(-1), hid[0].cpu().numpy()
+    node = _nodes(pos, L, ng)
+    on = hid_g >= 0
+    assert np.array_equal(hid_g[on], lab_g[node[on]])  # find used these labels
+    r = near_tie.classify_find(ref["cwt"], ref["cwt32"], C32g, ref["label"], lab_g, node, ref["halo_id"], hid_g)
+    assert r["cell_counts"]["unexplained"] == 0, (name, r["cell_counts"])
+    assert r["counts"]["unexplained"] == 0, (name, r["counts"])
+    got = pkg.catalogue_to_numpy(cat[0], nh[0])
+    want = ref["cat"]
+    bad = near_tie.classify_catalogues(want["seed"], got["seed"], ref["label"], lab_g,
+                                       dict(zip(r["cells"].tolist(), r["cell_class"].tolist())), r["touched_seeds"])
+    assert bad == [], (name, bad[:10])
+    common, gi, ri = np.intersect1d(got["seed"], want["seed"], return_indices=True)
+    same = ~np.isin(common, list(r["touched_seeds"]))  # identical members on both sides
+    for col in ("n_part", "n_cells", "mass", "centre"):
+        assert np.array_equal(got[col][gi[same]], want[col][ri[same]]), (name, col)
+    agree = float(np.mean(hid_g == ref["halo_id"]))
+    assert agree >= 0.999, (name, agree)
+    rel_l2, max_rel = cwt_errors(C32g, ref["cwt"])
+    record({"config": name, "ng": ng, "np": int(pos.shape[0]), "w": w, "cwt_rel_l2": rel_l2,
+            "cwt_max_rel": max_rel, "particle_agreement": agree, "particles_differing": int(len(r["particles"])),
+            "particle_classes": r["counts"], "cells_differing": int(len(r["cells"])),
+            "cell_classes": r["cell_counts"], "halos_gpu": int(nh[0]), "halos_oracle": int(len(want["seed"])),
+            "halos_one_side_only": int(len(np.setxor1d(got["seed"], want["seed"]))),
+            "halos_identical": int(same.sum())})
+    return hid, cat, nh, r
+
+
 def test_workload64_agreement(gctx, work64):
     wl, pos, ref = work64
-    hid, cat, nh = gctx.find(dev(pos), wl.box, wl.ng, [pkg.default_params(2.0)])
-    gctx.check()
-    agree = float(np.mean(hid[0].cpu().numpy() == ref["halo_id"]))
-    assert agree >= 0.999, agree
-    n = int(nh[0])
-    assert abs(n - len(ref["cat"]["seed"])) <= max(2, n // 50)
+    classified_find(gctx, "clumped 64^3 particles, 64^3 grid, L=50", pos.numpy(), wl.box, wl.ng, 2.0, ref)
 
 
 def _multi_equals_single(ctx, wl, p, ws):
@@ -64,13 +111,9 @@ def test_find_equals_stage_by_stage(gctx, work64):
 
 def test_workload256_agreement(gctx):
     wl = synth.WORKLOADS["clumped-256cube-L200"]
-    pos = wl.positions("cuda")
-    hid, cat, nh = gctx.find(pos, wl.box, wl.ng, [pkg.default_params(2.0)])
-    gctx.check()
-    ref = oracle.find(pos.cpu().numpy(), wl.box, wl.ng, 2.0)
-    agree = float(np.mean(hid[0].cpu().numpy() == ref["halo_id"]))
-    print(f"256^3 particle agreement {agree:.6f}, halos {int(nh[0])} vs {len(ref['cat']['seed'])}")
-    assert agree >= 0.999
+    pos = wl.positions().numpy()
+    ref = oracle.find(pos, wl.box, wl.ng, 2.0)
+    classified_find(gctx, "clumped 256^3 particles, 256^3 grid, L=200", pos, wl.box, wl.ng, 2.0, ref)
 
 
 def test_ragged_grid_agreement(gctx):
@@ -78,14 +121,16 @@ def test_ragged_grid_agreement(gctx):
     # part-filled along x and z; same cell size and density as the 64^3 case
     ng = 48
     box = ng * 0.78125
-    pos = synth.clumped_box(ng ** 3, box, 84, seed=11)
-    ref = oracle.find(pos.numpy(), box, ng, 2.0)
-    hid, cat, nh = gctx.find(dev(pos), box, ng, [pkg.default_params(2.0)])
-    gctx.check()
-    agree = float(np.mean(hid[0].cpu().numpy() == ref["halo_id"]))
-    assert agree >= 0.999, agree
-    n = int(nh[0])
-    assert abs(n - len(ref["cat"]["seed"])) <= max(2, n // 50)
+    pos = synth.clumped_box(ng ** 3, box, 84, seed=11).numpy()
+    ref = oracle.find(pos, box, ng, 2.0)
+    classified_find(gctx, "clumped 48^3 particles, 48^3 grid (ragged tiles)", pos, box, ng, 2.0, ref)
+
+
+@pytest.mark.parametrize("w", [3.0, 4.0])
+def test_workload64_other_scales(gctx, work64, w):
+    wl, pos, _ = work64
+    ref = oracle.find(pos.numpy(), wl.box, wl.ng, w)
+    classified_find(gctx, f"clumped 64^3 particles, 64^3 grid, L=50, w={w:g}", pos.numpy(), wl.box, wl.ng, w, ref)
 
 
 def test_empty_particle_set_find(gctx):
@@ -105,16 +150,6 @@ def test_variable_masses_agreement(gctx, work64):
     m = np.random.default_rng(3).uniform(0.5, 2.0, pos.shape[0]).astype(np.float32)
     mu = 1.0 / 64
     ref = oracle.find(pos.numpy(), wl.box, wl.ng, 2.0, mass=m, mass_unit=mu)
-    hid, cat, nh = gctx.find(dev(pos), wl.box, wl.ng, [pkg.default_params(2.0)], mass=dev(m), mass_unit=mu)
-    gctx.check()
-    agree = float(np.mean(hid[0].cpu().numpy() == ref["halo_id"]))
-    assert agree >= 0.999, agree
-    n = int(nh[0])
-    assert abs(n - len(ref["cat"]["seed"])) <= max(2, n // 50)
-    # halos both sides found with the same members' count carry the same exact mass
-    got = pkg.catalogue_to_numpy(cat[0], n)
-    common, gi, ri = np.intersect1d(got["seed"], ref["cat"]["seed"], return_indices=True)
-    same = got["n_part"][gi] == ref["cat"]["n_part"][ri]
-    assert same.sum() >= 0.9 * len(common) > 0
-    eq = got["mass"][gi][same] == ref["cat"]["mass"][ri][same]
-    assert eq.mean() >= 0.99, eq.mean()
+    hid, cat, nh, r = classified_find(gctx, "clumped 64^3, variable masses", pos.numpy(), wl.box, wl.ng, 2.0, ref,
+                                      mass=m, mass_unit=mu)
+    assert int(nh[0]) > 0

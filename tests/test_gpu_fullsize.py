@@ -104,6 +104,24 @@ def test_segmentation_properties(big):
     assert np.all(_strict_parent(C, seeds) == seeds) and np.all(C.reshape(-1)[seeds] > 0.0)
 
 
+def test_segmentation_bit_exact_on_the_gpu_field(big):
+    # the oracle's sequential segmentation of the GPU's own 1024^3 fp32 field
+    # (one C pass over 2^30 cells): every label bit for bit
+    ctx, pos, grid_ref = big
+    g = torch.from_numpy(grid_ref).cuda()
+    c = ctx.transform(g, WL.box, WL.scales[0])
+    del g
+    lab = ctx.segment(c, 0.0)
+    ctx.check()
+    C = c.cpu().numpy()
+    del c
+    got = lab.cpu().numpy()
+    del lab
+    torch.cuda.empty_cache()
+    ref = oracle.segment(C, 0.0)
+    assert np.array_equal(got, ref)
+
+
 def test_grid512_deposit_and_cwt_spots(gctx):
     # the 512^3 grid takes the other compile-time FFT instances
     wl = synth.WORKLOADS["clumped-256cube-grid512-L250"]

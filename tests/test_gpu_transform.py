@@ -56,3 +56,31 @@ def test_workload256(gctx):
     rel, mx = cwt_errors(c.cpu().numpy(), ref)
     print(f"256^3 CWT rel-L2 {rel:.3e} max-rel {mx:.3e}")
     assert rel <= CWT_REL_L2 and mx <= CWT_MAX_REL
+
+
+@pytest.mark.parametrize("ng", [16, 256])
+def test_stuck_copy_reports_timeout(gctx, ng):
+    # Fault injection without a fault: in the next y/z pass one CTA arms its
+    # transfer barrier for the tile but issues no copy, so its bounded wait runs
+    # out with nothing in flight.  The call must come back as CWTHF_E_TIMEOUT,
+    # and the same context must then transform correctly (16^3 takes the
+    # run-time FFT plan, 256^3 a compile-time one).
+    import paper_2501_10622_gb300 as pkg
+    L, w = 0.78125 * ng, 2.0
+    pos = synth.clumped_box(ng ** 3 // 4, L, 4, seed=ng).numpy()
+    grid, _ = oracle.cic(pos, L, ng)
+    g = dev(grid)
+    gctx.debug_set(pkg._lib.DEBUG_TMA_NO_COPY, 1)
+    gctx.transform(g, L, w)
+    assert gctx.sync() == pkg._lib.E_TIMEOUT
+    assert gctx.debug_get(pkg._lib.DEBUG_TMA_NO_COPY) == 0  # one-shot
+    c = gctx.transform(g, L, w)
+    gctx.check()
+    if ng <= 64:
+        rel, mx = cwt_errors(c.cpu().numpy(), oracle.cwt(grid, L, w))
+        assert rel <= CWT_REL_L2 and mx <= CWT_MAX_REL, (rel, mx)
+    else:
+        nodes = np.random.default_rng(1).integers(0, ng ** 3, 24)
+        ref = oracle.cwt_at(grid, L, w, nodes)
+        got = c.cpu().numpy().reshape(-1)[nodes].astype(np.float64)
+        assert np.max(np.abs(got - ref)) <= CWT_MAX_REL * np.max(np.abs(c.cpu().numpy()))
