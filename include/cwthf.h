@@ -72,7 +72,8 @@ enum {
     CWTHF_E_TIMEOUT = 7,          /* a bounded device wait gave up */
     CWTHF_E_CAPACITY = 8,         /* more halos than cat_cap; the count is still reported */
     CWTHF_E_BAD_INPUT = 9,        /* non-finite or out-of-range position / mass / CWT value */
-    CWTHF_E_SCRATCH_LIMIT = 10    /* too large for cwthf_deposit_noalloc's fixed scratch */
+    CWTHF_E_SCRATCH_LIMIT = 10,   /* too large for cwthf_deposit_noalloc's fixed scratch */
+    CWTHF_E_TABLE_CACHE = 11      /* no FFT / wavelet table slot left (see cwthf_create) */
 };
 
 typedef struct cwthf_ctx cwthf_ctx;
@@ -106,7 +107,15 @@ CWTHF_API void cwthf_default_params(double w, cwthf_params *p);
  * cwthf_find call will use (scales beyond the first need a second complex
  * workspace).  Allocates all device memory up front (cudaMalloc), so later
  * calls allocate nothing.  Returns CWTHF_E_OOM if that fails (nothing is
- * leaked), CWTHF_E_CUDA if the device cannot be used. */
+ * leaked), CWTHF_E_CUDA if the device cannot be used.
+ * The context keeps 48 slots for the FFT twiddles (one per grid size) and the
+ * wavelet spectra (one per grid size, box and scale) that the transform
+ * needs.  A call that needs a table not yet held computes it on the host in
+ * fp64 and queues one copy on its stream; a full cache reuses the least
+ * recently used slot (waiting, on the host, for that slot's previous copy).
+ * A slot used by work captured into a CUDA graph is kept for the context's
+ * lifetime; during a capture, a call that needs a new table while no slot is
+ * free fails with CWTHF_E_TABLE_CACHE (nothing queued). */
 CWTHF_API int cwthf_create(int device, int max_ng, int64_t max_np, int max_scales, cwthf_ctx **out);
 CWTHF_API void cwthf_destroy(cwthf_ctx *ctx);
 
@@ -128,6 +137,13 @@ CWTHF_API int cwthf_check_ng(int ng);
  *   mtot  device, int64 [1] or NULL: receives sum_i m_q. */
 CWTHF_API int cwthf_deposit(cwthf_ctx *ctx, const float *pos, const float *mass, double mass_unit, int64_t np,
                   double L, int ng, int64_t *grid, int64_t *mtot, void *stream);
+
+/* Fills the context's table slots (see cwthf_create) with the FFT twiddles
+ * of grid size ng and the wavelet spectra of the n_scales scales w[] (host,
+ * double [n_scales]) for a box of side L, so that later calls with these
+ * parameters do no host-side table work.  Queues one small copy per new table
+ * on `stream`.  Errors: as cwthf_transform, and CWTHF_E_TABLE_CACHE. */
+CWTHF_API int cwthf_prepare(cwthf_ctx *ctx, int ng, double L, const double *w, int n_scales, void *stream);
 
 /* Sec. 2.1, Eq. 2-4.  Grid CWT at scale w of the CIC mass grid: the circular
  * convolution C(x_g) = sum_g' m_g' Psi(w, x_g - x_g') with the Mexican hat
@@ -243,12 +259,15 @@ CWTHF_API int cwthf_deposit_noalloc(const float *pos, const float *mass, double 
  *   CWTHF_DEBUG_FALLBACK_RAN (get only): 1 if the last segmentation needed
  *       the doubling rounds (a chain outlived the bounded walks), else 0;
  *       waits for `stream`.
+ *   CWTHF_DEBUG_TABLE_FILLS (get only): table slots filled since the context
+ *       was created (each a host-side table computation and one copy).
  * cwthf_debug_set returns CWTHF_E_INVALID_ARG for an unknown key or a value
  * out of range; settings persist for the context's lifetime. */
 #define CWTHF_DEBUG_JUMP_ROUNDS 1
 #define CWTHF_DEBUG_CHASE_LIMIT 2
 #define CWTHF_DEBUG_TMA_NO_COPY 3
 #define CWTHF_DEBUG_FALLBACK_RAN 4
+#define CWTHF_DEBUG_TABLE_FILLS 5
 CWTHF_API int cwthf_debug_set(cwthf_ctx *ctx, int key, int64_t value);
 CWTHF_API int cwthf_debug_get(cwthf_ctx *ctx, int key, int64_t *value, void *stream);
 

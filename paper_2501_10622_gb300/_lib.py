@@ -21,10 +21,11 @@ HEADER = _PKG.parent / "include" / "cwthf.h"
 OK = 0
 E_INVALID_ARG, E_UNSUPPORTED_SIZE, E_OVERFLOW, E_OOM, E_CUDA, E_NOT_CONVERGED, E_TIMEOUT, E_CAPACITY, E_BAD_INPUT = range(1, 10)
 E_SCRATCH_LIMIT = 10
+E_TABLE_CACHE = 11
 FRAC_BITS = 10
 MIN_NG, MAX_NG = 8, 1024
 # cwthf_debug_set / cwthf_debug_get keys
-DEBUG_JUMP_ROUNDS, DEBUG_CHASE_LIMIT, DEBUG_TMA_NO_COPY, DEBUG_FALLBACK_RAN = 1, 2, 3, 4
+DEBUG_JUMP_ROUNDS, DEBUG_CHASE_LIMIT, DEBUG_TMA_NO_COPY, DEBUG_FALLBACK_RAN, DEBUG_TABLE_FILLS = 1, 2, 3, 4, 5
 
 HALO_DTYPE = np.dtype([("seed", "<i8"), ("n_part", "<i8"), ("n_cells", "<i8"), ("mass", "<f8"),
                        ("centre", "<f8", (3,)), ("peak", "<f4"), ("reserved", "<i4")])
@@ -67,6 +68,7 @@ def lib() -> ctypes.CDLL:
         L.cwthf_transform.argtypes = [P, P, i32, d, d, d, P, P]
         L.cwthf_segment.argtypes = [P, P, i32, f, P, P]
         L.cwthf_segment_sizes.argtypes = [P, P, P, i64, P, P]
+        L.cwthf_prepare.argtypes = [P, i32, d, ctypes.POINTER(d), i32, P]
         L.cwthf_debug_set.argtypes = [P, i32, i64]
         L.cwthf_debug_get.argtypes = [P, i32, ctypes.POINTER(i64), P]
         L.cwthf_assign.argtypes = [P, P, P, d, i64, d, i32, P, P, ctypes.POINTER(Params), P, P, i64, P, P]
@@ -224,6 +226,14 @@ class Context:
                                          self._stream(stream)), "cwthf_segment_sizes")
         k = int(n)
         return seeds[:min(k, cap)], n_cells[:min(k, cap)], k
+
+    def prepare(self, ng, L, ws, stream=None):
+        """Fill the table slots for grid size ng, box L and scales ws."""
+        arr = (ctypes.c_double * max(len(ws), 1))(*ws)
+        _check(lib().cwthf_prepare(self._h, int(ng), float(L), arr, len(ws), self._stream(stream)), "cwthf_prepare")
+
+    def table_fills(self) -> int:
+        return self.debug_get(DEBUG_TABLE_FILLS)
 
     def debug_set(self, key: int, value: int):
         _check(lib().cwthf_debug_set(self._h, int(key), int(value)), "cwthf_debug_set")

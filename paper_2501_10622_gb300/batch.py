@@ -7,10 +7,10 @@ on its slot's stream, the slot streams forked from and joined back into one
 capture stream -- is recorded once into a CUDA graph; a batch then costs a
 single graph launch, and jobs on different slots overlap on the GPU.
 
-Before capture every job runs once eagerly, so that the library's per-size
-FFT and wavelet tables exist (their first use allocates, which a capture
-cannot contain).  Results are deterministic: each job's halo ids equal those
-of a single cwthf_find call.
+Nothing runs eagerly before the capture: the library keeps its FFT and
+wavelet tables in slots sized when the contexts are created, and a captured
+call records the copies of the tables it needs into the graph.  Results are
+deterministic: each job's halo ids equal those of a single cwthf_find call.
 """
 from __future__ import annotations
 
@@ -83,7 +83,6 @@ class Batch:
         self.check()
 
     def capture(self):
-        self.run_eager()  # tables for every (grid, box, scale) exist before capture
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph, stream=self.main):
             self._enqueue(self.main)

@@ -3,12 +3,22 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "internal.cuh"
 
 namespace cwthf {
 
 bool fft_size_supported(int ng);
+
+// An NVTX range around the host-side enqueue of one stage (profilers show it
+// on the CPU timeline and project it onto the kernels it launched).
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 int check_ng(int ng) {
     if (ng < CWTHF_MIN_NG || ng > CWTHF_MAX_NG || ng % 2) return CWTHF_E_UNSUPPORTED_SIZE;
@@ -53,6 +63,8 @@ Sizes sizes_for(int max_ng, int64_t max_np) {
     return z;
 }
 
+size_t table_slot_floats(int max_ng) { return 3 * size_t(max_ng); }
+
 // The allocation plan: (pointer slot, bytes).  One list drives both
 // cwthf_create and cwthf_workspace_bytes.
 template <class F>
@@ -87,6 +99,7 @@ void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, F
     f(reinterpret_cast<void**>(&c->grid), size_t(z.cells) * 8);
     f(reinterpret_cast<void**>(&c->cwt), size_t(z.cells) * 4);
     f(reinterpret_cast<void**>(&c->label), size_t(z.cells) * 4);
+    f(reinterpret_cast<void**>(&c->table_dev), table_slot_floats(max_ng) * kTableSlots * 4);
 }
 
 void release(cwthf_ctx* c) {
@@ -96,6 +109,8 @@ void release(cwthf_ctx* c) {
     });
     if (c->h_status) cudaFreeHost(c->h_status);
     c->h_status = nullptr;
+    if (c->table_host) cudaFreeHost(c->table_host);
+    c->table_host = nullptr;
     free_tables(c);
 }
 
@@ -174,6 +189,9 @@ int cwthf_create(int device, int max_ng, int64_t max_np, int max_scales, cwthf_c
         }
     });
     if (!failed && cudaMallocHost(&c->h_status, sizeof(int) * 2) != cudaSuccess) failed = true;
+    c->table_slot_floats = table_slot_floats(max_ng);
+    if (!failed && cudaMallocHost(&c->table_host, c->table_slot_floats * kTableSlots * 4) != cudaSuccess) failed = true;
+    if (!failed && init_tables(c) != CWTHF_OK) failed = true;
     if (!failed) {
         Sizes z = sizes_for(max_ng, max_np);
         c->scan_tmp_cap = z.scan_words;
@@ -207,6 +225,7 @@ int cwthf_deposit(cwthf_ctx* ctx, const float* pos, const float* mass, double ma
     if (!rc && !grid) rc = CWTHF_E_INVALID_ARG;
     if (rc) return rc;
     DeviceGuard g(ctx->device);
+    Range r("cwthf_deposit (S1)");
     return deposit_impl(ctx, pos, mass, mass_unit, np, L, ng, grid, mtot, as_stream(stream));
 }
 
@@ -217,9 +236,23 @@ int cwthf_transform(cwthf_ctx* ctx, const int64_t* grid, int ng, double L, doubl
     if (!grid || !cwt || !(w > 0) || !std::isfinite(w) || !(mass_unit > 0)) return CWTHF_E_INVALID_ARG;
     DeviceGuard g(ctx->device);
     cudaStream_t s = as_stream(stream);
-    rc = transform_forward_xy(ctx, grid, ng, ctx->spec, s);
-    if (!rc) rc = transform_wavelet_inverse(ctx, ctx->spec, ctx->spec, ng, L, w, mass_unit, cwt, s);
+    const float* wtab = nullptr;
+    Range r("cwthf_transform (S2-S4)");
+    rc = transform_tables(ctx, ng, L, &w, 1, &wtab, s);
+    if (!rc) rc = transform_forward_xy(ctx, grid, ng, ctx->spec, s);
+    if (!rc) rc = transform_wavelet_inverse(ctx, ctx->spec, ctx->spec, ng, L, w, mass_unit, wtab, cwt, s);
     return rc;
+}
+
+int cwthf_prepare(cwthf_ctx* ctx, int ng, double L, const double* w, int n_scales, void* stream) {
+    int rc = check_common(ctx, ng, L);
+    if (rc) return rc;
+    if (n_scales < 0 || (n_scales > 0 && !w)) return CWTHF_E_INVALID_ARG;
+    for (int i = 0; i < n_scales; i++)
+        if (!(w[i] > 0) || !std::isfinite(w[i])) return CWTHF_E_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    std::vector<const float*> wtab(size_t(std::max(n_scales, 1)));
+    return transform_tables(ctx, ng, L, w, n_scales, wtab.data(), as_stream(stream));
 }
 
 int cwthf_segment(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_t* cell_label, void* stream) {
@@ -227,6 +260,7 @@ int cwthf_segment(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32
     if (rc) return rc;
     if (!cwt || !cell_label || std::isnan(cwt_min)) return CWTHF_E_INVALID_ARG;
     DeviceGuard g(ctx->device);
+    Range r("cwthf_segment (S5-S6)");
     return segment_impl(ctx, cwt, ng, cwt_min, cell_label, false, as_stream(stream));
 }
 
@@ -247,6 +281,7 @@ int cwthf_assign(cwthf_ctx* ctx, const float* pos, const float* mass, double mas
         std::isnan(params->dens_th))
         return CWTHF_E_INVALID_ARG;
     DeviceGuard g(ctx->device);
+    Range r("cwthf_assign (S7-S8)");
     return assign_impl(ctx, pos, mass, mass_unit, np, L, ng, cell_label, cwt, params, 0, 1, halo_id, cat, cat_cap,
                        n_halo, false, false, as_stream(stream));
 }
@@ -266,15 +301,34 @@ int cwthf_find(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_
             return CWTHF_E_INVALID_ARG;
     DeviceGuard g(ctx->device);
     cudaStream_t s = as_stream(stream);
-    rc = deposit_impl(ctx, pos, mass, mass_unit, np, L, ng, ctx->grid, nullptr, s);
-    if (!rc) rc = transform_forward_xy(ctx, ctx->grid, ng, ctx->spec, s);
+    std::vector<double> ws(n_scales);
+    std::vector<const float*> wtab(n_scales);
+    for (int i = 0; i < n_scales; i++) ws[i] = params[i].w;
+    Range r("cwthf_find");
+    rc = transform_tables(ctx, ng, L, ws.data(), n_scales, wtab.data(), s);
+    if (!rc) {
+        Range r1("S1 deposit");
+        rc = deposit_impl(ctx, pos, mass, mass_unit, np, L, ng, ctx->grid, nullptr, s);
+    }
+    if (!rc) {
+        Range r2("S2 forward FFT (x, y)");
+        rc = transform_forward_xy(ctx, ctx->grid, ng, ctx->spec, s);
+    }
     for (int i = 0; i < n_scales && !rc; i++) {
         float2* dst = n_scales > 1 ? ctx->spec2 : ctx->spec;
-        rc = transform_wavelet_inverse(ctx, ctx->spec, dst, ng, L, params[i].w, mass_unit, ctx->cwt, s);
-        if (!rc) rc = segment_impl(ctx, ctx->cwt, ng, params[i].cwt_min, ctx->label, true, s);
-        if (!rc)
+        {
+            Range r3("S2-S4 z FFT, wavelet multiply, inverse FFT");
+            rc = transform_wavelet_inverse(ctx, ctx->spec, dst, ng, L, params[i].w, mass_unit, wtab[i], ctx->cwt, s);
+        }
+        if (!rc) {
+            Range r5("S5-S6 maxima and segmentation");
+            rc = segment_impl(ctx, ctx->cwt, ng, params[i].cwt_min, ctx->label, true, s);
+        }
+        if (!rc) {
+            Range r7("S7-S8 assignment and halo sums");
             rc = assign_impl(ctx, pos, mass, mass_unit, np, L, ng, ctx->label, ctx->cwt, &params[i], i, n_scales,
                              halo_id, cat + int64_t(i) * cat_cap, cat_cap, n_halo + i, true, true, s);
+        }
     }
     return rc;
 }
@@ -303,6 +357,7 @@ const char* cwthf_error_string(int code) {
         case CWTHF_E_CAPACITY: return "more halos than the catalogue capacity";
         case CWTHF_E_BAD_INPUT: return "non-finite or out-of-range input value";
         case CWTHF_E_SCRATCH_LIMIT: return "size beyond the fixed scratch of cwthf_deposit_noalloc (ng <= 128, np <= 262144)";
+        case CWTHF_E_TABLE_CACHE: return "no free FFT / wavelet table slot (all in use by captured graphs, or a capture needs a new one)";
         default: return "unknown status";
     }
 }
@@ -334,6 +389,11 @@ int cwthf_debug_get(cwthf_ctx* ctx, int key, int64_t* value, void* stream) {
         case CWTHF_DEBUG_JUMP_ROUNDS: *value = ctx->dbg_jump_rounds; return CWTHF_OK;
         case CWTHF_DEBUG_CHASE_LIMIT: *value = ctx->dbg_chase_limit; return CWTHF_OK;
         case CWTHF_DEBUG_TMA_NO_COPY: *value = ctx->dbg_tma_no_copy; return CWTHF_OK;
+        case CWTHF_DEBUG_TABLE_FILLS: {
+            std::lock_guard<std::mutex> lk(ctx->table_mu);
+            *value = int64_t(ctx->table_fills);
+            return CWTHF_OK;
+        }
         case CWTHF_DEBUG_FALLBACK_RAN: {
             DeviceGuard g(ctx->device);
             cudaStream_t s = as_stream(stream);

@@ -35,8 +35,8 @@ namespace cwthf {
 
 struct Tables {
     int ng = 0;
-    float2* twN = nullptr;  // [ng]   exp(-2 pi i m / ng)
-    float2* twM = nullptr;  // [ng/2] exp(-2 pi i m / (ng/2))
+    const float2* twN = nullptr;  // [ng]   exp(-2 pi i m / ng)
+    const float2* twM = nullptr;  // [ng/2] exp(-2 pi i m / (ng/2))
 };
 
 namespace {
@@ -913,35 +913,10 @@ void host_twiddles(int n, std::vector<float2>& out) {
     }
 }
 
-Tables* get_tables(cwthf_ctx* ctx, int ng, cudaStream_t s) {
-    std::lock_guard<std::mutex> g(ctx->table_mu);
-    auto it = ctx->fft_tables.find(ng);
-    if (it != ctx->fft_tables.end()) return it->second;
-    Tables* t = new Tables;
-    t->ng = ng;
-    std::vector<float2> a, b;
-    host_twiddles(ng, a);
-    host_twiddles(ng / 2, b);
-    if (cudaMalloc(&t->twN, a.size() * 8) != cudaSuccess || cudaMalloc(&t->twM, b.size() * 8) != cudaSuccess ||
-        cudaMemcpy(t->twN, a.data(), a.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(t->twM, b.data(), b.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(t->twN);
-        cudaFree(t->twM);
-        delete t;
-        return nullptr;
-    }
-    (void)s;
-    ctx->fft_tables[ng] = t;
-    return t;
-}
-
 // G^(k) and H^(k), k < ng: 1D DFTs (real, even sequences) of the sampled
-// Gaussian factor and of its w^2 u^2 multiple, in fp64, stored as fp32.
-float* get_wavelet_tables(cwthf_ctx* ctx, int ng, double L, double w) {
-    std::lock_guard<std::mutex> g(ctx->table_mu);
-    auto key = std::make_tuple(ng, L, w);
-    auto it = ctx->wavelet_tables.find(key);
-    if (it != ctx->wavelet_tables.end()) return it->second;
+// Gaussian factor and of its w^2 u^2 multiple, in fp64, stored as fp32
+// (out[k] = G^(k), out[ng + k] = H^(k)).
+void host_wavelet_tables(int ng, double L, double w, float* out) {
     const double dx = L / ng;
     std::vector<double> gn(ng), hn(ng), cosn(ng);
     for (int n = 0; n < ng; n++) {
@@ -951,7 +926,6 @@ float* get_wavelet_tables(cwthf_ctx* ctx, int ng, double L, double w) {
         hn[n] = w * w * u2 * gn[n];
         cosn[n] = std::cos(2.0 * kPi * double(n) / double(ng));
     }
-    std::vector<float> tab(2 * size_t(ng));
     for (int k = 0; k < ng; k++) {
         double sg = 0.0, sh = 0.0;
         for (int n = 0; n < ng; n++) {
@@ -959,17 +933,88 @@ float* get_wavelet_tables(cwthf_ctx* ctx, int ng, double L, double w) {
             sg += gn[n] * c;
             sh += hn[n] * c;
         }
-        tab[k] = float(sg);
-        tab[ng + k] = float(sh);
+        out[k] = float(sg);
+        out[ng + k] = float(sh);
     }
-    float* d = nullptr;
-    if (cudaMalloc(&d, tab.size() * 4) != cudaSuccess) return nullptr;
-    if (cudaMemcpy(d, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(d);
-        return nullptr;
+}
+
+// The context's table slots (allocated by cwthf_create, never grown).  A
+// miss fills a slot on the host (the slot's pinned staging) and queues one
+// copy to the device on the call's stream, so a call allocates nothing and
+// never waits for the device, except when it must reuse a slot whose
+// previous copy may still be pending.  Slots read by work captured into a
+// CUDA graph are never reused, and a captured call always captures the copy
+// of the tables it reads, so the graph brings its own tables on every replay
+// whatever ran before it; an uncaptured call that finds a slot filled only
+// inside a capture queues the copy itself.  During a capture only free slots
+// can be filled; with none left the call fails with CWTHF_E_TABLE_CACHE.
+int table_lookup(cwthf_ctx* ctx, int kind, int ng, double L, double w, cudaStream_t s, const float** out) {
+    std::lock_guard<std::mutex> g(ctx->table_mu);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return CWTHF_E_CUDA;
+    const bool capturing = cap != cudaStreamCaptureStatusNone;
+    const size_t stride = ctx->table_slot_floats;
+    const size_t n = (kind == kTableTwiddles ? 3 : 2) * size_t(ng);
+    int pick = -1;
+    for (int i = 0; i < kTableSlots && pick < 0; i++) {
+        const TableSlot& t = ctx->table_slot[i];
+        if (t.kind == kind && t.ng == ng && t.L == L && t.w == w) pick = i;
     }
-    ctx->wavelet_tables[key] = d;
-    return d;
+    bool fill = pick < 0;
+    if (fill) {
+        for (int i = 0; i < kTableSlots && pick < 0; i++)
+            if (ctx->table_slot[i].kind < 0) pick = i;
+        if (pick < 0 && !capturing)  // least recently used slot that no graph reads
+            for (int i = 0; i < kTableSlots; i++) {
+                const TableSlot& t = ctx->table_slot[i];
+                if (!t.graph_ref && (pick < 0 || t.last_use < ctx->table_slot[pick].last_use)) pick = i;
+            }
+        if (pick < 0) return CWTHF_E_TABLE_CACHE;
+    }
+    TableSlot& t = ctx->table_slot[pick];
+    float* host = ctx->table_host + pick * stride;
+    float* dev = ctx->table_dev + pick * stride;
+    if (fill) {
+        // an evicted slot (only ever filled outside a capture): its last copy
+        // must have read the staging before the staging is rewritten
+        if (t.kind >= 0 && cudaEventSynchronize(t.filled) != cudaSuccess) return CWTHF_E_CUDA;
+        t = TableSlot{-1, 0, 0.0, 0.0, 0, false, false, t.filled};
+        if (kind == kTableTwiddles) {  // exp(-2 pi i m / ng), m < ng, then exp(-2 pi i m / (ng/2)), m < ng/2
+            std::vector<float2> a, b;
+            host_twiddles(ng, a);
+            host_twiddles(ng / 2, b);
+            std::memcpy(host, a.data(), a.size() * 8);
+            std::memcpy(host + 2 * ng, b.data(), b.size() * 8);
+        } else {
+            host_wavelet_tables(ng, L, w, host);
+        }
+        t.kind = kind;
+        t.ng = ng;
+        t.L = L;
+        t.w = w;
+        ctx->table_fills++;
+    }
+    if (capturing || !t.on_device) {
+        if (cudaMemcpyAsync(dev, host, n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return CWTHF_E_CUDA;
+        if (!capturing) {
+            if (cudaEventRecord(t.filled, s) != cudaSuccess) return CWTHF_E_CUDA;
+            t.on_device = true;
+        }
+    }
+    t.graph_ref |= capturing;
+    t.last_use = ++ctx->table_clock;
+    *out = dev;
+    return CWTHF_OK;
+}
+
+int get_tables(cwthf_ctx* ctx, int ng, cudaStream_t s, Tables& t) {
+    const float* p = nullptr;
+    int rc = table_lookup(ctx, kTableTwiddles, ng, 0.0, 0.0, s, &p);
+    if (rc) return rc;
+    t.ng = ng;
+    t.twN = reinterpret_cast<const float2*>(p);
+    t.twM = reinterpret_cast<const float2*>(p + 2 * ng);
+    return CWTHF_OK;
 }
 
 // Compile-time instances for the plans of the large power-of-two grids; any
@@ -1065,10 +1110,12 @@ int x_args(int ng, const Tables* t, XArgs& a) {
 
 int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, float2* spec, cudaStream_t s) {
     if (ng / 2 > 512) return CWTHF_E_UNSUPPORTED_SIZE;
-    Tables* t = get_tables(ctx, ng, s);
-    if (!t) return CWTHF_E_CUDA;
+    Tables tb;
+    int rc = get_tables(ctx, ng, s, tb);
+    if (rc) return rc;
+    const Tables* t = &tb;
     XArgs a;
-    int rc = x_args(ng, t, a);
+    rc = x_args(ng, t, a);
     if (rc) return rc;
     XFwdKernel k = pick_x_fwd(a.p);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(x_smem(a.p)));
@@ -1077,12 +1124,22 @@ int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, float2* sp
     return launch_yz(ctx, spec, spec, ng, false, kYzForward, t, nullptr, 0.0, 1.0, s);
 }
 
+int transform_tables(cwthf_ctx* ctx, int ng, double L, const double* w, int n, const float** wtab,
+                     cudaStream_t s) {
+    if (n + 1 > kTableSlots) return CWTHF_E_TABLE_CACHE;
+    Tables tb;
+    int rc = get_tables(ctx, ng, s, tb);
+    for (int i = 0; i < n && !rc; i++) rc = table_lookup(ctx, kTableWavelet, ng, L, w[i], s, &wtab[i]);
+    return rc;
+}
+
 int transform_wavelet_inverse(cwthf_ctx* ctx, float2* src, float2* dst, int ng, double L, double w,
-                              double mass_unit, float* cwt, cudaStream_t s) {
-    Tables* t = get_tables(ctx, ng, s);
-    float* wtab = get_wavelet_tables(ctx, ng, L, w);
-    if (!t || !wtab) return CWTHF_E_CUDA;
-    int rc = launch_yz(ctx, src, dst, ng, true, kYzWavelet, t, wtab, w, mass_unit, s);
+                              double mass_unit, const float* wtab, float* cwt, cudaStream_t s) {
+    Tables tb;
+    int rc = get_tables(ctx, ng, s, tb);
+    if (rc) return rc;
+    const Tables* t = &tb;
+    rc = launch_yz(ctx, src, dst, ng, true, kYzWavelet, t, wtab, w, mass_unit, s);
     if (!rc) rc = launch_yz(ctx, dst, dst, ng, false, kYzInverse, t, nullptr, 0.0, 1.0, s);
     if (rc) return rc;
     XArgs a;
@@ -1099,14 +1156,16 @@ bool fft_size_supported(int ng) {
 }
 
 void free_tables(cwthf_ctx* ctx) {
-    for (auto& kv : ctx->fft_tables) {
-        cudaFree(kv.second->twN);
-        cudaFree(kv.second->twM);
-        delete kv.second;
+    for (TableSlot& t : ctx->table_slot) {
+        if (t.filled) cudaEventDestroy(t.filled);
+        t = TableSlot();
     }
-    ctx->fft_tables.clear();
-    for (auto& kv : ctx->wavelet_tables) cudaFree(kv.second);
-    ctx->wavelet_tables.clear();
+}
+
+int init_tables(cwthf_ctx* ctx) {
+    for (TableSlot& t : ctx->table_slot)
+        if (cudaEventCreateWithFlags(&t.filled, cudaEventDisableTiming) != cudaSuccess) return CWTHF_E_CUDA;
+    return CWTHF_OK;
 }
 
 }  // namespace cwthf

@@ -52,7 +52,22 @@ constexpr int kDefaultChaseLimit = 64;
 // A bounded device wait gives up after this many polls.
 constexpr long long kSpinLimit = 1ll << 20;
 
-struct Tables;  // FFT and wavelet tables for one grid size (fft.cu)
+struct Tables;  // FFT twiddles of one grid size (fft.cu)
+
+// Table slots of a context, allocated by cwthf_create: FFT twiddles (per grid
+// size) and wavelet spectra (per grid size, box and scale), each slot holding
+// up to 3 * max_ng floats on the device, with a pinned host staging copy.
+constexpr int kTableSlots = 48;
+constexpr int kTableTwiddles = 0, kTableWavelet = 1;
+struct TableSlot {
+    int kind = -1;  // -1: free
+    int ng = 0;
+    double L = 0.0, w = 0.0;
+    unsigned long long last_use = 0;
+    bool graph_ref = false;          // read by work captured into a CUDA graph: never reused
+    bool on_device = false;          // a copy was queued outside any capture
+    cudaEvent_t filled = nullptr;    // recorded after that copy
+};
 
 struct cwthf_ctx_impl;
 
@@ -154,8 +169,12 @@ struct cwthf_ctx {
     std::vector<int64_t> prof_n;
 
     std::mutex table_mu;
-    std::map<int, cwthf::Tables*> fft_tables;                                 // per ng
-    std::map<std::tuple<int, double, double>, float*> wavelet_tables;        // (ng, L, w) -> device [2*ng]
+    float* table_dev = nullptr;   // [kTableSlots][table_slot_floats]
+    float* table_host = nullptr;  // pinned staging, same shape
+    size_t table_slot_floats = 0;
+    unsigned long long table_clock = 0;
+    unsigned long long table_fills = 0;  // slots filled since creation
+    cwthf::TableSlot table_slot[cwthf::kTableSlots];
 };
 
 namespace cwthf {
@@ -290,10 +309,15 @@ int bin_particles(cwthf_ctx* ctx, const float* pos, const float* mass, double ma
                   cudaStream_t s);
 // Forward half of the transform: x r2c and y c2c -> ctx spectrum `spec`.
 int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, float2* spec, cudaStream_t s);
-// z forward, wavelet multiply, z inverse (src -> dst, may alias), then
-// y inverse and x c2r into cwt.
+// The FFT twiddles of ng and the wavelet spectra of the n scales w[] for a box
+// of side L, from the context's table slots (wtab[i]: device [2 * ng]).
+// Called before anything else of a call is queued.
+int transform_tables(cwthf_ctx* ctx, int ng, double L, const double* w, int n, const float** wtab,
+                     cudaStream_t s);
+// z forward, wavelet multiply with the spectrum wtab, z inverse (src -> dst,
+// may alias), then y inverse and x c2r into cwt.
 int transform_wavelet_inverse(cwthf_ctx* ctx, float2* src, float2* dst, int ng, double L, double w,
-                              double mass_unit, float* cwt, cudaStream_t s);
+                              double mass_unit, const float* wtab, float* cwt, cudaStream_t s);
 int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_t* label, bool seeds_ready,
                  cudaStream_t s);
 // CTAs of the segmentation fallback's cooperative launch (-1 on failure).
@@ -311,6 +335,7 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
                 int32_t* halo_id, cwthf_halo* cat, int64_t cat_cap, int64_t* n_halo, bool seeds_ready,
                 bool bins_ready, cudaStream_t s);
 void free_tables(cwthf_ctx* ctx);
+int init_tables(cwthf_ctx* ctx);
 
 // ---- deposit on caller-provided scratch (used by cwthf_deposit_noalloc) ------
 struct DepositScratch {

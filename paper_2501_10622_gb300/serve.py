@@ -146,6 +146,19 @@ class Server:
             s.ctx.close()
         self.slots = []
 
+    def prepare(self, jobs):
+        """Fill every slot's FFT and wavelet table slots for the (grid, box,
+        scales) of the jobs it can take, so that serving does no table work."""
+        seen = {(j.ng, j.box, tuple(p.w for p in j.params)) for j in jobs}
+        for slot in self.slots:
+            for ng, box, ws in sorted(seen):
+                if ng <= slot.ng and len(ws) <= slot.n_scales:
+                    slot.ctx.prepare(ng, box, ws, stream=slot.stream)
+        torch.cuda.synchronize(self.device)
+
+    def table_fills(self) -> int:
+        return sum(s.ctx.table_fills() for s in self.slots if hasattr(s, "ctx"))
+
     def _pick(self, job):
         for s in self.slots:  # smallest fitting free slot first
             if s.job is None and s.fits(job):
@@ -153,9 +166,11 @@ class Server:
         return None
 
     def run(self, jobs, poll_s=50e-6):
-        """Serve `jobs` against their arrival times; returns statistics."""
+        """Serve `jobs` against their arrival times; returns statistics (with
+        the number of table slots the run had to fill, 0 after prepare())."""
         if any(not any(s.fits(j) for s in self.slots) for j in jobs):
             raise ValueError("a job does not fit any slot class")
+        fills0 = self.table_fills()
         queue, order = [], sorted(jobs, key=lambda j: j.arrival)
         torch.cuda.synchronize(self.device)
         t0 = time.perf_counter()
@@ -183,7 +198,7 @@ class Server:
                 time.sleep(max(0.0, min(order[nxt].arrival - (time.perf_counter() - t0), 1e-3)))
             elif running:
                 time.sleep(poll_s)
-        return stats(jobs)
+        return {**stats(jobs), "table_fills": self.table_fills() - fills0}
 
     def run_back_to_back(self, jobs):
         """The same jobs one at a time in arrival order on one stream (no overlap)."""
@@ -201,6 +216,20 @@ class Server:
             job.done = time.perf_counter() - t0
             slot.finish()
         return stats(jobs)
+
+
+def with_arrivals(jobs, arrivals):
+    """The same jobs (same snapshots and parameters) with new arrival times."""
+    return [Job(j.jid, j.ng, j.box, j.pos, float(a), j.params) for j, a in zip(jobs, arrivals)]
+
+
+def scaled_load(jobs, rate, drawn_rate):
+    """The jobs' Poisson arrivals, drawn at `drawn_rate` jobs per second,
+    stretched or squeezed to `rate` (the same draws: same order, same
+    relative gaps).  rate = inf: every job arrives at time 0."""
+    if math.isinf(rate):
+        return with_arrivals(jobs, [0.0] * len(jobs))
+    return with_arrivals(jobs, [j.arrival * drawn_rate / rate for j in jobs])
 
 
 def stats(jobs):

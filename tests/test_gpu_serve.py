@@ -33,6 +33,24 @@ def test_results_identical_alone_back_to_back_and_in_the_mix():
         srv.close()
 
 
+def test_prepared_server_does_no_table_work_while_serving():
+    jobs = serve.poisson_jobs(10, rate=300.0, lo_ng=24, hi_ng=64, per_cell=2.0, seed=8, scales=(2.0, 3.0))
+    srv = serve.Server(budget_bytes=8 * 2 ** 30, slots_per_class={64: 3}, classes=(64,), per_cell=2.0, n_scales=2)
+    try:
+        srv.prepare(jobs)
+        fills = srv.table_fills()
+        assert fills > 0
+        st = srv.run(jobs)
+        assert st["table_fills"] == 0 and srv.table_fills() == fills
+        # a load point built from the same draws gives the same results
+        got = {j.jid: (j.n_halo, j.checksum) for j in jobs}
+        js = serve.scaled_load(jobs, 900.0, 300.0)
+        srv.run(js)
+        assert {j.jid: (j.n_halo, j.checksum) for j in js} == got
+    finally:
+        srv.close()
+
+
 def test_admission_respects_budget():
     with pytest.raises(ValueError):
         serve.Server(budget_bytes=2 ** 20, slots_per_class={96: 1}, classes=(96,), per_cell=2.0)

@@ -105,3 +105,12 @@ def test_poisson_jobs_sizes_and_arrivals():
     assert all(j.np == round(0.5 * j.ng ** 3) for j in jobs)
     for j in jobs:
         assert float(j.pos.min()) >= 0.0 and float(j.pos.max()) < j.box
+
+
+def test_scaled_load_keeps_the_draws():
+    jobs = [serve.Job(i, 32, 25.0, torch.zeros((5, 3)), 0.01 * i * i) for i in range(6)]
+    fast = serve.scaled_load(jobs, 400.0, 200.0)
+    assert [j.arrival for j in fast] == pytest.approx([0.005 * i * i for i in range(6)])
+    assert [j.jid for j in fast] == [j.jid for j in jobs] and fast[3].pos is jobs[3].pos
+    burst = serve.scaled_load(jobs, float("inf"), 200.0)
+    assert all(j.arrival == 0.0 for j in burst)
