@@ -5,8 +5,8 @@ grid, the particle stages' by the particle count).  Timed on this host:
 * grid stages (CWT, segmentation) from a 96^3 to a 192^3 grid: 8x the cells,
   so 8x the time (the CWT by FFT: 8 * log(192^3)/log(96^3)), within a factor 2;
 * particle stages (CIC deposit, assignment) on one 96^3 grid: the time added by
-  particles grows in proportion to the particles added (from 2^18 to 2^20 and
-  from 2^20 to 2^21 particles), within a factor 2.
+  particles grows in proportion to the particles added (from 2^20 to 2^22 and
+  from 2^22 to 2^23 particles), within a factor 2.
 
 Particles are presented in cell order at every size, so that the host's cache
 hierarchy does not change the cost per particle between sizes; the arithmetic
@@ -64,18 +64,18 @@ def test_particle_stages_scale_with_the_particles():
     ng, L = 96, 75.0
     lab = C32 = None
     t = {}
-    for n in (1 << 18, 1 << 20, 1 << 21):
+    for n in (1 << 20, 1 << 22, 1 << 23):
         pos = _cell_ordered(n, L, ng, 675, seed=3)
         if lab is None:
             grid, _ = oracle.cic(pos, L, ng)
             C32 = oracle.cwt(grid, L, 2.0).astype(np.float32)
             lab = oracle.segment(C32)
-        t[n] = (_best(lambda: oracle.cic(pos, L, ng), 3), _best(lambda: oracle.assign(pos, L, lab, C32), 3))
-    a, b, c = 1 << 18, 1 << 20, 1 << 21
+        t[n] = (_best(lambda: oracle.cic(pos, L, ng), 7), _best(lambda: oracle.assign(pos, L, lab, C32), 7))
+    a, b, c = 1 << 20, 1 << 22, 1 << 23
     for k, name in enumerate(("CIC deposit", "assignment")):
-        d1 = t[b][k] - t[a][k]  # time of 3 * 2^18 more particles
-        d2 = t[c][k] - t[b][k]  # time of 4 * 2^18 more particles
+        d1 = t[b][k] - t[a][k]  # time of 3 * 2^20 more particles
+        d2 = t[c][k] - t[b][k]  # time of 4 * 2^20 more particles
         r = d2 / d1
-        print(f"{name}: {d1 * 1e3:.1f} ms per 3*2^18 particles, {d2 * 1e3:.1f} ms per 4*2^18 (ratio {r:.2f}, "
+        print(f"{name}: {d1 * 1e3:.1f} ms per 3*2^20 particles, {d2 * 1e3:.1f} ms per 4*2^20 (ratio {r:.2f}, "
               f"linear: 1.33)")
         assert d1 > 0 and (4 / 3) / 2 <= r <= (4 / 3) * 2, (name, d1, d2)
