@@ -61,6 +61,7 @@ def lib() -> ctypes.CDLL:
         L.orc_cwt.argtypes = [P, i32, d, d, d, P]
         L.orc_cwt_direct.argtypes = [P, i32, d, d, d, P]
         L.orc_cwt_at.argtypes = [P, i32, d, d, d, P, i64, P]
+        L.orc_cwt_stencil.argtypes = [P, i32, d, d, d, i32, P]
         L.orc_parent.argtypes = [P, i32, P]
         L.orc_segment.argtypes = [P, i32, f, P]
         L.orc_assign.argtypes = [P, P, d, i64, d, i32, P, P, d, i64, P, i64, P, P, P, P, P, P, P]
@@ -162,6 +163,23 @@ def cwt_at(grid, L: float, w: float, nodes, mass_unit: float = 1.0) -> np.ndarra
     _check(lib().orc_cwt_at(_ptr(grid), ng, float(L), float(mass_unit), float(w), _ptr(nodes), nodes.shape[0],
                             _ptr(out)), "cwt_at")
     return out
+
+
+def gdw_resolution(kw: float) -> int:
+    """Table 1: stencil size of the sampled wavelet, Int(1.5 / k_w + 5)."""
+    return int(1.5 / kw + 5)
+
+
+def cwt_stencil(grid, L: float, w: float, R: int, mass_unit: float = 1.0) -> np.ndarray:
+    """Sec. 2.1 as the paper evaluates it: every node adds its mass times the
+    wavelet sampled on the cube of offsets |d_x|, |d_y|, |d_z| <= R around it
+    (periodic), fp64 literal sum."""
+    grid = np.ascontiguousarray(grid, dtype=np.int64)
+    ng = grid.shape[0]
+    C = np.empty(grid.shape, dtype=np.float64)
+    _check(lib().orc_cwt_stencil(_ptr(grid), ng, float(L), float(mass_unit), float(w), int(R), _ptr(C)),
+           "cwt_stencil")
+    return C
 
 
 def parent(C) -> np.ndarray:

@@ -349,6 +349,43 @@ int orc_cwt_direct(const int64_t *grid, int ng, double L, double mass_unit, doub
  * offsets within that support (every offset once, also on small grids);
  * the result is the full sum up to the order of the additions.  Cost per
  * node: the support, not N^3. */
+/* Sec. 2.1 as the paper evaluates it: the CIC grid's pseudo-particles each add
+ * their mass times the wavelet sampled on the grid around them, over a
+ * truncated stencil.  Here the stencil is the cube of offsets d with
+ * |d_x|, |d_y|, |d_z| <= R (R = gdw_resolution of Table 1 read as a radius),
+ * periodic:  C(g) = sum_{d in cube} m(g - d) Psi(w, Delta |d|).  Literal sum,
+ * fp64; 2R + 1 <= ng, so that no node is counted twice. */
+int orc_cwt_stencil(const int64_t *grid, int ng, double L, double mass_unit, double w, int R, double *C) {
+    if (ng < 1 || !(L > 0) || !(w > 0) || !(mass_unit > 0) || R < 0 || 2 * (int64_t)R + 1 > ng) return ORC_E_ARG;
+    const double dx = L / ng;
+    const int64_t side = 2 * (int64_t)R + 1;
+    double *psi = malloc(sizeof(double) * (size_t)(side * side * side));
+    if (!psi) return ORC_E_NOMEM;
+    for (int64_t dz = -R; dz <= R; dz++)
+        for (int64_t dy = -R; dy <= R; dy++)
+            for (int64_t dxo = -R; dxo <= R; dxo++) {
+                double ox = dx * (double)dxo, oy = dx * (double)dy, oz = dx * (double)dz;
+                psi[((dz + R) * side + (dy + R)) * side + (dxo + R)] = orc_wavelet(w, ox * ox + oy * oy + oz * oz);
+            }
+    for (int64_t z = 0; z < ng; z++)
+        for (int64_t y = 0; y < ng; y++)
+            for (int64_t x = 0; x < ng; x++) {
+                double s = 0.0;
+                for (int64_t dz = -R; dz <= R; dz++)
+                    for (int64_t dy = -R; dy <= R; dy++)
+                        for (int64_t dxo = -R; dxo <= R; dxo++) {
+                            int64_t gx = ((x - dxo) % ng + ng) % ng, gy = ((y - dy) % ng + ng) % ng,
+                                    gz = ((z - dz) % ng + ng) % ng;
+                            int64_t g = (gz * ng + gy) * ng + gx;
+                            if (grid[g] == 0) continue;
+                            s += node_mass(grid, g, mass_unit) * psi[((dz + R) * side + (dy + R)) * side + (dxo + R)];
+                        }
+                C[(z * ng + y) * ng + x] = s;
+            }
+    free(psi);
+    return ORC_OK;
+}
+
 int orc_cwt_at(const int64_t *grid, int ng, double L, double mass_unit, double w, const int64_t *nodes,
                int64_t n_nodes, double *out) {
     if (ng < 1 || !(L > 0) || !(w > 0) || !(mass_unit > 0) || n_nodes < 0) return ORC_E_ARG;

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+from paper_2501_10622_gb300 import synth
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 16, 18, 24, 27, 32, 48, 64, 96, 128])
@@ -155,3 +156,67 @@ def test_cwt_at_far_nodes_see_only_the_support():
     v = oracle.cwt_at(grid, L, w, [near, far])
     assert v[0] == pytest.approx(oracle.wavelet(w, 1.0))
     assert v[1] == 0.0
+
+
+# ---- the paper's direct-space stencil evaluation (Sec. 2.1, Table 1) --------
+
+def test_stencil_point_mass_is_the_truncated_wavelet():
+    # a unit mass on one node: C is the sampled wavelet on the cube around it
+    # and exactly zero outside (closed form, Eq. 4)
+    ng, L, w, R = 16, 16.0, 1.3, 3  # one cell per unit length: the mass sits exactly on node (5, 9, 2)
+    pos = np.array([[5 * L / ng, 9 * L / ng, 2 * L / ng]], np.float32)
+    assert np.count_nonzero(oracle.cic(pos, L, ng)[0]) == 1
+    grid, _ = oracle.cic(pos, L, ng)
+    C = oracle.cwt_stencil(grid, L, w, R)
+    dx = L / ng
+    for z in range(ng):
+        for y in range(ng):
+            for x in range(ng):
+                d = [((x - 5 + 8) % 16) - 8, ((y - 9 + 8) % 16) - 8, ((z - 2 + 8) % 16) - 8]
+                if max(abs(v) for v in d) <= R:
+                    r2 = dx * dx * sum(v * v for v in d)
+                    want = w ** 1.5 * (6 - w * w * r2) * np.exp(-w * w * r2 / 4)
+                    assert abs(C[z, y, x] - want) <= 1e-12 * 6 * w ** 1.5
+                else:
+                    assert C[z, y, x] == 0.0
+
+
+def test_stencil_covering_the_support_equals_the_fft_cwt():
+    # once the cube holds every offset where the wavelet is not negligible in
+    # fp64 (here w * Delta * R = 9.6: Psi < 1e-9 of its peak beyond), the stencil
+    # sum and the whole-box convolution agree
+    ng, L, w = 24, 24.0, 2.4
+    pos = synth.clumped_box(3000, L, 4, seed=2).numpy()
+    grid, _ = oracle.cic(pos, L, ng)
+    R = 11  # 2R + 1 = 23 <= 24
+    Cs = oracle.cwt_stencil(grid, L, w, R)
+    Cf = oracle.cwt(grid, L, w)
+    assert np.max(np.abs(Cs - Cf)) <= 1e-9 * np.max(np.abs(Cf))
+
+
+def test_stencil_is_linear_and_roll_equivariant():
+    ng, L, w, R = 20, 15.0, 1.3, 4
+    rng = np.random.default_rng(4)
+    a = rng.integers(0, 1 << 30, (ng, ng, ng)).astype(np.int64)
+    b = rng.integers(0, 1 << 30, (ng, ng, ng)).astype(np.int64)
+    Ca, Cb = oracle.cwt_stencil(a, L, w, R), oracle.cwt_stencil(b, L, w, R)
+    np.testing.assert_allclose(oracle.cwt_stencil(a + b, L, w, R), Ca + Cb, rtol=0, atol=1e-9 * np.abs(Ca).max())
+    sh = (3, -5, 7)
+    np.testing.assert_allclose(oracle.cwt_stencil(np.roll(a, sh, (0, 1, 2)), L, w, R), np.roll(Ca, sh, (0, 1, 2)),
+                               rtol=0, atol=1e-12 * np.abs(Ca).max())
+
+
+def test_stencil_truncation_error_is_the_dropped_tail():
+    # the difference between the whole-box CWT and the stencil CWT of a point
+    # mass is the wavelet outside the cube; Table 1's stencil Int(1.5/k_w + 5)
+    # drops at most a few 1e-3 of the peak at the paper's grid sizes
+    for kw in (0.1, 0.5, 1.0, 2.5):
+        L = 50.0
+        ng = int(400 * kw + 150)
+        w = kw * 1000.0 / L
+        R = oracle.gdw_resolution(kw)
+        dx = L / ng
+        # largest |Psi| on the cube's surface and beyond, relative to the peak 6 w^1.5
+        r = dx * (R + 1)
+        tail = max(abs((6 - w * w * rr * rr) * np.exp(-w * w * rr * rr / 4)) for rr in np.linspace(r, 3 * r, 400))
+        assert tail / 6.0 < 5e-3, (kw, R, tail / 6.0)
