@@ -596,6 +596,38 @@ def main():
         del x, kspec, X, Y, out
         torch.cuda.empty_cache()
 
+    # ---- the paper's direct-space stencil CWT beside the FFT path (rank 0, N = 1) ----
+    # Table 1's stencil is Int(1.5/k_w + 5) cells of the paper's grid
+    # Int(400 k_w + 150); the same physical extent on this grid gives R.
+    stencil = None
+    if rank == 0 and world == 1 and not args.no_cufft:
+        g = ctx.deposit(pos, wl.box, ng)
+        out = torch.empty((ng, ng, ng), dtype=torch.float32, device=dev)
+        per = []
+        fft_scale_ms = sum(v["ms_per_step"] for k, v in kernels.items()
+                           if k in ("k_fft_yz", "k_fft_x_inv")) / ns - kernels["k_fft_yz"]["avg_ms"] / ns
+        for w in wl.scales:
+            kw = w * wl.box / 1000.0
+            ng_paper = int(400 * kw + 150)
+            R = max(1, round(int(1.5 / kw + 5) * ng / ng_paper))
+            ctx.transform_stencil(g, wl.box, w, R, cwt=out)
+            torch.cuda.synchronize(dev)
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            for _ in range(args.steps):
+                ctx.transform_stencil(g, wl.box, w, R, cwt=out, stream=stream)
+            c1.record(stream)
+            torch.cuda.synchronize(dev)
+            t = c0.elapsed_time(c1) / args.steps
+            b = 44 * ng ** 3
+            per.append({"w": w, "k_w": kw, "R": R, "ms": t, "gbs": b / (t / 1e3) / 1e9, "frac": b / (t / 1e3) / 1e9 / peak})
+        ctx.check(what="stencil")
+        stencil = {"scales": per, "fft_ms_per_extra_scale": fft_scale_ms,
+                   "what": "cwthf_transform_stencil (three 1D passes, 44 B/cell) per scale; the FFT path's "
+                           "per-scale cost (fused z pass, y inverse, x inverse) beside it"}
+        del g, out
+        torch.cuda.empty_cache()
+
     halos = [int(x) for x in nh.cpu()]
     ctx.close()
     del hid, cat
@@ -630,7 +662,7 @@ def main():
                 "gpu_launches": launches,
                 "halos_per_scale": halos,
                 "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "served": served, "batched": batched,
-                "cufft": cufft}
+                "cufft": cufft, "stencil": stencil}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

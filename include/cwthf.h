@@ -60,6 +60,7 @@ extern "C" {
 #define CWTHF_FRAC_BITS 10
 #define CWTHF_MAX_NG 1024
 #define CWTHF_MIN_NG 8
+#define CWTHF_MAX_STENCIL_R 64
 
 enum {
     CWTHF_OK = 0,
@@ -154,6 +155,22 @@ CWTHF_API int cwthf_prepare(cwthf_ctx *ctx, int ng, double L, const double *w, i
  *   cwt   device, float [ng][ng][ng]; overwritten.  Must not alias grid. */
 CWTHF_API int cwthf_transform(cwthf_ctx *ctx, const int64_t *grid, int ng, double L, double mass_unit, double w,
                     float *cwt, void *stream);
+
+/* Sec. 2.1 as the paper evaluates the grid CWT: every node adds its mass
+ * times the wavelet sampled on the grid around it, over the cube of offsets
+ * |d_x|, |d_y|, |d_z| <= R (Table 1's gdw_resolution = Int(1.5 / k_w + 5),
+ * read as the cube's radius), periodic:
+ *   C(x_g) = sum_{|d| <= R per axis} m_{g - d} Psi(w, (L / ng) |d|).
+ * Computed exactly separably (the Mexican hat restricted to a cube is a sum
+ * of products of 1D factors) as seven 1D convolutions in three passes, fp32.
+ * For R large enough that the wavelet vanishes beyond the cube this equals
+ * cwthf_transform.
+ *   grid  device, int64 [ng^3] as written by cwthf_deposit
+ *   R     0 <= R <= CWTHF_MAX_STENCIL_R and 2R + 1 <= ng (CWTHF_E_INVALID_ARG)
+ *   cwt   device, float [ng][ng][ng]; overwritten.  Must not alias grid.
+ * Uses the context's grid, CWT and label scratch. */
+CWTHF_API int cwthf_transform_stencil(cwthf_ctx *ctx, const int64_t *grid, int ng, double L, double mass_unit,
+                                      double w, int R, float *cwt, void *stream);
 
 /* Sec. 2 steps 4-5, Sec. 2.3.  Every cell points at the best of itself and
  * its 26 periodic neighbours under the strict order (C[a] > C[b]) or

@@ -62,6 +62,7 @@ def lib() -> ctypes.CDLL:
         L.orc_cwt_direct.argtypes = [P, i32, d, d, d, P]
         L.orc_cwt_at.argtypes = [P, i32, d, d, d, P, i64, P]
         L.orc_cwt_stencil.argtypes = [P, i32, d, d, d, i32, P]
+        L.orc_cwt_stencil_at.argtypes = [P, i32, d, d, d, i32, P, i64, P]
         L.orc_parent.argtypes = [P, i32, P]
         L.orc_segment.argtypes = [P, i32, f, P]
         L.orc_assign.argtypes = [P, P, d, i64, d, i32, P, P, d, i64, P, i64, P, P, P, P, P, P, P]
@@ -180,6 +181,17 @@ def cwt_stencil(grid, L: float, w: float, R: int, mass_unit: float = 1.0) -> np.
     _check(lib().orc_cwt_stencil(_ptr(grid), ng, float(L), float(mass_unit), float(w), int(R), _ptr(C)),
            "cwt_stencil")
     return C
+
+
+def cwt_stencil_at(grid, L: float, w: float, R: int, nodes, mass_unit: float = 1.0) -> np.ndarray:
+    """cwt_stencil at the given linear node indices only."""
+    grid = np.ascontiguousarray(grid, dtype=np.int64)
+    ng = grid.shape[0]
+    nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+    out = np.empty(nodes.shape[0], dtype=np.float64)
+    _check(lib().orc_cwt_stencil_at(_ptr(grid), ng, float(L), float(mass_unit), float(w), int(R), _ptr(nodes),
+                                    nodes.shape[0], _ptr(out)), "cwt_stencil_at")
+    return out
 
 
 def parent(C) -> np.ndarray:

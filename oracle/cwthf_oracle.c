@@ -386,6 +386,34 @@ int orc_cwt_stencil(const int64_t *grid, int ng, double L, double mass_unit, dou
     return ORC_OK;
 }
 
+/* The stencil sum of orc_cwt_stencil at the given linear node indices only
+ * (full-size spot checks). */
+int orc_cwt_stencil_at(const int64_t *grid, int ng, double L, double mass_unit, double w, int R, const int64_t *nodes,
+                       int64_t n_nodes, double *out) {
+    if (ng < 1 || !(L > 0) || !(w > 0) || !(mass_unit > 0) || R < 0 || 2 * (int64_t)R + 1 > ng || n_nodes < 0)
+        return ORC_E_ARG;
+    const double dx = L / ng;
+    const int64_t cells = (int64_t)ng * ng * ng;
+    for (int64_t i = 0; i < n_nodes; i++) {
+        int64_t c = nodes[i];
+        if (c < 0 || c >= cells) return ORC_E_ARG;
+        int64_t x = c % ng, y = (c / ng) % ng, z = c / ((int64_t)ng * ng);
+        double s = 0.0;
+        for (int64_t dz = -R; dz <= R; dz++)
+            for (int64_t dy = -R; dy <= R; dy++)
+                for (int64_t dxo = -R; dxo <= R; dxo++) {
+                    int64_t gx = ((x - dxo) % ng + ng) % ng, gy = ((y - dy) % ng + ng) % ng,
+                            gz = ((z - dz) % ng + ng) % ng;
+                    int64_t g = (gz * ng + gy) * ng + gx;
+                    if (grid[g] == 0) continue;
+                    double ox = dx * (double)dxo, oy = dx * (double)dy, oz = dx * (double)dz;
+                    s += node_mass(grid, g, mass_unit) * orc_wavelet(w, ox * ox + oy * oy + oz * oz);
+                }
+        out[i] = s;
+    }
+    return ORC_OK;
+}
+
 int orc_cwt_at(const int64_t *grid, int ng, double L, double mass_unit, double w, const int64_t *nodes,
                int64_t n_nodes, double *out) {
     if (ng < 1 || !(L > 0) || !(w > 0) || !(mass_unit > 0) || n_nodes < 0) return ORC_E_ARG;

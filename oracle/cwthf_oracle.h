@@ -25,6 +25,8 @@ int orc_dft3d(double *re, double *im, int n, int sign);
 int orc_cwt(const int64_t *grid, int ng, double L, double mass_unit, double w, double *C);
 int orc_cwt_direct(const int64_t *grid, int ng, double L, double mass_unit, double w, double *C);
 int orc_cwt_stencil(const int64_t *grid, int ng, double L, double mass_unit, double w, int R, double *C);
+int orc_cwt_stencil_at(const int64_t *grid, int ng, double L, double mass_unit, double w, int R, const int64_t *nodes,
+                       int64_t n_nodes, double *out);
 int orc_cwt_at(const int64_t *grid, int ng, double L, double mass_unit, double w, const int64_t *nodes,
                int64_t n_nodes, double *out);
 int orc_parent(const float *C, int ng, int32_t *parent);

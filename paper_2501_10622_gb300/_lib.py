@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
         L.cwthf_check_ng.argtypes = [i32]
         L.cwthf_deposit.argtypes = [P, P, P, d, i64, d, i32, P, P, P]
         L.cwthf_transform.argtypes = [P, P, i32, d, d, d, P, P]
+        L.cwthf_transform_stencil.argtypes = [P, P, i32, d, d, d, i32, P, P]
         L.cwthf_segment.argtypes = [P, P, i32, f, P, P]
         L.cwthf_segment_sizes.argtypes = [P, P, P, i64, P, P]
         L.cwthf_prepare.argtypes = [P, i32, d, ctypes.POINTER(d), i32, P]
@@ -204,6 +205,16 @@ class Context:
             cwt = t.empty((ng, ng, ng), dtype=t.float32, device=self.device)
         _check(lib().cwthf_transform(self._h, _ptr(grid), int(ng), float(L), float(mass_unit), float(w), _ptr(cwt),
                                      self._stream(stream)), "cwthf_transform")
+        return cwt
+
+    def transform_stencil(self, grid, L, w, R, mass_unit=1.0, cwt=None, stream=None):
+        """The paper's direct-space CWT over the cube of radius R (Sec. 2.1)."""
+        t = self.torch
+        ng = grid.shape[0]
+        if cwt is None:
+            cwt = t.empty((ng, ng, ng), dtype=t.float32, device=self.device)
+        _check(lib().cwthf_transform_stencil(self._h, _ptr(grid), int(ng), float(L), float(mass_unit), float(w),
+                                             int(R), _ptr(cwt), self._stream(stream)), "cwthf_transform_stencil")
         return cwt
 
     def segment(self, cwt, cwt_min=0.0, label=None, stream=None):

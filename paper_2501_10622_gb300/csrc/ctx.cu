@@ -244,6 +244,18 @@ int cwthf_transform(cwthf_ctx* ctx, const int64_t* grid, int ng, double L, doubl
     return rc;
 }
 
+int cwthf_transform_stencil(cwthf_ctx* ctx, const int64_t* grid, int ng, double L, double mass_unit, double w, int R,
+                            float* cwt, void* stream) {
+    int rc = check_common(ctx, ng, L);
+    if (rc) return rc;
+    if (!grid || !cwt || !(w > 0) || !std::isfinite(w) || !(mass_unit > 0) || !std::isfinite(mass_unit) || R < 0 ||
+        R > CWTHF_MAX_STENCIL_R || 2 * R + 1 > ng)
+        return CWTHF_E_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    Range r("cwthf_transform_stencil (S2-S4, direct space)");
+    return transform_stencil_impl(ctx, grid, ng, L, mass_unit, w, R, cwt, as_stream(stream));
+}
+
 int cwthf_prepare(cwthf_ctx* ctx, int ng, double L, const double* w, int n_scales, void* stream) {
     int rc = check_common(ctx, ng, L);
     if (rc) return rc;

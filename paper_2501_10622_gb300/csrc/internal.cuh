@@ -318,6 +318,8 @@ int transform_tables(cwthf_ctx* ctx, int ng, double L, const double* w, int n, c
 // may alias), then y inverse and x c2r into cwt.
 int transform_wavelet_inverse(cwthf_ctx* ctx, float2* src, float2* dst, int ng, double L, double w,
                               double mass_unit, const float* wtab, float* cwt, cudaStream_t s);
+int transform_stencil_impl(cwthf_ctx* ctx, const int64_t* grid, int ng, double L, double mass_unit, double w, int R,
+                           float* cwt, cudaStream_t s);
 int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_t* label, bool seeds_ready,
                  cudaStream_t s);
 // CTAs of the segmentation fallback's cooperative launch (-1 on failure).

@@ -220,3 +220,13 @@ def test_stencil_truncation_error_is_the_dropped_tail():
         r = dx * (R + 1)
         tail = max(abs((6 - w * w * rr * rr) * np.exp(-w * w * rr * rr / 4)) for rr in np.linspace(r, 3 * r, 400))
         assert tail / 6.0 < 5e-3, (kw, R, tail / 6.0)
+
+
+def test_stencil_at_nodes_equals_the_whole_stencil_grid():
+    ng, L, w, R = 20, 16.0, 1.9, 4
+    pos = synth.clumped_box(2500, L, 5, seed=9).numpy()
+    grid, _ = oracle.cic(pos, L, ng)
+    C = oracle.cwt_stencil(grid, L, w, R).reshape(-1)
+    nodes = np.random.default_rng(0).integers(0, ng ** 3, 40)
+    np.testing.assert_allclose(oracle.cwt_stencil_at(grid, L, w, R, nodes), C[nodes], rtol=0,
+                               atol=1e-12 * np.abs(C).max())
