@@ -66,6 +66,10 @@ def lib() -> ctypes.CDLL:
         L.orc_parent.argtypes = [P, i32, P]
         L.orc_segment.argtypes = [P, i32, f, P]
         L.orc_assign.argtypes = [P, P, d, i64, d, i32, P, P, d, i64, P, i64, P, P, P, P, P, P, P]
+        L.orc_corrected_peak.argtypes = [P, i32, i64, i32]
+        L.orc_corrected_peak.restype = f
+        L.orc_cross_scale.argtypes = [P, i32, i64, P, i32]
+        L.orc_multiscale.argtypes = [P, P, d, i64, d, i32, P, P, f, d, i64, P, i64, P, P, P, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -244,3 +248,57 @@ def find(pos, L: float, ng: int, w: float, mass=None, mass_unit: float = 1.0, cw
     lab = segment(C32, cwt_min)
     hid, cat = assign(pos, L, lab, C32, mass, mass_unit, dens_th, particle_th)
     return dict(grid=grid, cwt=C64, cwt32=C32, label=lab, halo_id=hid, cat=cat)
+
+
+# ---- the multi-scale identification loop (Sec. 2, Fig. 1, App. B, Sec. 2.4) ----
+
+def corrected_peak(C, seed: int, ng_next: int = 0) -> float:
+    """App. B: the maximum at linear node `seed` plus the per-axis quadratic
+    terms l1^2/(16 l2 - 8 l1) (Eq. B1), plus the grid-size term when the next
+    scale's grid has ng_next nodes per side (0: none).  fp32, as both sides."""
+    C = np.ascontiguousarray(C, dtype=np.float32)
+    return float(lib().orc_corrected_peak(_ptr(C), C.shape[0], int(seed), int(ng_next)))
+
+
+def cross_scale(C, seed: int, C_next=None) -> bool:
+    """Sec. 2: the corrected peak exceeds the 2x2x2 nodes of the next scale's
+    field enclosing the seed's position (a zero field when C_next is None)."""
+    C = np.ascontiguousarray(C, dtype=np.float32)
+    Cn = None if C_next is None else np.ascontiguousarray(C_next, dtype=np.float32)
+    ngn = 0 if Cn is None else Cn.shape[0]
+    return bool(lib().orc_cross_scale(_ptr(C), C.shape[0], int(seed), _ptr(Cn), ngn))
+
+
+def multiscale_on_fields(pos, L: float, fields, mass=None, mass_unit: float = 1.0, cwt_min: float = 0.0,
+                         dens_th: float = 4.0, particle_th: int = 15, cap: int = 1 << 20):
+    """The loop of Fig. 1 on given fp32 fields (largest physical scale first):
+    final halo ids and the catalogue (dict of columns, in halo-id order)."""
+    pos, mass = _pos(pos), _mass(mass)
+    fs = [np.ascontiguousarray(f, dtype=np.float32) for f in fields]
+    n = len(fs)
+    ngs = np.array([f.shape[0] for f in fs], dtype=np.int32)
+    ptrs = (ctypes.c_void_p * n)(*[f.ctypes.data for f in fs])
+    hid = np.empty(pos.shape[0], np.int32)
+    sc = np.empty(cap, np.int32); seed = np.empty(cap, np.int64); npart = np.empty(cap, np.int64)
+    ncell = np.empty(cap, np.int64); mass_o = np.empty(cap, np.float64); cen = np.empty((cap, 3), np.float64)
+    peak = np.empty(cap, np.float32); nh = np.zeros(1, np.int64)
+    _check(lib().orc_multiscale(_ptr(pos), _ptr(mass), float(mass_unit), pos.shape[0], float(L), n, _ptr(ngs),
+                                ctypes.cast(ptrs, ctypes.c_void_p), float(cwt_min), float(dens_th), int(particle_th),
+                                _ptr(hid), int(cap), _ptr(sc), _ptr(seed), _ptr(npart), _ptr(ncell), _ptr(mass_o),
+                                _ptr(cen), _ptr(peak), _ptr(nh)), "multiscale")
+    k = int(nh[0])
+    cat = dict(scale=sc[:k], seed=seed[:k], n_part=npart[:k], n_cells=ncell[:k], mass=mass_o[:k], centre=cen[:k],
+               peak=peak[:k])
+    return hid, cat
+
+
+def find_multiscale(pos, L: float, ws, ngs, mass=None, mass_unit: float = 1.0, cwt_min: float = 0.0,
+                    dens_th: float = 4.0, particle_th: int = 15):
+    """The whole loop: per scale the CIC grid on its own ng^3 grid and the
+    fp64 CWT rounded to fp32, then multiscale_on_fields."""
+    fields = []
+    for w, ng in zip(ws, ngs):
+        grid, _ = cic(pos, L, ng, mass, mass_unit)
+        fields.append(cwt(grid, L, w, mass_unit).astype(np.float32))
+    hid, cat = multiscale_on_fields(pos, L, fields, mass, mass_unit, cwt_min, dens_th, particle_th)
+    return dict(fields=fields, halo_id=hid, cat=cat)

@@ -600,3 +600,175 @@ int orc_assign(const float *pos, const float *mass, double mass_unit, int64_t np
     free(np_c); free(mq_c); free(mom); free(nc_c); free(tmp); free(keepflag);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2 (steps 1-8 and 10 of the step list; the self-boundness check of    */
+/* step 9 is not part of this loop), Fig. 1, Sec. 2.2 and App. B, Sec. 2.4:  */
+/* the multi-scale identification loop.                                      */
+/* ------------------------------------------------------------------------ */
+
+/* App. B, Eq. B1 along one axis.  B is the maximum node with value vb, its
+ * two neighbours have values vm and vp; A is the higher and C the lower of
+ * the two, and with values measured from C, l1 = v_A - v_C and
+ * l2 = v_B - v_C, the quadratic through A, B, C peaks
+ * l1^2 / (16 l2 - 8 l1) above B.  Single precision, in this order. */
+static float peak_term(float vm, float vb, float vp, float *l1_out, float *l2_out) {
+    float va = vm > vp ? vm : vp, vc = vm > vp ? vp : vm;
+    float l1 = va - vc, l2 = vb - vc;
+    float den = 16.0f * l2 - 8.0f * l1;
+    *l1_out = l1;
+    *l2_out = l2;
+    return den > 0.0f ? (l1 * l1) / den : 0.0f;
+}
+
+/* The corrected peak of the maximum at node s of the ng^3 field C (App. B):
+ * the node value plus the three axes' quadratic terms (x, y, z in this
+ * order), plus, when the next (smaller) scale's grid is finer by the factor
+ * ratio = ng / ng_next < 1, the grid-size term
+ * (5/16) (2 mean(l2) - mean(l1)) (1 - ratio^2): App. B's cube-average
+ * difference with the factor 3/5 removed, as the paper prescribes. */
+float orc_corrected_peak(const float *C, int ng, int64_t s, int ng_next) {
+    int64_t x = s % ng, y = (s / ng) % ng, z = s / ((int64_t)ng * ng);
+    int64_t n = ng;
+    float vb = C[s];
+    float l1[3], l2[3], t[3];
+    int64_t xm = (x + n - 1) % n, xp = (x + 1) % n, ym = (y + n - 1) % n, yp = (y + 1) % n;
+    int64_t zm = (z + n - 1) % n, zp = (z + 1) % n;
+    t[0] = peak_term(C[(z * n + y) * n + xm], vb, C[(z * n + y) * n + xp], &l1[0], &l2[0]);
+    t[1] = peak_term(C[(z * n + ym) * n + x], vb, C[(z * n + yp) * n + x], &l1[1], &l2[1]);
+    t[2] = peak_term(C[(zm * n + y) * n + x], vb, C[(zp * n + y) * n + x], &l1[2], &l2[2]);
+    float p = ((vb + t[0]) + t[1]) + t[2];
+    if (ng_next > 0) {
+        float r = (float)ng / (float)ng_next;
+        float m1 = ((l1[0] + l1[1]) + l1[2]) / 3.0f, m2 = ((l2[0] + l2[1]) + l2[2]) / 3.0f;
+        p = p + (5.0f / 16.0f) * (2.0f * m2 - m1) * (1.0f - r * r);
+    }
+    return p;
+}
+
+/* Sec. 2 (Fig. 1): a maximum of the current scale is a maximum in 4D iff its
+ * corrected peak exceeds every node of the next (smaller) scale's field near
+ * the same physical position: the 2 x 2 x 2 nodes of that grid enclosing the
+ * node's position s * L / ng.  With no next scale (the last one) the
+ * comparison is with a zero field. */
+int orc_cross_scale(const float *C, int ng, int64_t s, const float *Cn, int ng_next) {
+    float p = orc_corrected_peak(C, ng, s, ng_next);
+    if (!Cn || ng_next <= 0) return p > 0.0f;
+    int64_t c[3] = {s % ng, (s / ng) % ng, s / ((int64_t)ng * ng)};
+    int64_t lo[3], hi[3];
+    for (int a = 0; a < 3; a++) {
+        lo[a] = (c[a] * ng_next) / ng; /* floor of the position in next-grid cells */
+        hi[a] = (lo[a] + 1) % ng_next;
+    }
+    int64_t m = ng_next;
+    for (int k = 0; k < 8; k++) {
+        int64_t gx = (k & 1) ? hi[0] : lo[0], gy = (k & 2) ? hi[1] : lo[1], gz = (k & 4) ? hi[2] : lo[2];
+        if (!(p > Cn[(gz * m + gy) * m + gx])) return 0;
+    }
+    return 1;
+}
+
+/* The loop of Fig. 1 on given fields: fields[j] is the fp32 CWT of scale j
+ * on an ngs[j]^3 grid, scales ordered from the largest physical scale
+ * (smallest k_w) to the smallest.  Scale j is processed with scale j + 1 as
+ * its "current_grid" (a zero field after the last scale):
+ *   segments of fields[j] (orc_segment, seeds above cwt_min);
+ *   groups: the particles that hold no halo id yet, by the label of their
+ *     nearest node; per group n_part, integer mass, first moment about the
+ *     seed; n_cells = cells of the segment;
+ *   keep a group iff n_part >= particle_th, mass / (n_cells cell volume) >=
+ *     dens_th * (total mass / box volume) (same operands as orc_assign), and
+ *     its seed is a cross-scale maximum (orc_cross_scale);
+ *   kept groups, in seed order, take the next halo ids; their particles keep
+ *     them for good.
+ * Outputs: halo_id[np] (-1: none), and per halo (at most cap): scale index,
+ * seed, n_part, n_cells, mass, centre[3], corrected peak. */
+int orc_multiscale(const float *pos, const float *mass, double mass_unit, int64_t np, double L, int n_scales,
+                   const int *ngs, const float *const *fields, float cwt_min, double dens_th, int64_t particle_th,
+                   int32_t *halo_id, int64_t cap, int32_t *scale_out, int64_t *seed_out, int64_t *npart_out,
+                   int64_t *ncell_out, double *mass_out, double *centre_out, float *peak_out, int64_t *n_halo) {
+    if (np < 0 || !(L > 0) || !(mass_unit > 0) || n_scales < 1) return ORC_E_ARG;
+    int max_ng = 0;
+    for (int j = 0; j < n_scales; j++) {
+        if (ngs[j] < 3 || !fields[j]) return ORC_E_ARG;
+        if (ngs[j] > max_ng) max_ng = ngs[j];
+    }
+    int64_t max_cells = (int64_t)max_ng * max_ng * max_ng;
+    int32_t *lab = malloc(sizeof(int32_t) * (size_t)max_cells);
+    int64_t *np_c = malloc(sizeof(int64_t) * (size_t)max_cells), *mq_c = malloc(sizeof(int64_t) * (size_t)max_cells);
+    int64_t *nc_c = malloc(sizeof(int64_t) * (size_t)max_cells), *mom = malloc(sizeof(int64_t) * 3 * (size_t)max_cells);
+    int32_t *tmp = malloc(sizeof(int32_t) * (size_t)(np > 0 ? np : 1));
+    int32_t *hid_c = malloc(sizeof(int32_t) * (size_t)max_cells);
+    int rc = (lab && np_c && mq_c && nc_c && mom && tmp && hid_c) ? ORC_OK : ORC_E_NOMEM;
+    int64_t mtot = 0, kept = 0;
+    for (int64_t p = 0; p < np && rc == ORC_OK; p++) {
+        int64_t mq;
+        rc = mass_quantum(mass, mass_unit, p, &mq);
+        mtot += mq;
+        halo_id[p] = -1;
+    }
+    for (int j = 0; j < n_scales && rc == ORC_OK; j++) {
+        const int ng = ngs[j];
+        const int64_t cells = (int64_t)ng * ng * ng, M = (int64_t)ng * FRAC_ONE;
+        const float *C = fields[j];
+        const float *Cn = j + 1 < n_scales ? fields[j + 1] : NULL;
+        const int ngn = j + 1 < n_scales ? ngs[j + 1] : 0;
+        rc = orc_segment(C, ng, cwt_min, lab);
+        if (rc) break;
+        for (int64_t c = 0; c < cells; c++) { np_c[c] = mq_c[c] = nc_c[c] = 0; mom[3 * c] = mom[3 * c + 1] = mom[3 * c + 2] = 0; hid_c[c] = -1; }
+        for (int64_t c = 0; c < cells; c++)
+            if (lab[c] >= 0) nc_c[lab[c]] += 1;
+        double s = quant_scale(ng, L);
+        for (int64_t p = 0; p < np && rc == ORC_OK; p++) {
+            tmp[p] = -1;
+            if (halo_id[p] >= 0) continue; /* the particle already belongs to a halo */
+            int64_t q[3], mq, node[3];
+            for (int a = 0; a < 3 && rc == ORC_OK; a++) rc = quantise_coord(pos[3 * p + a], s, M, &q[a]);
+            if (rc == ORC_OK) rc = mass_quantum(mass, mass_unit, p, &mq);
+            if (rc) break;
+            for (int a = 0; a < 3; a++) node[a] = ((q[a] + FRAC_ONE / 2) >> FRAC_BITS) % ng;
+            int32_t l = lab[(node[2] * ng + node[1]) * ng + node[0]];
+            tmp[p] = l;
+            if (l < 0) continue;
+            int64_t sc[3] = {l % ng, (l / ng) % ng, l / ((int64_t)ng * ng)};
+            np_c[l] += 1;
+            mq_c[l] += mq;
+            for (int a = 0; a < 3; a++) mom[3 * l + a] += mq * min_image_q(q[a] - sc[a] * FRAC_ONE, M);
+        }
+        if (rc) break;
+        const double ncube = (double)cells, cell_q = (L / (double)ng) / (double)FRAC_ONE;
+        for (int64_t c = 0; c < cells; c++) {
+            if (lab[c] != c) continue;
+            int keep = np_c[c] >= particle_th && (double)mq_c[c] * ncube >= (dens_th * (double)mtot) * (double)nc_c[c] &&
+                       orc_cross_scale(C, ng, c, Cn, ngn);
+            if (!keep) continue;
+            hid_c[c] = (int32_t)kept;
+            if (kept < cap) {
+                int64_t sc[3] = {c % ng, (c / ng) % ng, c / ((int64_t)ng * ng)};
+                scale_out[kept] = j;
+                seed_out[kept] = c;
+                npart_out[kept] = np_c[c];
+                ncell_out[kept] = nc_c[c];
+                mass_out[kept] = (double)mq_c[c] * mass_unit;
+                for (int a = 0; a < 3; a++) {
+                    double u = (double)(sc[a] * FRAC_ONE);
+                    if (mq_c[c] > 0) u += (double)mom[3 * c + a] / (double)mq_c[c];
+                    double x = u * cell_q;
+                    if (x >= L) x -= L;
+                    else if (x < 0.0) x += L;
+                    centre_out[3 * kept + a] = x;
+                }
+                peak_out[kept] = orc_corrected_peak(C, ng, c, ngn);
+            }
+            kept++;
+        }
+        for (int64_t p = 0; p < np; p++)
+            if (halo_id[p] < 0 && tmp[p] >= 0 && hid_c[tmp[p]] >= 0) halo_id[p] = hid_c[tmp[p]];
+    }
+    free(lab); free(np_c); free(mq_c); free(nc_c); free(mom); free(tmp); free(hid_c);
+    if (rc == ORC_OK) {
+        *n_halo = kept;
+        if (kept > cap) rc = ORC_E_CAPACITY;
+    }
+    return rc;
+}
