@@ -100,6 +100,17 @@ typedef struct {
     int32_t reserved;
 } cwthf_halo;
 
+/* One halo of the multi-scale catalogue (64 bytes), in halo-id order. */
+typedef struct {
+    int64_t seed;      /* linear index of the seed on its scale's ng^3 grid */
+    int64_t n_part;    /* particles of the halo (none of which an earlier scale took) */
+    int64_t n_cells;   /* cells of its segment on its scale's grid */
+    double mass;       /* sum of particle masses */
+    double centre[3];  /* centre of mass, minimum image about the seed, in [0, L) */
+    float peak;        /* corrected peak (App. B): the value compared across scales */
+    int32_t scale;     /* index of the scale that found it */
+} cwthf_ms_halo;
+
 /* Fills *p with the defaults above for scale w. */
 CWTHF_API void cwthf_default_params(double w, cwthf_params *p);
 
@@ -224,6 +235,36 @@ CWTHF_API int cwthf_assign(cwthf_ctx *ctx, const float *pos, const float *mass, 
 CWTHF_API int cwthf_find(cwthf_ctx *ctx, const float *pos, const float *mass, double mass_unit, int64_t np, double L,
                int ng, const cwthf_params *params, int n_scales, int32_t *halo_id, cwthf_halo *cat,
                int64_t cat_cap, int64_t *n_halo, void *stream);
+
+/* Sec. 2 (step list 1-8 and 10; the self-boundness check of step 9 is not
+ * part of it), Fig. 1, Sec. 2.2 with App. B, Sec. 2.4: the multi-scale
+ * identification loop.  Scales are given from the largest physical scale
+ * (smallest k_w) to the smallest: w[j] (1/length) on an ng[j]^3 grid (each a
+ * supported size <= the context's max_ng; the paper's Int(400 k_w + 150)
+ * rounded to a supported size is the caller's choice).  For every scale all
+ * particles are deposited and the CWT computed; scale j is then decided with
+ * scale j + 1's field as its comparison field (a zero field after the last):
+ *   - segments of scale j's field (seeds: maxima above cwt_min);
+ *   - groups: the particles that hold no halo id yet, by the label of their
+ *     nearest node; per group count, mass, first moment; n_cells of the segment;
+ *   - a group is kept iff n_part >= particle_th, its mass over its segment's
+ *     volume is >= dens_th times the mean density of all particles, and its
+ *     seed is a maximum across scales: the seed's corrected peak (App. B:
+ *     the node value plus l1^2 / (16 l2 - 8 l1) per axis, plus
+ *     (5/16)(2 mean l2 - mean l1)(1 - (ng[j]/ng[j+1])^2)) exceeds the 2x2x2
+ *     nodes of scale j+1's field enclosing the seed's position (exceeds 0
+ *     after the last scale);
+ *   - kept groups, in seed order, take the next halo ids; their particles
+ *     keep them for good.
+ *   w, ng     host, [n_scales], n_scales >= 1
+ *   halo_id   device, int32 [np]: the particle's halo id, or -1
+ *   cat       device, cwthf_ms_halo [cat_cap], halos in id order
+ *   n_halo    device, int64 [1]: halos found (CWTHF_E_CAPACITY beyond cat_cap)
+ * Needs a context created with max_scales >= 2 (two fields are kept). */
+CWTHF_API int cwthf_find_multiscale(cwthf_ctx *ctx, const float *pos, const float *mass, double mass_unit,
+                                    int64_t np, double L, int n_scales, const double *w, const int *ng,
+                                    float cwt_min, double dens_th, int64_t particle_th, int32_t *halo_id,
+                                    cwthf_ms_halo *cat, int64_t cat_cap, int64_t *n_halo, void *stream);
 
 /* Waits for `stream`, then returns (and clears) the first error the device
  * recorded since the last cwthf_sync, or CWTHF_E_CUDA if the stream failed.

@@ -5,8 +5,10 @@ The compute lives in libcwthf.so (CUDA kernels behind the C ABI of
 include/cwthf.h); this package holds its ctypes binding, the seeded input
 generators and the build script.
 """
-from ._lib import (HALO_DTYPE, Context, CwthfError, Params, catalogue_to_numpy, check_ng, default_params,
-                   error_string, header_symbols, lib, workspace_bytes)
+from ._lib import (HALO_DTYPE, MS_HALO_DTYPE, Context, CwthfError, Params, catalogue_to_numpy, check_ng,
+                   default_params, error_string, header_symbols, lib, ms_catalogue_to_numpy, paper_scales,
+                   supported_sizes, workspace_bytes)
 
-__all__ = ["HALO_DTYPE", "Context", "CwthfError", "Params", "catalogue_to_numpy", "check_ng", "default_params",
-           "error_string", "header_symbols", "lib", "workspace_bytes"]
+__all__ = ["HALO_DTYPE", "MS_HALO_DTYPE", "Context", "CwthfError", "Params", "catalogue_to_numpy", "check_ng",
+           "default_params", "error_string", "header_symbols", "lib", "ms_catalogue_to_numpy", "paper_scales",
+           "supported_sizes", "workspace_bytes"]

@@ -32,6 +32,35 @@ HALO_DTYPE = np.dtype([("seed", "<i8"), ("n_part", "<i8"), ("n_cells", "<i8"), (
 assert HALO_DTYPE.itemsize == 64
 
 
+MS_HALO_DTYPE = np.dtype([("seed", "<i8"), ("n_part", "<i8"), ("n_cells", "<i8"), ("mass", "<f8"),
+                          ("centre", "<f8", (3,)), ("peak", "<f4"), ("scale", "<i4")])
+assert MS_HALO_DTYPE.itemsize == 64
+
+
+def supported_sizes(lo: int = 8, hi: int = MAX_NG) -> list[int]:
+    """Grid sizes the library takes: 2^a 3^b with a >= 1, within [lo, hi]."""
+    return sorted(n for n in {2 ** a * 3 ** b for a in range(1, 11) for b in range(0, 7)} if lo <= n <= hi
+                  and check_ng(n))
+
+
+def paper_scales(L: float, kw_low: float = 0.1, kw_high: float = 2.5, n: int | None = None, n_ref: int = 400,
+                 n_min: int = 150, max_ng: int = MAX_NG):
+    """The scale list of the multi-scale loop (Fig. 1, Table 1): n values of
+    k_w spaced linearly from kw_low to kw_high (n = Int((kw_high - kw_low) * 8)
+    by default), w = k_w * 1000 / L, and the grid Int(n_ref * k_w + n_min) per
+    scale rounded to the nearest supported size (the smaller on a tie), at
+    most max_ng.  Returns (k_w list, w list, ng list)."""
+    if n is None:
+        n = int((kw_high - kw_low) * 8)
+    kws = [kw_low + (kw_high - kw_low) * i / (n - 1) for i in range(n)] if n > 1 else [kw_low]
+    sizes = supported_sizes(8, max_ng)
+    ngs = []
+    for kw in kws:
+        want = int(n_ref * kw + n_min)
+        ngs.append(min(sizes, key=lambda s: (abs(s - want), s)))
+    return kws, [kw * 1000.0 / L for kw in kws], ngs
+
+
 class Params(ctypes.Structure):
     _fields_ = [("w", ctypes.c_double), ("cwt_min", ctypes.c_float), ("reserved0", ctypes.c_float),
                 ("dens_th", ctypes.c_double), ("particle_th", ctypes.c_int64)]
@@ -74,6 +103,8 @@ def lib() -> ctypes.CDLL:
         L.cwthf_debug_get.argtypes = [P, i32, ctypes.POINTER(i64), P]
         L.cwthf_assign.argtypes = [P, P, P, d, i64, d, i32, P, P, ctypes.POINTER(Params), P, P, i64, P, P]
         L.cwthf_find.argtypes = [P, P, P, d, i64, d, i32, ctypes.POINTER(Params), i32, P, P, i64, P, P]
+        L.cwthf_find_multiscale.argtypes = [P, P, P, d, i64, d, i32, ctypes.POINTER(d), ctypes.POINTER(i32), f, d,
+                                            i64, P, P, i64, P, P]
         L.cwthf_sync.argtypes = [P, P]
         L.cwthf_error_string.argtypes = [i32]
         L.cwthf_error_string.restype = ctypes.c_char_p
@@ -291,6 +322,34 @@ class Context:
                                 arr, ns, _ptr(halo_id), _ptr(cat), int(cat_cap), _ptr(n_halo), self._stream(stream)),
                "cwthf_find")
         return halo_id, cat, n_halo
+
+    def find_multiscale(self, pos, L, ws, ngs, mass=None, mass_unit=1.0, cwt_min=0.0, dens_th=4.0, particle_th=15,
+                        cat_cap=1 << 20, halo_id=None, cat=None, n_halo=None, stream=None):
+        """The multi-scale loop over scales ws (largest physical scale first)
+        on grids ngs.  Returns (halo_id [np], catalogue bytes [cap, 64], n_halo [1])."""
+        t = self.torch
+        pos = self._pos(pos)
+        n = len(ws)
+        if halo_id is None:
+            halo_id = t.empty(pos.shape[0], dtype=t.int32, device=self.device)
+        if cat is None:
+            cat = t.empty((max(cat_cap, 1), 64), dtype=t.uint8, device=self.device)
+        if n_halo is None:
+            n_halo = t.zeros(1, dtype=t.int64, device=self.device)
+        wa = (ctypes.c_double * n)(*ws)
+        na = (ctypes.c_int * n)(*ngs)
+        _check(lib().cwthf_find_multiscale(self._h, _ptr(pos), _ptr(mass), float(mass_unit), pos.shape[0], float(L),
+                                           n, wa, na, float(cwt_min), float(dens_th), int(particle_th), _ptr(halo_id),
+                                           _ptr(cat), int(cat_cap), _ptr(n_halo), self._stream(stream)),
+               "cwthf_find_multiscale")
+        return halo_id, cat, n_halo
+
+
+def ms_catalogue_to_numpy(cat, n) -> np.ndarray:
+    """Device multi-scale catalogue bytes -> numpy structured array."""
+    n = int(n)
+    raw = cat[:n].contiguous().cpu().numpy()
+    return raw.view(MS_HALO_DTYPE).reshape(n)
 
 
 def catalogue_to_numpy(cat, n) -> np.ndarray:

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kHsThreads) k_halo_sums(DepArgs a, const uint3
                                                        const uint32_t* __restrict__ prefix,
                                                        const uint32_t* __restrict__ n_slots, HaloAcc* acc,
                                                        int32_t* __restrict__ rec_slot, int slot_stride,
-                                                       u64* __restrict__ mtot) {
+                                                       u64* __restrict__ mtot, int skip_marked) {
     __shared__ uint32_t tkey[kTab], tcnt[kTab], tmq_lo[kTab], tmq_hi[kTab];
     __shared__ uint32_t tm_lo[3][kTab], tm_hi[3][kTab];
     __shared__ uint32_t tused[kTab];
@@ -138,8 +138,11 @@ __global__ void __launch_bounds__(kHsThreads) k_halo_sums(DepArgs a, const uint3
                 q[u][0] = rec_q(e, 0);
                 q[u][1] = rec_q(e, 1);
                 q[u][2] = rec_q(e, 2);
-                lab[u] = label[(size_t(nearest_node(q[u][2], N)) * N + nearest_node(q[u][1], N)) * N +
-                               nearest_node(q[u][0], N)];
+                // a record marked in bit 63 (its particle already holds a halo id)
+                // joins no group
+                if (!(skip_marked && (e >> 63)))
+                    lab[u] = label[(size_t(nearest_node(q[u][2], N)) * N + nearest_node(q[u][1], N)) * N +
+                                   nearest_node(q[u][0], N)];
             }
         }
         uint32_t word[kRecPerThread], pre[kRecPerThread];
@@ -417,7 +420,229 @@ void launch_ids(cwthf_ctx* ctx, cudaStream_t s, int blocks, int pblocks, int64_t
                  k_finalize<RS><<<pblocks, kThreads, 0, s>>>(ctx->part_rec, np, total, groups, n_scales, halo_id));
 }
 
+// ---- the multi-scale loop (Sec. 2, Fig. 1; App. B; Sec. 2.4) -----------------
+
+// Records of particles that already hold a halo id are marked in bit 63, so
+// that this scale's group sums skip them (Sec. 2 step 6: only particles
+// without a halo id are assigned).
+__global__ void __launch_bounds__(kThreads) k_ms_mark(const int32_t* __restrict__ halo_id,
+                                                     const uint32_t* __restrict__ part_rec, int64_t np,
+                                                     const uint32_t* __restrict__ total_ptr,
+                                                     unsigned long long* __restrict__ rec) {
+    const int64_t total = *total_ptr;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np; i += stride) {
+        const uint32_t r = part_rec[i];
+        if (halo_id[i] >= 0 && int64_t(r) < total) rec[r] |= 1ull << 63;
+    }
+}
+
+// Each particle's group slot at this scale (-1: in no group), kept until the
+// scale's halos are decided one iteration later.
+__global__ void __launch_bounds__(kThreads) k_ms_pslot(const uint32_t* __restrict__ part_rec, int64_t np,
+                                                      const uint32_t* __restrict__ total_ptr,
+                                                      const int32_t* __restrict__ rec_slot, int32_t* __restrict__ pslot) {
+    const int64_t total = *total_ptr;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np; i += stride) {
+        const uint32_t r = part_rec[i];
+        pslot[i] = int64_t(r) < total ? rec_slot[r] : -1;
+    }
+}
+
+// App. B, Eq. B1 along one axis: A the higher and C the lower neighbour of the
+// maximum B; l1 = v_A - v_C, l2 = v_B - v_C; the quadratic through A, B, C
+// peaks l1^2 / (16 l2 - 8 l1) above B.  Single precision, every operation
+// rounded on its own (no contraction), in a fixed order.
+__device__ __forceinline__ float ms_peak_term(float vm, float vb, float vp, float& l1, float& l2) {
+    const float va = vm > vp ? vm : vp, vc = vm > vp ? vp : vm;
+    l1 = __fsub_rn(va, vc);
+    l2 = __fsub_rn(vb, vc);
+    const float den = __fsub_rn(__fmul_rn(16.0f, l2), __fmul_rn(8.0f, l1));
+    return den > 0.0f ? __fdiv_rn(__fmul_rn(l1, l1), den) : 0.0f;
+}
+
+// The corrected peak of the maximum at node s (App. B): the node value plus
+// the x, y and z terms of Eq. B1, plus, when the next scale's grid has ngn
+// nodes per side, the grid-size term (5/16)(2 mean l2 - mean l1)(1 - (ng/ngn)^2).
+__device__ float ms_corrected_peak(const float* __restrict__ C, int ng, int64_t s, int ngn) {
+    const int64_t n = ng, x = s % n, y = (s / n) % n, z = s / (n * n);
+    const int64_t xm = (x + n - 1) % n, xp = (x + 1) % n, ym = (y + n - 1) % n, yp = (y + 1) % n;
+    const int64_t zm = (z + n - 1) % n, zp = (z + 1) % n;
+    const float vb = C[s];
+    float l1x, l2x, l1y, l2y, l1z, l2z;
+    const float tx = ms_peak_term(C[(z * n + y) * n + xm], vb, C[(z * n + y) * n + xp], l1x, l2x);
+    const float ty = ms_peak_term(C[(z * n + ym) * n + x], vb, C[(z * n + yp) * n + x], l1y, l2y);
+    const float tz = ms_peak_term(C[(zm * n + y) * n + x], vb, C[(zp * n + y) * n + x], l1z, l2z);
+    float p = __fadd_rn(__fadd_rn(__fadd_rn(vb, tx), ty), tz);
+    if (ngn > 0) {
+        const float r = __fdiv_rn(float(ng), float(ngn));
+        const float m1 = __fdiv_rn(__fadd_rn(__fadd_rn(l1x, l1y), l1z), 3.0f);
+        const float m2 = __fdiv_rn(__fadd_rn(__fadd_rn(l2x, l2y), l2z), 3.0f);
+        p = __fadd_rn(p, __fmul_rn(__fmul_rn(0.3125f, __fsub_rn(__fmul_rn(2.0f, m2), m1)),
+                                   __fsub_rn(1.0f, __fmul_rn(r, r))));
+    }
+    return p;
+}
+
+// Sec. 2 (Fig. 1): a maximum is kept as a maximum in 4D iff its corrected peak
+// exceeds every node of the next scale's field enclosing its position (the
+// 2 x 2 x 2 nodes around s * L / ng), or 0 after the last scale.
+__device__ bool ms_cross_scale(const float* __restrict__ C, int ng, int64_t s, const float* __restrict__ Cn,
+                               int ngn, float& peak) {
+    peak = ms_corrected_peak(C, ng, s, Cn ? ngn : 0);
+    if (!Cn) return peak > 0.0f;
+    const int64_t c[3] = {s % ng, (s / ng) % ng, s / (int64_t(ng) * ng)};
+    int64_t lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        lo[a] = (c[a] * ngn) / ng;
+        hi[a] = (lo[a] + 1) % ngn;
+    }
+    const int64_t m = ngn;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const int64_t gx = (k & 1) ? hi[0] : lo[0], gy = (k & 2) ? hi[1] : lo[1], gz = (k & 4) ? hi[2] : lo[2];
+        ok &= peak > Cn[(gz * m + gy) * m + gx];
+    }
+    return ok;
+}
+
+// Keep flag per group (slot): particle and density thresholds (same operands
+// as the single-scale path) and the cross-scale check.
+__global__ void __launch_bounds__(kThreads) k_ms_keep(const HaloAcc* __restrict__ acc,
+                                                     const int32_t* __restrict__ seed_list,
+                                                     const uint32_t* __restrict__ n_seeds,
+                                                     const u64* __restrict__ mtot, FilterArgs f,
+                                                     const float* __restrict__ C, const float* __restrict__ Cn,
+                                                     int ngn, uint32_t* __restrict__ keep) {
+    const uint32_t ns = *n_seeds;
+    const double ncube = double(int64_t(f.ng) * f.ng * f.ng);
+    const double rhs0 = __dmul_rn(f.dens_th, double(*mtot));
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < ns; s += stride) {
+        const HaloAcc h = acc[s];
+        float peak;
+        const bool k = int64_t(h.n_part) >= f.particle_th &&
+                       __dmul_rn(double(h.mq), ncube) >= __dmul_rn(rhs0, double(h.n_cells)) &&
+                       ms_cross_scale(C, f.ng, seed_list[s], Cn, ngn, peak);
+        keep[s] = k ? 1u : 0u;
+    }
+}
+
+// Kept groups become halos base + rank (base: halos of the earlier scales, read
+// from *n_halo); catalogue entries, and each slot's halo id (-1: not kept).
+__global__ void __launch_bounds__(kThreads) k_ms_catalogue(const HaloAcc* __restrict__ acc,
+                                                          const int32_t* __restrict__ seed_list,
+                                                          const uint32_t* __restrict__ n_seeds,
+                                                          const uint32_t* __restrict__ keep_off, FilterArgs f,
+                                                          const float* __restrict__ C, const float* __restrict__ Cn,
+                                                          int ngn, int scale, const int64_t* __restrict__ n_halo,
+                                                          cwthf_ms_halo* __restrict__ cat,
+                                                          int32_t* __restrict__ slot_halo) {
+    const uint32_t ns = *n_seeds;
+    const int64_t base = *n_halo;
+    const int64_t N = f.ng;
+    const double cell_q = (f.L / double(f.ng)) / double(kFracOne);
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < ns; s += stride) {
+        const uint32_t rank = keep_off[s];
+        const bool kept = keep_off[s + 1] != rank;
+        const int64_t id = base + rank;
+        slot_halo[s] = kept ? int32_t(id) : -1;
+        if (!kept || id >= f.cat_cap) continue;
+        const HaloAcc h = acc[s];
+        const int64_t seed = seed_list[s];
+        const int64_t sc[3] = {seed % N, (seed / N) % N, seed / (N * N)};
+        cwthf_ms_halo o;
+        o.seed = seed;
+        o.n_part = int64_t(h.n_part);
+        o.n_cells = int64_t(h.n_cells);
+        o.mass = __dmul_rn(double(h.mq), f.mass_unit);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            double u = double(sc[d] * kFracOne);
+            if (h.mq > 0) u = __dadd_rn(u, __ddiv_rn(double(h.mom[d]), double(h.mq)));
+            double x = __dmul_rn(u, cell_q);
+            if (x >= f.L) x = __dsub_rn(x, f.L);
+            else if (x < 0.0) x = __dadd_rn(x, f.L);
+            o.centre[d] = x;
+        }
+        o.peak = ms_corrected_peak(C, f.ng, seed, Cn ? ngn : 0);
+        o.scale = scale;
+        cat[id] = o;
+    }
+}
+
+// Particles without a halo id whose group was kept take the halo's id.
+__global__ void __launch_bounds__(kThreads) k_ms_ids(const int32_t* __restrict__ pslot, int64_t np,
+                                                    const int32_t* __restrict__ slot_halo,
+                                                    int32_t* __restrict__ halo_id) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np; i += stride) {
+        const int32_t sl = pslot[i];
+        if (sl >= 0 && halo_id[i] < 0) {
+            const int32_t id = slot_halo[sl];
+            if (id >= 0) halo_id[i] = id;
+        }
+    }
+}
+
+// The running halo count after a scale: n_halo += kept groups; more halos
+// than cat_cap is reported as CWTHF_E_CAPACITY (the count is still exact).
+__global__ void k_ms_advance(const uint32_t* __restrict__ keep_off, const uint32_t* __restrict__ n_seeds,
+                             int64_t* __restrict__ n_halo, int64_t cat_cap, int* status) {
+    const int64_t n = *n_halo + int64_t(keep_off[*n_seeds]);
+    *n_halo = n;
+    if (n > cat_cap) set_status(status, CWTHF_E_CAPACITY);
+}
+
 }  // namespace
+
+int ms_scale_sums(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L, int ng,
+                  const int32_t* halo_id, int32_t* pslot, cudaStream_t s) {
+    const int64_t total_key = deposit_geom(ng).ntiles * kDepClasses;
+    const uint32_t* total = ctx->dep_off + total_key;
+    const int pblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kThreads), int64_t(ctx->sm_count) * 16));
+    const int cblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kChunk), int64_t(ctx->sm_count) * kHsCtasPerSm));
+    CWTHF_LAUNCH(ctx, s, "k_ms_mark", k_ms_mark<<<pblocks, kThreads, 0, s>>>(halo_id, ctx->part_rec, np, total, ctx->dep_rec));
+    DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
+    int32_t* rec_slot = ctx->part_slot;
+    CWTHF_LAUNCH(ctx, s, "k_halo_sums",
+                 k_halo_sums<<<cblocks, kHsThreads, 0, s>>>(a, total, ctx->dep_rec, ctx->dep_mq, ctx->label,
+                                                          ctx->seed_bits, ctx->seed_prefix, ctx->n_seeds, ctx->acc,
+                                                          rec_slot, 1, ctx->d_mtot, 1));
+    CWTHF_LAUNCH(ctx, s, "k_ms_pslot", k_ms_pslot<<<pblocks, kThreads, 0, s>>>(ctx->part_rec, np, total, rec_slot, pslot));
+    return cuda_status(cudaGetLastError());
+}
+
+int ms_finalize(cwthf_ctx* ctx, int64_t np, double L, int ng, double mass_unit, const float* C, const float* Cn,
+                int ngn, int scale, double dens_th, int64_t particle_th, const int32_t* pslot,
+                const unsigned long long* mtot, int32_t* halo_id, cwthf_ms_halo* cat, int64_t cat_cap,
+                int64_t* n_halo, cudaStream_t s) {
+    const int64_t slot_cap = int64_t(ng) * ng * ng / 8 + 8;
+    const int blocks = ctx->sm_count * 8;
+    const int pblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kThreads), int64_t(ctx->sm_count) * 16));
+    FilterArgs f;
+    f.ng = ng;
+    f.L = L;
+    f.mass_unit = mass_unit;
+    f.dens_th = dens_th;
+    f.particle_th = particle_th;
+    f.cat_cap = cat_cap;
+    CWTHF_LAUNCH(ctx, s, "k_ms_keep", k_ms_keep<<<blocks, kThreads, 0, s>>>(ctx->acc, ctx->seed_list, ctx->n_seeds, mtot, f,
+                                                                           C, Cn, ngn, ctx->keep_off));
+    int rc = scan_u32_dev(ctx, ctx->keep_off, ctx->keep_off, ctx->n_seeds, slot_cap, s);
+    if (rc) return rc;
+    CWTHF_LAUNCH(ctx, s, "k_ms_catalogue",
+                 k_ms_catalogue<<<blocks, kThreads, 0, s>>>(ctx->acc, ctx->seed_list, ctx->n_seeds, ctx->keep_off, f, C,
+                                                            Cn, ngn, scale, n_halo, cat, ctx->slot_halo));
+    CWTHF_LAUNCH(ctx, s, "k_ms_ids", k_ms_ids<<<pblocks, kThreads, 0, s>>>(pslot, np, ctx->slot_halo, halo_id));
+    CWTHF_LAUNCH(ctx, s, "k_ms_advance", k_ms_advance<<<1, 1, 0, s>>>(ctx->keep_off, ctx->n_seeds, n_halo, cat_cap,
+                                                                     ctx->d_status));
+    return cuda_status(cudaGetLastError());
+}
 
 int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L, int ng,
                 const int32_t* label, const float* cwt, const cwthf_params* p, int scale, int n_scales,
@@ -443,7 +668,7 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
     CWTHF_LAUNCH(ctx, s, "k_halo_sums",
                  k_halo_sums<<<cblocks, kHsThreads, 0, s>>>(a, ctx->dep_off + total_key, ctx->dep_rec, ctx->dep_mq,
                                                           label, ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc,
-                                                          ctx->part_slot + int64_t(scale) * np, 1, ctx->d_mtot));
+                                                          ctx->part_slot + int64_t(scale) * np, 1, ctx->d_mtot, 0));
     FilterArgs f;
     f.ng = ng;
     f.L = L;

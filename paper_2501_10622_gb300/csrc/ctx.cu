@@ -345,6 +345,65 @@ int cwthf_find(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_
     return rc;
 }
 
+int cwthf_find_multiscale(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L,
+                          int n_scales, const double* w, const int* ng, float cwt_min, double dens_th,
+                          int64_t particle_th, int32_t* halo_id, cwthf_ms_halo* cat, int64_t cat_cap, int64_t* n_halo,
+                          void* stream) {
+    if (!ctx || !w || !ng || n_scales < 1 || ctx->max_scales < 2) return CWTHF_E_INVALID_ARG;
+    int rc = check_particles(ctx, pos, np, mass_unit);
+    if (rc) return rc;
+    if ((np > 0 && !halo_id) || cat_cap < 0 || (cat_cap > 0 && !cat) || !n_halo || std::isnan(cwt_min) ||
+        std::isnan(dens_th))
+        return CWTHF_E_INVALID_ARG;
+    for (int j = 0; j < n_scales; j++) {
+        if ((rc = check_common(ctx, ng[j], L))) return rc;
+        if (!(w[j] > 0) || !std::isfinite(w[j])) return CWTHF_E_INVALID_ARG;
+    }
+    DeviceGuard g(ctx->device);
+    cudaStream_t s = as_stream(stream);
+    Range r("cwthf_find_multiscale");
+    // every scale's tables before anything is queued
+    for (int j = 0; j < n_scales && !rc; j++) {
+        const float* wt = nullptr;
+        rc = transform_tables(ctx, ng[j], L, &w[j], 1, &wt, s);
+    }
+    if (rc) return rc;
+    // the two fields kept at a time: the CWT buffer and the second spectrum
+    float* field[2] = {ctx->cwt, reinterpret_cast<float*>(ctx->spec2)};
+    int32_t* pslot = ctx->part_slot + std::max<int64_t>(np, 1);
+    unsigned long long* mtot_all = ctx->d_mtot + 1;  // total mass of all particles
+    cudaError_t e = cudaMemsetAsync(n_halo, 0, sizeof(int64_t), s);
+    if (e == cudaSuccess && np > 0) e = cudaMemsetAsync(halo_id, 0xff, size_t(np) * sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int j = 0; j <= n_scales && !rc; j++) {
+        if (j < n_scales) {  // deposit and CWT of scale j
+            Range r1("scale: deposit and CWT");
+            const float* wt = nullptr;
+            rc = transform_tables(ctx, ng[j], L, &w[j], 1, &wt, s);
+            if (!rc) rc = deposit_impl(ctx, pos, mass, mass_unit, np, L, ng[j], ctx->grid, nullptr, s);
+            if (!rc && j == 0 &&
+                (e = cudaMemcpyAsync(mtot_all, ctx->d_mtot, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                                     s)) != cudaSuccess)
+                rc = cuda_status(e);
+            if (!rc) rc = transform_forward_xy(ctx, ctx->grid, ng[j], ctx->spec, s);
+            if (!rc) rc = transform_wavelet_inverse(ctx, ctx->spec, ctx->spec, ng[j], L, w[j], mass_unit, wt, field[j & 1], s);
+        }
+        if (j >= 1 && !rc) {  // decide scale j - 1 against scale j's field
+            Range r2("scale: cross-scale check, thresholds, halo ids");
+            const bool last = j == n_scales;
+            rc = ms_finalize(ctx, np, L, ng[j - 1], mass_unit, field[(j - 1) & 1], last ? nullptr : field[j & 1],
+                             last ? 0 : ng[j], j - 1, dens_th, particle_th, pslot, mtot_all, halo_id, cat, cat_cap,
+                             n_halo, s);
+        }
+        if (j < n_scales && !rc) {  // segments and groups of scale j
+            Range r3("scale: segmentation and group sums");
+            rc = segment_impl(ctx, field[j & 1], ng[j], cwt_min, ctx->label, true, s);
+            if (!rc) rc = ms_scale_sums(ctx, pos, mass, mass_unit, np, L, ng[j], halo_id, pslot, s);
+        }
+    }
+    return rc;
+}
+
 int cwthf_sync(cwthf_ctx* ctx, void* stream) {
     if (!ctx) return CWTHF_E_INVALID_ARG;
     DeviceGuard g(ctx->device);

@@ -336,6 +336,16 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
                 int ng, const int32_t* label, const float* cwt, const cwthf_params* p, int scale, int n_scales,
                 int32_t* halo_id, cwthf_halo* cat, int64_t cat_cap, int64_t* n_halo, bool seeds_ready,
                 bool bins_ready, cudaStream_t s);
+// The multi-scale loop's per-scale pieces (assign.cu): group sums of the
+// particles without a halo id at this scale's grid, and their slots (pslot);
+// then, one scale later, the keep decision with the cross-scale check against
+// the next field Cn (nullptr after the last scale), the catalogue and the ids.
+int ms_scale_sums(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L, int ng,
+                  const int32_t* halo_id, int32_t* pslot, cudaStream_t s);
+int ms_finalize(cwthf_ctx* ctx, int64_t np, double L, int ng, double mass_unit, const float* C, const float* Cn,
+                int ngn, int scale, double dens_th, int64_t particle_th, const int32_t* pslot,
+                const unsigned long long* mtot, int32_t* halo_id, cwthf_ms_halo* cat, int64_t cat_cap,
+                int64_t* n_halo, cudaStream_t s);
 void free_tables(cwthf_ctx* ctx);
 int init_tables(cwthf_ctx* ctx);
 
