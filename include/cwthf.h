@@ -126,8 +126,12 @@ CWTHF_API void cwthf_default_params(double w, cwthf_params *p);
  * fp64 and queues one copy on its stream; a full cache reuses the least
  * recently used slot (waiting, on the host, for that slot's previous copy).
  * A slot used by work captured into a CUDA graph is kept for the context's
- * lifetime; during a capture, a call that needs a new table while no slot is
- * free fails with CWTHF_E_TABLE_CACHE (nothing queued). */
+ * lifetime.  A captured call records the host-to-device copy of every table
+ * it needs that no uncaptured call has copied yet, so such a graph is self-
+ * contained; tables already copied (by cwthf_prepare or an earlier call) are
+ * only read by the graph, and those copies must have completed before the
+ * graph runs.  During a capture, a call that needs a new table while no slot
+ * is free fails with CWTHF_E_TABLE_CACHE (nothing queued). */
 CWTHF_API int cwthf_create(int device, int max_ng, int64_t max_np, int max_scales, cwthf_ctx **out);
 CWTHF_API void cwthf_destroy(cwthf_ctx *ctx);
 

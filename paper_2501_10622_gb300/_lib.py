@@ -317,6 +317,10 @@ class Context:
             cat = t.empty((ns, cat_cap, 64), dtype=t.uint8, device=self.device)
         if n_halo is None:
             n_halo = t.zeros(ns, dtype=t.int64, device=self.device)
+        for name, buf, n in (("halo_id", halo_id, ns * pos.shape[0]), ("cat", cat, ns * cat_cap * 64),
+                             ("n_halo", n_halo, ns)):
+            if not buf.is_contiguous() or buf.numel() < n:
+                raise ValueError(f"{name} must be a contiguous buffer of at least {n} elements")
         arr = (Params * ns)(*params)
         _check(lib().cwthf_find(self._h, _ptr(pos), _ptr(mass), float(mass_unit), pos.shape[0], float(L), int(ng),
                                 arr, ns, _ptr(halo_id), _ptr(cat), int(cat_cap), _ptr(n_halo), self._stream(stream)),

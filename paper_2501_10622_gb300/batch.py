@@ -7,10 +7,11 @@ on its slot's stream, the slot streams forked from and joined back into one
 capture stream -- is recorded once into a CUDA graph; a batch then costs a
 single graph launch, and jobs on different slots overlap on the GPU.
 
-Nothing runs eagerly before the capture: the library keeps its FFT and
-wavelet tables in slots sized when the contexts are created, and a captured
-call records the copies of the tables it needs into the graph.  Results are
-deterministic: each job's halo ids equal those of a single cwthf_find call.
+No job runs eagerly before the capture: the library keeps its FFT and
+wavelet tables in slots sized when the contexts are created; each slot's
+tables for its jobs are filled once (cwthf_prepare) before the capture, so
+the graph only reads them.  Results are deterministic: each job's halo ids
+equal those of a single cwthf_find call.
 """
 from __future__ import annotations
 
@@ -83,6 +84,9 @@ class Batch:
         self.check()
 
     def capture(self):
+        for j in self.jobs:  # tables on the device before the capture; no job runs
+            self.ctx[j.slot].prepare(j.ng, j.box, [p.w for p in j.params], stream=self.streams[j.slot])
+        torch.cuda.synchronize(self.device)
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph, stream=self.main):
             self._enqueue(self.main)

@@ -943,11 +943,14 @@ void host_wavelet_tables(int ng, double L, double w, float* out) {
 // copy to the device on the call's stream, so a call allocates nothing and
 // never waits for the device, except when it must reuse a slot whose
 // previous copy may still be pending.  Slots read by work captured into a
-// CUDA graph are never reused, and a captured call always captures the copy
-// of the tables it reads, so the graph brings its own tables on every replay
-// whatever ran before it; an uncaptured call that finds a slot filled only
-// inside a capture queues the copy itself.  During a capture only free slots
-// can be filled; with none left the call fails with CWTHF_E_TABLE_CACHE.
+// CUDA graph are never reused.  A captured call records the copy of a table
+// that no uncaptured call has put on the device yet, so such a graph brings
+// its own tables on every replay; a table already copied by an uncaptured
+// call (cwthf_prepare, or an earlier call) is only read, and that copy must
+// be complete before the graph runs.  An uncaptured call that finds a slot
+// filled only inside a capture queues the copy itself.  During a capture only
+// free slots can be filled; with none left the call fails with
+// CWTHF_E_TABLE_CACHE.
 int table_lookup(cwthf_ctx* ctx, int kind, int ng, double L, double w, cudaStream_t s, const float** out) {
     std::lock_guard<std::mutex> g(ctx->table_mu);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -994,7 +997,10 @@ int table_lookup(cwthf_ctx* ctx, int kind, int ng, double L, double w, cudaStrea
         t.w = w;
         ctx->table_fills++;
     }
-    if (capturing || !t.on_device) {
+    // a captured call that finds the table already on the device (an earlier
+    // uncaptured copy) records no copy: the graph reads the slot, which is
+    // kept from now on; otherwise the graph carries the copy itself
+    if (!t.on_device) {  // a fill always clears on_device
         if (cudaMemcpyAsync(dev, host, n * 4, cudaMemcpyHostToDevice, s) != cudaSuccess) return CWTHF_E_CUDA;
         if (!capturing) {
             if (cudaEventRecord(t.filled, s) != cudaSuccess) return CWTHF_E_CUDA;

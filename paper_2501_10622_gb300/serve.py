@@ -83,7 +83,7 @@ class Slot:
         self.ng, self.np_max, self.n_scales, self.cat_cap = ng, np_max, n_scales, cat_cap
         self.ctx = _lib.Context(device.index or 0, max_ng=ng, max_np=np_max, max_scales=n_scales)
         self.stream = torch.cuda.Stream(device)
-        self.halo_id = torch.empty((n_scales, np_max), dtype=torch.int32, device=device)
+        self.halo_id = torch.empty(n_scales * np_max, dtype=torch.int32, device=device)  # [ns][np] per job
         self.cat = torch.empty((n_scales, cat_cap, 64), dtype=torch.uint8, device=device)
         self.n_halo = torch.zeros(n_scales, dtype=torch.int64, device=device)
         self.event = torch.cuda.Event()
@@ -95,10 +95,14 @@ class Slot:
 
     def launch(self, job: Job):
         ns = len(job.params)
-        self.ctx.find(job.pos, job.box, job.ng, job.params, cat_cap=self.cat_cap, halo_id=self.halo_id[:ns, :job.np],
+        self.ctx.find(job.pos, job.box, job.ng, job.params, cat_cap=self.cat_cap, halo_id=self.job_ids(ns, job.np),
                       cat=self.cat[:ns], n_halo=self.n_halo[:ns], stream=self.stream)
         self.event.record(self.stream)
         self.job = job
+
+    def job_ids(self, ns, np_):
+        """The slot's id buffer as a contiguous [ns][np] array for one job."""
+        return self.halo_id[: ns * np_].view(ns, np_)
 
     def finish(self):
         """Called once the slot's event has completed."""
@@ -108,7 +112,7 @@ class Slot:
         if rc:
             raise _lib.CwthfError(rc, f"job {job.jid}")
         job.n_halo = [int(x) for x in self.n_halo[:ns].cpu()]
-        hid = self.halo_id[:ns, :job.np]
+        hid = self.job_ids(ns, job.np)
         job.checksum = int((hid.to(torch.int64) * torch.arange(1, job.np + 1, device=hid.device)).sum().item())
         self.job = None
 
