@@ -20,20 +20,23 @@ def mctx():
     c.close()
 
 
-def _gpu_fields(ctx, pos, L, ws, ngs):
+def _gpu_fields(ctx, pos, L, ws, ngs, mass=None, mass_unit=1.0):
     p = dev(pos)
+    m = None if mass is None else dev(mass)
     out = []
     for w, ng in zip(ws, ngs):
-        out.append(ctx.transform(ctx.deposit(p, L, ng), L, w).cpu().numpy())
+        g = ctx.deposit(p, L, ng, mass=m, mass_unit=mass_unit)
+        out.append(ctx.transform(g, L, w, mass_unit=mass_unit).cpu().numpy())
     ctx.check()
     return out
 
 
-def _compare(ctx, pos, L, ws, ngs, **kw):
-    hid, cat, nh = ctx.find_multiscale(dev(pos), L, ws, ngs, **kw)
+def _compare(ctx, pos, L, ws, ngs, mass=None, mass_unit=1.0, **kw):
+    hid, cat, nh = ctx.find_multiscale(dev(pos), L, ws, ngs, mass=None if mass is None else dev(mass),
+                                       mass_unit=mass_unit, **kw)
     ctx.check()
-    fields = _gpu_fields(ctx, pos, L, ws, ngs)
-    rhid, rcat = oracle.multiscale_on_fields(pos, L, fields, **kw)
+    fields = _gpu_fields(ctx, pos, L, ws, ngs, mass, mass_unit)
+    rhid, rcat = oracle.multiscale_on_fields(pos, L, fields, mass=mass, mass_unit=mass_unit, **kw)
     n = int(nh[0])
     assert n == len(rcat["seed"])
     np.testing.assert_array_equal(hid.cpu().numpy(), rhid)
@@ -73,7 +76,7 @@ def test_end_to_end_against_the_oracle(mctx, work64):
     got = pkg.ms_catalogue_to_numpy(cat, nh[0])
     h = hid.cpu().numpy()
     # halo ids are numbered per run: compare through (scale, seed)
-    key = lambda ids, c: np.where(ids >= 0, c["scale"][np.maximum(ids, 0)] * (1 << 40) +
+    key = lambda ids, c: np.where(ids >= 0, c["scale"][np.maximum(ids, 0)].astype(np.int64) * (1 << 40) +
                                   c["seed"][np.maximum(ids, 0)], -1)
     agree = float(np.mean(key(h, got) == key(ref["halo_id"], ref["cat"])))
     record({"config": "multi-scale loop, clumped 64^3, L=50, w = 1,2,3,4 on 32^3..96^3", "particle_agreement": agree,
