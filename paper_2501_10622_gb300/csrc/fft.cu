@@ -1156,9 +1156,11 @@ int transform_wavelet_inverse(cwthf_ctx* ctx, float2* src, float2* dst, int ng, 
     return cuda_status(cudaGetLastError());
 }
 
+// The same plans and TMA box the launches use: the y/z pass's tile width
+// decides the box, the x passes have a plan of their own.
 bool fft_size_supported(int ng) {
-    Plan p;
-    return (ng % 2 == 0) && ng / 2 <= 512 && yz_plan(ng, p) && x_plan(ng / 2, p) && pick_boxr(ng, p.C) > 0;
+    Plan yz, x;
+    return (ng % 2 == 0) && ng / 2 <= 512 && yz_plan(ng, yz) && pick_boxr(ng, yz.C) > 0 && x_plan(ng / 2, x);
 }
 
 void free_tables(cwthf_ctx* ctx) {

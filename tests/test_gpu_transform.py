@@ -84,3 +84,23 @@ def test_stuck_copy_reports_timeout(gctx, ng):
         ref = oracle.cwt_at(grid, L, w, nodes)
         got = c.cpu().numpy().reshape(-1)[nodes].astype(np.float64)
         assert np.max(np.abs(got - ref)) <= CWT_MAX_REL * np.max(np.abs(c.cpu().numpy()))
+
+
+def test_every_supported_size_transforms_a_point_mass():
+    # every grid size the library accepts must run its FFT plan: a unit mass on
+    # one node gives the wavelet's peak 6 w^1.5 there (Eq. 4)
+    import paper_2501_10622_gb300 as pkg
+    sizes = pkg.supported_sizes(8, 1024)
+    ctx = pkg.Context(0, max_ng=max(sizes), max_np=1, max_scales=1)
+    try:
+        w = 1.0
+        for ng in sizes:
+            g = torch.zeros((ng, ng, ng), dtype=torch.int64, device="cuda")
+            g[ng // 3, ng // 2, ng // 5] = 1 << 30
+            c = ctx.transform(g, float(ng), w)
+            ctx.check(what=f"ng={ng}")
+            assert abs(float(c[ng // 3, ng // 2, ng // 5]) - 6.0) <= 1e-4 * 6.0, ng
+            del g, c
+    finally:
+        ctx.close()
+        torch.cuda.empty_cache()
