@@ -835,15 +835,23 @@ int plan_threads(const Plan& p) {
     return (t + 31) / 32 * 32;
 }
 
-// Columns per y/z tile: <= 64 KB of complex data, preferring <= 256 threads
-// (two CTAs per SM at 128 registers) over <= 512.
+// Rows per TMA box for a y/z tile of C columns: the largest divisor of L (at
+// most 256) whose box spans a multiple of 128 bytes, or -1.
+int pick_boxr(int L, int C) {
+    for (int b = std::min(L, 256); b >= 1; b--)
+        if (L % b == 0 && (size_t(b) * C * 8) % 128 == 0) return b;
+    return -1;
+}
+
+// Columns per y/z tile: <= 64 KB of complex data and a valid TMA box,
+// preferring <= 256 threads (two CTAs per SM at 128 registers) over <= 512.
 bool yz_plan(int L, Plan& p) {
     if (!make_plan(L, p)) return false;
     for (int tmax : {256, 512})
         for (int C : {16, 8, 4, 2}) {
             p.C = C;
             p.T = plan_threads(p);
-            if (size_t(L) * C * 8 <= 65536 && p.T <= tmax) return true;
+            if (size_t(L) * C * 8 <= 65536 && p.T <= tmax && pick_boxr(L, C) > 0) return true;
         }
     return false;
 }
@@ -892,12 +900,6 @@ int make_spec_map(CUtensorMap* map, float2* base, int ng, bool along_z, int C, i
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? CWTHF_OK : CWTHF_E_CUDA;
-}
-
-int pick_boxr(int L, int C) {
-    for (int b = std::min(L, 256); b >= 1; b--)
-        if (L % b == 0 && (size_t(b) * C * 8) % 128 == 0) return b;
-    return -1;
 }
 
 size_t yz_smem(const Plan& p, bool global_tables) {
