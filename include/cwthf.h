@@ -14,8 +14,9 @@
  *
  * Conventions shared by every entry point
  *   - Grids are row-major [z][y][x] with x fastest; grid node g sits at
- *     g * (L / ng) in a periodic box of side L.  ng must be 2^a 3^b with
- *     a >= 1 and 8 <= ng <= 1024 (otherwise CWTHF_E_UNSUPPORTED_SIZE).
+ *     g * (L / ng) in a periodic box of side L.  ng must be 2^a 3^b 5^c 7^d
+ *     with a >= 1, 8 <= ng <= 1024, and have an FFT plan (every 2^a 3^b
+ *     size does; cwthf_check_ng tells), otherwise CWTHF_E_UNSUPPORTED_SIZE.
  *   - Positions are float [np][3] (x, y, z), in the units of L.  Any finite
  *     value with |x * ng / L| < 2^30 is accepted and wrapped into the box;
  *     others make the call fail with CWTHF_E_BAD_INPUT (reported by
@@ -65,7 +66,7 @@ extern "C" {
 enum {
     CWTHF_OK = 0,
     CWTHF_E_INVALID_ARG = 1,      /* NULL pointer, non-positive size or box, ... */
-    CWTHF_E_UNSUPPORTED_SIZE = 2, /* ng not 2^a 3^b (a >= 1) in [8, 1024], or above the context's limits */
+    CWTHF_E_UNSUPPORTED_SIZE = 2, /* ng without an FFT plan (see above), or above the context's limits */
     CWTHF_E_OVERFLOW = 3,         /* integer mass budget: m_q >= 2^31 or sum m_q >= 2^33 */
     CWTHF_E_OOM = 4,              /* device allocation failed in cwthf_create */
     CWTHF_E_CUDA = 5,             /* a CUDA runtime call failed */

@@ -38,9 +38,11 @@ assert MS_HALO_DTYPE.itemsize == 64
 
 
 def supported_sizes(lo: int = 8, hi: int = MAX_NG) -> list[int]:
-    """Grid sizes the library takes: 2^a 3^b with a >= 1, within [lo, hi]."""
-    return sorted(n for n in {2 ** a * 3 ** b for a in range(1, 11) for b in range(0, 7)} if lo <= n <= hi
-                  and check_ng(n))
+    """Grid sizes the library takes within [lo, hi]: 2^a 3^b 5^c 7^d with
+    a >= 1 for which it has an FFT plan."""
+    cand = {2 ** a * 3 ** b * 5 ** c * 7 ** d for a in range(1, 11) for b in range(7) for c in range(5)
+            for d in range(4)}
+    return sorted(n for n in cand if lo <= n <= hi and check_ng(n))
 
 
 def paper_scales(L: float, kw_low: float = 0.1, kw_high: float = 2.5, n: int | None = None, n_ref: int = 400,

@@ -23,8 +23,8 @@ struct Range {
 int check_ng(int ng) {
     if (ng < CWTHF_MIN_NG || ng > CWTHF_MAX_NG || ng % 2) return CWTHF_E_UNSUPPORTED_SIZE;
     int m = ng;
-    while (m % 2 == 0) m /= 2;
-    while (m % 3 == 0) m /= 3;
+    for (int f : {2, 3, 5, 7})
+        while (m % f == 0) m /= f;
     if (m != 1) return CWTHF_E_UNSUPPORTED_SIZE;
     return fft_size_supported(ng) ? CWTHF_OK : CWTHF_E_UNSUPPORTED_SIZE;
 }
@@ -419,7 +419,7 @@ const char* cwthf_error_string(int code) {
     switch (code) {
         case CWTHF_OK: return "ok";
         case CWTHF_E_INVALID_ARG: return "invalid argument";
-        case CWTHF_E_UNSUPPORTED_SIZE: return "unsupported grid size (need 2^a 3^b, a >= 1, 8 <= ng <= 1024, within the context's limits)";
+        case CWTHF_E_UNSUPPORTED_SIZE: return "unsupported grid size (need 2^a 3^b 5^c 7^d with a >= 1 and an FFT plan, 8 <= ng <= 1024, within the context's limits)";
         case CWTHF_E_OVERFLOW: return "integer mass budget exceeded (m_q >= 2^31 or sum m_q >= 2^33)";
         case CWTHF_E_OOM: return "device allocation failed";
         case CWTHF_E_CUDA: return "CUDA runtime error";

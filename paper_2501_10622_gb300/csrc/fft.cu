@@ -9,7 +9,8 @@
 //   x-inv   half spectrum -> real row, written to the CWT field          (k_fft_x_inv)
 //
 // Every 1D transform of length L runs in shared memory as a Stockham
-// autosort FFT with at most three radix stages (radices 2^a 3^b <= 32); each
+// autosort FFT with at most three radix stages (radices 2^a 3^b 5^c 7^d
+// <= 32); each
 // thread performs one radix-R butterfly per stage entirely in registers, with
 // compile-time constants inside the butterfly and fp32 twiddles (rounded once
 // from fp64 on the host) between stages.  Inverse transforms use
@@ -103,8 +104,10 @@ __device__ __forceinline__ void static_for(F&& f) {
     }
 }
 
-// Smallest prime factor of n (2 or 3 for the supported radices).
-__host__ __device__ constexpr int small_factor(int n) { return n % 2 == 0 ? 2 : 3; }
+// Smallest prime factor of n (2, 3, 5 or 7 for the supported radices).
+__host__ __device__ constexpr int small_factor(int n) {
+    return n % 2 == 0 ? 2 : (n % 3 == 0 ? 3 : (n % 5 == 0 ? 5 : 7));
+}
 
 // Position of output k of the in-place DIF below: for N = p*M, X[p*m + s]
 // ends in block s at the position its length-M sub-transform gives m.
@@ -119,9 +122,12 @@ __host__ __device__ constexpr int dig_rev(int n, int k) {
     return base + pos;
 }
 
-// In-register forward DFT of N values (N = 2^a 3^b), decimation in
+// In-register forward DFT of N values (N = 2^a 3^b 5^c 7^d), decimation in
 // frequency, in place on v[OFF .. OFF+N): input in natural order, output
 // X[k] at v[OFF + dig_rev(N, k)].  All indices are compile-time constants.
+// Each step splits N = P M on the smallest prime P: for k < M the P inputs
+// k + p M go through a P-point DFT, output q is multiplied by
+// exp(-2 pi i q k / N) and kept in block q, whose length-M DFT follows.
 template <int N>
 struct RegDif {
     static constexpr int P = small_factor(N);
@@ -136,7 +142,7 @@ struct RegDif {
                     v[OFF + k] = cadd(a, b);
                     v[OFF + k + M] = mul_w<N, k>(csub(a, b));
                 });
-            } else {
+            } else if constexpr (P == 3) {
                 constexpr float h = 0.866025403784438646763723170752936f;  // sqrt(3)/2
                 static_for<0, M>([&](auto kc) {
                     constexpr int k = decltype(kc)::value;
@@ -147,6 +153,21 @@ struct RegDif {
                     v[OFF + k] = cadd(a, t1);
                     v[OFF + k + M] = mul_w<N, k>(make_float2(t2.x + d.y, t2.y - d.x));          // t2 - i d
                     v[OFF + k + 2 * M] = mul_w<N, 2 * k>(make_float2(t2.x - d.y, t2.y + d.x));  // t2 + i d
+                });
+            } else {  // P = 5 or 7: the P-point DFT with constant roots
+                static_for<0, M>([&](auto kc) {
+                    constexpr int k = decltype(kc)::value;
+                    float2 a[P];
+                    static_for<0, P>([&](auto pc) { a[decltype(pc)::value] = v[OFF + k + decltype(pc)::value * M]; });
+                    static_for<0, P>([&](auto qc) {
+                        constexpr int q = decltype(qc)::value;
+                        float2 y = a[0];
+                        static_for<1, P>([&](auto pc) {
+                            constexpr int pp = decltype(pc)::value;
+                            y = cadd(y, mul_w<P, (pp * q) % P>(a[pp]));
+                        });
+                        v[OFF + k + q * M] = mul_w<N, q * k>(y);
+                    });
                 });
             }
             static_for<0, P>([&](auto sc) {
@@ -223,14 +244,24 @@ __device__ __forceinline__ void stage(int R, float2* tile, A addr, const float2*
         case 2: stage_r<2>(tile, addr, tw, L, Ns, C); break;
         case 3: stage_r<3>(tile, addr, tw, L, Ns, C); break;
         case 4: stage_r<4>(tile, addr, tw, L, Ns, C); break;
+        case 5: stage_r<5>(tile, addr, tw, L, Ns, C); break;
         case 6: stage_r<6>(tile, addr, tw, L, Ns, C); break;
+        case 7: stage_r<7>(tile, addr, tw, L, Ns, C); break;
         case 8: stage_r<8>(tile, addr, tw, L, Ns, C); break;
         case 9: stage_r<9>(tile, addr, tw, L, Ns, C); break;
+        case 10: stage_r<10>(tile, addr, tw, L, Ns, C); break;
         case 12: stage_r<12>(tile, addr, tw, L, Ns, C); break;
+        case 14: stage_r<14>(tile, addr, tw, L, Ns, C); break;
+        case 15: stage_r<15>(tile, addr, tw, L, Ns, C); break;
         case 16: stage_r<16>(tile, addr, tw, L, Ns, C); break;
         case 18: stage_r<18>(tile, addr, tw, L, Ns, C); break;
+        case 20: stage_r<20>(tile, addr, tw, L, Ns, C); break;
+        case 21: stage_r<21>(tile, addr, tw, L, Ns, C); break;
         case 24: stage_r<24>(tile, addr, tw, L, Ns, C); break;
+        case 25: stage_r<25>(tile, addr, tw, L, Ns, C); break;
         case 27: stage_r<27>(tile, addr, tw, L, Ns, C); break;
+        case 28: stage_r<28>(tile, addr, tw, L, Ns, C); break;
+        case 30: stage_r<30>(tile, addr, tw, L, Ns, C); break;
         case 32: stage_r<32>(tile, addr, tw, L, Ns, C); break;
         default: break;
     }
@@ -289,14 +320,24 @@ __device__ __forceinline__ void stage_fused(int R, float2* tile, A addr, const f
         case 2: stage_fused_r<2>(tile, addr, tw, L, Ns, C, wv); break;
         case 3: stage_fused_r<3>(tile, addr, tw, L, Ns, C, wv); break;
         case 4: stage_fused_r<4>(tile, addr, tw, L, Ns, C, wv); break;
+        case 5: stage_fused_r<5>(tile, addr, tw, L, Ns, C, wv); break;
         case 6: stage_fused_r<6>(tile, addr, tw, L, Ns, C, wv); break;
+        case 7: stage_fused_r<7>(tile, addr, tw, L, Ns, C, wv); break;
         case 8: stage_fused_r<8>(tile, addr, tw, L, Ns, C, wv); break;
         case 9: stage_fused_r<9>(tile, addr, tw, L, Ns, C, wv); break;
+        case 10: stage_fused_r<10>(tile, addr, tw, L, Ns, C, wv); break;
         case 12: stage_fused_r<12>(tile, addr, tw, L, Ns, C, wv); break;
+        case 14: stage_fused_r<14>(tile, addr, tw, L, Ns, C, wv); break;
+        case 15: stage_fused_r<15>(tile, addr, tw, L, Ns, C, wv); break;
         case 16: stage_fused_r<16>(tile, addr, tw, L, Ns, C, wv); break;
         case 18: stage_fused_r<18>(tile, addr, tw, L, Ns, C, wv); break;
+        case 20: stage_fused_r<20>(tile, addr, tw, L, Ns, C, wv); break;
+        case 21: stage_fused_r<21>(tile, addr, tw, L, Ns, C, wv); break;
         case 24: stage_fused_r<24>(tile, addr, tw, L, Ns, C, wv); break;
+        case 25: stage_fused_r<25>(tile, addr, tw, L, Ns, C, wv); break;
         case 27: stage_fused_r<27>(tile, addr, tw, L, Ns, C, wv); break;
+        case 28: stage_fused_r<28>(tile, addr, tw, L, Ns, C, wv); break;
+        case 30: stage_fused_r<30>(tile, addr, tw, L, Ns, C, wv); break;
         case 32: stage_fused_r<32>(tile, addr, tw, L, Ns, C, wv); break;
         default: break;
     }
@@ -782,7 +823,7 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks) k_fft_x_inv(XArgs 
 // ---------------------------------------------------------------------------
 // Host side: plans, tables, tensor maps, launches.
 // ---------------------------------------------------------------------------
-constexpr int kRadices[] = {2, 3, 4, 6, 8, 9, 12, 16, 18, 24, 27, 32};
+constexpr int kRadices[] = {2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 15, 16, 18, 20, 21, 24, 25, 27, 28, 30, 32};
 
 bool is_radix(int r) {
     for (int x : kRadices)

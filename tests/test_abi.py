@@ -26,7 +26,7 @@ def test_supported_grid_sizes():
     smooth = sorted({2 ** a * 3 ** b for a in range(1, 11) for b in range(0, 7) if 8 <= 2 ** a * 3 ** b <= 1024})
     for n in smooth:
         assert pkg.check_ng(n), n
-    for n in (4, 6, 7, 10, 20, 27, 81, 1000, 1152, 2048, 190, 1150):
+    for n in (4, 6, 7, 22, 26, 27, 81, 1152, 2048, 190, 1150):
         assert not pkg.check_ng(n), n
     assert synth.smooth_ng(190) in smooth and synth.smooth_ng(1150) == 1024
 
@@ -38,7 +38,7 @@ def test_workspace_bytes_monotone_and_errors():
     d = pkg.workspace_bytes(128, 1 << 20, 3)
     assert 0 < a < b < c < d
     with pytest.raises(pkg.CwthfError):
-        pkg.workspace_bytes(100, 10)
+        pkg.workspace_bytes(190, 10)
     with pytest.raises(pkg.CwthfError):
         pkg.workspace_bytes(64, -1)
 
@@ -57,6 +57,18 @@ def test_create_reports_instead_of_crashing_without_gpu():
         pytest.skip("a GPU is present")
     h = ctypes.c_void_p()
     assert pkg.lib().cwthf_create(0, 64, 100, 1, ctypes.byref(h)) == 5  # CWTHF_E_CUDA
-    assert pkg.lib().cwthf_create(0, 100, 100, 1, ctypes.byref(h)) == 2
+    assert pkg.lib().cwthf_create(0, 190, 100, 1, ctypes.byref(h)) == 2
     assert pkg.lib().cwthf_create(0, 64, -1, 1, ctypes.byref(h)) == 1
     assert pkg.lib().cwthf_sync(None, None) == 1
+
+
+def test_radix_five_and_seven_sizes():
+    # radix-5 and radix-7 stages: the paper's grid rule Int(400 k_w + 150) lands
+    # on sizes such as 350 = 2 5^2 7 or 750 = 2 3 5^3; sizes with a prime factor
+    # above 7 (190 = 2 5 19, 1150 = 2 5^2 23) need Bluestein and stay refused
+    for n in (10, 14, 20, 28, 30, 40, 50, 70, 100, 140, 250, 270, 350, 750, 1000):
+        assert pkg.check_ng(n), n
+    for n in (22, 26, 190, 230, 1150, 9, 15):
+        assert not pkg.check_ng(n), n
+    sizes = pkg.supported_sizes(8, 1024)
+    assert 350 in sizes and 190 not in sizes and all(s % 2 == 0 for s in sizes)

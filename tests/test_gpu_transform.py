@@ -19,7 +19,8 @@ def test_workload64(gctx, work64):
     assert rel <= CWT_REL_L2 and mx <= CWT_MAX_REL, (rel, mx)
 
 
-@pytest.mark.parametrize("ng", [8, 12, 16, 18, 24, 32, 36, 48, 54, 64, 72, 96, 128])
+@pytest.mark.parametrize("ng", [8, 10, 12, 14, 16, 18, 20, 24, 28, 30, 32, 36, 40, 48, 50, 54, 64, 70, 72, 96, 100,
+                                128, 140])
 def test_sizes(gctx, ng):
     L = 0.78125 * ng
     pos = synth.clumped_box(8 * ng ** 3 // 10, L, max(2, ng // 4), seed=ng).numpy()
