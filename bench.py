@@ -56,26 +56,42 @@ def run_batched(args, dev):
     import torch
     import paper_2501_10622_gb300 as pkg
     from paper_2501_10622_gb300 import batch, synth
+    from paper_2501_10622_gb300 import autotune
     subs = synth.batched_subvolumes(n_jobs=args.batch_jobs, seed=4)
     jobs = [batch.BatchJob(w.positions(dev), w.box, w.ng, [pkg.default_params(2.0)]) for w in subs]
     npart = sum(j.np for j in jobs)
+    grids = sorted({j.ng for j in jobs})
+    plans = autotune.tune(dev.index or 0, grids, reps=5)
+
+    def graph_ms(fft_plans):
+        gb = batch.Batch(jobs, n_slots=8, device=dev, fft_plans=fft_plans)
+        try:
+            gb.capture()
+            for _ in range(2):
+                gb.replay()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            e0.record(gb.main)
+            for _ in range(reps):
+                gb.replay()
+            e1.record(gb.main)
+            torch.cuda.synchronize(dev)
+            gb.check()
+            return e0.elapsed_time(e1) / reps, [(int(j.n_halo[0]), j.halo_id.clone()) for j in jobs]
+        finally:
+            gb.close()
+
+    base_ms, base_res = graph_ms(None)
+    g_ms, tuned_res = graph_ms(plans)
+    same_tuned = all(a[0] == t[0] and bool(torch.equal(a[1], t[1])) for a, t in zip(base_res, tuned_res))
+    del base_res
     b = batch.Batch(jobs, n_slots=8, device=dev)
     try:
-        b.capture()
-        for _ in range(2):
-            b.replay()
-        torch.cuda.synchronize(dev)
+        sums = [r[0] for r in tuned_res]
+        # back to back: one context, one stream, one call per job
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = 3
-        e0.record(b.main)
-        for _ in range(reps):
-            b.replay()
-        e1.record(b.main)
-        torch.cuda.synchronize(dev)
-        b.check()
-        g_ms = e0.elapsed_time(e1) / reps
-        sums = [int(j.n_halo[0]) for j in jobs]
-        # back to back: one context, one stream, one call per job
         ctx = b.ctx[0]
         s = torch.cuda.current_stream(dev)
         for j in jobs:
@@ -96,8 +112,10 @@ def run_batched(args, dev):
         b.close()
         del jobs
         torch.cuda.empty_cache()
-    return {"jobs": args.batch_jobs, "particles": npart, "grids": [32, 64, 96, 128, 192], "slots": 8,
+    return {"jobs": args.batch_jobs, "particles": npart, "grids": grids, "slots": 8,
             "graph_ms": g_ms, "graph_mparticles_per_s": npart / g_ms / 1e3,
+            "graph_ms_builtin_fft_plans": base_ms, "fft_plans": {str(k): v for k, v in plans.items()},
+            "halo_ids_identical_tuned_vs_builtin": same_tuned,
             "single_calls_ms": s_ms, "single_calls_mparticles_per_s": npart / s_ms / 1e3,
             "identical_halo_counts": same}
 

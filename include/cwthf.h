@@ -307,6 +307,21 @@ CWTHF_API int64_t cwthf_launch_count(const cwthf_ctx *ctx);
 CWTHF_API int cwthf_deposit_noalloc(const float *pos, const float *mass, double mass_unit, int64_t np, double L,
                                     int ng, int64_t *grid, int64_t *mtot, int *status, void *stream);
 
+/* Tuning: the FFT plan this context uses for grid size ng instead of its
+ * built-in rule (the paper has no counterpart; an autotuner picks plans by
+ * timing them).
+ *   which      0: the y/z passes (length ng), 1: the x passes (length ng / 2)
+ *   C          sequences per tile: 2, 4, 8 or 16
+ *   radices    host, int [n_radices]: 1-3 radices from {2, 3, 4, 5, 6, 7, 8, 9,
+ *              10, 12, 14, 15, 16, 18, 20, 21, 24, 25, 27, 28, 30, 32} whose
+ *              product is the length, applied in this order
+ *   n_radices  0 returns the pass to the built-in rule
+ * A plan the kernels cannot run (product, tile over 64 KB, over 512 threads, no
+ * TMA box for the y/z tile) is refused with CWTHF_E_INVALID_ARG.  Results
+ * change only by fp32 rounding; set plans between calls, not while work of
+ * this context is being enqueued. */
+CWTHF_API int cwthf_set_fft_plan(cwthf_ctx *ctx, int ng, int which, int C, const int *radices, int n_radices);
+
 /* Test and fault-injection settings of a context (instrumentation; the paper
  * has no counterpart).  They let a test reach the library's error paths
  * without faulting the GPU.  Keys and values:

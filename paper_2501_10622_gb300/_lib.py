@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
         L.cwthf_segment.argtypes = [P, P, i32, f, P, P]
         L.cwthf_segment_sizes.argtypes = [P, P, P, i64, P, P]
         L.cwthf_prepare.argtypes = [P, i32, d, ctypes.POINTER(d), i32, P]
+        L.cwthf_set_fft_plan.argtypes = [P, i32, i32, i32, ctypes.POINTER(i32), i32]
         L.cwthf_debug_set.argtypes = [P, i32, i64]
         L.cwthf_debug_get.argtypes = [P, i32, ctypes.POINTER(i64), P]
         L.cwthf_assign.argtypes = [P, P, P, d, i64, d, i32, P, P, ctypes.POINTER(Params), P, P, i64, P, P]
@@ -275,6 +276,17 @@ class Context:
         """Fill the table slots for grid size ng, box L and scales ws."""
         arr = (ctypes.c_double * max(len(ws), 1))(*ws)
         _check(lib().cwthf_prepare(self._h, int(ng), float(L), arr, len(ws), self._stream(stream)), "cwthf_prepare")
+
+    def set_fft_plan(self, ng: int, which: int, C: int = 0, radices=()) -> bool:
+        """Use plan (C, radices) for pass `which` (0: y/z, 1: x) of grid size
+        ng; radices=() restores the built-in rule.  False if the kernels
+        cannot run that plan."""
+        n = len(radices)
+        arr = (ctypes.c_int * max(n, 1))(*radices)
+        rc = lib().cwthf_set_fft_plan(self._h, int(ng), int(which), int(C), arr, n)
+        if rc not in (OK, E_INVALID_ARG):
+            raise CwthfError(rc, "cwthf_set_fft_plan")
+        return rc == OK
 
     def table_fills(self) -> int:
         return self.debug_get(DEBUG_TABLE_FILLS)

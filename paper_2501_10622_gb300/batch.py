@@ -11,13 +11,15 @@ No job runs eagerly before the capture: the library keeps its FFT and
 wavelet tables in slots sized when the contexts are created; each slot's
 tables for its jobs are filled once (cwthf_prepare) before the capture, so
 the graph only reads them.  Results are deterministic: each job's halo ids
-equal those of a single cwthf_find call.
+equal those of a single cwthf_find call.  With `fft_plans` (autotune.tune /
+autotune.load) every slot uses the FFT radix orders and tile widths the
+autotuner picked for each grid size.
 """
 from __future__ import annotations
 
 import torch
 
-from . import _lib
+from . import _lib, autotune
 
 
 class BatchJob:
@@ -44,7 +46,7 @@ def assign_slots(sizes, n_slots):
 
 
 class Batch:
-    def __init__(self, jobs, n_slots=8, cat_cap=1 << 16, device="cuda"):
+    def __init__(self, jobs, n_slots=8, cat_cap=1 << 16, device="cuda", fft_plans=None):
         self.device = torch.device(device)
         self.jobs = list(jobs)
         ns = max(len(j.params) for j in self.jobs)
@@ -53,6 +55,9 @@ class Batch:
         self.n_slots = min(n_slots, len(self.jobs))
         self.ctx = [_lib.Context(self.device.index or 0, max_ng=max_ng, max_np=max_np, max_scales=ns)
                     for _ in range(self.n_slots)]
+        if fft_plans:  # FFT plans picked by the autotuner (autotune.py)
+            for c in self.ctx:
+                autotune.apply(c, fft_plans)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(self.n_slots)]
         for j, s in zip(self.jobs, assign_slots([(j.ng, j.np) for j in self.jobs], self.n_slots)):
             j.slot = s

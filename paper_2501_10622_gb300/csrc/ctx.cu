@@ -435,6 +435,13 @@ const char* cwthf_error_string(int code) {
 
 int64_t cwthf_launch_count(const cwthf_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
 
+int cwthf_set_fft_plan(cwthf_ctx* ctx, int ng, int which, int C, const int* radices, int n_radices) {
+    if (!ctx || n_radices < 0 || n_radices > 3) return CWTHF_E_INVALID_ARG;
+    int rc = check_common(ctx, ng, 1.0);
+    if (rc) return rc;
+    return set_fft_plan(ctx, ng, which, C, radices, n_radices);
+}
+
 int cwthf_debug_set(cwthf_ctx* ctx, int key, int64_t value) {
     if (!ctx) return CWTHF_E_INVALID_ARG;
     switch (key) {

@@ -1101,10 +1101,41 @@ XInvKernel pick_x_inv(const Plan& p) {
     return k_fft_x_inv<DynFft>;
 }
 
+// A caller's plan (which = 0: y/z passes of length ng, 1: x passes of length
+// ng/2), checked against what the kernels can run: radices from kRadices
+// whose product is the length, C in {2, 4, 8, 16}, <= 64 KB of tile, <= 512
+// threads, and for the y/z passes a valid TMA box.
+bool plan_from(int L, int which, int C, const int* rad, int nst, Plan& p) {
+    if (nst < 1 || nst > 3 || !(C == 2 || C == 4 || C == 8 || C == 16)) return false;
+    int prod = 1;
+    for (int i = 0; i < nst; i++) {
+        if (!is_radix(rad[i])) return false;
+        prod *= rad[i];
+    }
+    if (prod != L) return false;
+    p.L = L;
+    p.nst = nst;
+    for (int i = 0; i < 3; i++) p.rad[i] = i < nst ? rad[i] : 1;
+    p.C = C;
+    p.T = which == 0 ? plan_threads(p) : std::max(plan_threads(p), 32 * std::min(C, 16));
+    if (size_t(L) * C * 8 > 65536 || p.T > 512) return false;
+    return which != 0 || pick_boxr(L, C) > 0;
+}
+
+// The plan a pass of this context uses: the caller's, else the built-in rule.
+bool pass_plan(cwthf_ctx* ctx, int ng, int which, Plan& p) {
+    {
+        std::lock_guard<std::mutex> g(ctx->table_mu);
+        for (const auto& o : ctx->fft_plans)
+            if (o.ng == ng && o.which == which) return plan_from(which == 0 ? ng : ng / 2, which, o.C, o.rad, o.nst, p);
+    }
+    return which == 0 ? yz_plan(ng, p) : x_plan(ng / 2, p);
+}
+
 int launch_yz(cwthf_ctx* ctx, float2* src, float2* dst, int ng, bool along_z, int mode, const Tables* t,
               const float* wtab, double w, double mass_unit, cudaStream_t s) {
     Plan p;
-    if (!yz_plan(ng, p)) return CWTHF_E_UNSUPPORTED_SIZE;
+    if (!pass_plan(ctx, ng, 0, p)) return CWTHF_E_UNSUPPORTED_SIZE;
     int boxr = pick_boxr(ng, p.C);
     if (boxr < 0) return CWTHF_E_UNSUPPORTED_SIZE;
     CUtensorMap in_map, out_map;
@@ -1142,9 +1173,9 @@ int launch_yz(cwthf_ctx* ctx, float2* src, float2* dst, int ng, bool along_z, in
     return cuda_status(cudaGetLastError());
 }
 
-int x_args(int ng, const Tables* t, XArgs& a) {
+int x_args(cwthf_ctx* ctx, int ng, const Tables* t, XArgs& a) {
     Plan p;
-    if (!x_plan(ng / 2, p)) return CWTHF_E_UNSUPPORTED_SIZE;
+    if (!pass_plan(ctx, ng, 1, p)) return CWTHF_E_UNSUPPORTED_SIZE;
     a.p = p;
     a.ng = ng;
     a.M = ng / 2;
@@ -1164,7 +1195,7 @@ int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, float2* sp
     if (rc) return rc;
     const Tables* t = &tb;
     XArgs a;
-    rc = x_args(ng, t, a);
+    rc = x_args(ctx, ng, t, a);
     if (rc) return rc;
     XFwdKernel k = pick_x_fwd(a.p);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(x_smem(a.p)));
@@ -1192,11 +1223,27 @@ int transform_wavelet_inverse(cwthf_ctx* ctx, float2* src, float2* dst, int ng, 
     if (!rc) rc = launch_yz(ctx, dst, dst, ng, false, kYzInverse, t, nullptr, 0.0, 1.0, s);
     if (rc) return rc;
     XArgs a;
-    if ((rc = x_args(ng, t, a))) return rc;
+    if ((rc = x_args(ctx, ng, t, a))) return rc;
     XInvKernel k = pick_x_inv(a.p);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(x_smem(a.p)));
     CWTHF_LAUNCH(ctx, s, "k_fft_x_inv", k<<<div_up(a.rows, a.p.C), a.p.T, x_smem(a.p), s>>>(a, dst, cwt));
     return cuda_status(cudaGetLastError());
+}
+
+int set_fft_plan(cwthf_ctx* ctx, int ng, int which, int C, const int* rad, int nst) {
+    if (which != 0 && which != 1) return CWTHF_E_INVALID_ARG;
+    std::lock_guard<std::mutex> g(ctx->table_mu);
+    auto& v = ctx->fft_plans;
+    v.erase(std::remove_if(v.begin(), v.end(), [&](const cwthf_ctx::PlanOverride& o) {
+                return o.ng == ng && o.which == which;
+            }), v.end());
+    if (nst == 0) return CWTHF_OK;  // back to the built-in rule
+    Plan p;
+    if (!rad || !plan_from(which == 0 ? ng : ng / 2, which, C, rad, nst, p)) return CWTHF_E_INVALID_ARG;
+    cwthf_ctx::PlanOverride o{ng, which, C, nst, {1, 1, 1}};
+    for (int i = 0; i < nst; i++) o.rad[i] = rad[i];
+    v.push_back(o);
+    return CWTHF_OK;
 }
 
 // The same plans and TMA box the launches use: the y/z pass's tile width

@@ -168,6 +168,13 @@ struct cwthf_ctx {
     std::vector<double> prof_ms;
     std::vector<int64_t> prof_n;
 
+    // FFT plans chosen by the caller (cwthf_set_fft_plan) instead of the
+    // built-in rule, per (grid size, pass): C, number of stages, radices
+    struct PlanOverride {
+        int ng, which, C, nst, rad[3];
+    };
+    std::vector<PlanOverride> fft_plans;
+
     std::mutex table_mu;
     float* table_dev = nullptr;   // [kTableSlots][table_slot_floats]
     float* table_host = nullptr;  // pinned staging, same shape
@@ -348,6 +355,8 @@ int ms_finalize(cwthf_ctx* ctx, int64_t np, double L, int ng, double mass_unit, 
                 int64_t* n_halo, cudaStream_t s);
 void free_tables(cwthf_ctx* ctx);
 int init_tables(cwthf_ctx* ctx);
+// A caller's FFT plan for one pass of grid size ng (fft.cu); nst = 0 clears it.
+int set_fft_plan(cwthf_ctx* ctx, int ng, int which, int C, const int* rad, int nst);
 
 // ---- deposit on caller-provided scratch (used by cwthf_deposit_noalloc) ------
 struct DepositScratch {
