@@ -83,7 +83,7 @@ void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, F
     if (max_scales > 1) f(reinterpret_cast<void**>(&c->spec2), spec_bytes(max_ng));
     f(reinterpret_cast<void**>(&c->seed_bits), size_t(z.nwords + 1) * 4);
     f(reinterpret_cast<void**>(&c->seed_prefix), size_t(z.nwords + 2) * 4);
-    f(reinterpret_cast<void**>(&c->seed_cells), size_t(z.cells) * 2);
+    f(reinterpret_cast<void**>(&c->seed_cells), size_t(z.cells) * 4);
     f(reinterpret_cast<void**>(&c->seed_list), size_t(z.slots) * 4);
     f(reinterpret_cast<void**>(&c->acc), size_t(z.slots) * sizeof(HaloAcc));
     f(reinterpret_cast<void**>(&c->keep_off), size_t(z.slots + 2) * 4);

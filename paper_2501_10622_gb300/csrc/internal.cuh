@@ -41,9 +41,9 @@ __host__ __device__ __forceinline__ int rec_q(unsigned long long e, int d) {
 constexpr int kMaxJumpRounds = 31;
 // The segmentation's control words (ctx->jump_changed, cleared per call):
 // [0 .. kMaxJumpRounds] "a pointer is still flagged" after the resolve pass
-// (0) and after each doubling round, then the resolve pass's row counter and
+// (0) and after each doubling round, then the resolve pass's tile counter and
 // the fallback's grid-barrier state (arrivals, generation).
-constexpr int kJumpRowCounter = kMaxJumpRounds + 1;
+constexpr int kJumpTileCounter = kMaxJumpRounds + 1;
 constexpr int kJumpBarrier = kMaxJumpRounds + 2;
 constexpr int kJumpWords = kMaxJumpRounds + 4;
 // Default length of the resolve pass's bounded chain walks.
@@ -131,7 +131,7 @@ struct cwthf_ctx {
     // segmentation / assignment scratch
     uint32_t* seed_bits = nullptr;    // [ng^3 / 32 + 1] seed bitmap
     uint32_t* seed_prefix = nullptr;  // [ng^3 / 32 + 1] exclusive popcount prefix
-    uint16_t* seed_cells = nullptr;   // [ng^3] in-tile cell count, valid at seed cells only
+    uint32_t* seed_cells = nullptr;   // [ng^3] a seed's segment cell count at the seed's cell (valid at seeds only)
     int32_t* seed_list = nullptr;     // [ng^3 / 8 + 1] seed cell of each slot
     uint32_t* n_seeds = nullptr;      // [1]
     cwthf::HaloAcc* acc = nullptr;    // [ng^3 / 8 + 1]

@@ -51,9 +51,10 @@ constexpr int kCountShift = 16;         // a seed's in-tile cell count rides abo
 constexpr uint8_t kCodeMax = 0x15, kCodeSeed = 0x40;
 
 // Parent-code blocks: a warp owns 30 columns (lanes 1-30; lanes 0 and 31 hold
-// the x-halo columns) x kParR rows (plus the two y-halo rows, all in each
-// thread's registers) x kParZ planes (plus one halo plane at each end).
-constexpr int kParR = 8, kParZ = 128, kParWarps = 4;
+// the x-halo columns) x kParR rows (plus the two y-halo rows) x kParZ planes
+// (plus one halo plane at each end), streamed through a ring of kParStages
+// planes in shared memory.
+constexpr int kParR = 4, kParZ = 128, kParWarps = 4, kParStages = 6, kParBlocks = 6;
 constexpr int kParThreads = 32 * kParWarps;
 
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
@@ -76,36 +77,71 @@ __device__ __forceinline__ int pick3(float a, float b, float c, float M, int ka,
     const int x = min(min(a == M ? ka : kNoMatch, b == M ? kb : kNoMatch), c == M ? kc : kNoMatch);
     return x & 3;
 }
-// The same away from the periodic boundary, where the strict order ranks the
-// three candidates in position order.
-__device__ __forceinline__ int pick3i(float a, float b, float M) { return a == M ? 0 : (b == M ? 1 : 2); }
+// Winner of a window of three candidates along one axis (offsets -1, 0, +1),
+// with their window maxima a, b, c and payloads qa, qb, qc (the choices made
+// along the axes searched before this one); the winner's choice (0, 1, 2) is
+// added to its payload at bit `shift`.  Away from the periodic boundary (I) the
+// strict order ranks the candidates in position order, so the winner is the
+// first one holding the maximum: a later candidate wins only if strictly
+// greater.  At the boundary the search codes of the wrapped coordinates decide.
+template <bool I>
+__device__ __forceinline__ void win3(float a, float b, float c, uint32_t qa, uint32_t qb, uint32_t qc, int ka, int kb,
+                                     int kc, int shift, float& m, uint32_t& q) {
+    if (I) {
+        const float m1 = fmaxf(a, b);
+        const uint32_t q1 = b > a ? (qb | (1u << shift)) : qa;
+        m = fmaxf(m1, c);
+        q = c > m1 ? (qc | (2u << shift)) : q1;
+    } else {
+        m = fmaxf(fmaxf(a, b), c);
+        const int k = pick3(a, b, c, m, ka, kb, kc);
+        q = (k == 0 ? qa : (k == 1 ? qb : qc)) | (uint32_t(k) << shift);
+    }
+}
 
-// Parent code of every cell.  The best of the 27 cells around c is found in
-// two steps: first the maximum value M, separably (x by warp shuffles, y
-// across the thread's registers, z over the last three planes, also in
-// registers); then the winner among the cells equal to M, which under the
-// strict order is the one with the smallest wrapped (z, y, x) in lexicographic
-// order: the first plane (in wrapped z order) whose window holds M, then in
-// that plane the first row whose x-window holds M, then in that row the first
-// column holding M.  The row and column choices of every plane are kept as
-// 2-bit codes per row (x: 10 rows in one word, y + x: 8 rows in one word), so
-// a cell's search ends with a z choice and a few bit extractions.
+// Asynchronous 4-byte copy global -> shared (sm_80+ cp.async), completed in
+// groups: each thread waits only for its own copies.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(uint32_t(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Parent code of every cell.  The best of the 27 cells around c is the first
+// cell, in wrapped (z, y, x) lexicographic order, holding the window's maximum
+// M, so it is found separably: per row and plane the x window (warp shuffles)
+// gives the row's maximum and x choice; per plane the y window over the
+// thread's rows gives the plane's maximum and (y, x) choice; the z window over
+// a ring of the last three planes gives M and the full choice, which is the
+// parent code itself (offset + 1 along x, y, z in bits 0-1, 2-3, 4-5).  The
+// choices ride along with the maxima as payloads, so no choice is searched for
+// twice.  Each lane streams its column's rows through a ring of kParStages
+// planes in shared memory (asynchronous copies issued kParStages - 1 planes
+// ahead), which keeps enough loads in flight without holding them in
+// registers.  The plane loop is unrolled six times, so that the ring slots
+// rotate by renaming rather than copying.
 // One warp's block.  XI / YI: the block's owned columns / rows are away from
 // the periodic boundary, where the x / y choices reduce to position order;
 // the z choice takes the same shortcut on every plane but the two wrapped ones.
 template <bool XI, bool YI>
 __device__ __forceinline__ void parent_block(const float* __restrict__ C, int N, float cwt_min,
                                              uint8_t* __restrict__ code_out, uint32_t* __restrict__ seed_bits,
-                                             int* status, int x0, int y0, int z0, int wzc) {
-    constexpr int R = kParR, NR = kParR + 2;
+                                             int* status, int x0, int y0, int z0, int wzc, float* ring) {
+    constexpr int R = kParR, NR = kParR + 2, S = kParStages;
+    static_assert(6 % S == 0, "the unrolled loop fixes each plane's ring slot");
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
     const int xc = ((x0 + lane - 1) % N + N) % N;
     const bool own_x = lane >= 1 && lane <= 30 && x0 + lane - 1 < N;
     int kxm = 0, kxc = 5, kxp = 10;
     if (!XI) codes3(wrap(xc - 1, N), xc, wrap(xc + 1, N), kxm, kxc, kxp);
-    // offsets of the rows y0-1 .. y0+R (wrapped) and the y codes of the owned
-    // rows, packed km | kc << 4 | kp << 8 per row
+    // offsets of the rows y0-1 .. y0+R (wrapped) and the y search codes of the
+    // owned rows, packed km | kc << 4 | kp << 8 per row
     int32_t yoff[NR];
 #pragma unroll
     for (int j = 0; j < NR; j++) yoff[j] = (((y0 - 1 + j) % N + N) % N) * N;
@@ -121,50 +157,41 @@ __device__ __forceinline__ void parent_block(const float* __restrict__ C, int N,
     }
     const int32_t plane = N * N;
     const float* colp = C + xc;
-    float v[NR], vn[NR];
-    auto load_plane = [&](int p, float (&dst)[NR]) {
-        const int z = ((z0 - 1 + p) % N + N) % N;
-        const float* base = colp + size_t(z) * size_t(plane);
-#pragma unroll
-        for (int j = 0; j < NR; j++) dst[j] = __ldg(base + yoff[j]);
-    };
-    load_plane(0, v);
-    float pm0[R], pm1[R], pm2[R];  // y-window maxima of planes p-2, p-1, p (per owned row)
-    uint32_t yx0 = 0, yx1 = 0, yx2 = 0;  // their packed (y code, x code) per row
-#pragma unroll
-    for (int r = 0; r < R; r++) pm0[r] = pm1[r] = pm2[r] = 0.f;
-    bool bad = false;
     const int np_ = wzc + 2;
-#pragma unroll 1
-    for (int p = 0; p < np_; p++) {
-        if (p + 1 < np_) load_plane(p + 1, vn);
-        // x windows of all rows, and each row's x choice
+    float* my = ring + lane;  // this lane's column of ring slot s, row j: my[(s * NR + j) * 32]
+    // copies of plane p (z = z0 - 1 + p, wrapped) into ring slot p % S, one group per plane
+    auto issue = [&](int p) {
+        if (p < np_) {
+            const int z = ((z0 - 1 + p) % N + N) % N;
+            const float* base = colp + size_t(z) * size_t(plane);
+            float* dst = my + (p % S) * NR * 32;
+#pragma unroll
+            for (int j = 0; j < NR; j++) cp_async4(dst + j * 32, base + yoff[j]);
+        }
+        cp_async_commit();  // empty groups past the end keep the count uniform
+    };
+    bool bad = false;
+    // plane p (ring slot p % S, unroll position u = p % 6): x and y windows
+    // into the window ring slot (mn, qn), then the z windows of plane p - 1
+    // from the slots of planes p - 2 (mo, qo), p - 1 (mm, qm) and p (mn, qn)
+    auto step = [&](int p, auto u, const float (&mo)[R], const uint32_t (&qo)[R], const float (&mm)[R],
+                    const uint32_t (&qm)[R], float (&mn)[R], uint32_t (&qn)[R]) {
+        issue(p + S - 1);
+        cp_async_wait<S - 1>();  // this lane's copies of plane p have landed
+        const float* src = my + (decltype(u)::value % S) * NR * 32;
         float rm[NR];
-        uint32_t xcp = 0;
+        uint32_t rq[NR];
 #pragma unroll
         for (int j = 0; j < NR; j++) {
-            bad |= (v[j] != v[j]);
-            const float vl = __shfl_up_sync(full, v[j], 1), vr = __shfl_down_sync(full, v[j], 1);
-            rm[j] = fmaxf(fmaxf(vl, v[j]), vr);
-            const int cx = XI ? pick3i(vl, v[j], rm[j]) : pick3(vl, v[j], vr, rm[j], kxm, kxc, kxp);
-            xcp |= uint32_t(cx) << (2 * j);
+            const float v = src[j * 32];
+            bad |= (v != v);
+            const float vl = __shfl_up_sync(full, v, 1), vr = __shfl_down_sync(full, v, 1);
+            win3<XI>(vl, v, vr, 0u, 0u, 0u, kxm, kxc, kxp, 0, rm[j], rq[j]);
         }
-        // y windows of the owned rows and their (y, x) choices
-        uint32_t yxp = 0;
 #pragma unroll
-        for (int r = 0; r < R; r++) {
-            const float m = fmaxf(fmaxf(rm[r], rm[r + 1]), rm[r + 2]);
-            const int cy = YI ? pick3i(rm[r], rm[r + 1], m)
-                              : pick3(rm[r], rm[r + 1], rm[r + 2], m, ykc[r] & 15, (ykc[r] >> 4) & 15, ykc[r] >> 8);
-            const uint32_t cx = (xcp >> (2 * (r + cy))) & 3u;
-            yxp |= (uint32_t(cy) | (cx << 2)) << (4 * r);
-            pm0[r] = pm1[r];
-            pm1[r] = pm2[r];
-            pm2[r] = m;
-        }
-        yx0 = yx1;
-        yx1 = yx2;
-        yx2 = yxp;
+        for (int r = 0; r < R; r++)
+            win3<YI>(rm[r], rm[r + 1], rm[r + 2], rq[r], rq[r + 1], rq[r + 2], ykc[r] & 15, (ykc[r] >> 4) & 15,
+                     ykc[r] >> 8, 2, mn[r], qn[r]);
         if (p >= 2) {
             // the cells of plane p-1 (z = z0 + p - 2)
             const int zc = z0 + p - 2;
@@ -175,16 +202,12 @@ __device__ __forceinline__ void parent_block(const float* __restrict__ C, int N,
             auto emit = [&](auto zi) {
 #pragma unroll
                 for (int r = 0; r < R; r++) {
-                    const float M = fmaxf(fmaxf(pm0[r], pm1[r]), pm2[r]);
-                    const int cz = decltype(zi)::value ? pick3i(pm0[r], pm1[r], M)
-                                                       : pick3(pm0[r], pm1[r], pm2[r], M, kzm, kzc, kzp);
-                    const uint32_t yx = cz == 0 ? yx0 : (cz == 1 ? yx1 : yx2);
-                    const uint32_t f = (yx >> (4 * r)) & 15u;
-                    uint32_t code = (f >> 2) | ((f & 3u) << 2) | (uint32_t(cz) << 4);
+                    float M;
+                    uint32_t code;
+                    win3<decltype(zi)::value>(mo[r], mm[r], mn[r], qo[r], qm[r], qn[r], kzm, kzc, kzp, 4, M, code);
                     const bool seed = code == kCodeMax && M > cwt_min;
-                    code |= seed ? kCodeSeed : 0u;
                     if (own_x && y0 + r < N) {
-                        out[yoff[r + 1]] = uint8_t(code);
+                        out[yoff[r + 1]] = uint8_t(code | (seed ? kCodeSeed : 0u));
                         if (seed) {
                             const uint32_t g = uint32_t(gz + yoff[r + 1]);
                             atomicOr(&seed_bits[g >> 5], 1u << (g & 31));
@@ -195,16 +218,41 @@ __device__ __forceinline__ void parent_block(const float* __restrict__ C, int N,
             if (!zlo && !zhi) emit(std::integral_constant<bool, true>{});  // uniform: once per plane
             else emit(std::integral_constant<bool, false>{});
         }
+    };
+    float m0[R], m1[R], m2[R];
+    uint32_t q0[R], q1[R], q2[R];
 #pragma unroll
-        for (int j = 0; j < NR; j++) v[j] = vn[j];
+    for (int p = 0; p < S - 1; p++) issue(p);
+    // plane p goes to window ring slot p % 3
+#pragma unroll 1
+    for (int p = 0; p < np_; p += 6) {
+        using I0 = std::integral_constant<int, 0>;
+        using I1 = std::integral_constant<int, 1>;
+        using I2 = std::integral_constant<int, 2>;
+        using I3 = std::integral_constant<int, 3>;
+        using I4 = std::integral_constant<int, 4>;
+        using I5 = std::integral_constant<int, 5>;
+        step(p, I0{}, m1, q1, m2, q2, m0, q0);
+        if (p + 1 >= np_) break;
+        step(p + 1, I1{}, m2, q2, m0, q0, m1, q1);
+        if (p + 2 >= np_) break;
+        step(p + 2, I2{}, m0, q0, m1, q1, m2, q2);
+        if (p + 3 >= np_) break;
+        step(p + 3, I3{}, m1, q1, m2, q2, m0, q0);
+        if (p + 4 >= np_) break;
+        step(p + 4, I4{}, m2, q2, m0, q0, m1, q1);
+        if (p + 5 >= np_) break;
+        step(p + 5, I5{}, m0, q0, m1, q1, m2, q2);
     }
+    cp_async_wait<0>();  // nothing left in flight (the trailing groups are empty)
     if (bad) set_status(status, CWTHF_E_BAD_INPUT);
 }
 
-__global__ void __launch_bounds__(kParThreads, 4) k_seg_parent(const float* __restrict__ C, int ng, float cwt_min,
-                                                            uint8_t* __restrict__ code_out,
-                                                            uint32_t* __restrict__ seed_bits, int* status) {
+__global__ void __launch_bounds__(kParThreads, kParBlocks) k_seg_parent(const float* __restrict__ C, int ng,
+                                                                     float cwt_min, uint8_t* __restrict__ code_out,
+                                                                     uint32_t* __restrict__ seed_bits, int* status) {
     constexpr int R = kParR;
+    __shared__ float ring[kParWarps][kParStages * (kParR + 2) * 32];
     const int N = ng;
     const int nbx = (N + 29) / 30, nby = (N + R - 1) / R;
     const int64_t warp = (int64_t(blockIdx.x) * kParThreads + threadIdx.x) >> 5;
@@ -213,11 +261,12 @@ __global__ void __launch_bounds__(kParThreads, 4) k_seg_parent(const float* __re
     const int by = int(warp % nby), bx = int((warp / nby) % nbx), bz = int(warp / (int64_t(nby) * nbx));
     const int x0 = bx * 30, y0 = by * R, z0 = bz * kParZ;
     const int wzc = min(kParZ, N - z0);
+    float* my_ring = ring[threadIdx.x >> 5];
     // warp-uniform: owned columns x0 .. x0+29 and rows y0 .. y0+R-1 clear of 0 and N-1
     if (x0 > 0 && x0 + 30 < N && y0 > 0 && y0 + R < N)
-        parent_block<true, true>(C, N, cwt_min, code_out, seed_bits, status, x0, y0, z0, wzc);
+        parent_block<true, true>(C, N, cwt_min, code_out, seed_bits, status, x0, y0, z0, wzc, my_ring);
     else
-        parent_block<false, false>(C, N, cwt_min, code_out, seed_bits, status, x0, y0, z0, wzc);
+        parent_block<false, false>(C, N, cwt_min, code_out, seed_bits, status, x0, y0, z0, wzc, my_ring);
 }
 
 // In-tile chains of a 32 x 16 x 32-cell tile from the parent codes.  Every
@@ -230,7 +279,7 @@ __global__ void __launch_bounds__(kParThreads, 4) k_seg_parent(const float* __re
 // entry.
 __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __restrict__ codes, int ng,
                                                            int32_t* __restrict__ label,
-                                                           uint16_t* __restrict__ seed_cells,
+                                                           uint32_t* __restrict__ seed_cells,
                                                            uint32_t* __restrict__ ballots, int* status) {
     extern __shared__ int32_t ptr[];  // [kLocal], dynamic
     __shared__ uint16_t tile_seeds[kTileSeedCap];
@@ -366,29 +415,53 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
     for (uint32_t j = threadIdx.x; j < min(nts, uint32_t(kTileSeedCap)); j += blockDim.x) {
         const int i = tile_seeds[j];
         const int px = i & (kPX - 1), py = (i >> kPXBits) & (kChTY - 1), pz = i >> kPlaneBits;
-        seed_cells[size_t(gbase + (pz * N + py) * N + px)] = uint16_t(uint32_t(ptr[i]) >> kCountShift);
+        seed_cells[size_t(gbase + (pz * N + py) * N + px)] = uint32_t(ptr[i]) >> kCountShift;
     }
 }
 
 constexpr int kResolveThreads = 256;
-constexpr int kResolveRows = 4;  // tile rows a warp takes at a time
+constexpr int kResTabBits = 9, kResTab = 1 << kResTabBits;  // per-tile count table (shared memory)
 
-// The global pass over the cells whose chain left their tile.  Each warp
-// takes kResolveRows tile rows at a time from a shared counter (the flagged
-// cells crowd where the field is clumped, so a fixed split of the rows leaves
-// some warps far more work than others) and gathers the flagged cells of their non-empty
-// plane masks into a shared batch; every full batch of 32 cells (and the last,
-// partial one) is resolved by the whole warp: each lane follows its cell's
-// chain through the label grid (at most `limit` steps, kChaseLimit by default), takes the label it
-// reaches and the cells are counted with one atomic per distinct seed.  A cell
-// still unfinished at the limit stays flagged and sets changed[0]; the
-// doubling rounds then finish it and the cells are recounted.  Labels read
-// while other threads update them are always a later point of the same chain,
-// so the result does not depend on timing.
-__device__ __forceinline__ void resolve_batch(int32_t* __restrict__ label, bool valid, uint32_t c,
-                                              const uint32_t* __restrict__ bits,
-                                              const uint32_t* __restrict__ prefix,
-                                              const uint32_t* __restrict__ n_slots, HaloAcc* acc, int limit,
+// The global pass over the cells whose chain left their tile.  A CTA takes one
+// chain tile at a time from a global counter, and its warps take the tile's
+// rows one at a time from a shared counter (the flagged cells crowd where the
+// field is clumped, so a fixed split leaves some warps far more work than
+// others).  A warp gathers the flagged cells of a row's non-empty plane masks
+// into a shared batch; every full batch of 32 cells (and the warp's last,
+// partial one of the tile) is resolved by the whole warp: each lane follows
+// its cell's chain through the label grid (at most `limit` steps, kChaseLimit
+// by default) and takes the label it reaches.  The tile's cells are counted
+// per seed in a shared table (one entry per distinct seed, one shared atomic
+// per distinct seed of a batch) that is added to the counts kept at the seeds'
+// cells once per tile (the tile pass wrote each seed's in-tile count there;
+// seed slots are ranked only afterwards).  A cell still unfinished at the
+// limit stays flagged and sets changed[0]; the doubling rounds then finish it
+// and the cells are recounted.  Labels read while other threads update them
+// are always a later point of the same chain, so the result does not depend
+// on timing.
+__device__ __forceinline__ void table_add(int32_t* tkey, uint32_t* tcnt, uint32_t* __restrict__ seed_cells,
+                                          int32_t lab, uint32_t n) {
+    uint32_t h = (uint32_t(lab) * 2654435761u) >> (32 - kResTabBits);
+    for (int p = 0; p < 16; p++) {
+        const int32_t k = tkey[h];
+        if (k == lab) {
+            atomicAdd(&tcnt[h], n);
+            return;
+        }
+        if (k == -1) {
+            const int32_t prev = atomicCAS(&tkey[h], -1, lab);
+            if (prev == -1 || prev == lab) {
+                atomicAdd(&tcnt[h], n);
+                return;
+            }
+        }
+        h = (h + 1) & (kResTab - 1);
+    }
+    atomicAdd(&seed_cells[lab], n);  // table crowded: straight to the seed's count
+}
+
+__device__ __forceinline__ void resolve_batch(int32_t* __restrict__ label, bool valid, uint32_t c, int32_t* tkey,
+                                              uint32_t* tcnt, uint32_t* __restrict__ seed_cells, int limit,
                                               bool& left) {
     int32_t lab = -1;
     if (valid) {
@@ -403,41 +476,51 @@ __device__ __forceinline__ void resolve_batch(int32_t* __restrict__ label, bool 
         else lab = w;
     }
     const unsigned peers = __match_any_sync(0xffffffffu, lab);  // every lane
-    uint32_t slot;
-    if (lab >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1 && seed_slot(bits, prefix, n_slots, lab, slot))
-        atomicAdd(&acc[slot].n_cells, (unsigned long long)__popc(peers));
+    if (lab >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1)
+        table_add(tkey, tcnt, seed_cells, lab, uint32_t(__popc(peers)));
 }
 
 __global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __restrict__ label, int ng,
                                                                  const uint32_t* __restrict__ ballots,
-                                                                 const uint32_t* __restrict__ bits,
-                                                                 const uint32_t* __restrict__ prefix,
-                                                                 const uint32_t* __restrict__ n_slots,
-                                                                 HaloAcc* acc, int* __restrict__ changed,
-                                                                 unsigned* __restrict__ next_row, int limit) {
+                                                                 uint32_t* __restrict__ seed_cells,
+                                                                 int* __restrict__ changed,
+                                                                 unsigned* __restrict__ next_tile, int limit) {
     __shared__ uint32_t batch[kResolveThreads / 32][64];  // pending cells (fewer than 32 between batches)
+    __shared__ int32_t tkey[kResTab];
+    __shared__ uint32_t tcnt[kResTab];
+    __shared__ unsigned s_tile, s_row;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     uint32_t* wl = batch[threadIdx.x >> 5];
     const int N = ng;
     const int ntx = (N + kChTX - 1) / kChTX, nty = (N + kChTY - 1) / kChTY, ntz = (N + kChTZ - 1) / kChTZ;
-    const int64_t rows = int64_t(ntx) * nty * ntz * kChTY;
+    const unsigned ntiles = unsigned(ntx) * unsigned(nty) * unsigned(ntz);
     const uint32_t plane32 = uint32_t(N) * uint32_t(N);
+    for (int i = threadIdx.x; i < kResTab; i += blockDim.x) {
+        tkey[i] = -1;
+        tcnt[i] = 0;
+    }
     bool left = false;
-    uint32_t k = 0;  // warp-uniform
     for (;;) {
-        unsigned r0 = 0;
-        if (lane == 0) r0 = atomicAdd(next_row, unsigned(kResolveRows));
-        r0 = __shfl_sync(full, r0, 0);
-        if (int64_t(r0) >= rows) break;  // warp-uniform (rows < 2^21 for ng <= 1024)
-        const int64_t rend = min(int64_t(r0) + kResolveRows, rows);
-        for (int64_t rw = int64_t(r0); rw < rend; rw++) {
-            const int64_t t = rw / kChTY;
-            const int ly = int(rw % kChTY);
-            const int tx = int(t % ntx), ty = int((t / ntx) % nty), tz = int(t / (int64_t(ntx) * nty));
-            const int yc = ty * kChTY + ly;
+        if (threadIdx.x == 0) {
+            s_tile = atomicAdd(next_tile, 1u);
+            s_row = 0;
+        }
+        __syncthreads();
+        const unsigned t = s_tile;
+        if (t >= ntiles) break;  // block-uniform
+        const int tx = int(t % unsigned(ntx)), ty = int((t / unsigned(ntx)) % unsigned(nty)),
+                  tz = int(t / (unsigned(ntx) * unsigned(nty)));
+        uint32_t k = 0;  // warp-uniform
+        for (;;) {
+            unsigned ly = 0;
+            if (lane == 0) ly = atomicAdd(&s_row, 1u);
+            ly = __shfl_sync(full, ly, 0);
+            if (ly >= unsigned(kChTY)) break;  // warp-uniform
+            const int yc = ty * kChTY + int(ly);
             if (yc >= N) continue;  // warp-uniform
+            const int64_t rw = int64_t(t) * kChTY + ly;
             const uint32_t mine = ballots[rw * kChTZ + lane];  // plane `lane`'s mask
             uint32_t planes = __ballot_sync(full, mine != 0u);
             const uint32_t cell0 = uint32_t((int64_t(tz) * kChTZ * N + yc) * N + int64_t(tx) * kChTX) + uint32_t(lane);
@@ -449,7 +532,7 @@ __global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __rest
                 k += __popc(b);
                 if (k >= 32) {
                     __syncwarp();
-                    resolve_batch(label, true, wl[lane], bits, prefix, n_slots, acc, limit, left);
+                    resolve_batch(label, true, wl[lane], tkey, tcnt, seed_cells, limit, left);
                     const uint32_t rest = wl[32 + lane];
                     __syncwarp();
                     if (uint32_t(lane) + 32 < k) wl[lane] = rest;
@@ -458,10 +541,22 @@ __global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __rest
                 }
             }
         }
+        __syncwarp();
+        if (k)
+            resolve_batch(label, uint32_t(lane) < k, uint32_t(lane) < k ? wl[lane] : 0u, tkey, tcnt, seed_cells,
+                          limit, left);
+        __syncthreads();
+        // the tile's counts go to the seeds' cells; the table is cleared for the next tile
+        for (int i = threadIdx.x; i < kResTab; i += blockDim.x) {
+            const int32_t key = tkey[i];
+            if (key >= 0) {
+                atomicAdd(&seed_cells[key], tcnt[i]);
+                tkey[i] = -1;
+                tcnt[i] = 0;
+            }
+        }
+        __syncthreads();
     }
-    __syncwarp();
-    if (k) resolve_batch(label, uint32_t(lane) < k, uint32_t(lane) < k ? wl[lane] : 0u, bits, prefix, n_slots, acc, limit,
-                         left);
     if (__any_sync(full, left) && lane == 0) changed[0] = 1;
 }
 
@@ -503,14 +598,13 @@ __device__ bool grid_sync(unsigned* bar, int* status) {
 // or more links further, so 31 rounds finish any chain of a grid of at most
 // 2^30 cells; changed[r] records whether a pointer is still flagged after it.
 // Rounds are separated by grid barriers.  Then the cell counts of every seed
-// are cleared and recounted from the finished labels.  A flag still set after
+// (kept at the seed's cell) are cleared and recounted from the finished
+// labels.  A flag still set after
 // the last round is reported as CWTHF_E_NOT_CONVERGED (the labels are then
 // unspecified, and flagged values are skipped by the recount).
 __global__ void __launch_bounds__(256) k_seg_fallback(int32_t* __restrict__ label, int64_t cells, int* changed,
                                                       int rounds, const uint32_t* __restrict__ bits,
-                                                      const uint32_t* __restrict__ prefix,
-                                                      const uint32_t* __restrict__ n_slots, HaloAcc* acc,
-                                                      unsigned* bar, int* status) {
+                                                      uint32_t* __restrict__ seed_cells, unsigned* bar, int* status) {
     if (*reinterpret_cast<volatile int*>(&changed[0]) == 0) return;  // the same answer in every CTA
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     const int64_t gid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -533,14 +627,13 @@ __global__ void __launch_bounds__(256) k_seg_fallback(int32_t* __restrict__ labe
         }
     }
     if (!done && gid == 0) set_status(status, CWTHF_E_NOT_CONVERGED);
-    const int64_t ns = *n_slots;
-    for (int64_t s = gid; s < ns; s += stride) acc[s].n_cells = 0;
+    auto is_seed = [&](int64_t c) { return (bits[c >> 5] >> (c & 31)) & 1u; };
+    for (int64_t c = gid; c < cells; c += stride)
+        if (is_seed(c)) seed_cells[c] = 0;
     if (!grid_sync(bar, status)) return;
     for (int64_t c = gid; c < cells; c += stride) {
-        uint32_t slot;
         const int32_t l = label[c];
-        if (l >= 0 && int64_t(l) < cells && seed_slot(bits, prefix, n_slots, l, slot))
-            atomicAdd(&acc[slot].n_cells, 1ull);
+        if (l >= 0 && int64_t(l) < cells && is_seed(l)) atomicAdd(&seed_cells[l], 1u);
     }
 }
 
@@ -554,7 +647,7 @@ __global__ void k_popc(const uint32_t* __restrict__ bits, int64_t nwords, uint32
 // *n_slots = number of seeds, clamped to slot_cap (more seeds than that can
 // only come from an inconsistent label grid, reported as bad input).
 __global__ void k_seed_list(const uint32_t* __restrict__ bits, const uint32_t* __restrict__ prefix, int64_t nwords,
-                            int64_t slot_cap, int32_t* __restrict__ seed_list, const uint16_t* __restrict__ seed_cells,
+                            int64_t slot_cap, int32_t* __restrict__ seed_list, const uint32_t* __restrict__ seed_cells,
                             HaloAcc* __restrict__ acc, uint32_t* __restrict__ n_slots, int* status) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         uint32_t total = prefix[nwords];
@@ -614,7 +707,7 @@ int segment_sizes_impl(cwthf_ctx* ctx, int32_t* seeds, int64_t* n_cells, int64_t
     return cuda_status(cudaGetLastError());
 }
 
-int seeds_rank(cwthf_ctx* ctx, int ng, const uint16_t* seed_cells, cudaStream_t s) {
+int seeds_rank(cwthf_ctx* ctx, int ng, const uint32_t* seed_cells, cudaStream_t s) {
     int64_t cells = int64_t(ng) * ng * ng;
     int64_t nwords = (cells + 31) / 32;
     int blocks = ctx->sm_count * 8;
@@ -650,8 +743,7 @@ int launch_fallback(cwthf_ctx* ctx, int32_t* label, int64_t cells, cudaStream_t 
     int* changed = ctx->jump_changed;
     unsigned* bar = reinterpret_cast<unsigned*>(changed + kJumpBarrier);
     int rounds = ctx->dbg_jump_rounds;
-    void* args[] = {&label, &cells, &changed, &rounds, &ctx->seed_bits, &ctx->seed_prefix,
-                    &ctx->n_seeds, &ctx->acc, &bar, &ctx->d_status};
+    void* args[] = {&label, &cells, &changed, &rounds, &ctx->seed_bits, &ctx->seed_cells, &bar, &ctx->d_status};
     cudaError_t e;
     CWTHF_LAUNCH(ctx, s, "k_seg_fallback",
                  e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_seg_fallback),
@@ -681,21 +773,20 @@ int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_
     CWTHF_LAUNCH(ctx, s, "k_seg_chase",
                  k_seg_chase<<<unsigned(ntiles), kChThreads, sizeof(int32_t) * kLocal, s>>>(
                      codes, ng, label, ctx->seed_cells, ballots, ctx->d_status));
-    // seed ranks first (the resolve pass counts cells per seed slot)
-    int rc = seeds_rank(ctx, ng, ctx->seed_cells, s);
-    if (rc) return rc;
+    // chains that left their tile, counted at their seed's cell
     int blocks = ctx->sm_count * 8;
     int* changed = ctx->jump_changed;  // see kJumpWords
     CWTHF_LAUNCH(ctx, s, "k_seg_resolve",
-                 k_seg_resolve<<<blocks, kResolveThreads, 0, s>>>(label, ng, ballots, ctx->seed_bits,
-                                                                   ctx->seed_prefix, ctx->n_seeds, ctx->acc, changed,
-                                                                   reinterpret_cast<unsigned*>(changed + kJumpRowCounter),
+                 k_seg_resolve<<<blocks, kResolveThreads, 0, s>>>(label, ng, ballots, ctx->seed_cells, changed,
+                                                                   reinterpret_cast<unsigned*>(changed + kJumpTileCounter),
                                                                    ctx->dbg_chase_limit));
     // pointer doubling and a recount for whatever the bounded walks left
     // (normally nothing: the kernel then returns at once)
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
-    return launch_fallback(ctx, label, cells, s);
-    return cuda_status(cudaGetLastError());
+    int rc = launch_fallback(ctx, label, cells, s);
+    if (rc) return rc;
+    // seed slots in cell order, each with its segment's cell count
+    return seeds_rank(ctx, ng, ctx->seed_cells, s);
 }
 
 }  // namespace cwthf
