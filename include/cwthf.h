@@ -14,9 +14,13 @@
  *
  * Conventions shared by every entry point
  *   - Grids are row-major [z][y][x] with x fastest; grid node g sits at
- *     g * (L / ng) in a periodic box of side L.  ng must be 2^a 3^b 5^c 7^d
- *     with a >= 1, 8 <= ng <= 1024, and have an FFT plan (every 2^a 3^b
- *     size does; cwthf_check_ng tells), otherwise CWTHF_E_UNSUPPORTED_SIZE.
+ *     g * (L / ng) in a periodic box of side L.  ng must be even with
+ *     8 <= ng <= 1024 (cwthf_check_ng tells), otherwise
+ *     CWTHF_E_UNSUPPORTED_SIZE.  Pass lengths (ng along y and z, ng / 2 for
+ *     the paired real samples along x) whose factors are all radices of
+ *     2, 3, 5, 7 run mixed-radix FFTs; any other length (a prime factor above
+ *     7, or no tile that fits the kernels) runs a Bluestein (chirp-z) pass
+ *     through an inner FFT of length >= 2 n - 1.
  *   - Positions are float [np][3] (x, y, z), in the units of L.  Any finite
  *     value with |x * ng / L| < 2^30 is accepted and wrapped into the box;
  *     others make the call fail with CWTHF_E_BAD_INPUT (reported by
@@ -66,7 +70,7 @@ extern "C" {
 enum {
     CWTHF_OK = 0,
     CWTHF_E_INVALID_ARG = 1,      /* NULL pointer, non-positive size or box, ... */
-    CWTHF_E_UNSUPPORTED_SIZE = 2, /* ng without an FFT plan (see above), or above the context's limits */
+    CWTHF_E_UNSUPPORTED_SIZE = 2, /* ng odd or out of range (see above), or above the context's limits */
     CWTHF_E_OVERFLOW = 3,         /* integer mass budget: m_q >= 2^31 or sum m_q >= 2^33 */
     CWTHF_E_OOM = 4,              /* device allocation failed in cwthf_create */
     CWTHF_E_CUDA = 5,             /* a CUDA runtime call failed */
@@ -246,7 +250,7 @@ CWTHF_API int cwthf_find(cwthf_ctx *ctx, const float *pos, const float *mass, do
  * identification loop.  Scales are given from the largest physical scale
  * (smallest k_w) to the smallest: w[j] (1/length) on an ng[j]^3 grid (each a
  * supported size <= the context's max_ng; the paper's Int(400 k_w + 150)
- * rounded to a supported size is the caller's choice).  For every scale all
+ * rounded to an even size is the caller's choice).  For every scale all
  * particles are deposited and the CWT computed; scale j is then decided with
  * scale j + 1's field as its comparison field (a zero field after the last):
  *   - segments of scale j's field (seeds: maxima above cwt_min);
@@ -317,7 +321,8 @@ CWTHF_API int cwthf_deposit_noalloc(const float *pos, const float *mass, double 
  *              product is the length, applied in this order
  *   n_radices  0 returns the pass to the built-in rule
  * A plan the kernels cannot run (product, tile over 64 KB, over 512 threads, no
- * TMA box for the y/z tile) is refused with CWTHF_E_INVALID_ARG.  Results
+ * TMA box for the y/z tile) is refused with CWTHF_E_INVALID_ARG, so a pass
+ * whose length has a prime factor above 7 keeps its Bluestein plan.  Results
  * change only by fp32 rounding; set plans between calls, not while work of
  * this context is being enqueued. */
 CWTHF_API int cwthf_set_fft_plan(cwthf_ctx *ctx, int ng, int which, int C, const int *radices, int n_radices);

@@ -38,11 +38,10 @@ assert MS_HALO_DTYPE.itemsize == 64
 
 
 def supported_sizes(lo: int = 8, hi: int = MAX_NG) -> list[int]:
-    """Grid sizes the library takes within [lo, hi]: 2^a 3^b 5^c 7^d with
-    a >= 1 for which it has an FFT plan."""
-    cand = {2 ** a * 3 ** b * 5 ** c * 7 ** d for a in range(1, 11) for b in range(7) for c in range(5)
-            for d in range(4)}
-    return sorted(n for n in cand if lo <= n <= hi and check_ng(n))
+    """Grid sizes the library takes within [lo, hi]: even sizes with an FFT
+    plan (radix stages, or a Bluestein pass where the length has a larger
+    prime factor)."""
+    return [n for n in range(max(lo, 2) + (max(lo, 2) % 2), hi + 1, 2) if check_ng(n)]
 
 
 def paper_scales(L: float, kw_low: float = 0.1, kw_high: float = 2.5, n: int | None = None, n_ref: int = 400,
@@ -50,8 +49,9 @@ def paper_scales(L: float, kw_low: float = 0.1, kw_high: float = 2.5, n: int | N
     """The scale list of the multi-scale loop (Fig. 1, Table 1): n values of
     k_w spaced linearly from kw_low to kw_high (n = Int((kw_high - kw_low) * 8)
     by default), w = k_w * 1000 / L, and the grid Int(n_ref * k_w + n_min) per
-    scale rounded to the nearest supported size (the smaller on a tie), at
-    most max_ng.  Returns (k_w list, w list, ng list)."""
+    scale rounded to the nearest supported size (an even size, since the real
+    transform pairs the x samples; the smaller on a tie), at most max_ng.
+    Returns (k_w list, w list, ng list)."""
     if n is None:
         n = int((kw_high - kw_low) * 8)
     kws = [kw_low + (kw_high - kw_low) * i / (n - 1) for i in range(n)] if n > 1 else [kw_low]

@@ -22,10 +22,6 @@ struct Range {
 
 int check_ng(int ng) {
     if (ng < CWTHF_MIN_NG || ng > CWTHF_MAX_NG || ng % 2) return CWTHF_E_UNSUPPORTED_SIZE;
-    int m = ng;
-    for (int f : {2, 3, 5, 7})
-        while (m % f == 0) m /= f;
-    if (m != 1) return CWTHF_E_UNSUPPORTED_SIZE;
     return fft_size_supported(ng) ? CWTHF_OK : CWTHF_E_UNSUPPORTED_SIZE;
 }
 
@@ -63,7 +59,10 @@ Sizes sizes_for(int max_ng, int64_t max_np) {
     return z;
 }
 
-size_t table_slot_floats(int max_ng) { return 3 * size_t(max_ng); }
+// One table slot: the largest twiddle table of a grid size up to max_ng (3 ng
+// floats, plus for Bluestein passes chirps, transformed chirps and inner
+// twiddles of at most 2.25 times the pass length + 64: below 19.5 ng + 512).
+size_t table_slot_floats(int max_ng) { return 20 * size_t(max_ng) + 512; }
 
 // The allocation plan: (pointer slot, bytes).  One list drives both
 // cwthf_create and cwthf_workspace_bytes.

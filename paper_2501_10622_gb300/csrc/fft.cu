@@ -38,6 +38,15 @@ struct Tables {
     int ng = 0;
     const float2* twN = nullptr;  // [ng]   exp(-2 pi i m / ng)
     const float2* twM = nullptr;  // [ng/2] exp(-2 pi i m / (ng/2))
+    // Bluestein passes (null for passes with a radix plan): chirp b_n of the
+    // pass length, the transformed chirp of the inner length (scaled by its
+    // inverse), the inner length's twiddles
+    const float2* chirp_yz = nullptr;
+    const float2* bhat_yz = nullptr;
+    const float2* tw_yz = nullptr;
+    const float2* chirp_x = nullptr;
+    const float2* bhat_x = nullptr;
+    const float2* tw_x = nullptr;
 };
 
 namespace {
@@ -183,11 +192,14 @@ struct RegDif {
 // Element l of sequence c lives at Addr(l, c).
 // ---------------------------------------------------------------------------
 struct Plan {
-    int L;       // transform length
+    int L;       // transform length (the inner length Mb of a Bluestein pass)
     int nst;     // number of stages (1..3)
     int rad[3];  // radices, applied in this order (Ns = product of the earlier ones)
     int C;       // sequences per tile
     int T;       // threads per block (multiple of 32)
+    int Lb = 0;  // Bluestein pass: the pass length (L >= 2 Lb - 1), else 0
+    const float2* chirp = nullptr;  // [Lb] b_n = exp(i pi n^2 / Lb)
+    const float2* bhat = nullptr;   // [L]  DFT_L of the wrapped chirp, divided by L
 };
 
 struct AddrPlain {  // [L][C], row-major (TMA tiles)
@@ -427,9 +439,10 @@ __device__ __forceinline__ void stage_fused_ct(float2* tile, A addr, const float
 // most three radices (R2 = 1 for two stages).
 struct DynFft {
     static constexpr int kThreads = 512, kMinBlocks = 1;
-    static constexpr bool kGlobalTables = false;
+    static constexpr bool kGlobalTables = false, kBlue = false;
     static __device__ __forceinline__ int cols(const Plan& p) { return p.C; }
     static __device__ __forceinline__ int len(const Plan& p) { return p.L; }
+    static __device__ __forceinline__ int rows(const Plan& p) { return p.L; }
     template <class A>
     static __device__ __forceinline__ void fwd(const Plan& p, float2* t, A addr, const float2* tw) {
         fft_tile(p, t, addr, tw);
@@ -473,9 +486,11 @@ struct CtFft {
     static constexpr int kThreads = C_ * (L_ / kRmin) > 32 * C_ ? C_ * (L_ / kRmin) : 32 * C_;
     static constexpr int kMinBlocks = MinBlocks;
     static constexpr bool kGlobalTables = true;  // y/z pass: tables through the cache
+    static constexpr bool kBlue = false;
     static_assert(R0 * R1 * R2 == L_, "radices multiply to the length");
     static __device__ __forceinline__ int cols(const Plan&) { return C_; }
     static __device__ __forceinline__ int len(const Plan&) { return L_; }
+    static __device__ __forceinline__ int rows(const Plan&) { return L_; }
     template <bool kCI, bool kCO, class A>
     static __device__ __forceinline__ void run(float2* t, A addr, const float2* tw) {
         if constexpr (R1 == 1) {
@@ -512,6 +527,79 @@ struct CtFft {
             stage_ct<L_, C_, R1, R2, false, false>(t, addr, tw);
             stage_ct<L_, C_, R0, R2 * R1, false, true>(t, addr, tw);
         }
+    }
+};
+
+// Bluestein (chirp-z) policy for a pass length Lb with a prime factor the
+// radix stages lack: with nk = (n^2 + k^2 - (k - n)^2) / 2,
+//   X_k = conj(b_k) sum_n (x_n conj(b_n)) b_(k-n),   b_n = exp(i pi n^2 / Lb),
+// a circular convolution of length L >= 2 Lb - 1 (the run-time plan's length,
+// which has radix stages) done as DFT_L, a multiply by the DFT of the wrapped
+// chirp, and a conjugated DFT_L.  The tile holds L rows; the pass's Lb rows
+// come in and go out through its first rows.  Tables (chirp, transformed
+// chirp, twiddles of L) are read through the cache.
+struct BlueFft {
+    static constexpr int kThreads = 512, kMinBlocks = 1;
+    static constexpr bool kGlobalTables = true, kBlue = true;
+    static __device__ __forceinline__ int cols(const Plan& p) { return p.C; }
+    static __device__ __forceinline__ int len(const Plan& p) { return p.Lb; }
+    static __device__ __forceinline__ int rows(const Plan& p) { return p.L; }
+    // DFT_Lb of the tile's first Lb rows (each conjugated on the way in and/or
+    // out when asked), in place
+    template <bool kConjIn, bool kConjOut, class A>
+    static __device__ __forceinline__ void run(const Plan& p, float2* t, A addr, const float2* tw) {
+        const int Lb = p.Lb, Mb = p.L, C = p.C;
+        // a_n = x_n conj(b_n), zero-padded to Mb rows
+        for (int i = threadIdx.x; i < Mb * C; i += blockDim.x) {
+            const int l = i / C, c = i - l * C;
+            float2 v = make_float2(0.f, 0.f);
+            if (l < Lb) {
+                v = t[addr(l, c)];
+                if (kConjIn) v.y = -v.y;
+                v = cmul(v, conjf2(p.chirp[l]));
+            }
+            t[addr(l, c)] = v;
+        }
+        __syncthreads();
+        fft_tile(p, t, addr, tw);
+        // times the transformed chirp (already divided by Mb), conjugated: the
+        // second DFT then gives the conjugate of the circular convolution
+        for (int i = threadIdx.x; i < Mb * C; i += blockDim.x) {
+            const int l = i / C, c = i - l * C;
+            t[addr(l, c)] = conjf2(cmul(t[addr(l, c)], p.bhat[l]));
+        }
+        __syncthreads();
+        fft_tile(p, t, addr, tw);
+        // X_k = conj(b_k) conv_k = conj(b_k t_k)
+        for (int i = threadIdx.x; i < Lb * C; i += blockDim.x) {
+            const int l = i / C, c = i - l * C;
+            const float2 v = cmul(t[addr(l, c)], p.chirp[l]);
+            t[addr(l, c)] = kConjOut ? v : conjf2(v);
+        }
+        __syncthreads();
+    }
+    template <class A>
+    static __device__ __forceinline__ void fwd(const Plan& p, float2* t, A addr, const float2* tw) {
+        run<false, false>(p, t, addr, tw);
+    }
+    template <class A>
+    static __device__ __forceinline__ void inv(const Plan& p, float2* t, A addr, const float2* tw) {
+        run<true, true>(p, t, addr, tw);
+    }
+    // forward, multiply by Psi^ and conjugate, forward, conjugate: the
+    // unnormalised inverse of the product
+    template <class A>
+    static __device__ __forceinline__ void wave(const Plan& p, float2* t, A addr, const float2* tw, const Wave& wv) {
+        run<false, false>(p, t, addr, tw);
+        const int Lb = p.Lb, C = p.C;
+        for (int i = threadIdx.x; i < Lb * C; i += blockDim.x) {  // i % C == threadIdx.x % C: this thread's column
+            const int l = i / C, c = i - l * C;
+            const float psi = wv.a * wv.gz[l] + wv.b * wv.hz[l];
+            const float2 x = t[addr(l, c)];
+            t[addr(l, c)] = make_float2(x.x * psi, -(x.y * psi));
+        }
+        __syncthreads();
+        run<false, true>(p, t, addr, tw);
     }
 };
 
@@ -569,7 +657,8 @@ struct YzArgs {
     Plan p;
     int ncc;         // column chunks per plane
     int boxr;        // rows per TMA box
-    int nbox;        // boxes per tile (boxr * nbox == L)
+    int nbox;        // boxes per tile (boxr * nbox == L; >= L for a Bluestein pass, whose last box may
+                     // overhang the end of the axis)
     int mode;
     int along_z;     // 1: transform along z (plane index o = y), 0: along y (o = z)
     int nplanes;     // planes (ng)
@@ -603,12 +692,13 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks)
     const float2* tw = a.tw;
     const float* gz = a.ghat;
     const float* hz = a.hhat;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tile + L * C);
+    const int RW = F::rows(p);  // tile rows (more than L for a Bluestein pass)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tile + RW * C);
     if constexpr (!F::kGlobalTables) {
-        float2* tws = tile + L * C;
+        float2* tws = tile + RW * C;
         float* gzs = reinterpret_cast<float*>(tws + L);
         float* hzs = gzs + L;
-        bar = reinterpret_cast<uint64_t*>(hzs + L);  // 8-byte aligned: 8 * (L*C + 2L) bytes in
+        bar = reinterpret_cast<uint64_t*>(hzs + L);  // 8-byte aligned: 8 * (RW*C + 2L) bytes in
         for (int i = threadIdx.x; i < L; i += blockDim.x) {
             tws[i] = a.tw[i];
             if (a.mode == kYzWavelet) {
@@ -626,7 +716,9 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks)
     if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_expect_tx(bar, uint32_t(L) * C * 8u);
+        // whole boxes (a Bluestein pass's last box may overhang the axis: the
+        // rows past it arrive as zeros and count like the others)
+        mbar_expect_tx(bar, uint32_t(a.nbox) * uint32_t(a.boxr) * C * 8u);
         for (int b = 0; b < a.nbox && !no_copy; b++) {
             const int r = b * a.boxr;
             if (a.along_z) tma_load_3d(tile + r * C, &in_map, bar, 2 * cc * C, o, r);
@@ -676,7 +768,7 @@ struct XArgs {
     Plan p;          // complex FFT of length M = ng / 2 over C rows
     int ng, M, P;
     int64_t rows;    // ng * ng
-    const float2* twM;  // [M]   exp(-2 pi i m / M)
+    const float2* twM;  // [M]   exp(-2 pi i m / M)  (Bluestein: the inner length's twiddles)
     const float2* twN;  // [ng]  exp(-2 pi i k / ng)
 };
 
@@ -687,10 +779,13 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks) k_fft_x_fwd(XArgs 
     const Plan& p = a.p;
     const int M = F::len(p), C = F::cols(p);
     float2* tile = reinterpret_cast<float2*>(smem_raw);
-    float2* tw = tile + M * C;
-    double* rowdc = reinterpret_cast<double*>(tw + M);
+    float2* tws = tile + F::rows(p) * C;
+    double* rowdc = reinterpret_cast<double*>(tws + M);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = a.twM[i];
+    const float2* tw = tws;
+    if constexpr (F::kBlue) tw = a.twM;  // the inner length's twiddles, through the cache
+    else
+        for (int i = threadIdx.x; i < M; i += blockDim.x) tws[i] = a.twM[i];
     AddrSwz addr{C};
     // load, exact row sum, remove the row's integer mean exactly, round to fp32.
     // Dropping the mean's fractional part only shifts the row's DC bin, which is
@@ -763,9 +858,12 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks) k_fft_x_inv(XArgs 
     const Plan& p = a.p;
     const int M = F::len(p), C = F::cols(p);
     float2* tile = reinterpret_cast<float2*>(smem_raw);
-    float2* tw = tile + M * C;
+    float2* tws = tile + F::rows(p) * C;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int i = threadIdx.x; i < M; i += blockDim.x) tw[i] = a.twM[i];
+    const float2* tw = tws;
+    if constexpr (F::kBlue) tw = a.twM;
+    else
+        for (int i = threadIdx.x; i < M; i += blockDim.x) tws[i] = a.twM[i];
     AddrSwz addr{C};
     // c2r pre-processing: Z'[k] = (X[k] + X*[M-k]) + i W_N^-k (X[k] - X*[M-k]); stored conjugated.
     // All of a row's loads are issued before any is used (memory parallelism).
@@ -869,6 +967,23 @@ bool make_plan(int L, Plan& p) {
     return best > 0;
 }
 
+// A pass of length L runs its radix plan if one fits the kernel (fit picks
+// the tile width); otherwise it runs as a Bluestein pass whose inner length is
+// the smallest Mb >= 2 L - 1 (and at most 2.25 L + 64) with a radix plan that fits.
+template <class Fit>
+bool pass_plan_for(int L, Plan& p, Fit&& fit) {
+    p.Lb = 0;
+    if (make_plan(L, p) && fit(p)) return true;
+    for (int Mb = 2 * L - 1; Mb <= 2 * L + L / 4 + 64; Mb++) {
+        p.Lb = 0;
+        if (!make_plan(Mb, p)) continue;
+        p.Lb = L;
+        if (fit(p)) return true;
+    }
+    p.Lb = 0;
+    return false;
+}
+
 int plan_threads(const Plan& p) {
     int rmin = 64;
     for (int s = 0; s < p.nst; s++) rmin = std::min(rmin, p.rad[s]);
@@ -877,37 +992,45 @@ int plan_threads(const Plan& p) {
 }
 
 // Rows per TMA box for a y/z tile of C columns: the largest divisor of L (at
-// most 256) whose box spans a multiple of 128 bytes, or -1.
-int pick_boxr(int L, int C) {
+// most 256) whose box spans a multiple of 128 bytes; else, for a tile of
+// `rows` >= L rows (a Bluestein pass), the largest such box whose whole boxes
+// fit the tile, the last one overhanging the end of the axis (its loads read
+// zeros there and its stores are clipped); else -1.
+int pick_boxr(int L, int C, int rows = 0) {
     for (int b = std::min(L, 256); b >= 1; b--)
         if (L % b == 0 && (size_t(b) * C * 8) % 128 == 0) return b;
+    for (int b = std::min(L, 256); b >= 1 && rows >= L; b--)
+        if ((size_t(b) * C * 8) % 128 == 0 && div_up(L, b) * b <= rows) return b;
     return -1;
 }
+int plan_boxr(int L, const Plan& p) { return pick_boxr(L, p.C, p.Lb ? p.L : 0); }
 
 // Columns per y/z tile: <= 64 KB of complex data and a valid TMA box,
 // preferring <= 256 threads (two CTAs per SM at 128 registers) over <= 512.
 bool yz_plan(int L, Plan& p) {
-    if (!make_plan(L, p)) return false;
-    for (int tmax : {256, 512})
-        for (int C : {16, 8, 4, 2}) {
-            p.C = C;
-            p.T = plan_threads(p);
-            if (size_t(L) * C * 8 <= 65536 && p.T <= tmax && pick_boxr(L, C) > 0) return true;
-        }
-    return false;
+    return pass_plan_for(L, p, [L](Plan& q) {
+        for (int tmax : {256, 512})
+            for (int C : {16, 8, 4, 2}) {
+                q.C = C;
+                q.T = plan_threads(q);
+                if (size_t(q.L) * C * 8 <= 65536 && q.T <= tmax && plan_boxr(L, q) > 0) return true;
+            }
+        return false;
+    });
 }
 
 // Rows per x tile: <= 64 KB of complex data, one warp per row for the loads,
 // preferring <= 256 threads (two CTAs per SM) over <= 512.
 bool x_plan(int M, Plan& p) {
-    if (!make_plan(M, p)) return false;
-    for (int tmax : {256, 512})
-        for (int C : {16, 8, 4, 2}) {
-            p.C = C;
-            p.T = std::max(plan_threads(p), 32 * std::min(C, 16));
-            if (size_t(M) * C * 8 <= 65536 && p.T <= tmax) return true;
-        }
-    return false;
+    return pass_plan_for(M, p, [](Plan& q) {
+        for (int tmax : {256, 512})
+            for (int C : {16, 8, 4, 2}) {
+                q.C = C;
+                q.T = std::max(plan_threads(q), 32 * std::min(C, 16));
+                if (size_t(q.L) * C * 8 <= 65536 && q.T <= tmax) return true;
+            }
+        return false;
+    });
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -956,6 +1079,77 @@ void host_twiddles(int n, std::vector<float2>& out) {
     }
 }
 
+// The twiddle table of a grid size: twN [ng] and twM [ng/2], then for each
+// Bluestein pass its chirp, transformed chirp and inner twiddles (float
+// offsets; 0 = absent).
+struct TwLayout {
+    size_t n = 0;
+    size_t chirp_yz = 0, bhat_yz = 0, tw_yz = 0, chirp_x = 0, bhat_x = 0, tw_x = 0;
+    int lb_yz = 0, mb_yz = 0, lb_x = 0, mb_x = 0;
+};
+TwLayout tw_layout(int ng) {
+    TwLayout t;
+    size_t o = 3 * size_t(ng);
+    Plan p;
+    if (yz_plan(ng, p) && p.Lb) {
+        t.lb_yz = p.Lb;
+        t.mb_yz = p.L;
+        t.chirp_yz = o;
+        o += 2 * size_t(p.Lb);
+        t.bhat_yz = o;
+        o += 2 * size_t(p.L);
+        t.tw_yz = o;
+        o += 2 * size_t(p.L);
+    }
+    if (x_plan(ng / 2, p) && p.Lb) {
+        t.lb_x = p.Lb;
+        t.mb_x = p.L;
+        t.chirp_x = o;
+        o += 2 * size_t(p.Lb);
+        t.bhat_x = o;
+        o += 2 * size_t(p.L);
+        t.tw_x = o;
+        o += 2 * size_t(p.L);
+    }
+    t.n = o;
+    return t;
+}
+
+// Bluestein tables in fp64, stored as fp32: the chirp b_n = exp(i pi n^2 / Lb),
+// n < Lb (n^2 reduced mod 2 Lb exactly); the DFT of length Mb of the wrapped
+// chirp (b_n at n and at Mb - n, zero between), divided by Mb; the twiddles of Mb.
+void host_bluestein(int Lb, int Mb, float* chirp, float* bhat, float* tw) {
+    std::vector<double> br(Lb), bi(Lb);
+    for (int n = 0; n < Lb; n++) {
+        const long long q = (static_cast<long long>(n) * n) % (2LL * Lb);
+        const double ang = kPi * double(q) / double(Lb);
+        br[n] = std::cos(ang);
+        bi[n] = std::sin(ang);
+        chirp[2 * n] = float(br[n]);
+        chirp[2 * n + 1] = float(bi[n]);
+    }
+    std::vector<double> cm(Mb), sm(Mb);
+    for (int m = 0; m < Mb; m++) {
+        cm[m] = std::cos(2.0 * kPi * double(m) / double(Mb));
+        sm[m] = std::sin(2.0 * kPi * double(m) / double(Mb));
+    }
+    for (int k = 0; k < Mb; k++) {
+        double sr = 0.0, si = 0.0;
+        auto add = [&](int n, int j) {  // B_n = b_j, times exp(-2 pi i n k / Mb)
+            const int e = int((static_cast<long long>(n) * k) % Mb);
+            sr += br[j] * cm[e] + bi[j] * sm[e];
+            si += bi[j] * cm[e] - br[j] * sm[e];
+        };
+        for (int n = 0; n < Lb; n++) add(n, n);
+        for (int n = Mb - Lb + 1; n < Mb; n++) add(n, Mb - n);
+        bhat[2 * k] = float(sr / Mb);
+        bhat[2 * k + 1] = float(si / Mb);
+    }
+    std::vector<float2> w;
+    host_twiddles(Mb, w);
+    std::memcpy(tw, w.data(), w.size() * 8);
+}
+
 // G^(k) and H^(k), k < ng: 1D DFTs (real, even sequences) of the sampled
 // Gaussian factor and of its w^2 u^2 multiple, in fp64, stored as fp32
 // (out[k] = G^(k), out[ng + k] = H^(k)).
@@ -1000,7 +1194,9 @@ int table_lookup(cwthf_ctx* ctx, int kind, int ng, double L, double w, cudaStrea
     if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return CWTHF_E_CUDA;
     const bool capturing = cap != cudaStreamCaptureStatusNone;
     const size_t stride = ctx->table_slot_floats;
-    const size_t n = (kind == kTableTwiddles ? 3 : 2) * size_t(ng);
+    const TwLayout lay = kind == kTableTwiddles ? tw_layout(ng) : TwLayout();
+    const size_t n = kind == kTableTwiddles ? lay.n : 2 * size_t(ng);
+    if (n > stride) return CWTHF_E_UNSUPPORTED_SIZE;
     int pick = -1;
     for (int i = 0; i < kTableSlots && pick < 0; i++) {
         const TableSlot& t = ctx->table_slot[i];
@@ -1031,6 +1227,9 @@ int table_lookup(cwthf_ctx* ctx, int kind, int ng, double L, double w, cudaStrea
             host_twiddles(ng / 2, b);
             std::memcpy(host, a.data(), a.size() * 8);
             std::memcpy(host + 2 * ng, b.data(), b.size() * 8);
+            if (lay.lb_yz)
+                host_bluestein(lay.lb_yz, lay.mb_yz, host + lay.chirp_yz, host + lay.bhat_yz, host + lay.tw_yz);
+            if (lay.lb_x) host_bluestein(lay.lb_x, lay.mb_x, host + lay.chirp_x, host + lay.bhat_x, host + lay.tw_x);
         } else {
             host_wavelet_tables(ng, L, w, host);
         }
@@ -1063,6 +1262,14 @@ int get_tables(cwthf_ctx* ctx, int ng, cudaStream_t s, Tables& t) {
     t.ng = ng;
     t.twN = reinterpret_cast<const float2*>(p);
     t.twM = reinterpret_cast<const float2*>(p + 2 * ng);
+    const TwLayout lay = tw_layout(ng);
+    auto at = [&](size_t o) { return o ? reinterpret_cast<const float2*>(p + o) : nullptr; };
+    t.chirp_yz = at(lay.chirp_yz);
+    t.bhat_yz = at(lay.bhat_yz);
+    t.tw_yz = at(lay.tw_yz);
+    t.chirp_x = at(lay.chirp_x);
+    t.bhat_x = at(lay.bhat_x);
+    t.tw_x = at(lay.tw_x);
     return CWTHF_OK;
 }
 
@@ -1083,6 +1290,7 @@ using X256 = CtFft<256, 8, 16, 16, 1, 3>;
 using YzKernel = void (*)(const CUtensorMap, const CUtensorMap, YzArgs);
 YzKernel pick_yz(const Plan& p, bool& global_tables) {
     global_tables = true;
+    if (p.Lb) return k_fft_yz<BlueFft>;
     if (plan_is<Yz1024>(p, 1024, 8, 32, 32, 1)) return k_fft_yz<Yz1024>;
     if (plan_is<Yz512>(p, 512, 8, 16, 32, 1)) return k_fft_yz<Yz512>;
     global_tables = false;
@@ -1091,11 +1299,13 @@ YzKernel pick_yz(const Plan& p, bool& global_tables) {
 using XFwdKernel = void (*)(XArgs, const int64_t*, float2*);
 using XInvKernel = void (*)(XArgs, const float2*, float*);
 XFwdKernel pick_x_fwd(const Plan& p) {
+    if (p.Lb) return k_fft_x_fwd<BlueFft>;
     if (plan_is<X512>(p, 512, 8, 16, 32, 1)) return k_fft_x_fwd<X512>;
     if (plan_is<X256>(p, 256, 8, 16, 16, 1)) return k_fft_x_fwd<X256>;
     return k_fft_x_fwd<DynFft>;
 }
 XInvKernel pick_x_inv(const Plan& p) {
+    if (p.Lb) return k_fft_x_inv<BlueFft>;
     if (plan_is<X512>(p, 512, 8, 16, 32, 1)) return k_fft_x_inv<X512>;
     if (plan_is<X256>(p, 256, 8, 16, 16, 1)) return k_fft_x_inv<X256>;
     return k_fft_x_inv<DynFft>;
@@ -1136,8 +1346,11 @@ int launch_yz(cwthf_ctx* ctx, float2* src, float2* dst, int ng, bool along_z, in
               const float* wtab, double w, double mass_unit, cudaStream_t s) {
     Plan p;
     if (!pass_plan(ctx, ng, 0, p)) return CWTHF_E_UNSUPPORTED_SIZE;
-    int boxr = pick_boxr(ng, p.C);
+    int boxr = plan_boxr(ng, p);
     if (boxr < 0) return CWTHF_E_UNSUPPORTED_SIZE;
+    if (p.Lb && !(t->chirp_yz && t->bhat_yz && t->tw_yz)) return CWTHF_E_UNSUPPORTED_SIZE;
+    p.chirp = t->chirp_yz;
+    p.bhat = t->bhat_yz;
     CUtensorMap in_map, out_map;
     int rc = make_spec_map(&in_map, src, ng, along_z, p.C, boxr);
     if (!rc) rc = make_spec_map(&out_map, dst, ng, along_z, p.C, boxr);
@@ -1147,11 +1360,11 @@ int launch_yz(cwthf_ctx* ctx, float2* src, float2* dst, int ng, bool along_z, in
     a.M = ng / 2;
     a.ncc = div_up(a.M + 1, p.C);
     a.boxr = boxr;
-    a.nbox = ng / boxr;
+    a.nbox = div_up(ng, boxr);
     a.mode = mode;
     a.along_z = along_z ? 1 : 0;
     a.nplanes = ng;
-    a.tw = t->twN;
+    a.tw = p.Lb ? t->tw_yz : t->twN;
     a.ghat = wtab;
     a.hhat = wtab ? wtab + ng : nullptr;
     // w^1.5 (Eq. 4), the 1/ng^3 of the inverse DFT, and the mass of one spectrum
@@ -1176,12 +1389,15 @@ int launch_yz(cwthf_ctx* ctx, float2* src, float2* dst, int ng, bool along_z, in
 int x_args(cwthf_ctx* ctx, int ng, const Tables* t, XArgs& a) {
     Plan p;
     if (!pass_plan(ctx, ng, 1, p)) return CWTHF_E_UNSUPPORTED_SIZE;
+    if (p.Lb && !(t->chirp_x && t->bhat_x && t->tw_x)) return CWTHF_E_UNSUPPORTED_SIZE;
+    p.chirp = t->chirp_x;
+    p.bhat = t->bhat_x;
     a.p = p;
     a.ng = ng;
     a.M = ng / 2;
     a.P = spec_pitch(ng);
     a.rows = int64_t(ng) * ng;
-    a.twM = t->twM;
+    a.twM = p.Lb ? t->tw_x : t->twM;
     a.twN = t->twN;
     return CWTHF_OK;
 }
@@ -1250,7 +1466,7 @@ int set_fft_plan(cwthf_ctx* ctx, int ng, int which, int C, const int* rad, int n
 // decides the box, the x passes have a plan of their own.
 bool fft_size_supported(int ng) {
     Plan yz, x;
-    return (ng % 2 == 0) && ng / 2 <= 512 && yz_plan(ng, yz) && pick_boxr(ng, yz.C) > 0 && x_plan(ng / 2, x);
+    return (ng % 2 == 0) && ng / 2 <= 512 && yz_plan(ng, yz) && plan_boxr(ng, yz) > 0 && x_plan(ng / 2, x);
 }
 
 void free_tables(cwthf_ctx* ctx) {

@@ -23,11 +23,14 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_supported_grid_sizes():
-    smooth = sorted({2 ** a * 3 ** b for a in range(1, 11) for b in range(0, 7) if 8 <= 2 ** a * 3 ** b <= 1024})
-    for n in smooth:
+    # every even size from 8 to 1024: radix stages, or Bluestein passes where
+    # the length has a prime factor above 7; odd sizes and sizes out of range
+    # are refused
+    for n in range(8, 1025, 2):
         assert pkg.check_ng(n), n
-    for n in (4, 6, 7, 22, 26, 27, 81, 1152, 2048, 190, 1150):
+    for n in (4, 6, 7, 9, 27, 81, 191, 1023, 1026, 1152, 2048, 1150):
         assert not pkg.check_ng(n), n
+    smooth = sorted({2 ** a * 3 ** b for a in range(1, 11) for b in range(0, 7) if 8 <= 2 ** a * 3 ** b <= 1024})
     assert synth.smooth_ng(190) in smooth and synth.smooth_ng(1150) == 1024
 
 
@@ -38,7 +41,7 @@ def test_workspace_bytes_monotone_and_errors():
     d = pkg.workspace_bytes(128, 1 << 20, 3)
     assert 0 < a < b < c < d
     with pytest.raises(pkg.CwthfError):
-        pkg.workspace_bytes(190, 10)
+        pkg.workspace_bytes(191, 10)
     with pytest.raises(pkg.CwthfError):
         pkg.workspace_bytes(64, -1)
 
@@ -57,18 +60,24 @@ def test_create_reports_instead_of_crashing_without_gpu():
         pytest.skip("a GPU is present")
     h = ctypes.c_void_p()
     assert pkg.lib().cwthf_create(0, 64, 100, 1, ctypes.byref(h)) == 5  # CWTHF_E_CUDA
-    assert pkg.lib().cwthf_create(0, 190, 100, 1, ctypes.byref(h)) == 2
+    assert pkg.lib().cwthf_create(0, 191, 100, 1, ctypes.byref(h)) == 2
     assert pkg.lib().cwthf_create(0, 64, -1, 1, ctypes.byref(h)) == 1
     assert pkg.lib().cwthf_sync(None, None) == 1
 
 
-def test_radix_five_and_seven_sizes():
-    # radix-5 and radix-7 stages: the paper's grid rule Int(400 k_w + 150) lands
-    # on sizes such as 350 = 2 5^2 7 or 750 = 2 3 5^3; sizes with a prime factor
-    # above 7 (190 = 2 5 19, 1150 = 2 5^2 23) need Bluestein and stay refused
-    for n in (10, 14, 20, 28, 30, 40, 50, 70, 100, 140, 250, 270, 350, 750, 1000):
+def test_radix_five_seven_and_bluestein_sizes():
+    # radix-5 and radix-7 stages cover sizes such as 350 = 2 5^2 7 or
+    # 750 = 2 3 5^3; sizes with a larger prime factor (190 = 2 5 19,
+    # 1022 = 2 7 73) run Bluestein passes, so the paper's grid rule
+    # Int(400 k_w + 150) is taken to the nearest even size
+    for n in (10, 14, 20, 28, 30, 40, 50, 70, 100, 140, 250, 270, 350, 750, 1000, 22, 26, 190, 230, 1022):
         assert pkg.check_ng(n), n
-    for n in (22, 26, 190, 230, 1150, 9, 15):
+    for n in (1150, 9, 15, 189):
         assert not pkg.check_ng(n), n
     sizes = pkg.supported_sizes(8, 1024)
-    assert 350 in sizes and 190 not in sizes and all(s % 2 == 0 for s in sizes)
+    assert sizes == list(range(8, 1025, 2))
+    kws, ws, ngs = pkg.paper_scales(50.0, n=20)
+    want = [int(400 * k + 150) for k in kws]
+    # within one cell of the rule up to the largest grid, capped there above it
+    assert all((abs(g - v) <= 1 if v <= 1024 else g == 1024) and g % 2 == 0 for g, v in zip(ngs, want)), (ngs, want)
+    assert ngs[0] == 190

@@ -5,7 +5,7 @@ import torch
 
 import oracle
 from paper_2501_10622_gb300 import synth
-from tests.gpu_util import CWT_MAX_REL, CWT_REL_L2, cwt_errors, dev, random_box
+from tests.gpu_util import CWT_MAX_REL, CWT_REL_L2, cwt_errors, dev, random_box, record
 
 pytestmark = pytest.mark.gpu
 
@@ -31,6 +31,51 @@ def test_sizes(gctx, ng):
         gctx.check()
         rel, mx = cwt_errors(c.cpu().numpy(), ref)
         assert rel <= CWT_REL_L2 and mx <= CWT_MAX_REL, (ng, w, rel, mx)
+
+
+# Bluestein passes (Sec. 2.1's grid rule gives sizes with prime factors above
+# 7): y/z length with a large prime (22 = 2 11, 190 = 2 5 19), x length ng/2
+# prime (94: 47, 38: 19), both, and lengths whose TMA box overhangs the axis
+@pytest.mark.parametrize("ng", [22, 26, 34, 38, 46, 58, 62, 74, 94, 110, 146, 190])
+def test_bluestein_sizes(gctx, ng):
+    L = 0.78125 * ng
+    pos = synth.clumped_box(8 * ng ** 3 // 10, L, max(2, ng // 4), seed=ng).numpy()
+    grid, _ = oracle.cic(pos, L, ng)
+    for w in (2.0, 3.3):
+        ref = oracle.cwt(grid, L, w)
+        c = gctx.transform(dev(grid), L, w)
+        gctx.check()
+        rel, mx = cwt_errors(c.cpu().numpy(), ref)
+        record({"config": f"Bluestein CWT, clumped {ng}^3, w={w}", "rel_l2": rel, "max_rel": mx})
+        assert rel <= CWT_REL_L2 and mx <= CWT_MAX_REL, (ng, w, rel, mx)
+
+
+@pytest.mark.parametrize("ng", [490, 1022])
+def test_bluestein_large_spot_values(ng):
+    # 490 = 2 5 7^2 has radix stages but no tile width that fits a TMA box and
+    # 512 threads, so its y/z passes run Bluestein; 1022 = 2 7 73 runs Bluestein
+    # on every axis (inner lengths 2048 and 1024)
+    import paper_2501_10622_gb300 as pkg
+    L, w = 0.5 * ng, 2.0
+    ctx = pkg.Context(0, max_ng=ng, max_np=1 << 22, max_scales=1)
+    try:
+        pos = synth.clumped_box(1 << 22, L, 400, seed=ng, device="cuda")
+        g = ctx.deposit(pos, L, ng)
+        c = ctx.transform(g, L, w)
+        ctx.check()
+        grid = g.cpu().numpy()
+        # random nodes and the field's twelve largest values (the clumps)
+        top = torch.topk(c.reshape(-1), 12).indices.cpu().numpy()
+        nodes = np.concatenate([np.random.default_rng(ng).integers(0, ng ** 3, 12), top])
+        ref = oracle.cwt_at(grid, L, w, nodes)
+        got = c.reshape(-1)[torch.as_tensor(nodes, device="cuda")].double().cpu().numpy()
+        scale = float(c.abs().max())
+        err = float(np.max(np.abs(got - ref))) / scale
+        record({"config": f"Bluestein CWT spot values, clumped 2^22 on {ng}^3, w={w}", "max_rel_spot": err})
+        assert err <= CWT_MAX_REL, err
+    finally:
+        ctx.close()
+        torch.cuda.empty_cache()
 
 
 def test_point_mass_kernel_and_variable_unit(gctx):
