@@ -70,6 +70,7 @@ def lib() -> ctypes.CDLL:
         L.orc_corrected_peak.restype = f
         L.orc_cross_scale.argtypes = [P, i32, i64, P, i32]
         L.orc_multiscale.argtypes = [P, P, d, i64, d, i32, P, P, f, d, i64, P, i64, P, P, P, P, P, P, P, P]
+        L.orc_unbind.argtypes = [P, P, P, d, i64, d, d, P, i64, i32, P, P, P, P]
         _lib = L
     return _lib
 
@@ -302,3 +303,30 @@ def find_multiscale(pos, L: float, ws, ngs, mass=None, mass_unit: float = 1.0, c
         fields.append(cwt(grid, L, w, mass_unit).astype(np.float32))
     hid, cat = multiscale_on_fields(pos, L, fields, mass, mass_unit, cwt_min, dens_th, particle_th)
     return dict(fields=fields, halo_id=hid, cat=cat)
+
+
+# G in (Mpc/h) (km/s)^2 / (Msun/h): positions in Mpc/h, velocities in km/s,
+# masses in Msun/h (the h cancels in G M / r).
+G_MPC_KMS_MSUN = 4.30091727e-9
+
+
+def unbind(pos, vel, group, L: float, G: float = G_MPC_KMS_MSUN, mass=None, mass_unit: float = 1.0,
+           n_groups: int | None = None, max_iter: int = 100):
+    """Sec. 2.3: the self-boundness check of every group (group[i] = index or
+    -1).  Returns (group after the check, members kept per group, rounds per
+    group, smallest relative distance of any decision from its threshold)."""
+    pos, mass = _pos(pos), _mass(mass)
+    vel = _pos(vel)
+    group = np.ascontiguousarray(group, dtype=np.int32)
+    np_ = pos.shape[0]
+    assert vel.shape == pos.shape and group.shape == (np_,)
+    if n_groups is None:
+        n_groups = int(group.max()) + 1 if np_ else 0
+    out = np.empty(np_, dtype=np.int32)
+    n_out = np.zeros(max(n_groups, 1), dtype=np.int64)
+    it_out = np.zeros(max(n_groups, 1), dtype=np.int32)
+    margin = ctypes.c_double()
+    _check(lib().orc_unbind(_ptr(pos), _ptr(vel), _ptr(mass), float(mass_unit), np_, float(L), float(G), _ptr(group),
+                            int(n_groups), int(max_iter), _ptr(out), _ptr(n_out), _ptr(it_out), ctypes.byref(margin)),
+           "unbind")
+    return out, n_out[:n_groups], it_out[:n_groups], margin.value

@@ -16,6 +16,8 @@
  *   Sec. 2.1, Eq. 1: cloud-in-cell (CIC) deposit onto grid nodes.
  *   Sec. 2.1, Eq. 2-3: grid CWT = sum over nodes of m_g Psi(w, x - x_g).
  *   Sec. 2.1, Eq. 4: the isotropic 3D Mexican-hat wavelet.
+ *   Sec. 2.3: the self-boundness check (orc_unbind: spherical shell
+ *       potential, escape speed, iterative exclusion, the 40 % rule).
  *   Sec. 2.3: halo = region around a positive CWT peak, extended down to
  *       the CWT valley; halo centre = centre of mass.
  *   Sec. 2.4 and Table 1: density threshold dens_th (4 x mean density,
@@ -770,5 +772,135 @@ int orc_multiscale(const float *pos, const float *mass, double mass_unit, int64_
         *n_halo = kept;
         if (kept > cap) rc = ORC_E_CAPACITY;
     }
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.3: the self-boundness check (step 9 of the Sec. 2 step list).      */
+/* ------------------------------------------------------------------------ */
+
+/* Every group g (particles with group[i] == g, 0 <= g < n_groups) is checked
+ * on its own, following Sec. 2.3 in order:
+ *   1. the halo centre is the centre of mass of the group's current members
+ *      (mass-weighted mean of the minimum-image offsets from the group's
+ *      first member in particle order);
+ *   2. assuming spherical symmetry, the potential at member i is that of the
+ *      spherical shells of the other members about the centre (shell
+ *      theorem): Phi_i = -G sum_{j != i} m_j / max(r_i, r_j), so the local
+ *      escape speed is v_esc^2 = -2 Phi_i;
+ *   3. members whose speed relative to the group's mass-weighted mean velocity
+ *      exceeds v_esc are excluded (all at once), and the centre is recomputed
+ *      from the remaining members;
+ *   4. steps 1-3 repeat until no member is excluded (at most max_iter rounds);
+ *   5. if more than 40 % of the group's particles were excluded (5 excluded >
+ *      2 initial), the whole group is discarded.
+ * Masses are m_i = m_q * mass_unit with the integer mass quanta of the
+ * deposit (1 when mass is NULL).  A zero-mass member adds nothing to any
+ * potential; two members both at the centre (max(r_i, r_j) = 0, m_j > 0) make
+ * Phi_i infinite, so they stay.  With no mass left the centre is the first
+ * member and the mean velocity zero.
+ * Outputs: out_group[i] = g for members that stay in a group that is kept,
+ * else -1; out_n[g] = members kept (0 if discarded); out_iter[g] = rounds run;
+ * *out_margin = the smallest |v_rel^2 - v_esc^2| / v_esc^2 over every
+ * decision taken (how close any decision came to the other side). */
+int orc_unbind(const float *pos, const float *vel, const float *mass, double mass_unit, int64_t np, double L,
+               double G, const int32_t *group, int64_t n_groups, int max_iter, int32_t *out_group, int64_t *out_n,
+               int32_t *out_iter, double *out_margin) {
+    if (np < 0 || n_groups < 0 || !(L > 0.0) || !(G >= 0.0) || max_iter < 1 || !(mass_unit > 0.0))
+        return ORC_E_ARG;
+    double margin = INFINITY;
+    int64_t *mem = malloc(((size_t)np + 1) * sizeof(int64_t));
+    double *m = malloc(((size_t)np + 1) * sizeof(double));
+    double *r = malloc(((size_t)np + 1) * sizeof(double));
+    char *keep = malloc((size_t)np + 1);
+    if (!mem || !m || !r || !keep) {
+        free(mem); free(m); free(r); free(keep);
+        return ORC_E_NOMEM;
+    }
+    int rc = ORC_OK;
+    for (int64_t i = 0; i < np && rc == ORC_OK; i++) {
+        out_group[i] = -1;
+        int64_t mq;
+        if ((rc = mass_quantum(mass, mass_unit, i, &mq)) != ORC_OK) break;
+        m[i] = (double)mq * mass_unit;
+    }
+    for (int64_t g = 0; g < n_groups && rc == ORC_OK; g++) {
+        /* the group's members in particle order */
+        int64_t n = 0;
+        for (int64_t i = 0; i < np; i++)
+            if (group[i] == g) mem[n++] = i;
+        const int64_t n0 = n;
+        out_n[g] = 0;
+        out_iter[g] = 0;
+        if (n0 == 0) continue;
+        const float *a = pos + 3 * mem[0];
+        int it = 0;
+        while (it < max_iter) {
+            it++;
+            /* 1. centre of mass and mean velocity of the current members */
+            double M = 0.0, sd[3] = {0.0, 0.0, 0.0}, sv[3] = {0.0, 0.0, 0.0};
+            for (int64_t k = 0; k < n; k++) {
+                const int64_t i = mem[k];
+                M += m[i];
+                for (int c = 0; c < 3; c++) {
+                    double d = (double)pos[3 * i + c] - (double)a[c];
+                    d -= L * floor(d / L + 0.5);
+                    sd[c] += m[i] * d;
+                    sv[c] += m[i] * (double)vel[3 * i + c];
+                }
+            }
+            double cen[3] = {0.0, 0.0, 0.0}, vb[3] = {0.0, 0.0, 0.0};
+            if (M > 0.0)
+                for (int c = 0; c < 3; c++) {
+                    cen[c] = sd[c] / M;
+                    vb[c] = sv[c] / M;
+                }
+            for (int64_t k = 0; k < n; k++) {
+                const int64_t i = mem[k];
+                double s2 = 0.0;
+                for (int c = 0; c < 3; c++) {
+                    double d = (double)pos[3 * i + c] - (double)a[c];
+                    d -= L * floor(d / L + 0.5);
+                    s2 += (d - cen[c]) * (d - cen[c]);
+                }
+                r[i] = sqrt(s2);
+            }
+            /* 2-3. escape speeds from the shell potential; exclusions */
+            int64_t kept = 0;
+            for (int64_t k = 0; k < n; k++) {
+                const int64_t i = mem[k];
+                double S = 0.0;
+                for (int64_t l = 0; l < n; l++) {
+                    const int64_t j = mem[l];
+                    if (j == i || !(m[j] > 0.0)) continue;
+                    S += m[j] / fmax(r[i], r[j]);
+                }
+                const double vesc2 = 2.0 * G * S;
+                double v2 = 0.0;
+                for (int c = 0; c < 3; c++) {
+                    const double dv = (double)vel[3 * i + c] - vb[c];
+                    v2 += dv * dv;
+                }
+                keep[i] = !(v2 > vesc2);
+                if (vesc2 > 0.0 && isfinite(vesc2)) {
+                    const double q = fabs(v2 - vesc2) / vesc2;
+                    if (q < margin) margin = q;
+                }
+                kept += keep[i];
+            }
+            if (kept == n) break;
+            int64_t w = 0;
+            for (int64_t k = 0; k < n; k++)
+                if (keep[mem[k]]) mem[w++] = mem[k];
+            n = w;
+        }
+        out_iter[g] = it;
+        /* 5. more than 40 % excluded: the group is discarded */
+        if (5 * (n0 - n) > 2 * n0) continue;
+        out_n[g] = n;
+        for (int64_t k = 0; k < n; k++) out_group[mem[k]] = (int32_t)g;
+    }
+    *out_margin = margin;
+    free(mem); free(m); free(r); free(keep);
     return rc;
 }

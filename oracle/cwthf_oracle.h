@@ -42,4 +42,7 @@ int orc_multiscale(const float *pos, const float *mass, double mass_unit, int64_
                    int32_t *halo_id, int64_t cap, int32_t *scale_out, int64_t *seed_out, int64_t *npart_out,
                    int64_t *ncell_out, double *mass_out, double *centre_out, float *peak_out, int64_t *n_halo);
 
+int orc_unbind(const float *pos, const float *vel, const float *mass, double mass_unit, int64_t np, double L,
+               double G, const int32_t *group, int64_t n_groups, int max_iter, int32_t *out_group, int64_t *out_n,
+               int32_t *out_iter, double *out_margin);
 #endif
