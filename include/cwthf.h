@@ -275,6 +275,36 @@ CWTHF_API int cwthf_find_multiscale(cwthf_ctx *ctx, const float *pos, const floa
                                     float cwt_min, double dens_th, int64_t particle_th, int32_t *halo_id,
                                     cwthf_ms_halo *cat, int64_t cat_cap, int64_t *n_halo, void *stream);
 
+/* Sec. 2.3 (step 9 of the Sec. 2 step list): the self-boundness check of
+ * every group, each on its own:
+ *   1. centre = the centre of mass of the group's current members (mass-weighted
+ *      minimum-image offsets from the group's first member in particle order);
+ *   2. spherical symmetry: the potential at member i is that of the other
+ *      members' shells about the centre, Phi_i = -G sum_{j != i} m_j / max(r_i,
+ *      r_j) (shell theorem), the local escape speed sqrt(-2 Phi_i);
+ *   3. members whose speed relative to the group's mass-weighted mean velocity
+ *      exceeds it are excluded, all at once, and the centre is recomputed;
+ *   4. repeated until nothing is excluded, at most max_iter rounds;
+ *   5. a group that lost more than 40 % of its particles is discarded.
+ * Masses are the deposit's integer quanta times mass_unit (mass_unit each when
+ * mass is NULL).  A group whose extent reaches half the box is not supported
+ * (offsets are minimum images).
+ *   pos, vel    device, float [np][3]: positions (units of L), velocities
+ *   mass        device, float [np] or NULL
+ *   G           the gravitational constant in the caller's units (e.g.
+ *               4.30091727e-9 for Mpc/h, km/s and Msun/h)
+ *   group       device, int32 [np]: the particle's group, or -1 (ignored)
+ *   n_groups    groups 0 .. n_groups-1 (at most max_ng^3 / 8 + 8)
+ *   group_out   device, int32 [np]: the group after the check, or -1
+ *   n_kept      device, int64 [n_groups]: members kept (0 when discarded)
+ *   iters       device, int32 [n_groups]: rounds run
+ * Each group's sums run in a fixed order, so results repeat exactly; a member
+ * exactly at its escape speed within fp64 rounding may fall either way.
+ * Invalid masses are reported as in cwthf_deposit. */
+CWTHF_API int cwthf_unbind(cwthf_ctx *ctx, const float *pos, const float *vel, const float *mass, double mass_unit,
+                           int64_t np, double L, double G, const int32_t *group, int64_t n_groups, int max_iter,
+                           int32_t *group_out, int64_t *n_kept, int32_t *iters, void *stream);
+
 /* Waits for `stream`, then returns (and clears) the first error the device
  * recorded since the last cwthf_sync, or CWTHF_E_CUDA if the stream failed.
  * After CWTHF_E_TIMEOUT or CWTHF_E_NOT_CONVERGED every output of the calls

@@ -108,6 +108,7 @@ def lib() -> ctypes.CDLL:
         L.cwthf_find.argtypes = [P, P, P, d, i64, d, i32, ctypes.POINTER(Params), i32, P, P, i64, P, P]
         L.cwthf_find_multiscale.argtypes = [P, P, P, d, i64, d, i32, ctypes.POINTER(d), ctypes.POINTER(i32), f, d,
                                             i64, P, P, i64, P, P]
+        L.cwthf_unbind.argtypes = [P, P, P, P, d, i64, d, d, P, i64, i32, P, P, P, P]
         L.cwthf_sync.argtypes = [P, P]
         L.cwthf_error_string.argtypes = [i32]
         L.cwthf_error_string.restype = ctypes.c_char_p
@@ -361,6 +362,28 @@ class Context:
                                            _ptr(cat), int(cat_cap), _ptr(n_halo), self._stream(stream)),
                "cwthf_find_multiscale")
         return halo_id, cat, n_halo
+
+    def unbind(self, pos, vel, group, L, G=4.30091727e-9, mass=None, mass_unit=1.0, n_groups=None, max_iter=100,
+               group_out=None, n_kept=None, iters=None, stream=None):
+        """Sec. 2.3: the self-boundness check of every group (group[i] = its
+        index or -1).  G defaults to Mpc/h, km/s, Msun/h.  Returns
+        (group after the check [np], members kept [n_groups], rounds [n_groups])."""
+        t = self.torch
+        pos = self._pos(pos)
+        vel = self._pos(vel)
+        assert group.is_cuda and group.dtype == t.int32 and group.shape == (pos.shape[0],) and group.is_contiguous()
+        if n_groups is None:
+            n_groups = int(group.max().item()) + 1 if pos.shape[0] else 0
+        if group_out is None:
+            group_out = t.empty(pos.shape[0], dtype=t.int32, device=self.device)
+        if n_kept is None:
+            n_kept = t.zeros(max(n_groups, 1), dtype=t.int64, device=self.device)
+        if iters is None:
+            iters = t.zeros(max(n_groups, 1), dtype=t.int32, device=self.device)
+        _check(lib().cwthf_unbind(self._h, _ptr(pos), _ptr(vel), _ptr(mass), float(mass_unit), pos.shape[0], float(L),
+                                  float(G), _ptr(group), int(n_groups), int(max_iter), _ptr(group_out), _ptr(n_kept),
+                                  _ptr(iters), self._stream(stream)), "cwthf_unbind")
+        return group_out, n_kept[:n_groups], iters[:n_groups]
 
 
 def ms_catalogue_to_numpy(cat, n) -> np.ndarray:

@@ -94,6 +94,11 @@ void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, F
     const size_t groups = ms == 1 ? 0 : (ms == 2 ? 2 : (ms + 3) & ~size_t(3));
     f(reinterpret_cast<void**>(&c->part_slot), (size_t(z.np) * ms + 4) * 4 + size_t(z.np) * 4 * groups);
     f(reinterpret_cast<void**>(&c->jump_changed), sizeof(int) * kJumpWords);
+    f(reinterpret_cast<void**>(&c->ub_off), size_t(z.slots + 2) * 4);
+    f(reinterpret_cast<void**>(&c->ub_cur), size_t(z.slots + 1) * 4);
+    f(reinterpret_cast<void**>(&c->ub_mem), size_t(z.np) * 4);
+    f(reinterpret_cast<void**>(&c->ub_key), size_t(z.np) * 16);
+    f(reinterpret_cast<void**>(&c->ub_val), size_t(z.np) * 8);
     f(reinterpret_cast<void**>(&c->scan_tmp), z.scan_words * 4);
     f(reinterpret_cast<void**>(&c->grid), size_t(z.cells) * 8);
     f(reinterpret_cast<void**>(&c->cwt), size_t(z.cells) * 4);
@@ -273,6 +278,22 @@ int cwthf_segment(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32
     DeviceGuard g(ctx->device);
     Range r("cwthf_segment (S5-S6)");
     return segment_impl(ctx, cwt, ng, cwt_min, cell_label, false, as_stream(stream));
+}
+
+int cwthf_unbind(cwthf_ctx* ctx, const float* pos, const float* vel, const float* mass, double mass_unit, int64_t np,
+                 double L, double G, const int32_t* group, int64_t n_groups, int max_iter, int32_t* group_out,
+                 int64_t* n_kept, int32_t* iters, void* stream) {
+    if (!ctx) return CWTHF_E_INVALID_ARG;
+    int rc = check_particles(ctx, pos, np, mass_unit);
+    if (rc) return rc;
+    if ((np > 0 && (!vel || !group || !group_out)) || n_groups < 0 || (n_groups > 0 && (!n_kept || !iters)) ||
+        max_iter < 1 || !(L > 0) || !std::isfinite(L) || !(G >= 0) || !std::isfinite(G))
+        return CWTHF_E_INVALID_ARG;
+    if (n_groups > int64_t(ctx->max_ng) * ctx->max_ng * ctx->max_ng / 8 + 8) return CWTHF_E_CAPACITY;
+    DeviceGuard g(ctx->device);
+    Range r("cwthf_unbind (Sec. 2.3)");
+    return unbind_impl(ctx, pos, vel, mass, mass_unit, np, L, G, group, n_groups, max_iter, group_out, n_kept, iters,
+                       as_stream(stream));
 }
 
 int cwthf_segment_sizes(cwthf_ctx* ctx, int32_t* seeds, int64_t* n_cells, int64_t cap, int64_t* n_seeds,

@@ -142,6 +142,13 @@ struct cwthf_ctx {
     uint32_t* scan_tmp = nullptr;     // block sums of the device scan
     size_t scan_tmp_cap = 0;          // words
 
+    // self-boundness check scratch (cwthf_unbind)
+    uint32_t* ub_off = nullptr;   // [max groups + 2] members per group, then their offsets
+    uint32_t* ub_cur = nullptr;   // [max groups + 1] scatter cursors
+    int32_t* ub_mem = nullptr;    // [max_np] members, grouped
+    uint64_t* ub_key = nullptr;   // [2 max_np] sort keys
+    int32_t* ub_val = nullptr;    // [2 max_np] sort values
+
     // cwthf_find internals
     int64_t* grid = nullptr;
     float* cwt = nullptr;
@@ -314,6 +321,10 @@ int deposit_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mas
 // in ctx->dep_rec / dep_mq with offsets ctx->dep_off, and sum m_q in d_mtot.
 int bin_particles(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L, int ng,
                   cudaStream_t s);
+// The self-boundness check of every group (Sec. 2.3).
+int unbind_impl(cwthf_ctx* ctx, const float* pos, const float* vel, const float* mass, double mass_unit, int64_t np,
+                double L, double G, const int32_t* group, int64_t n_groups, int max_iter, int32_t* group_out,
+                int64_t* n_kept, int32_t* iters, cudaStream_t s);
 // Forward half of the transform: x r2c and y c2c -> ctx spectrum `spec`.
 int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, float2* spec, cudaStream_t s);
 // The FFT twiddles of ng and the wavelet spectra of the n scales w[] for a box

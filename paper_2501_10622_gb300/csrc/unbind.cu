@@ -1,0 +1,363 @@
+// unbind.cu -- the self-boundness check (Sec. 2.3; step 9 of the Sec. 2 step
+// list), one CTA per group.
+//
+// For every group g, following Sec. 2.3 in order:
+//   1. the centre is the centre of mass of the current members (mass-weighted
+//      minimum-image offsets from the group's first member in particle order);
+//   2. with spherical symmetry the potential at member i is that of the
+//      shells of the other members about the centre (shell theorem):
+//      Phi_i = -G sum_{j != i} m_j / max(r_i, r_j), escape speed^2 = -2 Phi_i;
+//      with the members sorted by radius this is
+//      Phi_i = -G (M(before i) / r_i + sum_{j after i} m_j / r_j);
+//   3. members faster than their escape speed, relative to the group's
+//      mass-weighted mean velocity, are excluded, all at once;
+//   4. steps 1-3 repeat until nothing is excluded (at most max_iter rounds);
+//   5. a group that lost more than 40 % of its particles is discarded.
+// Each round: fixed-order block reductions (the sums do not depend on timing),
+// a bitonic sort of the radii (in shared memory for small groups, in the
+// group's slice of global scratch for large ones), chunked block scans for the
+// shell sums, and a stable compaction of the members that stay.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace cwthf {
+namespace {
+
+constexpr int kUbThreads = 512;
+constexpr int kUbWarps = kUbThreads / 32;
+constexpr int kUbSmemElems = 2048;  // groups up to this size sort in shared memory
+
+// Integer mass quanta (the deposit's rule): 1 when masses are equal, else
+// rint(m / mass_unit); invalid masses are reported once here.
+__global__ void k_ub_count(const float* __restrict__ mass, double mass_unit, const int32_t* __restrict__ group,
+                           int64_t np, int64_t n_groups, uint32_t* __restrict__ cnt, int32_t* __restrict__ group_out,
+                           int* status) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np; i += stride) {
+        group_out[i] = -1;
+        if (mass) {
+            const double r = rint(__ddiv_rn(double(mass[i]), mass_unit));
+            if (!(r >= 0.0)) set_status(status, CWTHF_E_BAD_INPUT);
+            else if (!(r < 2147483648.0)) set_status(status, CWTHF_E_OVERFLOW);
+        }
+        const int32_t g = group[i];
+        if (g >= 0 && int64_t(g) < n_groups) atomicAdd(&cnt[g], 1u);
+    }
+}
+
+__global__ void k_ub_scatter(const int32_t* __restrict__ group, int64_t np, int64_t n_groups,
+                             const uint32_t* __restrict__ off, uint32_t* __restrict__ cur, int32_t* __restrict__ mem) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np; i += stride) {
+        const int32_t g = group[i];
+        if (g >= 0 && int64_t(g) < n_groups) mem[off[g] + atomicAdd(&cur[g], 1u)] = int32_t(i);
+    }
+}
+
+struct UbArgs {
+    const float* pos;
+    const float* vel;
+    const float* mass;
+    double mass_unit, L, G;
+    const uint32_t* off;  // [n_groups + 1] first member of each group in mem
+    int32_t* mem;         // [np] members, grouped
+    uint64_t* key;        // [2 np] sort keys (group g: from 2 off[g], a power of two >= its size)
+    int32_t* val;         // [2 np] sort values
+    int max_iter;
+    int32_t* group_out;
+    int64_t* n_kept;
+    int32_t* iters;
+};
+
+__device__ __forceinline__ double mass_of(const UbArgs& a, int32_t i) {
+    const double q = a.mass ? rint(__ddiv_rn(double(a.mass[i]), a.mass_unit)) : 1.0;
+    return __dmul_rn(q, a.mass_unit);
+}
+
+// minimum-image offset of coordinate x from the anchor coordinate x0
+__device__ __forceinline__ double min_image(float x, float x0, double L) {
+    const double d = __dsub_rn(double(x), double(x0));
+    return __dsub_rn(d, __dmul_rn(L, floor(__dadd_rn(__ddiv_rn(d, L), 0.5))));
+}
+
+// Sums of NV values over the block in a fixed order (warp trees, then one
+// warp over the warp totals): the result does not depend on timing.
+template <int NV>
+__device__ __forceinline__ void block_sums(double (&v)[NV], double* sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; k++) sh[k * kUbWarps + w] = v[k];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            double x = lane < kUbWarps ? sh[k * kUbWarps + lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) sh[k * kUbWarps] = x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = sh[k * kUbWarps];
+    __syncthreads();
+}
+
+// Exclusive scan of one value per thread (thread order), in a fixed order;
+// *total receives the sum.
+template <class T>
+__device__ __forceinline__ T block_exclusive(T x, T* sh, T* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sh[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        T s = lane < kUbWarps ? sh[lane] : T(0);
+        T si = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += y;
+        }
+        if (lane < kUbWarps) sh[lane] = si - s;  // exclusive warp offsets
+        if (lane == kUbWarps - 1) sh[kUbWarps] = si;
+    }
+    __syncthreads();
+    const T r = sh[w] + incl - x;
+    *total = sh[kUbWarps];
+    __syncthreads();
+    return r;
+}
+
+// Bitonic sort of P (a power of two) (key, value) pairs, ascending keys.
+template <class K>
+__device__ void bitonic(K* k, int32_t* v, int P) {
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
+                const int lo = (t / stride) * 2 * stride + (t % stride), hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const K a = k[lo], b = k[hi];
+                if ((a > b) == up) {
+                    k[lo] = b;
+                    k[hi] = a;
+                    const int32_t va = v[lo];
+                    v[lo] = v[hi];
+                    v[hi] = va;
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// Sorts the group's first P slots of (K, V), in shared memory when they fit.
+__device__ void sort_pairs(uint64_t* K, int32_t* V, int P, uint64_t* sk, int32_t* sv) {
+    if (P <= kUbSmemElems) {
+        for (int t = threadIdx.x; t < P; t += blockDim.x) {
+            sk[t] = K[t];
+            sv[t] = V[t];
+        }
+        __syncthreads();
+        bitonic(sk, sv, P);
+        for (int t = threadIdx.x; t < P; t += blockDim.x) {
+            K[t] = sk[t];
+            V[t] = sv[t];
+        }
+        __syncthreads();
+    } else {
+        bitonic(K, V, P);
+    }
+}
+
+__device__ __forceinline__ int pow2_ceil(int n) {
+    int p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+__global__ void __launch_bounds__(kUbThreads) k_ub_group(UbArgs a) {
+    __shared__ uint64_t sk[kUbSmemElems];
+    __shared__ int32_t sv[kUbSmemElems];
+    __shared__ double shd[8 * kUbWarps];
+    __shared__ int64_t shi[kUbWarps + 1];
+    const int64_t g = blockIdx.x;
+    const uint32_t base = a.off[g];
+    const int n0 = int(a.off[g + 1] - base);
+    const int tid = threadIdx.x;
+    if (n0 == 0) {
+        if (tid == 0) {
+            a.n_kept[g] = 0;
+            a.iters[g] = 0;
+        }
+        return;
+    }
+    int32_t* X = a.mem + base;
+    uint64_t* K = a.key + 2 * size_t(base);
+    int32_t* V = a.val + 2 * size_t(base);
+    // members in particle order, so that every sum below runs in a fixed order
+    {
+        const int P = pow2_ceil(n0);
+        for (int t = tid; t < P; t += blockDim.x) {
+            K[t] = t < n0 ? uint64_t(uint32_t(X[t])) : ~0ull;
+            V[t] = t < n0 ? X[t] : -1;
+        }
+        __syncthreads();
+        sort_pairs(K, V, P, sk, sv);
+        for (int t = tid; t < n0; t += blockDim.x) X[t] = V[t];
+        __syncthreads();
+    }
+    const float* a0 = a.pos + 3 * size_t(X[0]);
+    const float ax = a0[0], ay = a0[1], az = a0[2];
+    const double L = a.L, twoG = 2.0 * a.G;
+    int n = n0, it = 0;
+    while (it < a.max_iter) {
+        it++;
+        // 1. centre of mass and mean velocity
+        double s[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int k = tid; k < n; k += blockDim.x) {
+            const int32_t i = X[k];
+            const double m = mass_of(a, i);
+            const float* p = a.pos + 3 * size_t(i);
+            const float* v = a.vel + 3 * size_t(i);
+            s[0] += m;
+            s[1] += m * min_image(p[0], ax, L);
+            s[2] += m * min_image(p[1], ay, L);
+            s[3] += m * min_image(p[2], az, L);
+            s[4] += m * double(v[0]);
+            s[5] += m * double(v[1]);
+            s[6] += m * double(v[2]);
+        }
+        block_sums<7>(s, shd);
+        const double M = s[0];
+        const double cx = M > 0.0 ? s[1] / M : 0.0, cy = M > 0.0 ? s[2] / M : 0.0, cz = M > 0.0 ? s[3] / M : 0.0;
+        const double vx = M > 0.0 ? s[4] / M : 0.0, vy = M > 0.0 ? s[5] / M : 0.0, vz = M > 0.0 ? s[6] / M : 0.0;
+        // radii about the centre, sorted
+        const int P = pow2_ceil(n);
+        for (int t = tid; t < P; t += blockDim.x) {
+            if (t < n) {
+                const int32_t i = X[t];
+                const float* p = a.pos + 3 * size_t(i);
+                const double dx = __dsub_rn(min_image(p[0], ax, L), cx);
+                const double dy = __dsub_rn(min_image(p[1], ay, L), cy);
+                const double dz = __dsub_rn(min_image(p[2], az, L), cz);
+                const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                K[t] = uint64_t(__double_as_longlong(__dsqrt_rn(r2)));  // r >= 0: the bits order like the values
+                V[t] = i;
+            } else {
+                K[t] = ~0ull;
+                V[t] = -1;
+            }
+        }
+        __syncthreads();
+        sort_pairs(K, V, P, sk, sv);
+        // 2-3. shell sums per member and the exclusions.  Thread t walks the
+        // chunk [t ch, (t+1) ch): mass before the chunk and m/r after it come
+        // from block scans of the chunk totals.  Massive members at the centre
+        // (r = 0, sorted first) enter the later members' sums through the mass
+        // before them; for another member at r = 0 they make the potential
+        // infinite (counted apart, so no infinity enters the scans).
+        const int ch = (n + blockDim.x - 1) / blockDim.x;
+        const int c0 = min(n, tid * ch), c1 = min(n, c0 + ch);
+        double tm = 0.0, tq = 0.0;
+        long long tz = 0;
+        for (int k = c0; k < c1; k++) {
+            const double r = __longlong_as_double((long long)K[k]);
+            const double m = mass_of(a, V[k]);
+            tm += m;
+            if (m > 0.0) {
+                if (r > 0.0) tq += m / r;
+                else tz++;
+            }
+        }
+        double tot_m, tot_q;
+        long long tot_z;
+        const double pre_m = block_exclusive(tm, shd, &tot_m);
+        const double pre_q = block_exclusive(tq, shd, &tot_q);
+        (void)block_exclusive(tz, reinterpret_cast<long long*>(shi), &tot_z);
+        const double after_q = tot_q - pre_q - tq;  // m/r of the chunks after this one
+        double run_m = pre_m, run_q = 0.0;
+        int nk = 0;
+        for (int k = c0; k < c1; k++) {
+            const int32_t i = V[k];
+            const double r = __longlong_as_double((long long)K[k]);
+            const double m = mass_of(a, i);
+            if (m > 0.0 && r > 0.0) run_q += m / r;
+            const double below = run_m > 0.0 ? run_m / r : 0.0;  // M(before) / r (r = 0: infinite)
+            double S = below + (after_q + (tq - run_q));
+            if (r == 0.0 && tot_z - (m > 0.0 ? 1 : 0) > 0) S = __longlong_as_double(0x7ff0000000000000ll);
+            run_m += m;
+            const float* v = a.vel + 3 * size_t(i);
+            const double ux = double(v[0]) - vx, uy = double(v[1]) - vy, uz = double(v[2]) - vz;
+            const double v2 = ux * ux + uy * uy + uz * uz;
+            const bool stay = !(v2 > twoG * S);
+            if (!stay) V[k] = ~i;  // marked for exclusion
+            nk += stay;
+        }
+        long long n_keep;
+        const long long dst0 = block_exclusive((long long)nk, reinterpret_cast<long long*>(shi), &n_keep);
+        if (n_keep == n) break;
+        // stable compaction of the members that stay
+        long long d = dst0;
+        for (int k = c0; k < c1; k++) {
+            const int32_t i = V[k];
+            if (i >= 0) X[d++] = i;
+        }
+        __syncthreads();
+        n = int(n_keep);
+    }
+    // 5. more than 40 % excluded: the group is discarded
+    const bool discard = 5ll * (n0 - n) > 2ll * n0;
+    if (!discard)
+        for (int k = tid; k < n; k += blockDim.x) a.group_out[X[k]] = int32_t(g);
+    if (tid == 0) {
+        a.n_kept[g] = discard ? 0 : n;
+        a.iters[g] = it;
+    }
+}
+
+}  // namespace
+
+int unbind_impl(cwthf_ctx* ctx, const float* pos, const float* vel, const float* mass, double mass_unit, int64_t np,
+                double L, double G, const int32_t* group, int64_t n_groups, int max_iter, int32_t* group_out,
+                int64_t* n_kept, int32_t* iters, cudaStream_t s) {
+    uint32_t* cnt = ctx->ub_off;
+    uint32_t* cur = ctx->ub_cur;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, size_t(n_groups + 1) * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cur, 0, size_t(n_groups + 1) * 4, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int blocks = ctx->sm_count * 8;
+    CWTHF_LAUNCH(ctx, s, "k_ub_count",
+                 k_ub_count<<<blocks, 256, 0, s>>>(mass, mass_unit, group, np, n_groups, cnt, group_out, ctx->d_status));
+    int rc = scan_u32(ctx, cnt, cnt, n_groups, s);  // in place: offsets, cnt[n_groups] = members
+    if (rc) return rc;
+    CWTHF_LAUNCH(ctx, s, "k_ub_scatter",
+                 k_ub_scatter<<<blocks, 256, 0, s>>>(group, np, n_groups, cnt, cur, ctx->ub_mem));
+    if (n_groups > 0) {
+        UbArgs a;
+        a.pos = pos;
+        a.vel = vel;
+        a.mass = mass;
+        a.mass_unit = mass_unit;
+        a.L = L;
+        a.G = G;
+        a.off = cnt;
+        a.mem = ctx->ub_mem;
+        a.key = ctx->ub_key;
+        a.val = ctx->ub_val;
+        a.max_iter = max_iter;
+        a.group_out = group_out;
+        a.n_kept = n_kept;
+        a.iters = iters;
+        CWTHF_LAUNCH(ctx, s, "k_ub_group", k_ub_group<<<unsigned(n_groups), kUbThreads, 0, s>>>(a));
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace cwthf

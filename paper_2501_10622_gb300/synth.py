@@ -14,7 +14,10 @@ clustered boxes of the same character stand in for it:
   r_s = R / c, radii from the inverse of the truncated NFW enclosed-mass
   profile mu(r/r_s)/mu(c), mu(y) = ln(1+y) - y/(1+y), isotropic directions;
 * periodic wrap into [0, L), float32 positions, equal masses, and the
-  particle order randomly permuted (snapshots are not sorted in space).
+  particle order randomly permuted (snapshots are not sorted in space);
+* on request, velocities for the self-boundness check (Sec. 2.3): Gaussian
+  field motions of 300 km/s per axis, and inside clumps an isotropic
+  Gaussian of virial dispersion sqrt(G M / R) about the clump's bulk motion.
 
 Everything is drawn from one ``torch.Generator`` seeded by the caller, so a
 box is reproducible on a given device type.  CPU and CUDA generators give
@@ -71,12 +74,37 @@ def clump_counts(n_in_clumps: int, n_clumps: int, gen: torch.Generator, device) 
     return base
 
 
+# Units of the velocities: positions in Mpc/h, velocities in km/s, masses in
+# Msun/h; G in those units, and the mean matter density (Omega_m = 0.3) that
+# gives the particle mass of a box.
+G_MPC_KMS_MSUN = 4.30091727e-9
+RHO_MEAN = 0.3 * 2.77536627e11  # (Msun/h) / (Mpc/h)^3
+SIGMA_FIELD = 300.0  # km/s per axis: uniform particles and clump bulk motions
+
+
+def particle_mass(n_particles: int, box: float) -> float:
+    """Msun/h per particle of an equal-mass box at the mean matter density."""
+    return RHO_MEAN * box ** 3 / max(n_particles, 1)
+
+
 def clumped_box(n_particles: int, box: float, n_clumps: int | None = None, seed: int = 0,
-                device="cpu", uniform_frac: float = 0.4, shuffle: bool = True) -> torch.Tensor:
-    """float32 [n_particles, 3] positions in [0, box)."""
+                device="cpu", uniform_frac: float = 0.4, shuffle: bool = True, velocities: bool = False):
+    """float32 [n_particles, 3] positions in [0, box); with velocities=True
+    also float32 [n_particles, 3] velocities (km/s): uniform particles and
+    clump bulk motions Gaussian with SIGMA_FIELD per axis, and clump members
+    their clump's bulk velocity plus an isotropic Gaussian of 3D dispersion
+    V_vir = sqrt(G M / R) (M = members x particle_mass, R the clump's virial
+    radius).  Velocities come from a second generator, so the positions are
+    those of velocities=False."""
     device = torch.device(device)
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed))
+    genv = None
+    if velocities:
+        genv = torch.Generator(device=device)
+        genv.manual_seed(int(seed) * 7919 + 104729)
+        vout = torch.empty((n_particles, 3), dtype=torch.float32, device=device)
+        mp = particle_mass(n_particles, box)
     if n_clumps is None:
         n_clumps = max(1, int(round(CLUMP_DENSITY * box ** 3)))
     n_uni = int(round(uniform_frac * n_particles))
@@ -94,12 +122,17 @@ def clumped_box(n_particles: int, box: float, n_clumps: int | None = None, seed:
     for s in range(0, n_uni, chunk):
         k = min(chunk, n_uni - s)
         store(s, torch.rand((k, 3), generator=gen, device=device, dtype=f64) * box)
+        if velocities:
+            vout[s:s + k] = (SIGMA_FIELD * torch.randn((k, 3), generator=genv, device=device, dtype=f64)).float()
     if n_cl > 0:
         counts = clump_counts(n_cl, n_clumps, gen, device)
         centres = torch.rand((n_clumps, 3), generator=gen, device=device, dtype=f64) * box
         conc = NFW_C_RANGE[0] + (NFW_C_RANGE[1] - NFW_C_RANGE[0]) * torch.rand(n_clumps, generator=gen, device=device, dtype=f64)
         rvir = RVIR_RANGE[0] + (RVIR_RANGE[1] - RVIR_RANGE[0]) * torch.rand(n_clumps, generator=gen, device=device, dtype=f64)
         owner = torch.repeat_interleave(torch.arange(n_clumps, device=device), counts)
+        if velocities:
+            bulk = SIGMA_FIELD * torch.randn((n_clumps, 3), generator=genv, device=device, dtype=f64)
+            sig1 = torch.sqrt(G_MPC_KMS_MSUN * counts.to(f64) * mp / rvir / 3.0)  # per axis
         for s in range(0, n_cl, chunk):
             o = owner[s:s + chunk]
             k = o.numel()
@@ -109,10 +142,17 @@ def clumped_box(n_particles: int, box: float, n_clumps: int | None = None, seed:
             d = torch.randn((k, 3), generator=gen, device=device, dtype=f64)
             d = d / d.norm(dim=1, keepdim=True).clamp_min(1e-300)
             store(n_uni + s, centres[o] + r[:, None] * d)
+            if velocities:
+                dv = torch.randn((k, 3), generator=genv, device=device, dtype=f64)
+                vout[n_uni + s:n_uni + s + k] = (bulk[o] + sig1[o, None] * dv).float()
         del owner
     if shuffle:
         perm = torch.randperm(n_particles, generator=gen, device=device)
         out = out[perm]
+        if velocities:
+            vout = vout[perm]
+    if velocities:
+        return out.contiguous(), vout.contiguous()
     return out.contiguous()
 
 
