@@ -138,11 +138,18 @@ CWTHF_API void cwthf_default_params(double w, cwthf_params *p);
  * graph runs.  During a capture, a call that needs a new table while no slot
  * is free fails with CWTHF_E_TABLE_CACHE (nothing queued). */
 CWTHF_API int cwthf_create(int device, int max_ng, int64_t max_np, int max_scales, cwthf_ctx **out);
+/* Optional parts of a context, for cwthf_create_ex and cwthf_workspace_bytes_ex. */
+#define CWTHF_CREATE_UNBIND 1u /* scratch of cwthf_unbind: 28 bytes per particle + 8 per group */
+/* cwthf_create with optional parts (flags: CWTHF_CREATE_*; unknown bits ->
+ * CWTHF_E_INVALID_ARG).  cwthf_create is this with flags 0. */
+CWTHF_API int cwthf_create_ex(int device, int max_ng, int64_t max_np, int max_scales, unsigned flags,
+                              cwthf_ctx **out);
 CWTHF_API void cwthf_destroy(cwthf_ctx *ctx);
 
 /* Device bytes a context created with these limits holds (for admission
  * against a memory budget).  Host-only; needs no GPU. */
 CWTHF_API int cwthf_workspace_bytes(int max_ng, int64_t max_np, int max_scales, size_t *out);
+CWTHF_API int cwthf_workspace_bytes_ex(int max_ng, int64_t max_np, int max_scales, unsigned flags, size_t *out);
 
 /* Checks a grid size against the supported set (CWTHF_OK or
  * CWTHF_E_UNSUPPORTED_SIZE).  Host-only. */
@@ -300,7 +307,8 @@ CWTHF_API int cwthf_find_multiscale(cwthf_ctx *ctx, const float *pos, const floa
  *   iters       device, int32 [n_groups]: rounds run
  * Each group's sums run in a fixed order, so results repeat exactly; a member
  * exactly at its escape speed within fp64 rounding may fall either way.
- * Invalid masses are reported as in cwthf_deposit. */
+ * Invalid masses are reported as in cwthf_deposit.  Needs a context created
+ * with CWTHF_CREATE_UNBIND (else CWTHF_E_INVALID_ARG). */
 CWTHF_API int cwthf_unbind(cwthf_ctx *ctx, const float *pos, const float *vel, const float *mass, double mass_unit,
                            int64_t np, double L, double G, const int32_t *group, int64_t n_groups, int max_iter,
                            int32_t *group_out, int64_t *n_kept, int32_t *iters, void *stream);

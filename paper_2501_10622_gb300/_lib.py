@@ -22,6 +22,7 @@ OK = 0
 E_INVALID_ARG, E_UNSUPPORTED_SIZE, E_OVERFLOW, E_OOM, E_CUDA, E_NOT_CONVERGED, E_TIMEOUT, E_CAPACITY, E_BAD_INPUT = range(1, 10)
 E_SCRATCH_LIMIT = 10
 E_TABLE_CACHE = 11
+CREATE_UNBIND = 1  # cwthf_create_ex: scratch of the self-boundness check
 FRAC_BITS = 10
 MIN_NG, MAX_NG = 8, 1024
 # cwthf_debug_set / cwthf_debug_get keys
@@ -91,6 +92,8 @@ def lib() -> ctypes.CDLL:
         L.cwthf_default_params.argtypes = [d, ctypes.POINTER(Params)]
         L.cwthf_default_params.restype = None
         L.cwthf_create.argtypes = [i32, i32, i64, i32, ctypes.POINTER(P)]
+        L.cwthf_create_ex.argtypes = [i32, i32, i64, i32, ctypes.c_uint, ctypes.POINTER(P)]
+        L.cwthf_workspace_bytes_ex.argtypes = [i32, i64, i32, ctypes.c_uint, ctypes.POINTER(ctypes.c_size_t)]
         L.cwthf_destroy.argtypes = [P]
         L.cwthf_destroy.restype = None
         L.cwthf_workspace_bytes.argtypes = [i32, i64, i32, ctypes.POINTER(ctypes.c_size_t)]
@@ -137,11 +140,12 @@ def check_ng(ng: int) -> bool:
     return lib().cwthf_check_ng(int(ng)) == OK
 
 
-def workspace_bytes(max_ng: int, max_np: int, max_scales: int = 1) -> int:
+def workspace_bytes(max_ng: int, max_np: int, max_scales: int = 1, unbind: bool = False) -> int:
     out = ctypes.c_size_t(0)
-    rc = lib().cwthf_workspace_bytes(int(max_ng), int(max_np), int(max_scales), ctypes.byref(out))
+    rc = lib().cwthf_workspace_bytes_ex(int(max_ng), int(max_np), int(max_scales), CREATE_UNBIND if unbind else 0,
+                                        ctypes.byref(out))
     if rc:
-        raise CwthfError(rc, "cwthf_workspace_bytes")
+        raise CwthfError(rc, "cwthf_workspace_bytes_ex")
     return int(out.value)
 
 
@@ -167,14 +171,16 @@ class Context:
     """A cwthf_ctx: device scratch sized for grids up to max_ng and up to
     max_np particles (and max_scales scales per find call)."""
 
-    def __init__(self, device: int = 0, max_ng: int = 256, max_np: int = 1 << 24, max_scales: int = 1):
+    def __init__(self, device: int = 0, max_ng: int = 256, max_np: int = 1 << 24, max_scales: int = 1,
+                 unbind: bool = False):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
         self.max_ng, self.max_np, self.max_scales = max_ng, max_np, max_scales
         h = ctypes.c_void_p()
-        _check(lib().cwthf_create(int(device), int(max_ng), int(max_np), int(max_scales), ctypes.byref(h)),
-               "cwthf_create")
+        flags = CREATE_UNBIND if unbind else 0
+        _check(lib().cwthf_create_ex(int(device), int(max_ng), int(max_np), int(max_scales), flags, ctypes.byref(h)),
+               "cwthf_create_ex")
         self._h = h
 
     def close(self):

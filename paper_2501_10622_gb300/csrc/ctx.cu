@@ -20,6 +20,8 @@ struct Range {
     ~Range() { nvtxRangePop(); }
 };
 
+constexpr unsigned kCreateFlags = CWTHF_CREATE_UNBIND;
+
 int check_ng(int ng) {
     if (ng < CWTHF_MIN_NG || ng > CWTHF_MAX_NG || ng % 2) return CWTHF_E_UNSUPPORTED_SIZE;
     return fft_size_supported(ng) ? CWTHF_OK : CWTHF_E_UNSUPPORTED_SIZE;
@@ -67,7 +69,7 @@ size_t table_slot_floats(int max_ng) { return 20 * size_t(max_ng) + 512; }
 // The allocation plan: (pointer slot, bytes).  One list drives both
 // cwthf_create and cwthf_workspace_bytes.
 template <class F>
-void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, F&& f) {
+void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, unsigned flags, F&& f) {
     Sizes z = sizes_for(max_ng, max_np);
     f(reinterpret_cast<void**>(&c->d_status), sizeof(int) * 4);
     f(reinterpret_cast<void**>(&c->dep_count), size_t(z.keys + 1) * 4);
@@ -94,11 +96,13 @@ void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, F
     const size_t groups = ms == 1 ? 0 : (ms == 2 ? 2 : (ms + 3) & ~size_t(3));
     f(reinterpret_cast<void**>(&c->part_slot), (size_t(z.np) * ms + 4) * 4 + size_t(z.np) * 4 * groups);
     f(reinterpret_cast<void**>(&c->jump_changed), sizeof(int) * kJumpWords);
-    f(reinterpret_cast<void**>(&c->ub_off), size_t(z.slots + 2) * 4);
-    f(reinterpret_cast<void**>(&c->ub_cur), size_t(z.slots + 1) * 4);
-    f(reinterpret_cast<void**>(&c->ub_mem), size_t(z.np) * 4);
-    f(reinterpret_cast<void**>(&c->ub_key), size_t(z.np) * 16);
-    f(reinterpret_cast<void**>(&c->ub_val), size_t(z.np) * 8);
+    if (flags & CWTHF_CREATE_UNBIND) {  // self-boundness check scratch (28 bytes per particle)
+        f(reinterpret_cast<void**>(&c->ub_off), size_t(z.slots + 2) * 4);
+        f(reinterpret_cast<void**>(&c->ub_cur), size_t(z.slots + 1) * 4);
+        f(reinterpret_cast<void**>(&c->ub_mem), size_t(z.np) * 4);
+        f(reinterpret_cast<void**>(&c->ub_key), size_t(z.np) * 16);
+        f(reinterpret_cast<void**>(&c->ub_val), size_t(z.np) * 8);
+    }
     f(reinterpret_cast<void**>(&c->scan_tmp), z.scan_words * 4);
     f(reinterpret_cast<void**>(&c->grid), size_t(z.cells) * 8);
     f(reinterpret_cast<void**>(&c->cwt), size_t(z.cells) * 4);
@@ -107,7 +111,7 @@ void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, F
 }
 
 void release(cwthf_ctx* c) {
-    for_each_buffer(c, c->max_ng, c->max_np, c->max_scales, [](void** p, size_t) {
+    for_each_buffer(c, c->max_ng, c->max_np, c->max_scales, c->flags, [](void** p, size_t) {
         if (*p) cudaFree(*p);
         *p = nullptr;
     });
@@ -154,20 +158,31 @@ void cwthf_default_params(double w, cwthf_params* p) {
 
 int cwthf_check_ng(int ng) { return check_ng(ng) ? CWTHF_E_UNSUPPORTED_SIZE : CWTHF_OK; }
 
-int cwthf_workspace_bytes(int max_ng, int64_t max_np, int max_scales, size_t* out) {
-    if (!out || max_np < 0 || max_np >= (int64_t(1) << 31) || max_scales < 1) return CWTHF_E_INVALID_ARG;
+int cwthf_workspace_bytes_ex(int max_ng, int64_t max_np, int max_scales, unsigned flags, size_t* out) {
+    if (!out || max_np < 0 || max_np >= (int64_t(1) << 31) || max_scales < 1 || (flags & ~kCreateFlags))
+        return CWTHF_E_INVALID_ARG;
     if (check_ng(max_ng)) return CWTHF_E_UNSUPPORTED_SIZE;
     cwthf_ctx probe;
     size_t total = 0;
-    for_each_buffer(&probe, max_ng, max_np, max_scales, [&](void**, size_t b) { total += (b + 255) / 256 * 256; });
+    for_each_buffer(&probe, max_ng, max_np, max_scales, flags,
+                    [&](void**, size_t b) { total += (b + 255) / 256 * 256; });
     *out = total;
     return CWTHF_OK;
 }
 
+int cwthf_workspace_bytes(int max_ng, int64_t max_np, int max_scales, size_t* out) {
+    return cwthf_workspace_bytes_ex(max_ng, max_np, max_scales, 0u, out);
+}
+
 int cwthf_create(int device, int max_ng, int64_t max_np, int max_scales, cwthf_ctx** out) {
+    return cwthf_create_ex(device, max_ng, max_np, max_scales, 0u, out);
+}
+
+int cwthf_create_ex(int device, int max_ng, int64_t max_np, int max_scales, unsigned flags, cwthf_ctx** out) {
     if (!out) return CWTHF_E_INVALID_ARG;
     *out = nullptr;
-    if (max_np < 0 || max_np >= (int64_t(1) << 31) || max_scales < 1) return CWTHF_E_INVALID_ARG;
+    if (max_np < 0 || max_np >= (int64_t(1) << 31) || max_scales < 1 || (flags & ~kCreateFlags))
+        return CWTHF_E_INVALID_ARG;
     if (check_ng(max_ng)) return CWTHF_E_UNSUPPORTED_SIZE;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return CWTHF_E_CUDA;
@@ -179,13 +194,14 @@ int cwthf_create(int device, int max_ng, int64_t max_np, int max_scales, cwthf_c
     c->max_ng = max_ng;
     c->max_np = max_np;
     c->max_scales = max_scales;
+    c->flags = flags;
     if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
         (c->fallback_blocks = fallback_blocks(c->sm_count)) <= 0) {
         delete c;
         return CWTHF_E_CUDA;
     }
     bool failed = false;
-    for_each_buffer(c, max_ng, max_np, max_scales, [&](void** p, size_t b) {
+    for_each_buffer(c, max_ng, max_np, max_scales, flags, [&](void** p, size_t b) {
         if (failed) return;
         if (cudaMalloc(p, b) != cudaSuccess) {
             *p = nullptr;
@@ -283,7 +299,7 @@ int cwthf_segment(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32
 int cwthf_unbind(cwthf_ctx* ctx, const float* pos, const float* vel, const float* mass, double mass_unit, int64_t np,
                  double L, double G, const int32_t* group, int64_t n_groups, int max_iter, int32_t* group_out,
                  int64_t* n_kept, int32_t* iters, void* stream) {
-    if (!ctx) return CWTHF_E_INVALID_ARG;
+    if (!ctx || !(ctx->flags & CWTHF_CREATE_UNBIND)) return CWTHF_E_INVALID_ARG;
     int rc = check_particles(ctx, pos, np, mass_unit);
     if (rc) return rc;
     if ((np > 0 && (!vel || !group || !group_out)) || n_groups < 0 || (n_groups > 0 && (!n_kept || !iters)) ||

@@ -110,6 +110,7 @@ struct cwthf_ctx {
     int max_ng = 0;
     int64_t max_np = 0;
     int max_scales = 1;
+    unsigned flags = 0;  // CWTHF_CREATE_* given to cwthf_create_ex
     int sm_count = 0;
 
     int* d_status = nullptr;   // first device-side error since the last cwthf_sync

@@ -40,6 +40,9 @@ def test_workspace_bytes_monotone_and_errors():
     c = pkg.workspace_bytes(128, 1 << 20)
     d = pkg.workspace_bytes(128, 1 << 20, 3)
     assert 0 < a < b < c < d
+    # the self-boundness check's scratch only when asked for: 28 B per particle + 8 per group
+    u = pkg.workspace_bytes(128, 1 << 20, 3, unbind=True)
+    assert u - d >= 28 * (1 << 20) + 8 * (128 ** 3 // 8)
     with pytest.raises(pkg.CwthfError):
         pkg.workspace_bytes(191, 10)
     with pytest.raises(pkg.CwthfError):

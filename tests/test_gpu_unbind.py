@@ -19,7 +19,7 @@ NEAR_TIE = 1e-9
 
 @pytest.fixture(scope="module")
 def uctx():
-    c = pkg.Context(0, max_ng=64, max_np=1 << 20, max_scales=1)
+    c = pkg.Context(0, max_ng=64, max_np=1 << 20, max_scales=1, unbind=True)
     yield c
     c.close()
 
@@ -145,9 +145,11 @@ def test_repeatable_and_masses(uctx):
     _same(got, ref)
 
 
-def test_errors(uctx):
+def test_errors(uctx, gctx):
     pos = dev(np.zeros((4, 3), np.float32))
     grp = dev(np.zeros(4, np.int32))
+    with pytest.raises(pkg.CwthfError):  # a context without the check's scratch
+        gctx.unbind(pos, pos, grp, 10.0)
     with pytest.raises(pkg.CwthfError):
         uctx.unbind(pos, pos, grp, 10.0, max_iter=0)
     with pytest.raises(pkg.CwthfError):
