@@ -81,8 +81,8 @@ def test_bad_inputs_reported(gctx):
 
 def test_host_side_argument_errors(gctx):
     p = dev(random_box(10, 10.0, 1))
-    with pytest.raises(pkg.CwthfError) as e:
-        gctx.deposit(p, 10.0, 100)
+    with pytest.raises(pkg.CwthfError) as e:  # odd: the real transform pairs the x samples
+        gctx.deposit(p, 10.0, 101)
     assert e.value.code == pkg._lib.E_UNSUPPORTED_SIZE
     with pytest.raises(pkg.CwthfError) as e:
         gctx.deposit(p, -1.0, 16)
