@@ -69,7 +69,8 @@ def lib() -> ctypes.CDLL:
         L.orc_corrected_peak.argtypes = [P, i32, i64, i32]
         L.orc_corrected_peak.restype = f
         L.orc_cross_scale.argtypes = [P, i32, i64, P, i32]
-        L.orc_multiscale.argtypes = [P, P, d, i64, d, i32, P, P, f, d, i64, P, i64, P, P, P, P, P, P, P, P]
+        L.orc_multiscale.argtypes = [P, P, d, i64, d, i32, P, P, f, d, i64, P, d, i32, P, i64, P, P, P, P, P, P, P, P,
+                                     P]
         L.orc_unbind.argtypes = [P, P, P, d, i64, d, d, P, i64, i32, P, P, P, P]
         _lib = L
     return _lib
@@ -271,10 +272,18 @@ def cross_scale(C, seed: int, C_next=None) -> bool:
 
 
 def multiscale_on_fields(pos, L: float, fields, mass=None, mass_unit: float = 1.0, cwt_min: float = 0.0,
-                         dens_th: float = 4.0, particle_th: int = 15, cap: int = 1 << 20):
+                         dens_th: float = 4.0, particle_th: int = 15, cap: int = 1 << 20, vel=None,
+                         G: float = None, max_iter: int = 100):
     """The loop of Fig. 1 on given fp32 fields (largest physical scale first):
-    final halo ids and the catalogue (dict of columns, in halo-id order)."""
+    final halo ids and the catalogue (dict of columns, in halo-id order).
+    With velocities, every scale's kept groups pass the self-boundness check
+    (Sec. 2.3) before they get ids; cat["margin"] is then the smallest
+    relative distance of any of its decisions from its threshold."""
     pos, mass = _pos(pos), _mass(mass)
+    if vel is not None:
+        vel = _pos(vel)
+    if G is None:
+        G = G_MPC_KMS_MSUN
     fs = [np.ascontiguousarray(f, dtype=np.float32) for f in fields]
     n = len(fs)
     ngs = np.array([f.shape[0] for f in fs], dtype=np.int32)
@@ -283,25 +292,28 @@ def multiscale_on_fields(pos, L: float, fields, mass=None, mass_unit: float = 1.
     sc = np.empty(cap, np.int32); seed = np.empty(cap, np.int64); npart = np.empty(cap, np.int64)
     ncell = np.empty(cap, np.int64); mass_o = np.empty(cap, np.float64); cen = np.empty((cap, 3), np.float64)
     peak = np.empty(cap, np.float32); nh = np.zeros(1, np.int64)
+    margin = ctypes.c_double(float("inf"))
     _check(lib().orc_multiscale(_ptr(pos), _ptr(mass), float(mass_unit), pos.shape[0], float(L), n, _ptr(ngs),
                                 ctypes.cast(ptrs, ctypes.c_void_p), float(cwt_min), float(dens_th), int(particle_th),
-                                _ptr(hid), int(cap), _ptr(sc), _ptr(seed), _ptr(npart), _ptr(ncell), _ptr(mass_o),
-                                _ptr(cen), _ptr(peak), _ptr(nh)), "multiscale")
+                                _ptr(vel), float(G), int(max_iter), _ptr(hid), int(cap), _ptr(sc), _ptr(seed),
+                                _ptr(npart), _ptr(ncell), _ptr(mass_o), _ptr(cen), _ptr(peak), _ptr(nh),
+                                ctypes.byref(margin)), "multiscale")
     k = int(nh[0])
     cat = dict(scale=sc[:k], seed=seed[:k], n_part=npart[:k], n_cells=ncell[:k], mass=mass_o[:k], centre=cen[:k],
-               peak=peak[:k])
+               peak=peak[:k], margin=margin.value)
     return hid, cat
 
 
 def find_multiscale(pos, L: float, ws, ngs, mass=None, mass_unit: float = 1.0, cwt_min: float = 0.0,
-                    dens_th: float = 4.0, particle_th: int = 15):
+                    dens_th: float = 4.0, particle_th: int = 15, vel=None, G: float = None, max_iter: int = 100):
     """The whole loop: per scale the CIC grid on its own ng^3 grid and the
     fp64 CWT rounded to fp32, then multiscale_on_fields."""
     fields = []
     for w, ng in zip(ws, ngs):
         grid, _ = cic(pos, L, ng, mass, mass_unit)
         fields.append(cwt(grid, L, w, mass_unit).astype(np.float32))
-    hid, cat = multiscale_on_fields(pos, L, fields, mass, mass_unit, cwt_min, dens_th, particle_th)
+    hid, cat = multiscale_on_fields(pos, L, fields, mass, mass_unit, cwt_min, dens_th, particle_th, vel=vel, G=G,
+                                    max_iter=max_iter)
     return dict(fields=fields, halo_id=hid, cat=cat)
 
 

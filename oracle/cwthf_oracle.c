@@ -687,8 +687,9 @@ int orc_cross_scale(const float *C, int ng, int64_t s, const float *Cn, int ng_n
  * seed, n_part, n_cells, mass, centre[3], corrected peak. */
 int orc_multiscale(const float *pos, const float *mass, double mass_unit, int64_t np, double L, int n_scales,
                    const int *ngs, const float *const *fields, float cwt_min, double dens_th, int64_t particle_th,
-                   int32_t *halo_id, int64_t cap, int32_t *scale_out, int64_t *seed_out, int64_t *npart_out,
-                   int64_t *ncell_out, double *mass_out, double *centre_out, float *peak_out, int64_t *n_halo) {
+                   const float *vel, double G, int max_iter, int32_t *halo_id, int64_t cap, int32_t *scale_out,
+                   int64_t *seed_out, int64_t *npart_out, int64_t *ncell_out, double *mass_out, double *centre_out,
+                   float *peak_out, int64_t *n_halo, double *margin_out) {
     if (np < 0 || !(L > 0) || !(mass_unit > 0) || n_scales < 1) return ORC_E_ARG;
     int max_ng = 0;
     for (int j = 0; j < n_scales; j++) {
@@ -701,7 +702,17 @@ int orc_multiscale(const float *pos, const float *mass, double mass_unit, int64_
     int64_t *nc_c = malloc(sizeof(int64_t) * (size_t)max_cells), *mom = malloc(sizeof(int64_t) * 3 * (size_t)max_cells);
     int32_t *tmp = malloc(sizeof(int32_t) * (size_t)(np > 0 ? np : 1));
     int32_t *hid_c = malloc(sizeof(int32_t) * (size_t)max_cells);
-    int rc = (lab && np_c && mq_c && nc_c && mom && tmp && hid_c) ? ORC_OK : ORC_E_NOMEM;
+    /* self-boundness check (vel given): each particle's kept group, its group
+     * after the check, the groups' kept members and rounds */
+    int32_t *grp = malloc(sizeof(int32_t) * (size_t)(np > 0 ? np : 1));
+    int32_t *bound = malloc(sizeof(int32_t) * (size_t)(np > 0 ? np : 1));
+    int64_t *nk_g = malloc(sizeof(int64_t) * (size_t)max_cells);
+    int32_t *it_g = malloc(sizeof(int32_t) * (size_t)max_cells);
+    int64_t *rank_c = malloc(sizeof(int64_t) * (size_t)max_cells);
+    double margin = INFINITY;
+    int rc = (lab && np_c && mq_c && nc_c && mom && tmp && hid_c && grp && bound && nk_g && it_g && rank_c) ? ORC_OK
+                                                                                                              : ORC_E_NOMEM;
+    if (vel && (!(G >= 0.0) || max_iter < 1)) rc = ORC_E_ARG;
     int64_t mtot = 0, kept = 0;
     for (int64_t p = 0; p < np && rc == ORC_OK; p++) {
         int64_t mq;
@@ -739,11 +750,48 @@ int orc_multiscale(const float *pos, const float *mass, double mass_unit, int64_
         }
         if (rc) break;
         const double ncube = (double)cells, cell_q = (L / (double)ng) / (double)FRAC_ONE;
+        /* steps 7-8: density, particle count and cross-scale checks; kept
+         * groups ranked in seed (cell) order */
+        int64_t nkept_j = 0;
         for (int64_t c = 0; c < cells; c++) {
+            rank_c[c] = -1;
             if (lab[c] != c) continue;
             int keep = np_c[c] >= particle_th && (double)mq_c[c] * ncube >= (dens_th * (double)mtot) * (double)nc_c[c] &&
                        orc_cross_scale(C, ng, c, Cn, ngn);
-            if (!keep) continue;
+            if (keep) rank_c[c] = nkept_j++;
+        }
+        /* step 9: the self-boundness check of every kept group (Sec. 2.3);
+         * a discarded group is dropped, and the sums of a kept one are taken
+         * again over the members that stay (the ones that get its id) */
+        if (vel) {
+            for (int64_t p = 0; p < np; p++) grp[p] = (tmp[p] >= 0 && rank_c[tmp[p]] >= 0) ? (int32_t)rank_c[tmp[p]] : -1;
+            double mg;
+            rc = orc_unbind(pos, vel, mass, mass_unit, np, L, G, grp, nkept_j, max_iter, bound, nk_g, it_g, &mg);
+            if (rc) break;
+            if (mg < margin) margin = mg;
+            for (int64_t c = 0; c < cells; c++)
+                if (rank_c[c] >= 0) {
+                    if (nk_g[rank_c[c]] == 0) rank_c[c] = -1; /* discarded */
+                    np_c[c] = mq_c[c] = 0;
+                    mom[3 * c] = mom[3 * c + 1] = mom[3 * c + 2] = 0;
+                }
+            for (int64_t p = 0; p < np && rc == ORC_OK; p++) {
+                if (bound[p] < 0) continue;
+                const int32_t l = tmp[p];
+                int64_t q[3], mq;
+                for (int a = 0; a < 3 && rc == ORC_OK; a++) rc = quantise_coord(pos[3 * p + a], s, M, &q[a]);
+                if (rc == ORC_OK) rc = mass_quantum(mass, mass_unit, p, &mq);
+                if (rc) break;
+                int64_t sc[3] = {l % ng, (l / ng) % ng, l / ((int64_t)ng * ng)};
+                np_c[l] += 1;
+                mq_c[l] += mq;
+                for (int a = 0; a < 3; a++) mom[3 * l + a] += mq * min_image_q(q[a] - sc[a] * FRAC_ONE, M);
+            }
+            if (rc) break;
+        }
+        /* step 10: halo ids in seed order, the catalogue */
+        for (int64_t c = 0; c < cells; c++) {
+            if (rank_c[c] < 0) continue;
             hid_c[c] = (int32_t)kept;
             if (kept < cap) {
                 int64_t sc[3] = {c % ng, (c / ng) % ng, c / ((int64_t)ng * ng)};
@@ -765,9 +813,12 @@ int orc_multiscale(const float *pos, const float *mass, double mass_unit, int64_
             kept++;
         }
         for (int64_t p = 0; p < np; p++)
-            if (halo_id[p] < 0 && tmp[p] >= 0 && hid_c[tmp[p]] >= 0) halo_id[p] = hid_c[tmp[p]];
+            if (halo_id[p] < 0 && tmp[p] >= 0 && hid_c[tmp[p]] >= 0 && (!vel || bound[p] >= 0))
+                halo_id[p] = hid_c[tmp[p]];
     }
     free(lab); free(np_c); free(mq_c); free(nc_c); free(mom); free(tmp); free(hid_c);
+    free(grp); free(bound); free(nk_g); free(it_g); free(rank_c);
+    if (margin_out) *margin_out = margin;
     if (rc == ORC_OK) {
         *n_halo = kept;
         if (kept > cap) rc = ORC_E_CAPACITY;

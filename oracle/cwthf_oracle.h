@@ -39,8 +39,9 @@ float orc_corrected_peak(const float *C, int ng, int64_t s, int ng_next);
 int orc_cross_scale(const float *C, int ng, int64_t s, const float *Cn, int ng_next);
 int orc_multiscale(const float *pos, const float *mass, double mass_unit, int64_t np, double L, int n_scales,
                    const int *ngs, const float *const *fields, float cwt_min, double dens_th, int64_t particle_th,
-                   int32_t *halo_id, int64_t cap, int32_t *scale_out, int64_t *seed_out, int64_t *npart_out,
-                   int64_t *ncell_out, double *mass_out, double *centre_out, float *peak_out, int64_t *n_halo);
+                   const float *vel, double G, int max_iter, int32_t *halo_id, int64_t cap, int32_t *scale_out,
+                   int64_t *seed_out, int64_t *npart_out, int64_t *ncell_out, double *mass_out, double *centre_out,
+                   float *peak_out, int64_t *n_halo, double *margin_out);
 
 int orc_unbind(const float *pos, const float *vel, const float *mass, double mass_unit, int64_t np, double L,
                double G, const int32_t *group, int64_t n_groups, int max_iter, int32_t *out_group, int64_t *out_n,

@@ -99,3 +99,49 @@ def test_ids_are_kept_and_every_halo_is_consistent():
     in1 = (h1 >= 0) & (h1 < n1)
     np.testing.assert_array_equal(in1, (hid >= 0) & (hid < n1))
     np.testing.assert_array_equal(h1[in1], hid[in1])
+
+
+def _box_with_velocities(n=24000, L=40.0, seed=2):
+    from paper_2501_10622_gb300 import synth
+    pos, vel = synth.clumped_box(n, L, 40, seed=seed, velocities=True)
+    return pos.numpy(), vel.numpy(), synth.particle_mass(n, L)
+
+
+def test_self_boundness_in_the_loop_zero_velocities_change_nothing():
+    # no relative motion: every member is bound (0 > v_esc^2 never holds), so
+    # the loop with the check equals the loop without it
+    pos, vel, mp = _box_with_velocities()
+    ws, ngs = [1.5, 2.5], [24, 36]
+    a = oracle.find_multiscale(pos, 40.0, ws, ngs, mass_unit=mp)
+    b = oracle.find_multiscale(pos, 40.0, ws, ngs, mass_unit=mp, vel=np.zeros_like(vel))
+    np.testing.assert_array_equal(a["halo_id"], b["halo_id"])
+    for col in ("seed", "n_part", "mass", "centre", "scale"):
+        np.testing.assert_array_equal(a["cat"][col], b["cat"][col])
+    assert len(a["cat"]["seed"]) > 0
+
+
+def test_self_boundness_in_the_loop_no_gravity_discards_everything():
+    # G = 0: every member moving relative to its group's mean velocity is
+    # unbound, so every group loses more than 40 % and is discarded
+    pos, vel, mp = _box_with_velocities()
+    r = oracle.find_multiscale(pos, 40.0, [1.5, 2.5], [24, 36], mass_unit=mp, vel=vel, G=0.0)
+    assert len(r["cat"]["seed"]) == 0 and (r["halo_id"] < 0).all()
+
+
+def test_self_boundness_in_the_loop_halos_are_bound_and_consistent():
+    pos, vel, mp = _box_with_velocities()
+    L = 40.0
+    r = oracle.find_multiscale(pos, L, [1.5, 2.5, 3.5], [24, 36, 48], mass_unit=mp, vel=vel)
+    hid, cat = r["halo_id"], r["cat"]
+    n = len(cat["seed"])
+    assert n > 0 and r["cat"]["margin"] > 1e-9
+    # the catalogue describes exactly the particles holding each id
+    np.testing.assert_array_equal(np.bincount(hid[hid >= 0], minlength=n), cat["n_part"])
+    np.testing.assert_allclose(cat["mass"], cat["n_part"] * mp, rtol=1e-12)
+    # every final halo is bound: one more check of its members excludes no one
+    out, nk, it, _ = oracle.unbind(pos, vel, hid, L, G=oracle.G_MPC_KMS_MSUN, mass_unit=mp, n_groups=n)
+    np.testing.assert_array_equal(nk, cat["n_part"])
+    assert (it == 1).all()
+    # and the check changed the outcome against the loop without it
+    plain = oracle.find_multiscale(pos, L, [1.5, 2.5, 3.5], [24, 36, 48], mass_unit=mp)
+    assert not np.array_equal(plain["halo_id"], hid)
