@@ -139,7 +139,7 @@ CWTHF_API void cwthf_default_params(double w, cwthf_params *p);
  * is free fails with CWTHF_E_TABLE_CACHE (nothing queued). */
 CWTHF_API int cwthf_create(int device, int max_ng, int64_t max_np, int max_scales, cwthf_ctx **out);
 /* Optional parts of a context, for cwthf_create_ex and cwthf_workspace_bytes_ex. */
-#define CWTHF_CREATE_UNBIND 1u /* scratch of cwthf_unbind: 28 bytes per particle + 8 per group */
+#define CWTHF_CREATE_UNBIND 1u /* scratch of the self-boundness check: 36 bytes per particle + 24 per group */
 /* cwthf_create with optional parts (flags: CWTHF_CREATE_*; unknown bits ->
  * CWTHF_E_INVALID_ARG).  cwthf_create is this with flags 0. */
 CWTHF_API int cwthf_create_ex(int device, int max_ng, int64_t max_np, int max_scales, unsigned flags,
@@ -252,8 +252,7 @@ CWTHF_API int cwthf_find(cwthf_ctx *ctx, const float *pos, const float *mass, do
                int ng, const cwthf_params *params, int n_scales, int32_t *halo_id, cwthf_halo *cat,
                int64_t cat_cap, int64_t *n_halo, void *stream);
 
-/* Sec. 2 (step list 1-8 and 10; the self-boundness check of step 9 is not
- * part of it), Fig. 1, Sec. 2.2 with App. B, Sec. 2.4: the multi-scale
+/* Sec. 2 (step list 1-10), Fig. 1, Sec. 2.2 with App. B, Sec. 2.3, Sec. 2.4: the multi-scale
  * identification loop.  Scales are given from the largest physical scale
  * (smallest k_w) to the smallest: w[j] (1/length) on an ng[j]^3 grid (each a
  * supported size <= the context's max_ng; the paper's Int(400 k_w + 150)
@@ -270,8 +269,17 @@ CWTHF_API int cwthf_find(cwthf_ctx *ctx, const float *pos, const float *mass, do
  *     (5/16)(2 mean l2 - mean l1)(1 - (ng[j]/ng[j+1])^2)) exceeds the 2x2x2
  *     nodes of scale j+1's field enclosing the seed's position (exceeds 0
  *     after the last scale);
+ *   - with vel given (step 9), the particles of every kept group pass the
+ *     self-boundness check of cwthf_unbind (G, at most max_iter rounds): a
+ *     group that loses more than 40 % of them is dropped, and a kept group's
+ *     n_part, mass and centre are summed again over the members that stay
+ *     (the thresholds above are not applied again);
  *   - kept groups, in seed order, take the next halo ids; their particles
- *     keep them for good.
+ *     (with vel: the members that stayed) keep them for good; the others
+ *     remain free for the later scales.
+ *   vel       device, float [np][3] (velocities, the units of G), or NULL:
+ *             no self-boundness check; needs a context created with
+ *             CWTHF_CREATE_UNBIND
  *   w, ng     host, [n_scales], n_scales >= 1
  *   halo_id   device, int32 [np]: the particle's halo id, or -1
  *   cat       device, cwthf_ms_halo [cat_cap], halos in id order
@@ -279,8 +287,9 @@ CWTHF_API int cwthf_find(cwthf_ctx *ctx, const float *pos, const float *mass, do
  * Needs a context created with max_scales >= 2 (two fields are kept). */
 CWTHF_API int cwthf_find_multiscale(cwthf_ctx *ctx, const float *pos, const float *mass, double mass_unit,
                                     int64_t np, double L, int n_scales, const double *w, const int *ng,
-                                    float cwt_min, double dens_th, int64_t particle_th, int32_t *halo_id,
-                                    cwthf_ms_halo *cat, int64_t cat_cap, int64_t *n_halo, void *stream);
+                                    float cwt_min, double dens_th, int64_t particle_th, const float *vel, double G,
+                                    int max_iter, int32_t *halo_id, cwthf_ms_halo *cat, int64_t cat_cap,
+                                    int64_t *n_halo, void *stream);
 
 /* Sec. 2.3 (step 9 of the Sec. 2 step list): the self-boundness check of
  * every group, each on its own:

@@ -110,7 +110,7 @@ def lib() -> ctypes.CDLL:
         L.cwthf_assign.argtypes = [P, P, P, d, i64, d, i32, P, P, ctypes.POINTER(Params), P, P, i64, P, P]
         L.cwthf_find.argtypes = [P, P, P, d, i64, d, i32, ctypes.POINTER(Params), i32, P, P, i64, P, P]
         L.cwthf_find_multiscale.argtypes = [P, P, P, d, i64, d, i32, ctypes.POINTER(d), ctypes.POINTER(i32), f, d,
-                                            i64, P, P, i64, P, P]
+                                            i64, P, d, i32, P, P, i64, P, P]
         L.cwthf_unbind.argtypes = [P, P, P, P, d, i64, d, d, P, i64, i32, P, P, P, P]
         L.cwthf_sync.argtypes = [P, P]
         L.cwthf_error_string.argtypes = [i32]
@@ -349,11 +349,16 @@ class Context:
         return halo_id, cat, n_halo
 
     def find_multiscale(self, pos, L, ws, ngs, mass=None, mass_unit=1.0, cwt_min=0.0, dens_th=4.0, particle_th=15,
-                        cat_cap=1 << 20, halo_id=None, cat=None, n_halo=None, stream=None):
+                        cat_cap=1 << 20, halo_id=None, cat=None, n_halo=None, stream=None, vel=None,
+                        G=4.30091727e-9, max_iter=100):
         """The multi-scale loop over scales ws (largest physical scale first)
-        on grids ngs.  Returns (halo_id [np], catalogue bytes [cap, 64], n_halo [1])."""
+        on grids ngs; with velocities, the self-boundness check of every scale's
+        kept groups (a context created with unbind=True).  Returns
+        (halo_id [np], catalogue bytes [cap, 64], n_halo [1])."""
         t = self.torch
         pos = self._pos(pos)
+        if vel is not None:
+            vel = self._pos(vel)
         n = len(ws)
         if halo_id is None:
             halo_id = t.empty(pos.shape[0], dtype=t.int32, device=self.device)
@@ -364,8 +369,9 @@ class Context:
         wa = (ctypes.c_double * n)(*ws)
         na = (ctypes.c_int * n)(*ngs)
         _check(lib().cwthf_find_multiscale(self._h, _ptr(pos), _ptr(mass), float(mass_unit), pos.shape[0], float(L),
-                                           n, wa, na, float(cwt_min), float(dens_th), int(particle_th), _ptr(halo_id),
-                                           _ptr(cat), int(cat_cap), _ptr(n_halo), self._stream(stream)),
+                                           n, wa, na, float(cwt_min), float(dens_th), int(particle_th), _ptr(vel),
+                                           float(G), int(max_iter), _ptr(halo_id), _ptr(cat), int(cat_cap),
+                                           _ptr(n_halo), self._stream(stream)),
                "cwthf_find_multiscale")
         return halo_id, cat, n_halo
 

@@ -575,14 +575,94 @@ __global__ void __launch_bounds__(kThreads) k_ms_catalogue(const HaloAcc* __rest
     }
 }
 
-// Particles without a halo id whose group was kept take the halo's id.
-__global__ void __launch_bounds__(kThreads) k_ms_ids(const int32_t* __restrict__ pslot, int64_t np,
-                                                    const int32_t* __restrict__ slot_halo,
-                                                    int32_t* __restrict__ halo_id) {
+// The number of kept groups (keep_off[n_seeds]) as the check's group count.
+__global__ void k_ms_ub_count(const uint32_t* __restrict__ keep_off, const uint32_t* __restrict__ n_seeds,
+                              uint32_t* __restrict__ n_groups) {
+    *n_groups = keep_off[*n_seeds];
+}
+
+// The self-boundness check inside the loop (Sec. 2 step 9, Sec. 2.3): the
+// group of each candidate particle of a kept group (its rank among the kept
+// groups), or -1.
+__global__ void __launch_bounds__(kThreads) k_ms_ub_group(const int32_t* __restrict__ pslot,
+                                                         const int32_t* __restrict__ halo_id, int64_t np,
+                                                         const uint32_t* __restrict__ keep_off,
+                                                         int32_t* __restrict__ grp) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np; i += stride) {
         const int32_t sl = pslot[i];
+        int32_t g = -1;
         if (sl >= 0 && halo_id[i] < 0) {
+            const uint32_t r = keep_off[sl];
+            if (keep_off[sl + 1] != r) g = int32_t(r);
+        }
+        grp[i] = g;
+    }
+}
+
+// Kept groups that the check did not discard stay (flag per slot, scanned
+// into their ranks afterwards); their particle count, mass and first moment
+// are cleared, to be summed again over the members that stay.
+__global__ void __launch_bounds__(kThreads) k_ms_ub_keep(const uint32_t* __restrict__ n_seeds,
+                                                        const uint32_t* __restrict__ keep_off,
+                                                        const int64_t* __restrict__ n_kept, HaloAcc* acc,
+                                                        uint32_t* __restrict__ keep2) {
+    const uint32_t ns = *n_seeds;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < ns; s += stride) {
+        const uint32_t r = keep_off[s];
+        const bool kept = keep_off[s + 1] != r;
+        keep2[s] = (kept && n_kept[r] > 0) ? 1u : 0u;
+        if (kept) {
+            acc[s].n_part = 0;
+            acc[s].mq = 0;
+            acc[s].mom[0] = acc[s].mom[1] = acc[s].mom[2] = 0;
+        }
+    }
+}
+
+// The sums of the members that stay (bound[i] >= 0): count, integer mass and
+// first moment about the seed node, with the group sums' fixed-point rule on
+// this scale's grid.
+__global__ void __launch_bounds__(kThreads) k_ms_ub_sums(DepArgs a, const int32_t* __restrict__ pslot,
+                                                        const int32_t* __restrict__ bound,
+                                                        const int32_t* __restrict__ seed_list, HaloAcc* acc) {
+    const int N = a.ng;
+    const int64_t M = a.modulus;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < a.np; i += stride) {
+        if (bound[i] < 0) continue;
+        const int32_t sl = pslot[i];
+        int64_t q[3];
+        uint32_t mq;
+        const float* p = a.pos + 3 * i;
+        if (!quantise(p[0], a.scale_m, a.scale_e, M, q[0]) || !quantise(p[1], a.scale_m, a.scale_e, M, q[1]) ||
+            !quantise(p[2], a.scale_m, a.scale_e, M, q[2]) || mass_quantum(a, i, mq) != CWTHF_OK)
+            continue;  // (reported by the deposit of this scale)
+        const int32_t seed = seed_list[sl];
+        const int sc[3] = {seed % N, (seed / N) % N, seed / (N * N)};
+        HaloAcc* h = acc + sl;
+        atomicAdd(&h->n_part, 1ull);
+        atomicAdd(&h->mq, (u64)mq);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            int64_t dq = q[d] - int64_t(sc[d]) * kFracOne;
+            if (dq < 0) dq += M;
+            if (2 * dq >= M) dq -= M;  // minimum image in [-M/2, M/2)
+            atomicAdd(reinterpret_cast<u64*>(&h->mom[d]), u64((long long)mq * dq));
+        }
+    }
+}
+
+// Particles without a halo id whose group was kept take the halo's id (with
+// the self-boundness check: only the members that stayed).
+__global__ void __launch_bounds__(kThreads) k_ms_ids(const int32_t* __restrict__ pslot, int64_t np,
+                                                    const int32_t* __restrict__ slot_halo,
+                                                    const int32_t* __restrict__ bound, int32_t* __restrict__ halo_id) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np; i += stride) {
+        const int32_t sl = pslot[i];
+        if (sl >= 0 && halo_id[i] < 0 && (!bound || bound[i] >= 0)) {
             const int32_t id = slot_halo[sl];
             if (id >= 0) halo_id[i] = id;
         }
@@ -617,10 +697,10 @@ int ms_scale_sums(cwthf_ctx* ctx, const float* pos, const float* mass, double ma
     return cuda_status(cudaGetLastError());
 }
 
-int ms_finalize(cwthf_ctx* ctx, int64_t np, double L, int ng, double mass_unit, const float* C, const float* Cn,
-                int ngn, int scale, double dens_th, int64_t particle_th, const int32_t* pslot,
-                const unsigned long long* mtot, int32_t* halo_id, cwthf_ms_halo* cat, int64_t cat_cap,
-                int64_t* n_halo, cudaStream_t s) {
+int ms_finalize(cwthf_ctx* ctx, const float* pos, const float* mass, const float* vel, double G, int max_iter,
+                int64_t np, double L, int ng, double mass_unit, const float* C, const float* Cn, int ngn, int scale,
+                double dens_th, int64_t particle_th, const int32_t* pslot, const unsigned long long* mtot,
+                int32_t* halo_id, cwthf_ms_halo* cat, int64_t cat_cap, int64_t* n_halo, cudaStream_t s) {
     const int64_t slot_cap = int64_t(ng) * ng * ng / 8 + 8;
     const int blocks = ctx->sm_count * 8;
     const int pblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kThreads), int64_t(ctx->sm_count) * 16));
@@ -635,11 +715,32 @@ int ms_finalize(cwthf_ctx* ctx, int64_t np, double L, int ng, double mass_unit, 
                                                                            C, Cn, ngn, ctx->keep_off));
     int rc = scan_u32_dev(ctx, ctx->keep_off, ctx->keep_off, ctx->n_seeds, slot_cap, s);
     if (rc) return rc;
+    const uint32_t* keep = ctx->keep_off;  // ranks of the halos of this scale
+    const int32_t* bound = nullptr;
+    if (vel) {
+        // step 9: the self-boundness check of the kept groups' candidates
+        CWTHF_LAUNCH(ctx, s, "k_ms_ub_group",
+                     k_ms_ub_group<<<pblocks, kThreads, 0, s>>>(pslot, halo_id, np, ctx->keep_off, ctx->ub_grp));
+        CWTHF_LAUNCH(ctx, s, "k_ms_ub_count",
+                     k_ms_ub_count<<<1, 1, 0, s>>>(ctx->keep_off, ctx->n_seeds, ctx->ub_ngroups));
+        if ((rc = unbind_groups(ctx, pos, vel, mass, mass_unit, np, L, G, ctx->ub_grp, slot_cap, ctx->ub_ngroups,
+                                max_iter, ctx->ub_out, ctx->ub_nk, ctx->ub_it, s)))
+            return rc;
+        CWTHF_LAUNCH(ctx, s, "k_ms_ub_keep",
+                     k_ms_ub_keep<<<blocks, kThreads, 0, s>>>(ctx->n_seeds, ctx->keep_off, ctx->ub_nk, ctx->acc,
+                                                              ctx->ub_keep));
+        if ((rc = scan_u32_dev(ctx, ctx->ub_keep, ctx->ub_keep, ctx->n_seeds, slot_cap, s))) return rc;
+        const DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
+        CWTHF_LAUNCH(ctx, s, "k_ms_ub_sums",
+                     k_ms_ub_sums<<<pblocks, kThreads, 0, s>>>(a, pslot, ctx->ub_out, ctx->seed_list, ctx->acc));
+        keep = ctx->ub_keep;
+        bound = ctx->ub_out;
+    }
     CWTHF_LAUNCH(ctx, s, "k_ms_catalogue",
-                 k_ms_catalogue<<<blocks, kThreads, 0, s>>>(ctx->acc, ctx->seed_list, ctx->n_seeds, ctx->keep_off, f, C,
+                 k_ms_catalogue<<<blocks, kThreads, 0, s>>>(ctx->acc, ctx->seed_list, ctx->n_seeds, keep, f, C,
                                                             Cn, ngn, scale, n_halo, cat, ctx->slot_halo));
-    CWTHF_LAUNCH(ctx, s, "k_ms_ids", k_ms_ids<<<pblocks, kThreads, 0, s>>>(pslot, np, ctx->slot_halo, halo_id));
-    CWTHF_LAUNCH(ctx, s, "k_ms_advance", k_ms_advance<<<1, 1, 0, s>>>(ctx->keep_off, ctx->n_seeds, n_halo, cat_cap,
+    CWTHF_LAUNCH(ctx, s, "k_ms_ids", k_ms_ids<<<pblocks, kThreads, 0, s>>>(pslot, np, ctx->slot_halo, bound, halo_id));
+    CWTHF_LAUNCH(ctx, s, "k_ms_advance", k_ms_advance<<<1, 1, 0, s>>>(keep, ctx->n_seeds, n_halo, cat_cap,
                                                                      ctx->d_status));
     return cuda_status(cudaGetLastError());
 }

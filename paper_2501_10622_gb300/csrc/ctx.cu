@@ -96,12 +96,18 @@ void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, u
     const size_t groups = ms == 1 ? 0 : (ms == 2 ? 2 : (ms + 3) & ~size_t(3));
     f(reinterpret_cast<void**>(&c->part_slot), (size_t(z.np) * ms + 4) * 4 + size_t(z.np) * 4 * groups);
     f(reinterpret_cast<void**>(&c->jump_changed), sizeof(int) * kJumpWords);
-    if (flags & CWTHF_CREATE_UNBIND) {  // self-boundness check scratch (28 bytes per particle)
+    if (flags & CWTHF_CREATE_UNBIND) {  // self-boundness check scratch (36 bytes per particle + 24 per group)
         f(reinterpret_cast<void**>(&c->ub_off), size_t(z.slots + 2) * 4);
         f(reinterpret_cast<void**>(&c->ub_cur), size_t(z.slots + 1) * 4);
         f(reinterpret_cast<void**>(&c->ub_mem), size_t(z.np) * 4);
         f(reinterpret_cast<void**>(&c->ub_key), size_t(z.np) * 16);
         f(reinterpret_cast<void**>(&c->ub_val), size_t(z.np) * 8);
+        f(reinterpret_cast<void**>(&c->ub_grp), size_t(z.np) * 4);
+        f(reinterpret_cast<void**>(&c->ub_out), size_t(z.np) * 4);
+        f(reinterpret_cast<void**>(&c->ub_nk), size_t(z.slots + 1) * 8);
+        f(reinterpret_cast<void**>(&c->ub_it), size_t(z.slots + 1) * 4);
+        f(reinterpret_cast<void**>(&c->ub_keep), size_t(z.slots + 2) * 4);
+        f(reinterpret_cast<void**>(&c->ub_ngroups), 16);
     }
     f(reinterpret_cast<void**>(&c->scan_tmp), z.scan_words * 4);
     f(reinterpret_cast<void**>(&c->grid), size_t(z.cells) * 8);
@@ -383,9 +389,11 @@ int cwthf_find(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_
 
 int cwthf_find_multiscale(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L,
                           int n_scales, const double* w, const int* ng, float cwt_min, double dens_th,
-                          int64_t particle_th, int32_t* halo_id, cwthf_ms_halo* cat, int64_t cat_cap, int64_t* n_halo,
-                          void* stream) {
+                          int64_t particle_th, const float* vel, double G, int max_iter, int32_t* halo_id,
+                          cwthf_ms_halo* cat, int64_t cat_cap, int64_t* n_halo, void* stream) {
     if (!ctx || !w || !ng || n_scales < 1 || ctx->max_scales < 2) return CWTHF_E_INVALID_ARG;
+    if (vel && (!(ctx->flags & CWTHF_CREATE_UNBIND) || max_iter < 1 || !(G >= 0) || !std::isfinite(G)))
+        return CWTHF_E_INVALID_ARG;
     int rc = check_particles(ctx, pos, np, mass_unit);
     if (rc) return rc;
     if ((np > 0 && !halo_id) || cat_cap < 0 || (cat_cap > 0 && !cat) || !n_halo || std::isnan(cwt_min) ||
@@ -427,7 +435,8 @@ int cwthf_find_multiscale(cwthf_ctx* ctx, const float* pos, const float* mass, d
         if (j >= 1 && !rc) {  // decide scale j - 1 against scale j's field
             Range r2("scale: cross-scale check, thresholds, halo ids");
             const bool last = j == n_scales;
-            rc = ms_finalize(ctx, np, L, ng[j - 1], mass_unit, field[(j - 1) & 1], last ? nullptr : field[j & 1],
+            rc = ms_finalize(ctx, pos, mass, np > 0 ? vel : nullptr, G, max_iter, np, L, ng[j - 1], mass_unit,
+                             field[(j - 1) & 1], last ? nullptr : field[j & 1],
                              last ? 0 : ng[j], j - 1, dens_th, particle_th, pslot, mtot_all, halo_id, cat, cat_cap,
                              n_halo, s);
         }

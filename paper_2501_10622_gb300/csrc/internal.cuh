@@ -149,6 +149,12 @@ struct cwthf_ctx {
     int32_t* ub_mem = nullptr;    // [max_np] members, grouped
     uint64_t* ub_key = nullptr;   // [2 max_np] sort keys
     int32_t* ub_val = nullptr;    // [2 max_np] sort values
+    int32_t* ub_grp = nullptr;    // [max_np] the multi-scale loop's groups per particle
+    int32_t* ub_out = nullptr;    // [max_np] their groups after the check
+    int64_t* ub_nk = nullptr;     // [max groups] members kept per group
+    int32_t* ub_it = nullptr;     // [max groups] rounds per group
+    uint32_t* ub_keep = nullptr;  // [max groups + 2] groups that stay, then their ranks
+    uint32_t* ub_ngroups = nullptr;  // [1] groups of the check (device count)
 
     // cwthf_find internals
     int64_t* grid = nullptr;
@@ -326,6 +332,10 @@ int bin_particles(cwthf_ctx* ctx, const float* pos, const float* mass, double ma
 int unbind_impl(cwthf_ctx* ctx, const float* pos, const float* vel, const float* mass, double mass_unit, int64_t np,
                 double L, double G, const int32_t* group, int64_t n_groups, int max_iter, int32_t* group_out,
                 int64_t* n_kept, int32_t* iters, cudaStream_t s);
+// The same with the group count read from device memory (*d_groups <= n_groups).
+int unbind_groups(cwthf_ctx* ctx, const float* pos, const float* vel, const float* mass, double mass_unit, int64_t np,
+                  double L, double G, const int32_t* group, int64_t n_groups, const uint32_t* d_groups, int max_iter,
+                  int32_t* group_out, int64_t* n_kept, int32_t* iters, cudaStream_t s);
 // Forward half of the transform: x r2c and y c2c -> ctx spectrum `spec`.
 int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, float2* spec, cudaStream_t s);
 // The FFT twiddles of ng and the wavelet spectra of the n scales w[] for a box
@@ -361,10 +371,10 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
 // the next field Cn (nullptr after the last scale), the catalogue and the ids.
 int ms_scale_sums(cwthf_ctx* ctx, const float* pos, const float* mass, double mass_unit, int64_t np, double L, int ng,
                   const int32_t* halo_id, int32_t* pslot, cudaStream_t s);
-int ms_finalize(cwthf_ctx* ctx, int64_t np, double L, int ng, double mass_unit, const float* C, const float* Cn,
-                int ngn, int scale, double dens_th, int64_t particle_th, const int32_t* pslot,
-                const unsigned long long* mtot, int32_t* halo_id, cwthf_ms_halo* cat, int64_t cat_cap,
-                int64_t* n_halo, cudaStream_t s);
+int ms_finalize(cwthf_ctx* ctx, const float* pos, const float* mass, const float* vel, double G, int max_iter,
+                int64_t np, double L, int ng, double mass_unit, const float* C, const float* Cn, int ngn, int scale,
+                double dens_th, int64_t particle_th, const int32_t* pslot, const unsigned long long* mtot,
+                int32_t* halo_id, cwthf_ms_halo* cat, int64_t cat_cap, int64_t* n_halo, cudaStream_t s);
 void free_tables(cwthf_ctx* ctx);
 int init_tables(cwthf_ctx* ctx);
 // A caller's FFT plan for one pass of grid size ng (fft.cu); nst = 0 clears it.

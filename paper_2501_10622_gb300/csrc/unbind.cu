@@ -17,6 +17,7 @@
 // a bitonic sort of the radii (in shared memory for small groups, in the
 // group's slice of global scratch for large ones), chunked block scans for the
 // shell sums, and a stable compaction of the members that stay.
+#include <algorithm>
 #include <cmath>
 
 #include "internal.cuh"
@@ -31,8 +32,9 @@ constexpr int kUbSmemElems = 2048;  // groups up to this size sort in shared mem
 // Integer mass quanta (the deposit's rule): 1 when masses are equal, else
 // rint(m / mass_unit); invalid masses are reported once here.
 __global__ void k_ub_count(const float* __restrict__ mass, double mass_unit, const int32_t* __restrict__ group,
-                           int64_t np, int64_t n_groups, uint32_t* __restrict__ cnt, int32_t* __restrict__ group_out,
-                           int* status) {
+                           int64_t np, int64_t n_groups, const uint32_t* __restrict__ d_groups,
+                           uint32_t* __restrict__ cnt, int32_t* __restrict__ group_out, int* status) {
+    if (d_groups) n_groups = *d_groups;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np; i += stride) {
         group_out[i] = -1;
@@ -47,7 +49,9 @@ __global__ void k_ub_count(const float* __restrict__ mass, double mass_unit, con
 }
 
 __global__ void k_ub_scatter(const int32_t* __restrict__ group, int64_t np, int64_t n_groups,
-                             const uint32_t* __restrict__ off, uint32_t* __restrict__ cur, int32_t* __restrict__ mem) {
+                             const uint32_t* __restrict__ d_groups, const uint32_t* __restrict__ off,
+                             uint32_t* __restrict__ cur, int32_t* __restrict__ mem) {
+    if (d_groups) n_groups = *d_groups;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np; i += stride) {
         const int32_t g = group[i];
@@ -65,6 +69,8 @@ struct UbArgs {
     uint64_t* key;        // [2 np] sort keys (group g: from 2 off[g], a power of two >= its size)
     int32_t* val;         // [2 np] sort values
     int max_iter;
+    int64_t n_groups;            // groups (or read from d_groups when given)
+    const uint32_t* d_groups;
     int32_t* group_out;
     int64_t* n_kept;
     int32_t* iters;
@@ -182,12 +188,8 @@ __device__ __forceinline__ int pow2_ceil(int n) {
     return p;
 }
 
-__global__ void __launch_bounds__(kUbThreads) k_ub_group(UbArgs a) {
-    __shared__ uint64_t sk[kUbSmemElems];
-    __shared__ int32_t sv[kUbSmemElems];
-    __shared__ double shd[8 * kUbWarps];
-    __shared__ int64_t shi[kUbWarps + 1];
-    const int64_t g = blockIdx.x;
+// One group (all of the CTA's threads).
+__device__ void unbind_group(const UbArgs& a, int64_t g, uint64_t* sk, int32_t* sv, double* shd, int64_t* shi) {
     const uint32_t base = a.off[g];
     const int n0 = int(a.off[g + 1] - base);
     const int tid = threadIdx.x;
@@ -322,11 +324,25 @@ __global__ void __launch_bounds__(kUbThreads) k_ub_group(UbArgs a) {
     }
 }
 
+// A persistent grid over the groups: each CTA takes groups g, g + gridDim.x, ...
+__global__ void __launch_bounds__(kUbThreads) k_ub_group(UbArgs a) {
+    __shared__ uint64_t sk[kUbSmemElems];
+    __shared__ int32_t sv[kUbSmemElems];
+    __shared__ double shd[8 * kUbWarps];
+    __shared__ int64_t shi[kUbWarps + 1];
+    const int64_t n_groups = a.d_groups ? int64_t(*a.d_groups) : a.n_groups;
+    for (int64_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
+        unbind_group(a, g, sk, sv, shd, shi);
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
-int unbind_impl(cwthf_ctx* ctx, const float* pos, const float* vel, const float* mass, double mass_unit, int64_t np,
-                double L, double G, const int32_t* group, int64_t n_groups, int max_iter, int32_t* group_out,
-                int64_t* n_kept, int32_t* iters, cudaStream_t s) {
+int unbind_groups(cwthf_ctx* ctx, const float* pos, const float* vel, const float* mass, double mass_unit, int64_t np,
+                  double L, double G, const int32_t* group, int64_t n_groups, const uint32_t* d_groups, int max_iter,
+                  int32_t* group_out, int64_t* n_kept, int32_t* iters, cudaStream_t s) {
+    // n_groups: the groups, or with d_groups the most there can be
     uint32_t* cnt = ctx->ub_off;
     uint32_t* cur = ctx->ub_cur;
     cudaError_t e = cudaMemsetAsync(cnt, 0, size_t(n_groups + 1) * 4, s);
@@ -334,11 +350,13 @@ int unbind_impl(cwthf_ctx* ctx, const float* pos, const float* vel, const float*
     if (e != cudaSuccess) return cuda_status(e);
     const int blocks = ctx->sm_count * 8;
     CWTHF_LAUNCH(ctx, s, "k_ub_count",
-                 k_ub_count<<<blocks, 256, 0, s>>>(mass, mass_unit, group, np, n_groups, cnt, group_out, ctx->d_status));
-    int rc = scan_u32(ctx, cnt, cnt, n_groups, s);  // in place: offsets, cnt[n_groups] = members
+                 k_ub_count<<<blocks, 256, 0, s>>>(mass, mass_unit, group, np, n_groups, d_groups, cnt, group_out,
+                                                   ctx->d_status));
+    // in place: offsets, cnt[groups] = members
+    int rc = d_groups ? scan_u32_dev(ctx, cnt, cnt, d_groups, n_groups, s) : scan_u32(ctx, cnt, cnt, n_groups, s);
     if (rc) return rc;
     CWTHF_LAUNCH(ctx, s, "k_ub_scatter",
-                 k_ub_scatter<<<blocks, 256, 0, s>>>(group, np, n_groups, cnt, cur, ctx->ub_mem));
+                 k_ub_scatter<<<blocks, 256, 0, s>>>(group, np, n_groups, d_groups, cnt, cur, ctx->ub_mem));
     if (n_groups > 0) {
         UbArgs a;
         a.pos = pos;
@@ -352,12 +370,22 @@ int unbind_impl(cwthf_ctx* ctx, const float* pos, const float* vel, const float*
         a.key = ctx->ub_key;
         a.val = ctx->ub_val;
         a.max_iter = max_iter;
+        a.n_groups = n_groups;
+        a.d_groups = d_groups;
         a.group_out = group_out;
         a.n_kept = n_kept;
         a.iters = iters;
-        CWTHF_LAUNCH(ctx, s, "k_ub_group", k_ub_group<<<unsigned(n_groups), kUbThreads, 0, s>>>(a));
+        const unsigned grid = unsigned(std::min<int64_t>(n_groups, int64_t(ctx->sm_count) * 4));
+        CWTHF_LAUNCH(ctx, s, "k_ub_group", k_ub_group<<<grid, kUbThreads, 0, s>>>(a));
     }
     return cuda_status(cudaGetLastError());
+}
+
+int unbind_impl(cwthf_ctx* ctx, const float* pos, const float* vel, const float* mass, double mass_unit, int64_t np,
+                double L, double G, const int32_t* group, int64_t n_groups, int max_iter, int32_t* group_out,
+                int64_t* n_kept, int32_t* iters, cudaStream_t s) {
+    return unbind_groups(ctx, pos, vel, mass, mass_unit, np, L, G, group, n_groups, nullptr, max_iter, group_out,
+                         n_kept, iters, s);
 }
 
 }  // namespace cwthf

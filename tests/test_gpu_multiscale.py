@@ -111,3 +111,44 @@ def test_capacity_and_arguments(mctx):
         one.close()
     with pytest.raises(pkg.CwthfError):  # a grid beyond the context
         mctx.find_multiscale(pos, L, [2.0], [256])
+
+
+@pytest.fixture(scope="module")
+def uctx():
+    c = pkg.Context(0, max_ng=64, max_np=1 << 17, max_scales=2, unbind=True)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("ws,ngs", [((1.5, 2.5), (24, 36)), ((1.5, 2.5, 3.5), (24, 36, 48))])
+def test_self_boundness_in_the_loop_on_the_gpu_fields(uctx, ws, ngs):
+    # step 9 inside the loop: the oracle's loop with the check on the GPU's own
+    # fields gives the same halo ids and catalogue (a decision within 1e-9 of
+    # its threshold could fall either way; none comes that close here)
+    L = 40.0
+    pos, vel = synth.clumped_box(24000, L, 40, seed=2, velocities=True)
+    pos, vel = pos.numpy(), vel.numpy()
+    mp = synth.particle_mass(24000, L)
+    hid, cat, nh = uctx.find_multiscale(dev(pos), L, list(ws), list(ngs), mass_unit=mp, vel=dev(vel))
+    uctx.check()
+    fields = _gpu_fields(uctx, pos, L, ws, ngs, mass_unit=mp)
+    rhid, rcat = oracle.multiscale_on_fields(pos, L, fields, mass_unit=mp, vel=vel)
+    assert rcat["margin"] > 1e-9
+    n = int(nh[0])
+    assert n == len(rcat["seed"]) and n > 0
+    np.testing.assert_array_equal(hid.cpu().numpy(), rhid)
+    got = pkg.ms_catalogue_to_numpy(cat, n)
+    for col in ("seed", "n_part", "n_cells", "mass", "centre", "peak", "scale"):
+        np.testing.assert_array_equal(got[col], rcat[col], err_msg=col)
+    plain, _, np_plain = uctx.find_multiscale(dev(pos), L, list(ws), list(ngs), mass_unit=mp)
+    uctx.check()
+    record({"config": f"multi-scale loop with the self-boundness check, clumped 24000, L={L}, grids {list(ngs)}",
+            "halos": n, "halos_without_check": int(np_plain[0]),
+            "particles_in_halos": float(np.mean(rhid >= 0)),
+            "particles_in_halos_without_check": float(np.mean(plain.cpu().numpy() >= 0))})
+
+
+def test_self_boundness_in_the_loop_needs_its_scratch(mctx):
+    pos = dev(np.zeros((10, 3), np.float32))
+    with pytest.raises(pkg.CwthfError):
+        mctx.find_multiscale(pos, 10.0, [2.0], [32], vel=pos)
