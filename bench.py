@@ -130,36 +130,42 @@ def run_multiscale(args, dev):
     import paper_2501_10622_gb300 as pkg
     from paper_2501_10622_gb300 import synth
     L, npart = 50.0, 512 ** 3
-    pos = synth.clumped_box(npart, L, 200, seed=7, device=dev)
+    pos, vel = synth.clumped_box(npart, L, 200, seed=7, device=dev, velocities=True)
+    mp = synth.particle_mass(npart, L)
     kws, ws, ngs = pkg.paper_scales(L)
-    ctx = pkg.Context(dev.index or 0, max_ng=max(ngs), max_np=npart, max_scales=2)
+    ctx = pkg.Context(dev.index or 0, max_ng=max(ngs), max_np=npart, max_scales=2, unbind=True)
+    out = {}
     try:
         hid = torch.empty(npart, dtype=torch.int32, device=dev)
         cat = torch.empty((1 << 20, 64), dtype=torch.uint8, device=dev)
         nh = torch.zeros(1, dtype=torch.int64, device=dev)
         s = torch.cuda.current_stream(dev)
-        ctx.find_multiscale(pos, L, ws, ngs, halo_id=hid, cat=cat, n_halo=nh, cat_cap=1 << 20, stream=s)
-        ctx.check(what="multi-scale warm-up")
-        reps = max(1, min(args.steps, 2))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        for _ in range(reps):
-            ctx.find_multiscale(pos, L, ws, ngs, halo_id=hid, cat=cat, n_halo=nh, cat_cap=1 << 20, stream=s)
-        e1.record(s)
-        torch.cuda.synchronize(dev)
-        ctx.check(what="multi-scale")
-        ms = e0.elapsed_time(e1) / reps
-        n = int(nh[0])
-        got = pkg.ms_catalogue_to_numpy(cat, min(n, 1 << 20))
-        per_scale = [int((got["scale"] == j).sum()) for j in range(len(ws))]
-        assigned = float((hid >= 0).float().mean())
+        for key, v in (("", None), ("unbind_", vel)):
+            run = lambda: ctx.find_multiscale(pos, L, ws, ngs, mass_unit=mp, halo_id=hid, cat=cat, n_halo=nh,
+                                              cat_cap=1 << 20, stream=s, vel=v)
+            run()
+            ctx.check(what="multi-scale warm-up")
+            reps = max(1, min(args.steps, 2))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                run()
+            e1.record(s)
+            torch.cuda.synchronize(dev)
+            ctx.check(what="multi-scale")
+            ms = e0.elapsed_time(e1) / reps
+            n = int(nh[0])
+            got = pkg.ms_catalogue_to_numpy(cat, min(n, 1 << 20))
+            out.update({key + "ms": ms, key + "mparticles_per_s": npart / ms / 1e3, key + "halos": n,
+                        key + "halos_per_scale": [int((got["scale"] == j).sum()) for j in range(len(ws))],
+                        key + "particles_in_halos": float((hid >= 0).float().mean())})
     finally:
         ctx.close()
-        del pos
+        del pos, vel
         torch.cuda.empty_cache()
-    return {"workload": "512^3 clumped particles, L = 50 Mpc/h, 200 NFW clumps + 40 % uniform",
-            "k_w": kws, "grids": ngs, "ms": ms, "mparticles_per_s": npart / ms / 1e3, "halos": n,
-            "halos_per_scale": per_scale, "particles_in_halos": assigned,
+    return {"workload": "512^3 clumped particles, L = 50 Mpc/h, 200 NFW clumps + 40 % uniform; virial velocities "
+                        "for the unbind_ figures (self-boundness check of every scale's kept groups)",
+            "k_w": kws, "grids": ngs, **out,
             "paper": "about 3 h for the whole CWTHF catalogue (incl. unbinding) of SIMBA m50n512 on one process "
                      "of a dual Xeon E5-2678 v3 (Appendix A); context only"}
 
