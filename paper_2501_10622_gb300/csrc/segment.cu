@@ -27,15 +27,19 @@
 namespace cwthf {
 namespace {
 
-// Chain tiles: 32 x 16 x 32 cells, one warp per row of 32 columns.  Shared
-// parent pointers use the local index (lz * 16 + ly) * 32 + lx, so local
-// coordinates come back with shifts and masks.
-constexpr int kChTX = 32, kChTY = 16, kChTZ = 32;
+// Chain tiles: 64 x 16 x 16 cells, one warp per row of 64 columns, each lane
+// owning two adjacent columns (one 2-byte code load, one 8-byte pointer and
+// label store per cell pair).  Shared parent pointers use the local index
+// (lz * 16 + ly) * 64 + lx, so local coordinates come back with shifts and
+// masks.  A tile row's flagged cells go out as 32 masks: word 2 lz + p holds
+// plane lz's columns of parity p (bit = lane).
+constexpr int kChTX = 64, kChTY = 16, kChTZ = 16;
 constexpr int kChThreads = 32 * kChTY;  // 512
-constexpr int kPX = 32, kPXBits = 5;
-constexpr int kPlaneL = kPX * kChTY, kPlaneBits = 9;
+constexpr int kPX = 64, kPXBits = 6;
+constexpr int kPlaneL = kPX * kChTY, kPlaneBits = 10;
 constexpr int kLocal = kPlaneL * kChTZ;  // 16384 entries
-static_assert(kChTX == kPX && kPlaneL == (1 << kPlaneBits), "local index layout");
+constexpr int kRowWords = 2 * kChTZ;     // flagged-cell masks per tile row (32)
+static_assert(kChTX == kPX && kPlaneL == (1 << kPlaneBits) && kRowWords == 32, "local index layout");
 constexpr int32_t kFlag = 1 << 30;
 constexpr int32_t kMask = kFlag - 1;
 constexpr int kChaseLimit = 64;  // default: longest chain the global pass follows per cell before doubling rounds
@@ -269,7 +273,7 @@ __global__ void __launch_bounds__(kParThreads, kParBlocks) k_seg_parent(const fl
         parent_block<false, false>(C, N, cwt_min, code_out, seed_bits, status, x0, y0, z0, wzc, my_ring);
 }
 
-// In-tile chains of a 32 x 16 x 32-cell tile from the parent codes.  Every
+// In-tile chains of a 64 x 16 x 16-cell tile from the parent codes.  Every
 // cell's code becomes a shared-memory pointer (a local index, a seed's own
 // index, -1 for a maximum that is not a seed, or -2 - g for a parent g outside
 // the tile); pointer-jumping rounds over the whole tile then bring every
@@ -281,61 +285,67 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
                                                            int32_t* __restrict__ label,
                                                            uint32_t* __restrict__ seed_cells,
                                                            uint32_t* __restrict__ ballots, int* status) {
-    extern __shared__ int32_t ptr[];  // [kLocal], dynamic
+    extern __shared__ __align__(16) int32_t ptr[];  // [kLocal], dynamic
     __shared__ uint16_t tile_seeds[kTileSeedCap];
     __shared__ uint32_t n_tile_seeds;
-    const int N = ng;
+    const int N = ng;  // even
     const int ntx = (N + kChTX - 1) / kChTX, nty = (N + kChTY - 1) / kChTY;
     const int t = int(blockIdx.x);
     const int tx = t % ntx, ty = (t / ntx) % nty, tz = t / (ntx * nty);
     const int x0 = tx * kChTX, y0 = ty * kChTY, z0 = tz * kChTZ;
-    const int wx = min(kChTX, N - x0), wy = min(kChTY, N - y0), wz = min(kChTZ, N - z0);
-    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    const int wx = min(kChTX, N - x0), wy = min(kChTY, N - y0), wz = min(kChTZ, N - z0);  // wx even
+    const int lane = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    const int lx = 2 * lane;  // this lane's columns lx, lx + 1
     const bool own = lx < wx && ly < wy;
     const int xc = x0 + lx, yc = y0 + ly;
     const int32_t plane32 = N * N;
-    // global index pieces of the neighbours (one step, or across the periodic boundary)
-    const int32_t oxm = xc == 0 ? N - 1 : -1, oxp = xc == N - 1 ? -(N - 1) : 1;
+    // global index pieces of the neighbours (one step, or across the periodic
+    // boundary) of the even column xc and the odd column xc + 1
+    const int32_t oxm0 = xc == 0 ? N - 1 : -1, oxp1 = xc + 1 == N - 1 ? -(N - 1) : 1;
     const int32_t oym = yc == 0 ? (N - 1) * N : -N, oyp = yc == N - 1 ? -(N - 1) * N : N;
     if (threadIdx.x == 0) n_tile_seeds = 0;
     __syncthreads();
     const int i0 = ly * kPX + lx;
+    // a cell's shared-memory pointer from its parent code: a seed's own index,
+    // -1 for a maximum that is not a seed, a local index, or -2 - g for a
+    // parent g outside the tile
+    auto decode = [&](uint32_t code, int cx, int lz, int zc, int32_t g, int32_t oxm, int32_t oxp, int i) -> int32_t {
+        if ((code & 0x3fu) == kCodeMax) {
+            if (code & kCodeSeed) {
+                const uint32_t j = atomicAdd(&n_tile_seeds, 1u);
+                if (j < uint32_t(kTileSeedCap)) tile_seeds[j] = uint16_t(i);
+                return i;
+            }
+            return -1;
+        }
+        const int dx = int(code & 3u) - 1, dy = int((code >> 2) & 3u) - 1, dz = int((code >> 4) & 3u) - 1;
+        if (unsigned(cx + dx) < unsigned(wx) && unsigned(ly + dy) < unsigned(wy) && unsigned(lz + dz) < unsigned(wz))
+            return i + dx + dy * kPX + dz * kPlaneL;
+        const int32_t ozm = zc == 0 ? (N - 1) * plane32 : -plane32;
+        const int32_t ozp = zc == N - 1 ? -(N - 1) * plane32 : plane32;
+        return -2 - (g + (dx < 0 ? oxm : (dx > 0 ? oxp : 0)) + (dy < 0 ? oym : (dy > 0 ? oyp : 0)) +
+                     (dz < 0 ? ozm : (dz > 0 ? ozp : 0)));
+    };
     if (own) {
-        const int32_t grow = yc * N + xc;
+        const int32_t grow = yc * N + xc;  // even
         constexpr int kBatch = 8;  // planes whose codes are loaded together (independent loads in flight)
         for (int lb = 0; lb < wz; lb += kBatch) {
-        uint32_t cb[kBatch];
+            uint32_t cb[kBatch];
 #pragma unroll
-        for (int u = 0; u < kBatch; u++) cb[u] = lb + u < wz ? codes[(z0 + lb + u) * plane32 + grow] : 0u;
+            for (int u = 0; u < kBatch; u++)
+                cb[u] = lb + u < wz ? *reinterpret_cast<const uint16_t*>(codes + (z0 + lb + u) * plane32 + grow) : 0u;
 #pragma unroll
-        for (int u = 0; u < kBatch; u++) {
-            const int lz = lb + u;
-            if (lz >= wz) break;
-            const int zc = z0 + lz;
-            const int32_t g = zc * plane32 + grow;
-            const uint32_t code = cb[u];
-            const int i = i0 + lz * kPlaneL;
-            int32_t val;
-            if ((code & 0x3fu) == kCodeMax) {
-                val = (code & kCodeSeed) ? i : -1;
-                if (code & kCodeSeed) {
-                    const uint32_t j = atomicAdd(&n_tile_seeds, 1u);
-                    if (j < uint32_t(kTileSeedCap)) tile_seeds[j] = uint16_t(i);
-                }
-            } else {
-                const int dx = int(code & 3u) - 1, dy = int((code >> 2) & 3u) - 1, dz = int((code >> 4) & 3u) - 1;
-                if (unsigned(lx + dx) < unsigned(wx) && unsigned(ly + dy) < unsigned(wy) &&
-                    unsigned(lz + dz) < unsigned(wz)) {
-                    val = i + dx + dy * kPX + dz * kPlaneL;
-                } else {
-                    const int32_t ozm = zc == 0 ? (N - 1) * plane32 : -plane32;
-                    const int32_t ozp = zc == N - 1 ? -(N - 1) * plane32 : plane32;
-                    val = -2 - (g + (dx < 0 ? oxm : (dx > 0 ? oxp : 0)) + (dy < 0 ? oym : (dy > 0 ? oyp : 0)) +
-                                (dz < 0 ? ozm : (dz > 0 ? ozp : 0)));
-                }
+            for (int u = 0; u < kBatch; u++) {
+                const int lz = lb + u;
+                if (lz >= wz) break;
+                const int zc = z0 + lz;
+                const int32_t g = zc * plane32 + grow;
+                const int i = i0 + lz * kPlaneL;
+                int2 v;
+                v.x = decode(cb[u] & 0xffu, lx, lz, zc, g, oxm0, 1, i);
+                v.y = decode(cb[u] >> 8, lx + 1, lz, zc, g + 1, -1, oxp1, i + 1);
+                *reinterpret_cast<int2*>(&ptr[i]) = v;
             }
-            ptr[i] = val;
-        }
         }
     }
     __syncthreads();
@@ -344,9 +354,7 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
     // target's pointer, so a round triples the distance covered), until no
     // pointer changes.  A value read while another thread rewrites it is either
     // the old or the new pointer, both points of the same chain.
-    auto jump = [&](int lz, bool& changed) {
-        const int i = i0 + lz * kPlaneL;
-        const int32_t v = ptr[i];
+    auto jump1 = [&](int i, int32_t v, bool& changed) {
         if (v >= 0 && v != i) {
             int32_t w = ptr[v];
             if (w != v) {
@@ -355,6 +363,12 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
                 changed = true;
             }
         }
+    };
+    auto jump = [&](int lz, bool& changed) {
+        const int i = i0 + lz * kPlaneL;
+        const int2 v = *reinterpret_cast<const int2*>(&ptr[i]);
+        jump1(i, v.x, changed);
+        jump1(i + 1, v.y, changed);
     };
     for (int round = 0; round < kJumpRoundsInTile; round++) {
         bool changed = false;
@@ -371,41 +385,46 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
     // every pointer now names a root (its cell's seed), -1, or -2 - g (a cell
     // outside): labels, and one count per cell for the tile's seeds, kept in
     // the upper half of the seed's own entry (readers mask it off)
-    // Cells whose chain leaves the tile (flagged) are handed to the global pass
-    // as one 32-bit mask per row and plane of the tile (bit = column), written
-    // as the tile's [16 rows][32 planes] block of masks.
     const int32_t gbase = (z0 * N + y0) * N + x0;
     const unsigned full = 0xffffffffu;
+    auto finish = [&](int32_t v, bool& fl) -> int32_t {
+        const int32_t cur = v >= 0 ? (v & kLocalMask) : v;
+        if (cur == -1) return -1;
+        if (cur <= -2) {
+            fl = true;
+            return (-2 - cur) | kFlag;
+        }
+        const int px = cur & (kPX - 1), py = (cur >> kPXBits) & (kChTY - 1), pz = cur >> kPlaneBits;
+        const int32_t g = gbase + (pz * N + py) * N + px;
+        const int32_t nv = ptr[cur];
+        if (nv >= 0 && (nv & kLocalMask) == cur) {
+            atomicAdd(&ptr[cur], 1 << kCountShift);
+            return g;
+        }
+        fl = true;
+        return g | kFlag;  // not finished within the round bound: resume globally
+    };
     int32_t* out = label + (size_t(z0) * N + yc) * N + xc;
-    uint32_t* my_ballots = ballots + (size_t(t) * kChTY + ly) * kChTZ;
+    const bool vec = (reinterpret_cast<uintptr_t>(label) & 7u) == 0;  // xc is even: 8-byte label pairs
+    uint32_t* my_ballots = ballots + (size_t(t) * kChTY + ly) * kRowWords;
     for (int lz = 0; lz < kChTZ; lz++, out += size_t(plane32)) {  // block-uniform trip count
-        bool fl = false;
+        bool f0 = false, f1 = false;
         if (own && lz < wz) {
             const int i = i0 + lz * kPlaneL;
-            const int32_t v = ptr[i];
-            const int32_t cur = v >= 0 ? (v & kLocalMask) : v;
-            int32_t res;
-            if (cur == -1) {
-                res = -1;
-            } else if (cur <= -2) {
-                res = (-2 - cur) | kFlag;
-                fl = true;
+            const int2 v = *reinterpret_cast<const int2*>(&ptr[i]);
+            int2 res;
+            res.x = finish(v.x, f0);
+            res.y = finish(v.y, f1);
+            if (vec) {
+                *reinterpret_cast<int2*>(out) = res;
             } else {
-                const int px = cur & (kPX - 1), py = (cur >> kPXBits) & (kChTY - 1), pz = cur >> kPlaneBits;
-                const int32_t g = gbase + (pz * N + py) * N + px;
-                const int32_t nv = ptr[cur];
-                if (nv >= 0 && (nv & kLocalMask) == cur) {
-                    res = g;
-                    atomicAdd(&ptr[cur], 1 << kCountShift);
-                } else {
-                    res = g | kFlag;  // not finished within the round bound: resume globally
-                    fl = true;
-                }
+                out[0] = res.x;
+                out[1] = res.y;
             }
-            *out = res;
         }
-        const unsigned b = __ballot_sync(full, fl);
-        if (lx == lz) my_ballots[lz] = b;  // lane lz stores plane lz's mask (coalesced per warp)
+        const unsigned b0 = __ballot_sync(full, f0), b1 = __ballot_sync(full, f1);
+        if (lane == 2 * lz) my_ballots[2 * lz] = b0;  // plane lz, even columns
+        if (lane == 2 * lz + 1) my_ballots[2 * lz + 1] = b1;  // odd columns
     }
     __syncthreads();
     // in-tile cell counts of this tile's seeds (cells reaching them from other
@@ -521,14 +540,15 @@ __global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __rest
             const int yc = ty * kChTY + int(ly);
             if (yc >= N) continue;  // warp-uniform
             const int64_t rw = int64_t(t) * kChTY + ly;
-            const uint32_t mine = ballots[rw * kChTZ + lane];  // plane `lane`'s mask
-            uint32_t planes = __ballot_sync(full, mine != 0u);
-            const uint32_t cell0 = uint32_t((int64_t(tz) * kChTZ * N + yc) * N + int64_t(tx) * kChTX) + uint32_t(lane);
-            while (planes) {
-                const int lz = __ffs(planes) - 1;
-                planes &= planes - 1u;
-                const uint32_t b = __shfl_sync(full, mine, lz);
-                if (b & (1u << lane)) wl[k + __popc(b & lt)] = cell0 + uint32_t(lz) * plane32;
+            const uint32_t mine = ballots[rw * kRowWords + lane];  // plane lane / 2, columns of parity lane % 2
+            uint32_t words = __ballot_sync(full, mine != 0u);
+            const uint32_t cell0 =
+                uint32_t((int64_t(tz) * kChTZ * N + yc) * N + int64_t(tx) * kChTX) + 2u * uint32_t(lane);
+            while (words) {
+                const int wd = __ffs(words) - 1;
+                words &= words - 1u;
+                const uint32_t b = __shfl_sync(full, mine, wd);
+                if (b & (1u << lane)) wl[k + __popc(b & lt)] = cell0 + uint32_t(wd >> 1) * plane32 + uint32_t(wd & 1);
                 k += __popc(b);
                 if (k >= 32) {
                     __syncwarp();
@@ -764,7 +784,7 @@ int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_
     uint8_t* codes = reinterpret_cast<uint8_t*>(ctx->grid);
     uint32_t* ballots = reinterpret_cast<uint32_t*>(codes + (size_t(cells) + 255) / 256 * 256);
     const int64_t ntiles = int64_t(div_up(ng, kChTX)) * div_up(ng, kChTY) * div_up(ng, kChTZ);
-    if ((cells + 255) / 256 * 256 + ntiles * (kChTY * kChTZ * 4) > cells * 8) return CWTHF_E_UNSUPPORTED_SIZE;
+    if ((cells + 255) / 256 * 256 + ntiles * (kChTY * kRowWords * 4) > cells * 8) return CWTHF_E_UNSUPPORTED_SIZE;
     const int64_t pwarps = int64_t(div_up(ng, 30)) * div_up(ng, kParR) * div_up(ng, kParZ);
     CWTHF_LAUNCH(ctx, s, "k_seg_parent",
                  k_seg_parent<<<unsigned(div_up(pwarps, int64_t(kParWarps))), kParThreads, 0, s>>>(

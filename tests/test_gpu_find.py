@@ -117,8 +117,8 @@ def test_workload256_agreement(gctx):
 
 
 def test_ragged_grid_agreement(gctx):
-    # 48^3: the chain tiles (32 x 16 x 32) and the deposit tiles (32 x 8 x 8) end
-    # part-filled along x and z; same cell size and density as the 64^3 case
+    # 48^3: the chain tiles (64 x 16 x 16) end part-filled along x and the deposit
+    # tiles (32 x 8 x 8) along x; same cell size and density as the 64^3 case
     ng = 48
     box = ng * 0.78125
     pos = synth.clumped_box(ng ** 3, box, 84, seed=11).numpy()

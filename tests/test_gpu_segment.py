@@ -62,10 +62,10 @@ def test_nan_reported(gctx):
 
 def _zigzag_field(n=128, seed=21):
     """Three ascent chains that cross a chain-tile face at almost every step
-    (tiles are 32 x 16 x 32 cells along x, y, z), each hundreds of hops long,
+    (tiles are 64 x 16 x 16 cells along x, y, z), each hundreds of hops long,
     over a random background: chain A snakes along x over three z-planes with
     y alternating 15/16, chain B runs along x with z alternating 31/32, chain
-    C runs along y with x alternating 31/32.  The values rise along each chain
+    C runs along y with x alternating 63/64.  The values rise along each chain
     and stay clear of the periodic wrap, so the strict-order parent of every
     chain cell is the next chain cell (or a cell further along)."""
     rng = np.random.default_rng(seed)
@@ -80,7 +80,7 @@ def _zigzag_field(n=128, seed=21):
         C[z, 15 + (t & 1), x] = 100.0 + 0.5 * t
     for t, x in enumerate(range(1, n - 1)):
         C[31 + (t & 1), 40, x] = 300.0 + 0.5 * t
-        C[80, x, 31 + (t & 1)] = 500.0 + 0.5 * t
+        C[80, x, 63 + (t & 1)] = 500.0 + 0.5 * t
     return C
 
 
@@ -91,7 +91,7 @@ def _zigzag_chain_ends(n=128):
     t = n - 3
     return [(idx(4, 15, 1), idx(8, 15 + ((la - 1) & 1), n - 2)),
             (idx(31, 40, 1), idx(31 + (t & 1), 40, n - 2)),
-            (idx(80, 1, 31), idx(80, n - 2, 31 + (t & 1)))]
+            (idx(80, 1, 63), idx(80, n - 2, 63 + (t & 1)))]
 
 
 def _sizes_match_oracle(gctx, ref):
