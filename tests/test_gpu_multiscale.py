@@ -46,11 +46,13 @@ def _compare(ctx, pos, L, ws, ngs, mass=None, mass_unit=1.0, **kw):
     return got, rhid
 
 
-@pytest.mark.parametrize("ws,ngs", [((2.0, 3.0, 4.0), (32, 48, 64)), ((1.5, 2.5), (48, 36)), ((3.0,), (48,))])
+@pytest.mark.parametrize("ws,ngs", [((2.0, 3.0, 4.0), (32, 48, 64)), ((1.5, 2.5), (48, 36)), ((3.0,), (48,)),
+                                    ((1.0, 1.8, 2.6), (22, 38, 58))])
 def test_bit_exact_on_the_gpu_fields(mctx, ws, ngs):
     # the oracle's loop on the GPU's own fields: every halo id, every catalogue
-    # column (corrected peaks included) bit for bit; a coarser next grid and a
-    # single scale too
+    # column (corrected peaks included) bit for bit; a coarser next grid, a
+    # single scale, and grids of the paper's kind with large prime factors
+    # (22 = 2 11, 38 = 2 19, 58 = 2 29: Bluestein passes) too
     L = 37.5
     pos = synth.clumped_box(48 ** 3, L, 84, seed=11).numpy()
     got, hid = _compare(mctx, pos, L, list(ws), list(ngs))
