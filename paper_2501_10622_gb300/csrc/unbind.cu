@@ -163,33 +163,114 @@ __device__ void bitonic(K* k, int32_t* v, int P) {
         }
 }
 
-// Sorts the group's first P slots of (K, V), in shared memory when they fit.
-__device__ void sort_pairs(uint64_t* K, int32_t* V, int P, uint64_t* sk, int32_t* sv) {
+// Stable LSD radix sort (8-bit digits, the lowest nbytes bytes of the keys)
+// of the n pairs K[0..n), V[0..n), with K[n..2n), V[n..2n) as the other
+// buffer; the result ends in K[0..n), V[0..n).  Every warp owns a contiguous
+// chunk: per pass, per-warp digit counts (shared memory), their offsets
+// digit-major then warp by warp, and a scatter that keeps each warp's chunk in
+// order (lanes of one digit ranked by match_any).  A pass in which every key
+// has the same digit moves nothing and is skipped.  All threads of the block.
+__device__ void radix_sort_pairs(uint64_t* K, int32_t* V, int n, int nbytes, uint32_t* hist, int* skip) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int chunk = (n + nw - 1) / nw;
+    const int c0 = min(n, warp * chunk), c1 = min(n, c0 + chunk);
+    const uint32_t lt = (1u << lane) - 1u;
+    uint64_t *ka = K, *kb = K + n;
+    int32_t *va = V, *vb = V + n;
+    for (int pass = 0; pass < nbytes; pass++) {
+        const int sh = 8 * pass;
+        for (int i = threadIdx.x; i < nw * 256; i += blockDim.x) hist[i] = 0u;
+        if (threadIdx.x == 0) *skip = 0;
+        __syncthreads();
+        for (int k = c0 + lane; k < c1; k += 32) atomicAdd(&hist[warp * 256 + int((ka[k] >> sh) & 255u)], 1u);
+        __syncthreads();
+        // offsets: digit d's block starts after all smaller digits; within it, warp by warp
+        uint32_t tot = 0;
+        if (threadIdx.x < 256)
+            for (int w = 0; w < nw; w++) tot += hist[w * 256 + threadIdx.x];
+        if (threadIdx.x < 256 && tot == uint32_t(n)) *skip = 1;
+        // exclusive scan of the 256 digit totals (threads 0..255, 8 warps)
+        __shared__ uint32_t wsum[8];
+        uint32_t incl = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (threadIdx.x < 256 && lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            uint32_t base = incl - tot;
+            for (int w = 0; w < warp; w++) base += wsum[w];
+            for (int w = 0; w < nw; w++) {
+                const uint32_t c = hist[w * 256 + threadIdx.x];
+                hist[w * 256 + threadIdx.x] = base;
+                base += c;
+            }
+        }
+        __syncthreads();
+        if (*skip) {  // block-uniform; the barrier keeps the next pass's reset behind every read
+            __syncthreads();
+            continue;
+        }
+        uint32_t* off = hist + warp * 256;
+        for (int k0 = c0; k0 < c1; k0 += 32) {
+            const int k = k0 + lane;
+            const bool valid = k < c1;
+            const int d = valid ? int((ka[k] >> sh) & 255u) : 256;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (valid) {
+                const uint32_t pos = off[d] + __popc(peers & lt);
+                kb[pos] = ka[k];
+                vb[pos] = va[k];
+            }
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) off[d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        uint64_t* tk = ka;
+        ka = kb;
+        kb = tk;
+        int32_t* tv = va;
+        va = vb;
+        vb = tv;
+    }
+    if (ka != K) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            K[i] = ka[i];
+            V[i] = va[i];
+        }
+    }
+    __syncthreads();
+}
+
+// Sorts the group's first n pairs of (K, V) (keys below 2^(8 nbytes)): a
+// bitonic sort in shared memory when the padded length fits, else the radix
+// sort in the group's slice of global scratch (2n entries).
+__device__ void sort_pairs(uint64_t* K, int32_t* V, int n, int nbytes, uint64_t* sk, int32_t* sv, uint32_t* hist,
+                           int* skip) {
+    int P = 1;
+    while (P < n) P <<= 1;
     if (P <= kUbSmemElems) {
         for (int t = threadIdx.x; t < P; t += blockDim.x) {
-            sk[t] = K[t];
-            sv[t] = V[t];
+            sk[t] = t < n ? K[t] : ~0ull;
+            sv[t] = t < n ? V[t] : -1;
         }
         __syncthreads();
         bitonic(sk, sv, P);
-        for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        for (int t = threadIdx.x; t < n; t += blockDim.x) {
             K[t] = sk[t];
             V[t] = sv[t];
         }
         __syncthreads();
     } else {
-        bitonic(K, V, P);
+        radix_sort_pairs(K, V, n, nbytes, hist, skip);
     }
 }
 
-__device__ __forceinline__ int pow2_ceil(int n) {
-    int p = 1;
-    while (p < n) p <<= 1;
-    return p;
-}
-
 // One group (all of the CTA's threads).
-__device__ void unbind_group(const UbArgs& a, int64_t g, uint64_t* sk, int32_t* sv, double* shd, int64_t* shi) {
+__device__ void unbind_group(const UbArgs& a, int64_t g, uint64_t* sk, int32_t* sv, double* shd, int64_t* shi,
+                             uint32_t* hist, int* skip) {
     const uint32_t base = a.off[g];
     const int n0 = int(a.off[g + 1] - base);
     const int tid = threadIdx.x;
@@ -204,17 +285,14 @@ __device__ void unbind_group(const UbArgs& a, int64_t g, uint64_t* sk, int32_t* 
     uint64_t* K = a.key + 2 * size_t(base);
     int32_t* V = a.val + 2 * size_t(base);
     // members in particle order, so that every sum below runs in a fixed order
-    {
-        const int P = pow2_ceil(n0);
-        for (int t = tid; t < P; t += blockDim.x) {
-            K[t] = t < n0 ? uint64_t(uint32_t(X[t])) : ~0ull;
-            V[t] = t < n0 ? X[t] : -1;
-        }
-        __syncthreads();
-        sort_pairs(K, V, P, sk, sv);
-        for (int t = tid; t < n0; t += blockDim.x) X[t] = V[t];
-        __syncthreads();
+    for (int t = tid; t < n0; t += blockDim.x) {
+        K[t] = uint64_t(uint32_t(X[t]));
+        V[t] = X[t];
     }
+    __syncthreads();
+    sort_pairs(K, V, n0, 4, sk, sv, hist, skip);
+    for (int t = tid; t < n0; t += blockDim.x) X[t] = V[t];
+    __syncthreads();
     const float* a0 = a.pos + 3 * size_t(X[0]);
     const float ax = a0[0], ay = a0[1], az = a0[2];
     const double L = a.L, twoG = 2.0 * a.G;
@@ -241,24 +319,18 @@ __device__ void unbind_group(const UbArgs& a, int64_t g, uint64_t* sk, int32_t* 
         const double cx = M > 0.0 ? s[1] / M : 0.0, cy = M > 0.0 ? s[2] / M : 0.0, cz = M > 0.0 ? s[3] / M : 0.0;
         const double vx = M > 0.0 ? s[4] / M : 0.0, vy = M > 0.0 ? s[5] / M : 0.0, vz = M > 0.0 ? s[6] / M : 0.0;
         // radii about the centre, sorted
-        const int P = pow2_ceil(n);
-        for (int t = tid; t < P; t += blockDim.x) {
-            if (t < n) {
-                const int32_t i = X[t];
-                const float* p = a.pos + 3 * size_t(i);
-                const double dx = __dsub_rn(min_image(p[0], ax, L), cx);
-                const double dy = __dsub_rn(min_image(p[1], ay, L), cy);
-                const double dz = __dsub_rn(min_image(p[2], az, L), cz);
-                const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                K[t] = uint64_t(__double_as_longlong(__dsqrt_rn(r2)));  // r >= 0: the bits order like the values
-                V[t] = i;
-            } else {
-                K[t] = ~0ull;
-                V[t] = -1;
-            }
+        for (int t = tid; t < n; t += blockDim.x) {
+            const int32_t i = X[t];
+            const float* p = a.pos + 3 * size_t(i);
+            const double dx = __dsub_rn(min_image(p[0], ax, L), cx);
+            const double dy = __dsub_rn(min_image(p[1], ay, L), cy);
+            const double dz = __dsub_rn(min_image(p[2], az, L), cz);
+            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            K[t] = uint64_t(__double_as_longlong(__dsqrt_rn(r2)));  // r >= 0: the bits order like the values
+            V[t] = i;
         }
         __syncthreads();
-        sort_pairs(K, V, P, sk, sv);
+        sort_pairs(K, V, n, 8, sk, sv, hist, skip);
         // 2-3. shell sums per member and the exclusions.  Thread t walks the
         // chunk [t ch, (t+1) ch): mass before the chunk and m/r after it come
         // from block scans of the chunk totals.  Massive members at the centre
@@ -330,9 +402,11 @@ __global__ void __launch_bounds__(kUbThreads) k_ub_group(UbArgs a) {
     __shared__ int32_t sv[kUbSmemElems];
     __shared__ double shd[8 * kUbWarps];
     __shared__ int64_t shi[kUbWarps + 1];
+    __shared__ uint32_t hist[kUbWarps * 256];
+    __shared__ int skip;
     const int64_t n_groups = a.d_groups ? int64_t(*a.d_groups) : a.n_groups;
     for (int64_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
-        unbind_group(a, g, sk, sv, shd, shi);
+        unbind_group(a, g, sk, sv, shd, shi, hist, &skip);
         __syncthreads();
     }
 }
