@@ -65,23 +65,43 @@ __device__ __forceinline__ int nearest_node(int64_t q, int ng) {
     return n == ng ? 0 : n;
 }
 
+// Quotient by the grid size without a divide instruction: with
+// m = ceil(2^64 / d), the high word of n * m is floor(n / d) for every 32-bit
+// n and 2 <= d < 2^32 (n * m / 2^64 exceeds n / d by less than n / 2^64 < 1/d,
+// which cannot reach the next integer).
+struct FastDiv {
+    unsigned long long m;
+    uint32_t d;
+};
+inline FastDiv make_fastdiv(uint32_t d) { return {~0ull / d + 1ull, d}; }
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, FastDiv f) { return uint32_t(__umul64hi((unsigned long long)n, f.m)); }
+
 // Per-halo integer sums over the binned records.  A CTA takes kChunk
 // consecutive records at a time (records are grouped by deposit tile, a
 // 32 x 8 x 8-cell block, so a chunk covers a few neighbouring tiles and a
 // few dozen halos), kRecPerThread per thread with independent gather chains
 // (record -> label -> seed bitmap and prefix).  The chunk is first folded into
-// a small open-addressing table of halo slots in shared memory (exact 64-bit
-// sums from 32-bit atomics), then each table entry is added to the global
-// accumulators once; a record whose slot finds no entry within kProbe probes
-// goes straight to the global atomics.  A warp whose 32 records share one
-// halo is folded with warp reductions first.  Each record's halo slot (or -1)
-// is kept for the final pass, at rec_slot[r * slot_stride].
-constexpr int kHsThreads = 256, kHsCtasPerSm = 4;
+// a small open-addressing table of halo slots in shared memory, then each
+// table entry is added to the global accumulators once; a record whose slot
+// finds no entry within kProbe probes goes straight to the global atomics.  A
+// warp whose 32 records share one halo is folded with warp reductions first.
+// Each record's halo slot (or -1) is kept for the final pass, at
+// rec_slot[r * slot_stride].
+//
+// Equal masses (kMass false): a record's moment is its offset dq from the
+// seed, |dq| < ng 2^9 <= 2^20, so a chunk's sum per entry stays below 2^30 and
+// the table holds plain 32-bit integers.  Per-particle masses: products
+// m_q dq need 64 bits, kept exactly as two 32-bit words with the carry.
+constexpr int kHsThreads = 256;
+// resident CTAs per SM: registers (equal masses) or the 45 KB table (masses)
+template <bool kMass> constexpr int hs_ctas_per_sm() { return kMass ? 4 : 6; }
 constexpr int kTabBits = 10, kTab = 1 << kTabBits;  // table entries per CTA
 constexpr int kProbe = 16;
 constexpr int kRecPerThread = 4;
 constexpr int kChunk = kHsThreads * kRecPerThread;
 constexpr uint32_t kEmpty = 0xffffffffu;
+static_assert(int64_t(kChunk) * (int64_t(CWTHF_MAX_NG) << (CWTHF_FRAC_BITS - 1)) < (int64_t(1) << 31),
+              "a chunk's equal-mass moment sums must fit 32 bits");
 
 __device__ __forceinline__ void global_halo_add(HaloAcc* h, u64 cnt, u64 mq, u64 m0, u64 m1, u64 m2) {
     atomicAdd(&h->n_part, cnt);
@@ -91,7 +111,30 @@ __device__ __forceinline__ void global_halo_add(HaloAcc* h, u64 cnt, u64 mq, u64
     atomicAdd(reinterpret_cast<u64*>(&h->mom[2]), m2);
 }
 
-__global__ void __launch_bounds__(kHsThreads) k_halo_sums(DepArgs a, const uint32_t* __restrict__ total_ptr,
+// A 32-bit two's-complement sum as the 64-bit word the accumulators add.
+__device__ __forceinline__ u64 sext(uint32_t v) { return u64((long long)int32_t(v)); }
+__device__ __forceinline__ u64 sext(int32_t v) { return u64((long long)v); }
+
+// The table entry of halo slot `key`: found, or claimed (and listed in tused)
+// when an empty entry comes first; -1 after kProbe probes.
+__device__ __forceinline__ int table_find(uint32_t* tkey, uint32_t* tused, uint32_t* used, uint32_t key) {
+    uint32_t h = (key * 2654435761u) >> (32 - kTabBits);  // multiplicative hash
+    for (int pr = 0; pr < kProbe; pr++, h = (h + 1) & (kTab - 1)) {
+        uint32_t k = tkey[h];
+        if (k == kEmpty) {
+            k = atomicCAS(&tkey[h], kEmpty, key);
+            if (k == kEmpty) {
+                tused[atomicAdd(used, 1u)] = h;
+                return int(h);
+            }
+        }
+        if (k == key) return int(h);
+    }
+    return -1;
+}
+
+template <bool kMass>
+__global__ void __launch_bounds__(kHsThreads, hs_ctas_per_sm<kMass>()) k_halo_sums(DepArgs a, FastDiv divn, const uint32_t* __restrict__ total_ptr,
                                                        const unsigned long long* __restrict__ rec,
                                                        const uint32_t* __restrict__ rec_mq,
                                                        const int32_t* __restrict__ label,
@@ -100,21 +143,25 @@ __global__ void __launch_bounds__(kHsThreads) k_halo_sums(DepArgs a, const uint3
                                                        const uint32_t* __restrict__ n_slots, HaloAcc* acc,
                                                        int32_t* __restrict__ rec_slot, int slot_stride,
                                                        u64* __restrict__ mtot, int skip_marked) {
-    __shared__ uint32_t tkey[kTab], tcnt[kTab], tmq_lo[kTab], tmq_hi[kTab];
-    __shared__ uint32_t tm_lo[3][kTab], tm_hi[3][kTab];
-    __shared__ uint32_t tused[kTab];
+    constexpr int kW = kMass ? kTab : 1;  // the 64-bit words exist with masses only
+    __shared__ uint32_t tkey[kTab], tcnt[kTab], tused[kTab];
+    __shared__ uint32_t tm_lo[3][kTab];  // moments (equal masses: the whole 32-bit sum)
+    __shared__ uint32_t tm_hi[3][kW], tmq_lo[kW], tmq_hi[kW];
     __shared__ uint32_t n_used[2];
     const int lane = threadIdx.x & 31;
     const int N = a.ng;
-    const int64_t M = a.modulus;
+    const int32_t M = int32_t(a.modulus);
     const int64_t cells = int64_t(N) * N * N;
     const int64_t total = *total_ptr;  // records binned
     const uint32_t ns = *n_slots;
     for (int e = threadIdx.x; e < kTab; e += blockDim.x) {
         tkey[e] = kEmpty;
-        tcnt[e] = tmq_lo[e] = tmq_hi[e] = 0u;
+        tcnt[e] = 0u;
         tm_lo[0][e] = tm_lo[1][e] = tm_lo[2][e] = 0u;
-        tm_hi[0][e] = tm_hi[1][e] = tm_hi[2][e] = 0u;
+        if (kMass) {
+            tmq_lo[e] = tmq_hi[e] = 0u;
+            tm_hi[0][e] = tm_hi[1][e] = tm_hi[2][e] = 0u;
+        }
     }
     if (threadIdx.x < 2) n_used[threadIdx.x] = 0;
     __syncthreads();
@@ -123,7 +170,7 @@ __global__ void __launch_bounds__(kHsThreads) k_halo_sums(DepArgs a, const uint3
     for (int64_t c0 = int64_t(blockIdx.x) * kChunk; c0 < total; c0 += int64_t(gridDim.x) * kChunk, it ^= 1) {
         uint32_t* used = &n_used[it];
         // gathers for kRecPerThread records, warp-contiguous runs of 32
-        int64_t q[kRecPerThread][3];
+        u64 e[kRecPerThread];
         uint32_t mq[kRecPerThread];
         int32_t lab[kRecPerThread];
 #pragma unroll
@@ -131,18 +178,15 @@ __global__ void __launch_bounds__(kHsThreads) k_halo_sums(DepArgs a, const uint3
             const int64_t r = c0 + u * kHsThreads + threadIdx.x;
             mq[u] = 0;
             lab[u] = -1;
-            q[u][0] = q[u][1] = q[u][2] = 0;
+            e[u] = 0;
             if (r < total) {
-                const u64 e = rec[r];
-                mq[u] = a.mass ? rec_mq[r] : 1u;
-                q[u][0] = rec_q(e, 0);
-                q[u][1] = rec_q(e, 1);
-                q[u][2] = rec_q(e, 2);
+                e[u] = rec[r];
+                mq[u] = kMass ? rec_mq[r] : 1u;
                 // a record marked in bit 63 (its particle already holds a halo id)
                 // joins no group
-                if (!(skip_marked && (e >> 63)))
-                    lab[u] = label[(size_t(nearest_node(q[u][2], N)) * N + nearest_node(q[u][1], N)) * N +
-                                   nearest_node(q[u][0], N)];
+                if (!(skip_marked && (e[u] >> 63)))
+                    lab[u] = label[(size_t(nearest_node(rec_q(e[u], 2), N)) * N + nearest_node(rec_q(e[u], 1), N)) * N +
+                                   nearest_node(rec_q(e[u], 0), N)];
             }
         }
         uint32_t word[kRecPerThread], pre[kRecPerThread];
@@ -156,19 +200,20 @@ __global__ void __launch_bounds__(kHsThreads) k_halo_sums(DepArgs a, const uint3
         for (int u = 0; u < kRecPerThread; u++) {
             const int64_t r = c0 + u * kHsThreads + threadIdx.x;
             uint32_t key = kEmpty;
-            long long mom[3] = {0, 0, 0};
+            int32_t dq[3] = {0, 0, 0};
             if (r < total) {
                 const uint32_t bit = 1u << (lab[u] & 31);
                 const uint32_t slot = pre[u] + __popc(word[u] & (bit - 1u));
                 if ((word[u] & bit) && slot < ns) {
                     key = slot;
-                    const int sc[3] = {lab[u] % N, (lab[u] / N) % N, lab[u] / (N * N)};
+                    const uint32_t t = fdiv(uint32_t(lab[u]), divn), z = fdiv(t, divn);
+                    const int32_t sc[3] = {int32_t(uint32_t(lab[u]) - t * divn.d), int32_t(t - z * divn.d), int32_t(z)};
 #pragma unroll
                     for (int d = 0; d < 3; d++) {
-                        int64_t dq = q[u][d] - int64_t(sc[d]) * kFracOne;  // in (-M, M)
-                        if (dq < 0) dq += M;
-                        if (2 * dq >= M) dq -= M;  // minimum image in [-M/2, M/2)
-                        mom[d] = (long long)mq[u] * dq;
+                        int32_t v = rec_q(e[u], d) - (sc[d] << kFracBits);  // in (-M, M)
+                        if (v < 0) v += M;
+                        if (2 * v >= M) v -= M;  // minimum image in [-M/2, M/2)
+                        dq[d] = v;
                     }
                 }
                 rec_slot[r * slot_stride] = int32_t(key);  // kEmpty reads as -1
@@ -178,40 +223,46 @@ __global__ void __launch_bounds__(kHsThreads) k_halo_sums(DepArgs a, const uint3
             // shuffle runs on every lane)
             const uint32_t k0 = __shfl_sync(kFull, key, 0);
             const bool uniform = __all_sync(kFull, key == k0) && key != kEmpty;
-            u64 cnt = 1, m_sum = mq[u], m0 = u64(mom[0]), m1 = u64(mom[1]), m2 = u64(mom[2]);
-            if (uniform) {
-                cnt = 32;
-                m_sum = a.mass ? warp_sum32(mq[u]) : 32u;
-                m0 = warp_sum64(m0);
-                m1 = warp_sum64(m1);
-                m2 = warp_sum64(m2);
-            }
-            if (key != kEmpty && (!uniform || lane == 0)) {
-                // find or claim the table entry of this slot
-                uint32_t h = (key * 2654435761u) >> (32 - kTabBits);  // multiplicative hash
-                int found = -1;
-                for (int pr = 0; pr < kProbe; pr++, h = (h + 1) & (kTab - 1)) {
-                    uint32_t k = tkey[h];
-                    if (k == kEmpty) {
-                        k = atomicCAS(&tkey[h], kEmpty, key);
-                        if (k == kEmpty) {
-                            tused[atomicAdd(used, 1u)] = h;
-                            k = key;
-                        }
-                    }
-                    if (k == key) {
-                        found = int(h);
-                        break;
+            if (kMass) {
+                u64 cnt = 1, m_sum = mq[u];
+                u64 m[3];
+#pragma unroll
+                for (int d = 0; d < 3; d++) m[d] = u64((long long)mq[u] * dq[d]);
+                if (uniform) {
+                    cnt = 32;
+                    m_sum = warp_sum32(mq[u]);
+#pragma unroll
+                    for (int d = 0; d < 3; d++) m[d] = warp_sum64(m[d]);
+                }
+                if (key != kEmpty && (!uniform || lane == 0)) {
+                    const int f = table_find(tkey, tused, used, key);
+                    if (f >= 0) {
+                        atomicAdd(&tcnt[f], uint32_t(cnt));
+                        shared_add64(tmq_lo, tmq_hi, f, m_sum);
+#pragma unroll
+                        for (int d = 0; d < 3; d++) shared_add64(tm_lo[d], tm_hi[d], f, m[d]);
+                    } else {
+                        global_halo_add(acc + key, cnt, m_sum, m[0], m[1], m[2]);
                     }
                 }
-                if (found >= 0) {
-                    atomicAdd(&tcnt[found], uint32_t(cnt));
-                    if (a.mass) shared_add64(tmq_lo, tmq_hi, found, m_sum);
-                    shared_add64(tm_lo[0], tm_hi[0], found, m0);
-                    shared_add64(tm_lo[1], tm_hi[1], found, m1);
-                    shared_add64(tm_lo[2], tm_hi[2], found, m2);
-                } else {
-                    global_halo_add(acc + key, cnt, m_sum, m0, m1, m2);
+            } else {
+                uint32_t cnt = 1;
+                int32_t m[3] = {dq[0], dq[1], dq[2]};
+                if (uniform) {
+                    cnt = 32;
+#pragma unroll
+                    for (int d = 0; d < 3; d++) m[d] = __reduce_add_sync(kFull, m[d]);
+                }
+                if (key != kEmpty && (!uniform || lane == 0)) {
+                    const int f = table_find(tkey, tused, used, key);
+                    if (f >= 0) {
+                        atomicAdd(&tcnt[f], cnt);
+#pragma unroll
+                        for (int d = 0; d < 3; d++) atomicAdd(reinterpret_cast<int*>(&tm_lo[d][f]), m[d]);
+                    } else {
+                        global_halo_add(acc + key, cnt, cnt, sext(m[0]), sext(m[1]),
+                                        sext(m[2]));
+                    }
                 }
             }
         }
@@ -224,19 +275,45 @@ __global__ void __launch_bounds__(kHsThreads) k_halo_sums(DepArgs a, const uint3
         for (uint32_t j = threadIdx.x; j < nu; j += blockDim.x) {
             const uint32_t h = tused[j];
             const u64 c = tcnt[h];
-            const u64 mqs = a.mass ? ((u64(tmq_hi[h]) << 32) | tmq_lo[h]) : c;
-            global_halo_add(acc + tkey[h], c, mqs, (u64(tm_hi[0][h]) << 32) | tm_lo[0][h],
-                            (u64(tm_hi[1][h]) << 32) | tm_lo[1][h], (u64(tm_hi[2][h]) << 32) | tm_lo[2][h]);
+            if (kMass) {
+                global_halo_add(acc + tkey[h], c, (u64(tmq_hi[h]) << 32) | tmq_lo[h],
+                                (u64(tm_hi[0][h]) << 32) | tm_lo[0][h], (u64(tm_hi[1][h]) << 32) | tm_lo[1][h],
+                                (u64(tm_hi[2][h]) << 32) | tm_lo[2][h]);
+                tmq_lo[h] = tmq_hi[h] = 0u;
+                tm_hi[0][h] = tm_hi[1][h] = tm_hi[2][h] = 0u;
+            } else {  // the 32-bit sums sign-extended to the 64-bit accumulators
+                global_halo_add(acc + tkey[h], c, c, sext(tm_lo[0][h]),
+                                sext(tm_lo[1][h]), sext(tm_lo[2][h]));
+            }
             tkey[h] = kEmpty;
-            tcnt[h] = tmq_lo[h] = tmq_hi[h] = 0u;
+            tcnt[h] = 0u;
             tm_lo[0][h] = tm_lo[1][h] = tm_lo[2][h] = 0u;
-            tm_hi[0][h] = tm_hi[1][h] = tm_hi[2][h] = 0u;
         }
         __syncthreads();
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) msum += __shfl_xor_sync(kFull, msum, o);
     if (lane == 0 && msum) atomicAdd(mtot, msum);
+}
+
+// Launches the equal-mass or the per-particle-mass form of k_halo_sums: one
+// wave of resident CTAs (fewer for small inputs) striding over the chunks.
+void launch_halo_sums(cwthf_ctx* ctx, cudaStream_t s, int64_t np, const DepArgs& a, const uint32_t* total,
+                      const unsigned long long* rec, const uint32_t* rec_mq, const int32_t* label,
+                      const uint32_t* bits, const uint32_t* prefix, const uint32_t* n_slots, HaloAcc* acc,
+                      int32_t* rec_slot, int slot_stride, u64* mtot, int skip_marked) {
+    const FastDiv dn = make_fastdiv(uint32_t(a.ng));
+    const int64_t chunks = div_up(std::max<int64_t>(np, 1), kChunk);
+    if (a.mass)
+        CWTHF_LAUNCH(ctx, s, "k_halo_sums",
+                     k_halo_sums<true><<<int(std::min<int64_t>(chunks, int64_t(ctx->sm_count) * hs_ctas_per_sm<true>())),
+                                         kHsThreads, 0, s>>>(a, dn, total, rec, rec_mq, label, bits, prefix, n_slots,
+                                                             acc, rec_slot, slot_stride, mtot, skip_marked));
+    else
+        CWTHF_LAUNCH(ctx, s, "k_halo_sums",
+                     k_halo_sums<false><<<int(std::min<int64_t>(chunks, int64_t(ctx->sm_count) * hs_ctas_per_sm<false>())),
+                                          kHsThreads, 0, s>>>(a, dn, total, rec, rec_mq, label, bits, prefix, n_slots,
+                                                              acc, rec_slot, slot_stride, mtot, skip_marked));
 }
 
 struct FilterArgs {
@@ -685,14 +762,11 @@ int ms_scale_sums(cwthf_ctx* ctx, const float* pos, const float* mass, double ma
     const int64_t total_key = deposit_geom(ng).ntiles * kDepClasses;
     const uint32_t* total = ctx->dep_off + total_key;
     const int pblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kThreads), int64_t(ctx->sm_count) * 16));
-    const int cblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kChunk), int64_t(ctx->sm_count) * kHsCtasPerSm));
     CWTHF_LAUNCH(ctx, s, "k_ms_mark", k_ms_mark<<<pblocks, kThreads, 0, s>>>(halo_id, ctx->part_rec, np, total, ctx->dep_rec));
     DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
     int32_t* rec_slot = ctx->part_slot;
-    CWTHF_LAUNCH(ctx, s, "k_halo_sums",
-                 k_halo_sums<<<cblocks, kHsThreads, 0, s>>>(a, total, ctx->dep_rec, ctx->dep_mq, ctx->label,
-                                                          ctx->seed_bits, ctx->seed_prefix, ctx->n_seeds, ctx->acc,
-                                                          rec_slot, 1, ctx->d_mtot, 1));
+    launch_halo_sums(ctx, s, np, a, total, ctx->dep_rec, ctx->dep_mq, ctx->label, ctx->seed_bits,
+                     ctx->seed_prefix, ctx->n_seeds, ctx->acc, rec_slot, 1, ctx->d_mtot, 1);
     CWTHF_LAUNCH(ctx, s, "k_ms_pslot", k_ms_pslot<<<pblocks, kThreads, 0, s>>>(ctx->part_rec, np, total, rec_slot, pslot));
     return cuda_status(cudaGetLastError());
 }
@@ -765,11 +839,8 @@ int assign_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mass
     DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
     const int64_t total_key = deposit_geom(ng).ntiles * kDepClasses;  // dep_off[total_key] = records binned
     int pblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kThreads), int64_t(ctx->sm_count) * 16));
-    int cblocks = int(std::min<int64_t>(div_up(std::max<int64_t>(np, 1), kChunk), int64_t(ctx->sm_count) * kHsCtasPerSm));
-    CWTHF_LAUNCH(ctx, s, "k_halo_sums",
-                 k_halo_sums<<<cblocks, kHsThreads, 0, s>>>(a, ctx->dep_off + total_key, ctx->dep_rec, ctx->dep_mq,
-                                                          label, ctx->seed_bits, ctx->seed_prefix, d_nseeds, ctx->acc,
-                                                          ctx->part_slot + int64_t(scale) * np, 1, ctx->d_mtot, 0));
+    launch_halo_sums(ctx, s, np, a, ctx->dep_off + total_key, ctx->dep_rec, ctx->dep_mq, label, ctx->seed_bits,
+                     ctx->seed_prefix, d_nseeds, ctx->acc, ctx->part_slot + int64_t(scale) * np, 1, ctx->d_mtot, 0);
     FilterArgs f;
     f.ng = ng;
     f.L = L;
