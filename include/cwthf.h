@@ -139,7 +139,7 @@ CWTHF_API void cwthf_default_params(double w, cwthf_params *p);
  * is free fails with CWTHF_E_TABLE_CACHE (nothing queued). */
 CWTHF_API int cwthf_create(int device, int max_ng, int64_t max_np, int max_scales, cwthf_ctx **out);
 /* Optional parts of a context, for cwthf_create_ex and cwthf_workspace_bytes_ex. */
-#define CWTHF_CREATE_UNBIND 1u /* scratch of the self-boundness check: 36 bytes per particle + 24 per group */
+#define CWTHF_CREATE_UNBIND 1u /* scratch of the self-boundness check: 36 bytes per particle + 24 per group + 2.2 MB */
 /* cwthf_create with optional parts (flags: CWTHF_CREATE_*; unknown bits ->
  * CWTHF_E_INVALID_ARG).  cwthf_create is this with flags 0. */
 CWTHF_API int cwthf_create_ex(int device, int max_ng, int64_t max_np, int max_scales, unsigned flags,
@@ -391,6 +391,10 @@ CWTHF_API int cwthf_set_fft_plan(cwthf_ctx *ctx, int ng, int which, int C, const
  *       waits for `stream`.
  *   CWTHF_DEBUG_TABLE_FILLS (get only): table slots filled since the context
  *       was created (each a host-side table computation and one copy).
+ *   CWTHF_DEBUG_UNBIND_GRID_MIN  1..2^31-1 (default 65536): groups of the
+ *       self-boundness check with more members than this are processed by
+ *       the whole grid (one cooperative launch, one group at a time), smaller
+ *       ones by one CTA each; both give the same decisions up to rounding.
  * cwthf_debug_set returns CWTHF_E_INVALID_ARG for an unknown key or a value
  * out of range; settings persist for the context's lifetime. */
 #define CWTHF_DEBUG_JUMP_ROUNDS 1
@@ -398,6 +402,7 @@ CWTHF_API int cwthf_set_fft_plan(cwthf_ctx *ctx, int ng, int which, int C, const
 #define CWTHF_DEBUG_TMA_NO_COPY 3
 #define CWTHF_DEBUG_FALLBACK_RAN 4
 #define CWTHF_DEBUG_TABLE_FILLS 5
+#define CWTHF_DEBUG_UNBIND_GRID_MIN 6
 CWTHF_API int cwthf_debug_set(cwthf_ctx *ctx, int key, int64_t value);
 CWTHF_API int cwthf_debug_get(cwthf_ctx *ctx, int key, int64_t *value, void *stream);
 

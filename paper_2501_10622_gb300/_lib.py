@@ -27,6 +27,7 @@ FRAC_BITS = 10
 MIN_NG, MAX_NG = 8, 1024
 # cwthf_debug_set / cwthf_debug_get keys
 DEBUG_JUMP_ROUNDS, DEBUG_CHASE_LIMIT, DEBUG_TMA_NO_COPY, DEBUG_FALLBACK_RAN, DEBUG_TABLE_FILLS = 1, 2, 3, 4, 5
+DEBUG_UNBIND_GRID_MIN = 6
 
 HALO_DTYPE = np.dtype([("seed", "<i8"), ("n_part", "<i8"), ("n_cells", "<i8"), ("mass", "<f8"),
                        ("centre", "<f8", (3,)), ("peak", "<f4"), ("reserved", "<i4")])

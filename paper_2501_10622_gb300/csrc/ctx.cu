@@ -108,6 +108,10 @@ void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, u
         f(reinterpret_cast<void**>(&c->ub_it), size_t(z.slots + 1) * 4);
         f(reinterpret_cast<void**>(&c->ub_keep), size_t(z.slots + 2) * 4);
         f(reinterpret_cast<void**>(&c->ub_ngroups), 16);
+        // the whole-grid path for large groups: per-CTA partial sums and digit counts, barrier
+        f(reinterpret_cast<void**>(&c->ub_part), size_t(kUnbindGridCtaCap) * 16 * 8);
+        f(reinterpret_cast<void**>(&c->ub_hist), size_t(kUnbindGridCtaCap) * 2 * 256 * 4);
+        f(reinterpret_cast<void**>(&c->ub_bar), 16);
     }
     f(reinterpret_cast<void**>(&c->scan_tmp), z.scan_words * 4);
     f(reinterpret_cast<void**>(&c->grid), size_t(z.cells) * 8);
@@ -202,7 +206,9 @@ int cwthf_create_ex(int device, int max_ng, int64_t max_np, int max_scales, unsi
     c->max_scales = max_scales;
     c->flags = flags;
     if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        (c->fallback_blocks = fallback_blocks(c->sm_count)) <= 0) {
+        (c->fallback_blocks = fallback_blocks(c->sm_count)) <= 0 ||
+        ((flags & CWTHF_CREATE_UNBIND) &&
+         (c->ub_grid_blocks = std::min(unbind_grid_blocks(c->sm_count), kUnbindGridCtaCap)) <= 0)) {
         delete c;
         return CWTHF_E_CUDA;
     }
@@ -501,6 +507,10 @@ int cwthf_debug_set(cwthf_ctx* ctx, int key, int64_t value) {
         case CWTHF_DEBUG_TMA_NO_COPY:
             ctx->dbg_tma_no_copy = value != 0;
             return CWTHF_OK;
+        case CWTHF_DEBUG_UNBIND_GRID_MIN:
+            if (value < 1 || value >= (int64_t(1) << 31)) return CWTHF_E_INVALID_ARG;
+            ctx->dbg_unbind_grid_min = value;
+            return CWTHF_OK;
         default:
             return CWTHF_E_INVALID_ARG;
     }
@@ -512,6 +522,7 @@ int cwthf_debug_get(cwthf_ctx* ctx, int key, int64_t* value, void* stream) {
         case CWTHF_DEBUG_JUMP_ROUNDS: *value = ctx->dbg_jump_rounds; return CWTHF_OK;
         case CWTHF_DEBUG_CHASE_LIMIT: *value = ctx->dbg_chase_limit; return CWTHF_OK;
         case CWTHF_DEBUG_TMA_NO_COPY: *value = ctx->dbg_tma_no_copy; return CWTHF_OK;
+        case CWTHF_DEBUG_UNBIND_GRID_MIN: *value = ctx->dbg_unbind_grid_min; return CWTHF_OK;
         case CWTHF_DEBUG_TABLE_FILLS: {
             std::lock_guard<std::mutex> lk(ctx->table_mu);
             *value = int64_t(ctx->table_fills);

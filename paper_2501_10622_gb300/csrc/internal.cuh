@@ -2,6 +2,7 @@
 // libcwthf.so (not part of the public ABI; see include/cwthf.h).
 #pragma once
 
+#include <cuda/atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -48,6 +49,12 @@ constexpr int kJumpBarrier = kMaxJumpRounds + 2;
 constexpr int kJumpWords = kMaxJumpRounds + 4;
 // Default length of the resolve pass's bounded chain walks.
 constexpr int kDefaultChaseLimit = 64;
+
+// Groups of the self-boundness check with more members than this are
+// processed by the whole grid, one at a time; smaller ones by one CTA each.
+constexpr int64_t kUnbindGridMin = 1 << 16;
+// Most CTAs of that whole-grid launch (its per-CTA scratch is sized for them).
+constexpr int kUnbindGridCtaCap = 1024;
 
 // A bounded device wait gives up after this many polls.
 constexpr long long kSpinLimit = 1ll << 20;
@@ -155,6 +162,10 @@ struct cwthf_ctx {
     int32_t* ub_it = nullptr;     // [max groups] rounds per group
     uint32_t* ub_keep = nullptr;  // [max groups + 2] groups that stay, then their ranks
     uint32_t* ub_ngroups = nullptr;  // [1] groups of the check (device count)
+    double* ub_part = nullptr;       // [ub_grid_blocks][16] per-CTA partial sums of the whole-grid path
+    uint32_t* ub_hist = nullptr;     // [2][ub_grid_blocks][256] per-CTA digit counts of its radix sort
+    unsigned* ub_bar = nullptr;      // [2] its grid barrier
+    int ub_grid_blocks = 0;          // CTAs of the whole-grid path's cooperative launch
 
     // cwthf_find internals
     int64_t* grid = nullptr;
@@ -167,6 +178,7 @@ struct cwthf_ctx {
     int dbg_jump_rounds = cwthf::kMaxJumpRounds;
     int dbg_chase_limit = cwthf::kDefaultChaseLimit;
     int dbg_tma_no_copy = 0;  // one-shot: the next y/z FFT pass runs one CTA without its copy
+    int64_t dbg_unbind_grid_min = cwthf::kUnbindGridMin;  // groups above this size take the whole grid
 
     std::atomic<int64_t> launches{0};
 
@@ -202,6 +214,39 @@ namespace cwthf {
 
 // ---- status helpers ---------------------------------------------------------
 __device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
+
+// Bounded grid-wide barrier for kernels launched cooperatively (every CTA
+// resident).  bar[0] counts arrivals, bar[1] is the generation.  The wait
+// gives up after kSpinLimit polls, records CWTHF_E_TIMEOUT and returns false;
+// the CTA then leaves the kernel.  Data that other CTAs wrote before the
+// barrier is read with L1-bypassing loads (__ldcg) after it.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* status) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(bar[0]), gen(bar[1]);
+        const unsigned g = gen.load(cuda::memory_order_acquire);
+        __threadfence();
+        if (cnt.fetch_add(1u, cuda::memory_order_acq_rel) == gridDim.x - 1) {
+            cnt.store(0u, cuda::memory_order_relaxed);
+            gen.store(g + 1u, cuda::memory_order_release);
+        } else {
+            long long it = 0;
+            while (gen.load(cuda::memory_order_acquire) == g) {
+                if (++it > kSpinLimit) {
+                    ok = 0;
+                    set_status(status, CWTHF_E_TIMEOUT);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
 
 // Slot (rank among all seeds, in cell order) of seed cell `lab`, from the seed
 // bitmap and its per-word popcount prefix; false if lab is not a seed or its
@@ -353,6 +398,8 @@ int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_
                  cudaStream_t s);
 // CTAs of the segmentation fallback's cooperative launch (-1 on failure).
 int fallback_blocks(int sm_count);
+// CTAs of the self-boundness check's whole-grid launch (-1 on failure).
+int unbind_grid_blocks(int sm_count);
 // Seeds of the last segmentation and the cell count of each segment.
 int segment_sizes_impl(cwthf_ctx* ctx, int32_t* seeds, int64_t* n_cells, int64_t cap, int64_t* n_seeds,
                        cudaStream_t s);

@@ -580,38 +580,6 @@ __global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __rest
     if (__any_sync(full, left) && lane == 0) changed[0] = 1;
 }
 
-// Bounded grid-wide barrier of the fallback kernel, which is launched
-// cooperatively (every CTA resident).  bar[0] counts arrivals, bar[1] is the
-// generation.  The wait gives up after kSpinLimit polls, records
-// CWTHF_E_TIMEOUT and returns false; the CTA then leaves the kernel.
-__device__ bool grid_sync(unsigned* bar, int* status) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        cuda::atomic_ref<unsigned, cuda::thread_scope_device> cnt(bar[0]), gen(bar[1]);
-        const unsigned g = gen.load(cuda::memory_order_acquire);
-        __threadfence();
-        if (cnt.fetch_add(1u, cuda::memory_order_acq_rel) == gridDim.x - 1) {
-            cnt.store(0u, cuda::memory_order_relaxed);
-            gen.store(g + 1u, cuda::memory_order_release);
-        } else {
-            long long it = 0;
-            while (gen.load(cuda::memory_order_acquire) == g) {
-                if (++it > kSpinLimit) {
-                    ok = 0;
-                    set_status(status, CWTHF_E_TIMEOUT);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
 // Fallback for chains that outlived the bounded walks (changed[0] set by the
 // resolve pass); returns at once otherwise.  Round r (1 <= r <= rounds)
 // replaces every flagged pointer by its target's label, which moves it 2^(r-1)

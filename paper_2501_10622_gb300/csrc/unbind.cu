@@ -14,9 +14,11 @@
 //   4. steps 1-3 repeat until nothing is excluded (at most max_iter rounds);
 //   5. a group that lost more than 40 % of its particles is discarded.
 // Each round: fixed-order block reductions (the sums do not depend on timing),
-// a bitonic sort of the radii (in shared memory for small groups, in the
-// group's slice of global scratch for large ones), chunked block scans for the
-// shell sums, and a stable compaction of the members that stay.
+// a sort of the radii (bitonic in shared memory for small groups, a stable
+// radix sort in the group's slice of global scratch for larger ones), chunked
+// block scans for the shell sums, and a stable compaction of the members that
+// stay.  Groups above a size threshold are processed by the whole grid instead
+// (k_ub_grid, one group at a time), with the same steps over per-CTA chunks.
 #include <algorithm>
 #include <cmath>
 
@@ -69,6 +71,7 @@ struct UbArgs {
     uint64_t* key;        // [2 np] sort keys (group g: from 2 off[g], a power of two >= its size)
     int32_t* val;         // [2 np] sort values
     int max_iter;
+    int64_t grid_min;            // larger groups are left to the whole-grid path
     int64_t n_groups;            // groups (or read from d_groups when given)
     const uint32_t* d_groups;
     int32_t* group_out;
@@ -274,6 +277,7 @@ __device__ void unbind_group(const UbArgs& a, int64_t g, uint64_t* sk, int32_t* 
     const uint32_t base = a.off[g];
     const int n0 = int(a.off[g + 1] - base);
     const int tid = threadIdx.x;
+    if (int64_t(n0) > a.grid_min) return;  // the whole-grid path's group
     if (n0 == 0) {
         if (tid == 0) {
             a.n_kept[g] = 0;
@@ -396,6 +400,317 @@ __device__ void unbind_group(const UbArgs& a, int64_t g, uint64_t* sk, int32_t* 
     }
 }
 
+// ---- the whole-grid path: one large group at a time, every CTA ---------------
+//
+// The same steps as unbind_group, with each CTA owning a contiguous chunk of
+// the group's members and grid barriers between the phases.  Partial sums go
+// through per-CTA slots and are combined in CTA order by every CTA, so the
+// sums do not depend on timing either; the radix sort takes per-CTA digit
+// counts, so its scatter keeps (CTA, warp, member) order and stays stable.
+// Cross-CTA data is read with __ldcg after the barriers (L1 is not coherent).
+
+constexpr int kUbPart = 16;  // per-CTA partial slots: 0-6 centre of mass, 8-10 shell sums, 11 kept
+
+struct UbGrid {
+    double* part;    // [gridDim][kUbPart]
+    uint32_t* hist;  // [2][gridDim][256] by pass parity
+    unsigned* bar;
+    int* status;
+};
+
+// [b, e) of the CTA's chunk of n members
+__device__ __forceinline__ void cta_chunk(int n, int& b, int& e) {
+    const int ch = (n + int(gridDim.x) - 1) / int(gridDim.x);
+    b = min(n, int(blockIdx.x) * ch);
+    e = min(n, b + ch);
+}
+
+// Sums over the CTAs of partial slot k, in CTA order: over all CTAs (*all)
+// and over the CTAs before this one (returned).  Thread-local.
+__device__ __forceinline__ double part_prefix(const double* part, int k, double* all) {
+    double s = 0.0, before = 0.0;
+    for (int c = 0; c < int(gridDim.x); c++) {
+        if (c == int(blockIdx.x)) before = s;
+        s += __ldcg(part + size_t(c) * kUbPart + k);
+    }
+    *all = s;
+    return before;
+}
+
+// The stable LSD radix sort of radix_sort_pairs over the whole grid: the
+// digit offsets add the counts of all CTAs before this one.  Returns false on
+// a barrier timeout.
+__device__ bool grid_radix(uint64_t* K, int32_t* V, int n, int nbytes, const UbGrid& b, uint32_t* hist,
+                           uint32_t* dsum, uint32_t* dbase, int* skip, int& parity) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    int C0, C1;
+    cta_chunk(n, C0, C1);
+    const int wch = (C1 - C0 + nw - 1) / nw;
+    const int w0 = min(C1, C0 + warp * wch), w1 = min(C1, w0 + wch);
+    const uint32_t lt = (1u << lane) - 1u;
+    __shared__ uint32_t wsum[8];
+    uint64_t *ka = K, *kb = K + n;
+    int32_t *va = V, *vb = V + n;
+    for (int pass = 0; pass < nbytes; pass++) {
+        const int sh = 8 * pass;
+        for (int i = tid; i < nw * 256; i += blockDim.x) hist[i] = 0u;
+        if (tid == 0) *skip = 0;
+        __syncthreads();
+        for (int k = w0 + lane; k < w1; k += 32) atomicAdd(&hist[warp * 256 + int((__ldcg(ka + k) >> sh) & 255u)], 1u);
+        __syncthreads();
+        uint32_t* gh = b.hist + (size_t(parity) * gridDim.x + blockIdx.x) * 256;
+        if (tid < 256) {
+            uint32_t t = 0;
+            for (int w = 0; w < nw; w++) t += hist[w * 256 + tid];
+            gh[tid] = t;
+        }
+        if (!grid_sync(b.bar, b.status)) return false;
+        if (tid < 256) {
+            uint32_t all = 0, before = 0;
+            const uint32_t* col = b.hist + size_t(parity) * gridDim.x * 256 + tid;
+            for (int c = 0; c < int(gridDim.x); c++) {
+                if (c == int(blockIdx.x)) before = all;
+                all += __ldcg(col + size_t(c) * 256);
+            }
+            dsum[tid] = all;
+            dbase[tid] = before;
+            if (all == uint32_t(n)) *skip = 1;
+        }
+        parity ^= 1;  // the next pass writes the other copy while slower CTAs may still read this one
+        __syncthreads();
+        if (*skip) {  // the same decision in every CTA (same totals)
+            __syncthreads();
+            continue;
+        }
+        // digit d starts after all smaller digits of every CTA, then after the
+        // CTAs before this one, then warp by warp
+        const uint32_t tot = tid < 256 ? dsum[tid] : 0u;
+        uint32_t incl = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (tid < 256 && lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (tid < 256) {
+            uint32_t base = incl - tot + dbase[tid];
+            for (int w = 0; w < warp; w++) base += wsum[w];
+            for (int w = 0; w < nw; w++) {
+                const uint32_t c = hist[w * 256 + tid];
+                hist[w * 256 + tid] = base;
+                base += c;
+            }
+        }
+        __syncthreads();
+        uint32_t* off = hist + warp * 256;
+        for (int k0 = w0; k0 < w1; k0 += 32) {
+            const int k = k0 + lane;
+            const bool valid = k < w1;
+            const uint64_t key = valid ? __ldcg(ka + k) : 0ull;
+            const int d = valid ? int((key >> sh) & 255u) : 256;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (valid) {
+                const uint32_t pos = off[d] + __popc(peers & lt);
+                kb[pos] = key;
+                vb[pos] = __ldcg(va + k);
+            }
+            __syncwarp();
+            if (valid && lane == __ffs(peers) - 1) off[d] += __popc(peers);
+            __syncwarp();
+        }
+        if (!grid_sync(b.bar, b.status)) return false;  // every scatter lands before the next pass reads
+        uint64_t* tk = ka;
+        ka = kb;
+        kb = tk;
+        int32_t* tv = va;
+        va = vb;
+        vb = tv;
+    }
+    if (ka != K) {
+        for (int i = C0 + tid; i < C1; i += blockDim.x) {
+            K[i] = __ldcg(ka + i);
+            V[i] = __ldcg(va + i);
+        }
+        if (!grid_sync(b.bar, b.status)) return false;
+    }
+    return true;
+}
+
+// One group with every CTA of the grid.  Returns false on a barrier timeout.
+__device__ bool unbind_group_grid(const UbArgs& a, const UbGrid& b, int64_t g, double* shd, int64_t* shi,
+                                  uint32_t* hist, uint32_t* dsum, uint32_t* dbase, int* skip, int& parity) {
+    __shared__ double bc[8];
+    const uint32_t base = a.off[g];
+    const int n0 = int(a.off[g + 1] - base);
+    const int tid = threadIdx.x;
+    double* mypart = b.part + size_t(blockIdx.x) * kUbPart;
+    int32_t* X = a.mem + base;
+    uint64_t* K = a.key + 2 * size_t(base);
+    int32_t* V = a.val + 2 * size_t(base);
+    int C0, C1;
+    // members in particle order
+    cta_chunk(n0, C0, C1);
+    for (int t = C0 + tid; t < C1; t += blockDim.x) {
+        const int32_t i = X[t];
+        K[t] = uint64_t(uint32_t(i));
+        V[t] = i;
+    }
+    if (!grid_sync(b.bar, b.status)) return false;
+    if (!grid_radix(K, V, n0, 4, b, hist, dsum, dbase, skip, parity)) return false;
+    for (int t = C0 + tid; t < C1; t += blockDim.x) X[t] = __ldcg(V + t);
+    if (!grid_sync(b.bar, b.status)) return false;
+    const int32_t first = __ldcg(X);
+    const float* a0 = a.pos + 3 * size_t(first);
+    const float ax = a0[0], ay = a0[1], az = a0[2];
+    const double L = a.L, twoG = 2.0 * a.G;
+    int n = n0, it = 0;
+    while (it < a.max_iter) {
+        it++;
+        cta_chunk(n, C0, C1);
+        // 1. centre of mass and mean velocity: CTA sums, then all CTAs in order
+        double s[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int k = C0 + tid; k < C1; k += blockDim.x) {
+            const int32_t i = __ldcg(X + k);
+            const double m = mass_of(a, i);
+            const float* p = a.pos + 3 * size_t(i);
+            const float* v = a.vel + 3 * size_t(i);
+            s[0] += m;
+            s[1] += m * min_image(p[0], ax, L);
+            s[2] += m * min_image(p[1], ay, L);
+            s[3] += m * min_image(p[2], az, L);
+            s[4] += m * double(v[0]);
+            s[5] += m * double(v[1]);
+            s[6] += m * double(v[2]);
+        }
+        block_sums<7>(s, shd);
+        if (tid < 7) mypart[tid] = s[tid];
+        if (!grid_sync(b.bar, b.status)) return false;
+        if (tid < 7) {
+            double all;
+            (void)part_prefix(b.part, tid, &all);
+            bc[tid] = all;
+        }
+        __syncthreads();
+        const double M = bc[0];
+        const double cx = M > 0.0 ? bc[1] / M : 0.0, cy = M > 0.0 ? bc[2] / M : 0.0, cz = M > 0.0 ? bc[3] / M : 0.0;
+        const double vx = M > 0.0 ? bc[4] / M : 0.0, vy = M > 0.0 ? bc[5] / M : 0.0, vz = M > 0.0 ? bc[6] / M : 0.0;
+        // radii about the centre, sorted over the grid
+        for (int t = C0 + tid; t < C1; t += blockDim.x) {
+            const int32_t i = __ldcg(X + t);
+            const float* p = a.pos + 3 * size_t(i);
+            const double dx = __dsub_rn(min_image(p[0], ax, L), cx);
+            const double dy = __dsub_rn(min_image(p[1], ay, L), cy);
+            const double dz = __dsub_rn(min_image(p[2], az, L), cz);
+            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            K[t] = uint64_t(__double_as_longlong(__dsqrt_rn(r2)));
+            V[t] = i;
+        }
+        if (!grid_sync(b.bar, b.status)) return false;
+        if (!grid_radix(K, V, n, 8, b, hist, dsum, dbase, skip, parity)) return false;
+        // 2-3. shell sums: thread chunks inside the CTA's chunk; the mass
+        // before and m/r after come from block scans and the CTA partials
+        const int ch = (C1 - C0 + int(blockDim.x) - 1) / int(blockDim.x);
+        const int c0 = min(C1, C0 + tid * ch), c1 = min(C1, c0 + ch);
+        double tm = 0.0, tq = 0.0;
+        long long tz = 0;
+        for (int k = c0; k < c1; k++) {
+            const double r = __longlong_as_double((long long)__ldcg(K + k));
+            const double m = mass_of(a, __ldcg(V + k));
+            tm += m;
+            if (m > 0.0) {
+                if (r > 0.0) tq += m / r;
+                else tz++;
+            }
+        }
+        double cta_m, cta_q;
+        long long cta_z;
+        const double pre_m_t = block_exclusive(tm, shd, &cta_m);
+        const double pre_q_t = block_exclusive(tq, shd, &cta_q);
+        (void)block_exclusive(tz, reinterpret_cast<long long*>(shi), &cta_z);
+        if (tid == 0) {
+            mypart[8] = cta_m;
+            mypart[9] = cta_q;
+            mypart[10] = double(cta_z);
+        }
+        if (!grid_sync(b.bar, b.status)) return false;
+        if (tid < 3) {
+            double all;
+            const double before = part_prefix(b.part, 8 + tid, &all);
+            bc[tid] = before;
+            bc[3 + tid] = all;
+        }
+        __syncthreads();
+        const double pre_m = bc[0] + pre_m_t, pre_q = bc[1] + pre_q_t, tot_q = bc[4];
+        const long long tot_z = (long long)bc[5];
+        const double after_q = tot_q - pre_q - tq;
+        double run_m = pre_m, run_q = 0.0;
+        int nk = 0;
+        for (int k = c0; k < c1; k++) {
+            const int32_t i = __ldcg(V + k);
+            const double r = __longlong_as_double((long long)__ldcg(K + k));
+            const double m = mass_of(a, i);
+            if (m > 0.0 && r > 0.0) run_q += m / r;
+            const double below = run_m > 0.0 ? run_m / r : 0.0;
+            double S = below + (after_q + (tq - run_q));
+            if (r == 0.0 && tot_z - (m > 0.0 ? 1 : 0) > 0) S = __longlong_as_double(0x7ff0000000000000ll);
+            run_m += m;
+            const float* v = a.vel + 3 * size_t(i);
+            const double ux = double(v[0]) - vx, uy = double(v[1]) - vy, uz = double(v[2]) - vz;
+            const double v2 = ux * ux + uy * uy + uz * uz;
+            const bool stay = !(v2 > twoG * S);
+            if (!stay) V[k] = ~i;
+            nk += stay;
+        }
+        long long cta_keep;
+        const long long dst_t = block_exclusive((long long)nk, reinterpret_cast<long long*>(shi), &cta_keep);
+        if (tid == 0) mypart[11] = double(cta_keep);
+        if (!grid_sync(b.bar, b.status)) return false;
+        if (tid == 0) {
+            double all;
+            const double before = part_prefix(b.part, 11, &all);
+            bc[0] = before;
+            bc[1] = all;
+        }
+        __syncthreads();
+        const long long n_keep = (long long)bc[1];
+        if (n_keep == n) break;  // the same in every CTA
+        long long d = (long long)bc[0] + dst_t;
+        for (int k = c0; k < c1; k++) {
+            const int32_t i = V[k];  // this thread's own marks
+            if (i >= 0) X[d++] = i;
+        }
+        if (!grid_sync(b.bar, b.status)) return false;
+        n = int(n_keep);
+    }
+    const bool discard = 5ll * (n0 - n) > 2ll * n0;
+    cta_chunk(n, C0, C1);
+    if (!discard)
+        for (int k = C0 + tid; k < C1; k += blockDim.x) a.group_out[__ldcg(X + k)] = int32_t(g);
+    if (blockIdx.x == 0 && tid == 0) {
+        a.n_kept[g] = discard ? 0 : n;
+        a.iters[g] = it;
+    }
+    // the partial slots and X are reused by the next group
+    return grid_sync(b.bar, b.status);
+}
+
+// The groups above a.grid_min, one after another, each with the whole grid
+// (a cooperative launch: every CTA resident).  A barrier that runs out ends
+// the kernel with CWTHF_E_TIMEOUT.
+__global__ void __launch_bounds__(kUbThreads) k_ub_grid(UbArgs a, UbGrid b) {
+    __shared__ double shd[8 * kUbWarps];
+    __shared__ int64_t shi[kUbWarps + 1];
+    __shared__ uint32_t hist[kUbWarps * 256];
+    __shared__ uint32_t dsum[256], dbase[256];
+    __shared__ int skip;
+    const int64_t n_groups = a.d_groups ? int64_t(*a.d_groups) : a.n_groups;
+    int parity = 0;
+    for (int64_t g = 0; g < n_groups; g++) {
+        if (int64_t(a.off[g + 1] - a.off[g]) <= a.grid_min) continue;
+        if (!unbind_group_grid(a, b, g, shd, shi, hist, dsum, dbase, &skip, parity)) return;
+    }
+}
+
 // A persistent grid over the groups: each CTA takes groups g, g + gridDim.x, ...
 __global__ void __launch_bounds__(kUbThreads) k_ub_group(UbArgs a) {
     __shared__ uint64_t sk[kUbSmemElems];
@@ -444,6 +759,7 @@ int unbind_groups(cwthf_ctx* ctx, const float* pos, const float* vel, const floa
         a.key = ctx->ub_key;
         a.val = ctx->ub_val;
         a.max_iter = max_iter;
+        a.grid_min = ctx->dbg_unbind_grid_min;
         a.n_groups = n_groups;
         a.d_groups = d_groups;
         a.group_out = group_out;
@@ -451,8 +767,29 @@ int unbind_groups(cwthf_ctx* ctx, const float* pos, const float* vel, const floa
         a.iters = iters;
         const unsigned grid = unsigned(std::min<int64_t>(n_groups, int64_t(ctx->sm_count) * 4));
         CWTHF_LAUNCH(ctx, s, "k_ub_group", k_ub_group<<<grid, kUbThreads, 0, s>>>(a));
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+        // the large groups: one cooperative launch (its barrier state starts cleared)
+        if ((e = cudaMemsetAsync(ctx->ub_bar, 0, 16, s)) != cudaSuccess) return cuda_status(e);
+        UbGrid b;
+        b.part = ctx->ub_part;
+        b.hist = ctx->ub_hist;
+        b.bar = ctx->ub_bar;
+        b.status = ctx->d_status;
+        void* args[] = {&a, &b};
+        CWTHF_LAUNCH(ctx, s, "k_ub_grid",
+                     e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_ub_grid),
+                                                     dim3(unsigned(ctx->ub_grid_blocks)), dim3(kUbThreads), args, 0,
+                                                     s));
+        if (e != cudaSuccess) return cuda_status(e);
     }
     return cuda_status(cudaGetLastError());
+}
+
+int unbind_grid_blocks(int sm_count) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ub_grid, kUbThreads, 0) != cudaSuccess || per_sm < 1)
+        return -1;
+    return std::min(per_sm, 2) * sm_count;
 }
 
 int unbind_impl(cwthf_ctx* ctx, const float* pos, const float* vel, const float* mass, double mass_unit, int64_t np,

@@ -122,17 +122,23 @@ def uctx():
     c.close()
 
 
-@pytest.mark.parametrize("ws,ngs", [((1.5, 2.5), (24, 36)), ((1.5, 2.5, 3.5), (24, 36, 48))])
-def test_self_boundness_in_the_loop_on_the_gpu_fields(uctx, ws, ngs):
+@pytest.mark.parametrize("ws,ngs,grid_min", [((1.5, 2.5), (24, 36), 1 << 16), ((1.5, 2.5, 3.5), (24, 36, 48), 1 << 16),
+                                             ((1.5, 2.5, 3.5), (24, 36, 48), 40)])
+def test_self_boundness_in_the_loop_on_the_gpu_fields(uctx, ws, ngs, grid_min):
     # step 9 inside the loop: the oracle's loop with the check on the GPU's own
     # fields gives the same halo ids and catalogue (a decision within 1e-9 of
-    # its threshold could fall either way; none comes that close here)
+    # its threshold could fall either way; none comes that close here); with
+    # grid_min = 40 nearly every group takes the whole-grid path
     L = 40.0
     pos, vel = synth.clumped_box(24000, L, 40, seed=2, velocities=True)
     pos, vel = pos.numpy(), vel.numpy()
     mp = synth.particle_mass(24000, L)
-    hid, cat, nh = uctx.find_multiscale(dev(pos), L, list(ws), list(ngs), mass_unit=mp, vel=dev(vel))
-    uctx.check()
+    uctx.debug_set(pkg._lib.DEBUG_UNBIND_GRID_MIN, grid_min)
+    try:
+        hid, cat, nh = uctx.find_multiscale(dev(pos), L, list(ws), list(ngs), mass_unit=mp, vel=dev(vel))
+        uctx.check()
+    finally:
+        uctx.debug_set(pkg._lib.DEBUG_UNBIND_GRID_MIN, 1 << 16)
     fields = _gpu_fields(uctx, pos, L, ws, ngs, mass_unit=mp)
     rhid, rcat = oracle.multiscale_on_fields(pos, L, fields, mass_unit=mp, vel=vel)
     assert rcat["margin"] > 1e-9
@@ -144,6 +150,8 @@ def test_self_boundness_in_the_loop_on_the_gpu_fields(uctx, ws, ngs):
         np.testing.assert_array_equal(got[col], rcat[col], err_msg=col)
     plain, _, np_plain = uctx.find_multiscale(dev(pos), L, list(ws), list(ngs), mass_unit=mp)
     uctx.check()
+    if grid_min != 1 << 16:
+        return
     record({"config": f"multi-scale loop with the self-boundness check, clumped 24000, L={L}, grids {list(ngs)}",
             "halos": n, "halos_without_check": int(np_plain[0]),
             "particles_in_halos": float(np.mean(rhid >= 0)),

@@ -1,7 +1,8 @@
 """The self-boundness check (Sec. 2.3) on the GPU against the oracle: the
 closed-form cases, groups from a clumped box with virial velocities (small
-groups sort in shared memory, large ones in global memory), repeatability,
-and the error paths."""
+groups sort in shared memory, larger ones in global memory, groups above a
+size threshold take the whole-grid path), repeatability, and the error
+paths."""
 import numpy as np
 import pytest
 import torch
@@ -130,6 +131,35 @@ def test_large_groups_sort_in_global_memory(uctx):
     assert (np.bincount(group, minlength=3)[:2] > 2048).all()
 
 
+@pytest.mark.parametrize("grid_min", [1000, 1])
+def test_whole_grid_path_matches_the_oracle(uctx, grid_min):
+    # groups above grid_min members are processed by the whole grid, one at a
+    # time (grid_min = 1: every group); the same decisions as the oracle, and
+    # the same result on a second call
+    L = 50.0
+    pos, vel, group, ng = _box_groups(16, 1 << 16, L, seed=3)
+    sizes = np.bincount(group[group >= 0], minlength=ng)
+    assert (sizes > 1000).sum() >= 5 and sizes.max() > 16000
+    mp = synth.particle_mass(1 << 16, L)
+    uctx.debug_set(pkg._lib.DEBUG_UNBIND_GRID_MIN, grid_min)
+    try:
+        assert uctx.debug_get(pkg._lib.DEBUG_UNBIND_GRID_MIN) == grid_min
+        got, ref = _both(uctx, pos, vel, group, L, synth.G_MPC_KMS_MSUN, mass_unit=mp, n_groups=ng)
+        margin = _same(got, ref)
+        again = uctx.unbind(dev(pos), dev(vel), dev(group), L, mass_unit=mp, n_groups=ng)
+        uctx.check()
+        for x, y in zip(again, got):
+            np.testing.assert_array_equal(x.cpu().numpy(), y)
+    finally:
+        uctx.debug_set(pkg._lib.DEBUG_UNBIND_GRID_MIN, 1 << 16)
+    out, nk, it = got
+    record({"config": f"self-boundness check, whole-grid path for groups above {grid_min}, clumped 2^16 (L={L}), "
+                      f"{ng} groups up to {int(sizes.max())}",
+            "groups_kept": int((nk > 0).sum()), "members_kept": int(nk.sum()), "max_rounds": int(it.max()),
+            "oracle_margin": margin})
+    assert 0 < (nk > 0).sum() < ng
+
+
 def test_repeatable_and_masses(uctx):
     L = 50.0
     pos, vel, group, ng = _box_groups(16, 1 << 15, L, seed=5, max_members=1000)
@@ -156,6 +186,9 @@ def test_errors(uctx, gctx):
         uctx.unbind(pos, pos, grp, -1.0)
     with pytest.raises(pkg.CwthfError):
         uctx.unbind(pos, pos, grp, 10.0, n_groups=64 ** 3)
+    for v in (0, 1 << 31):
+        with pytest.raises(pkg.CwthfError):
+            uctx.debug_set(pkg._lib.DEBUG_UNBIND_GRID_MIN, v)
     bad = dev(np.array([1.0, -1.0, 1.0, 1.0], np.float32))
     uctx.unbind(pos, pos, grp, 10.0, mass=bad, n_groups=1)
     assert uctx.sync() == pkg._lib.E_BAD_INPUT
