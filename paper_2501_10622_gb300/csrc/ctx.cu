@@ -96,6 +96,8 @@ void for_each_buffer(cwthf_ctx* c, int max_ng, int64_t max_np, int max_scales, u
     const size_t groups = ms == 1 ? 0 : (ms == 2 ? 2 : (ms + 3) & ~size_t(3));
     f(reinterpret_cast<void**>(&c->part_slot), (size_t(z.np) * ms + 4) * 4 + size_t(z.np) * 4 * groups);
     f(reinterpret_cast<void**>(&c->jump_changed), sizeof(int) * kJumpWords);
+    f(reinterpret_cast<void**>(&c->dep_parts), size_t(tile_parts_cap(z.np)) * 8);
+    f(reinterpret_cast<void**>(&c->dep_nparts), 16);
     if (flags & CWTHF_CREATE_UNBIND) {  // self-boundness check scratch (36 bytes per particle + 24 per group)
         f(reinterpret_cast<void**>(&c->ub_off), size_t(z.slots + 2) * 4);
         f(reinterpret_cast<void**>(&c->ub_cur), size_t(z.slots + 1) * 4);

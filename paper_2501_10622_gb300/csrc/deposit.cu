@@ -140,19 +140,38 @@ __device__ __forceinline__ void reach_pair(int j, int& m, int& cls) {
 // flattened list, so every warp works on full batches whatever the segment
 // sizes; the write-out also clears the shared accumulators for the next tile.
 // Three barriers per tile.
+//
+// Dense tiles (a clump's core can put millions of records into one tile) are
+// split when a part list is given: the tile pass (kParts false) takes a
+// tile's first kTileSplit records and stores the tile as usual, and lists the
+// remaining parts of kTileSplit records; the part pass (kParts true, launched
+// after it) spreads those parts over all CTAs, each accumulating its part in
+// shared memory and adding the nonzero cells to the grid with 64-bit atomics.
+// Integer sums do not depend on their order, so the grid is the same.
+
+struct TileParts {
+    uint2* list;      // (tile, part >= 1), or nullptr: every tile whole
+    uint32_t* count;  // parts listed
+    uint32_t cap;
+};
+
+template <bool kParts>
 __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_dep_tile(DepArgs a, const uint32_t* __restrict__ off,
                                                           const unsigned long long* __restrict__ rec,
                                                           const uint32_t* __restrict__ rec_mq,
                                                           const unsigned long long* __restrict__ mtot,
-                                                          int64_t* __restrict__ grid, int* status) {
+                                                          int64_t* __restrict__ grid, int* status, TileParts tp) {
     constexpr int kCells = kDepTX * kDepTY * kDepTZ;
     __shared__ __align__(16) uint32_t acc_lo[kCells];
     __shared__ __align__(16) uint32_t acc_hi[kCells];
     __shared__ uint32_t seg_beg[kReachSegments], seg_pre[kReachSegments + 1];
     __shared__ uint8_t seg_m[kReachSegments];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && *mtot >= (1ull << 33)) set_status(status, CWTHF_E_OVERFLOW);
+    if (!kParts && blockIdx.x == 0 && threadIdx.x == 0 && *mtot >= (1ull << 33)) set_status(status, CWTHF_E_OVERFLOW);
     const int64_t ntiles = int64_t(a.ntx) * a.nty * a.ntz;
+    // work items: tiles, or the listed parts
+    const int64_t nitems = kParts ? int64_t(min(*tp.count, tp.cap)) : ntiles;
+    auto item_tile = [&](int64_t j) -> int64_t { return kParts ? int64_t(tp.list[j].x) : j; };
     const int64_t ng = a.ng;
     const bool vec = (reinterpret_cast<uintptr_t>(grid) & 15u) == 0 && (ng & 1) == 0;  // 16-byte cell pairs
     for (int c = threadIdx.x; c < kCells; c += kTileThreads) {
@@ -176,8 +195,9 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_dep_tile(DepAr
         }
     };
     uint32_t nb = 0, ne = 0;
-    if (warp == 0) fetch(blockIdx.x, nb, ne);
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (warp == 0) fetch(blockIdx.x < nitems ? item_tile(blockIdx.x) : ntiles, nb, ne);
+    for (int64_t j = blockIdx.x; j < nitems; j += gridDim.x) {
+        const int64_t t = item_tile(j);
         const int tx = int(t % a.ntx), ty = int((t / a.ntx) % a.nty), tz = int(t / (int64_t(a.ntx) * a.nty));
         const int x0 = tx * kDepTX, y0 = ty * kDepTY, z0 = tz * kDepTZ;
         const int wx = min(kDepTX, a.ng - x0), wy = min(kDepTY, a.ng - y0), wz = min(kDepTZ, a.ng - z0);
@@ -198,9 +218,23 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_dep_tile(DepAr
         }
         __syncthreads();
         const uint32_t total = seg_pre[kReachSegments];
-        for (uint32_t k0 = (threadIdx.x & ~31u); k0 < total; k0 += kTileThreads) {  // warp-uniform trip count
+        // this pass's records of the tile's flattened list
+        uint32_t kbeg = 0, kend = total;
+        if (kParts) {
+            kbeg = tp.list[j].y * kTileSplit;
+            kend = min(total, kbeg + kTileSplit);
+        } else if (tp.list && total > kTileSplit) {
+            kend = kTileSplit;
+            if (threadIdx.x == 0) {
+                const uint32_t extra = (total - 1) / kTileSplit;  // parts after the first
+                const uint32_t p0 = atomicAdd(tp.count, extra);
+                if (p0 + extra > tp.cap) set_status(status, CWTHF_E_OVERFLOW);  // cannot happen: the list holds 8 np / split
+                for (uint32_t p = 0; p < extra && p0 + p < tp.cap; p++) tp.list[p0 + p] = make_uint2(uint32_t(t), p + 1);
+            }
+        }
+        for (uint32_t k0 = kbeg + (threadIdx.x & ~31u); k0 < kend; k0 += kTileThreads) {  // warp-uniform trip count
             const uint32_t k = k0 + uint32_t(lane);
-            const bool live = k < total;
+            const bool live = k < kend;
             int sgi = 0;  // segment of k: last j with seg_pre[j] <= k
 #pragma unroll
             for (int w = 16; w > 0; w >>= 1)
@@ -239,8 +273,19 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_dep_tile(DepAr
             }
         }
         __syncthreads();
-        if (warp == 0) fetch(t + gridDim.x, nb, ne);  // the next tile's ranges, in flight during the write-out
-        if (vec && wx == kDepTX && wy == kDepTY && wz == kDepTZ) {
+        if (warp == 0)  // the next item's ranges, in flight during the write-out
+            fetch(j + gridDim.x < nitems ? item_tile(j + gridDim.x) : ntiles, nb, ne);
+        if (kParts) {
+            // a part: its nonzero cells are added to the grid
+            for (int c = threadIdx.x; c < kCells; c += kTileThreads) {
+                const int cx = c % kDepTX, cy = (c / kDepTX) % kDepTY, cz = c / (kDepTX * kDepTY);
+                const u64 v = (u64(acc_hi[c]) << 32) | u64(acc_lo[c]);
+                if (v && cx < wx && cy < wy && cz < wz)
+                    atomicAdd(reinterpret_cast<u64*>(grid + (int64_t(z0 + cz) * ng + (y0 + cy)) * ng + (x0 + cx)), v);
+                acc_lo[c] = 0u;
+                acc_hi[c] = 0u;
+            }
+        } else if (vec && wx == kDepTX && wy == kDepTY && wz == kDepTZ) {
             // a whole tile: two cells per thread and step, one 16-byte store each
             // (a warp writes two 256-byte row segments)
             int64_t* tg = grid + (int64_t(z0) * ng + y0) * ng + x0;
@@ -296,9 +341,18 @@ int deposit_impl(cwthf_ctx* ctx, const float* pos, const float* mass, double mas
     DepositGeom g = deposit_geom(ng);
     DepArgs a = make_dep_args(pos, mass, mass_unit, np, L, ng);
     int tblocks = int(std::min<int64_t>(g.ntiles, int64_t(ctx->sm_count) * kTileCtasPerSm));
-    CWTHF_LAUNCH(ctx, s, "k_dep_tile", k_dep_tile<<<tblocks, kTileThreads, 0, s>>>(a, ctx->dep_off, ctx->dep_rec, ctx->dep_mq, ctx->d_mtot, grid,
-                                                ctx->d_status));
     cudaError_t e;
+    TileParts tp;
+    tp.list = reinterpret_cast<uint2*>(ctx->dep_parts);
+    tp.count = ctx->dep_nparts;
+    tp.cap = uint32_t(tile_parts_cap(ctx->max_np));
+    if ((e = cudaMemsetAsync(tp.count, 0, 4, s)) != cudaSuccess) return cuda_status(e);
+    CWTHF_LAUNCH(ctx, s, "k_dep_tile", k_dep_tile<false><<<tblocks, kTileThreads, 0, s>>>(a, ctx->dep_off, ctx->dep_rec, ctx->dep_mq, ctx->d_mtot, grid,
+                                                ctx->d_status, tp));
+    // the dense tiles' further parts (returns at once when there are none)
+    CWTHF_LAUNCH(ctx, s, "k_dep_parts",
+                 k_dep_tile<true><<<ctx->sm_count * kTileCtasPerSm, kTileThreads, 0, s>>>(
+                     a, ctx->dep_off, ctx->dep_rec, ctx->dep_mq, ctx->d_mtot, grid, ctx->d_status, tp));
     if (mtot && (e = cudaMemcpyAsync(mtot, ctx->d_mtot, 8, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return cuda_status(e);
     return cuda_status(cudaGetLastError());
@@ -322,7 +376,11 @@ int deposit_into_scratch(const DepositScratch& sc, const float* pos, const float
         return cuda_status(e);
     k_dep_scatter<<<blocks, kCountThreads, 0, s>>>(a, sc.cursor, sc.rec, sc.mq, nullptr);
     int tblocks = int(std::min<int64_t>(g.ntiles, int64_t(sc.sm_count) * kTileCtasPerSm));
-    k_dep_tile<<<tblocks, kTileThreads, 0, s>>>(a, sc.off, sc.rec, sc.mq, sc.mtot, grid, sc.status);
+    TileParts whole;  // no part list: every tile whole
+    whole.list = nullptr;
+    whole.count = nullptr;
+    whole.cap = 0;
+    k_dep_tile<false><<<tblocks, kTileThreads, 0, s>>>(a, sc.off, sc.rec, sc.mq, sc.mtot, grid, sc.status, whole);
     return cuda_status(cudaGetLastError());
 }
 

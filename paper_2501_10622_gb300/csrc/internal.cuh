@@ -23,6 +23,12 @@ constexpr int64_t kFracOne = int64_t(1) << kFracBits;
 // (the last tile along an axis may be partial).
 constexpr int kDepTX = 32, kDepTY = 8, kDepTZ = 8;
 constexpr int kDepClasses = 8;  // boundary class bits (x, y, z) per particle
+// Records of a deposit tile per CTA pass: denser tiles are split into parts.
+// The records reaching into all tiles number at most 8 np (a particle reaches
+// its own tile and at most 7 neighbours), so the parts after each tile's
+// first number at most 8 np / kTileSplit.
+constexpr uint32_t kTileSplit = 4096;
+inline int64_t tile_parts_cap(int64_t np) { return 8 * (np > 0 ? np : 1) / kTileSplit + 1; }
 
 // A binned particle record: its three fixed-point coordinates q (each below
 // ng * 2^10 <= 2^20) in 21-bit fields, x lowest.
@@ -162,6 +168,8 @@ struct cwthf_ctx {
     int32_t* ub_it = nullptr;     // [max groups] rounds per group
     uint32_t* ub_keep = nullptr;  // [max groups + 2] groups that stay, then their ranks
     uint32_t* ub_ngroups = nullptr;  // [1] groups of the check (device count)
+    unsigned long long* dep_parts = nullptr;  // [tile_parts_cap(max_np)] (tile, part) of dense deposit tiles
+    uint32_t* dep_nparts = nullptr;          // [1] parts listed
     double* ub_part = nullptr;       // [ub_grid_blocks][16] per-CTA partial sums of the whole-grid path
     uint32_t* ub_hist = nullptr;     // [2][ub_grid_blocks][256] per-CTA digit counts of its radix sort
     unsigned* ub_bar = nullptr;      // [2] its grid barrier

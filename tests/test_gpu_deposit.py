@@ -53,6 +53,26 @@ def test_deterministic_and_order_free(gctx, work64):
     assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("masses", [False, True])
+def test_dense_tiles_split_into_parts(gctx, masses):
+    # cores of tens of thousands of particles in a cell or two, one at a tile
+    # corner (reaching into eight tiles), so their tiles hold many more than
+    # 4096 records: the first part of each is stored by the tile pass, the
+    # others are added by the part pass; the grid is bit-exact all the same
+    ng, L = 48, 24.0
+    rng = np.random.default_rng(7)
+    corner = (np.array([15.8, 3.8, 3.8]) + rng.random((150000, 3)) * 0.35).astype(np.float32)  # x 31.6-32.3 cells
+    inner = (np.array([5.2, 9.1, 17.3]) + rng.random((50000, 3)) * 0.9).astype(np.float32)
+    pos = np.concatenate([corner, inner, random_box(20000, L, 5)])
+    # masses of 1-3 quanta: the oracle's fp64 cell sums stay below 2^53
+    mass = rng.integers(1, 4, pos.shape[0]).astype(np.float32) if masses else None
+    unit = 1.0
+    g = gctx.deposit(dev(pos), L, ng, mass=None if mass is None else dev(mass), mass_unit=unit)
+    gctx.check()
+    ref, _ = oracle.cic(pos, L, ng, mass=mass, mass_unit=unit)
+    np.testing.assert_array_equal(g.cpu().numpy(), ref)
+
+
 def test_empty_particle_set(gctx):
     g = gctx.deposit(torch.zeros((0, 3), dtype=torch.float32, device="cuda"), 10.0, 16)
     gctx.check()
