@@ -15,7 +15,7 @@
  * Conventions shared by every entry point
  *   - Grids are row-major [z][y][x] with x fastest; grid node g sits at
  *     g * (L / ng) in a periodic box of side L.  ng must be even with
- *     8 <= ng <= 1024 (cwthf_check_ng tells), otherwise
+ *     8 <= ng <= 1152 (cwthf_check_ng tells), otherwise
  *     CWTHF_E_UNSUPPORTED_SIZE.  Pass lengths (ng along y and z, ng / 2 for
  *     the paired real samples along x) whose factors are all radices of
  *     2, 3, 5, 7 run mixed-radix FFTs; any other length (a prime factor above
@@ -63,7 +63,7 @@ extern "C" {
 #endif
 
 #define CWTHF_FRAC_BITS 10
-#define CWTHF_MAX_NG 1024
+#define CWTHF_MAX_NG 1152
 #define CWTHF_MIN_NG 8
 #define CWTHF_MAX_STENCIL_R 64
 

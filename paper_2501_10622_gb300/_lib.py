@@ -24,7 +24,7 @@ E_SCRATCH_LIMIT = 10
 E_TABLE_CACHE = 11
 CREATE_UNBIND = 1  # cwthf_create_ex: scratch of the self-boundness check
 FRAC_BITS = 10
-MIN_NG, MAX_NG = 8, 1024
+MIN_NG, MAX_NG = 8, 1152
 # cwthf_debug_set / cwthf_debug_get keys
 DEBUG_JUMP_ROUNDS, DEBUG_CHASE_LIMIT, DEBUG_TMA_NO_COPY, DEBUG_FALLBACK_RAN, DEBUG_TABLE_FILLS = 1, 2, 3, 4, 5
 DEBUG_UNBIND_GRID_MIN = 6

@@ -440,6 +440,7 @@ __device__ __forceinline__ void stage_fused_ct(float2* tile, A addr, const float
 struct DynFft {
     static constexpr int kThreads = 512, kMinBlocks = 1;
     static constexpr bool kGlobalTables = false, kBlue = false;
+    static constexpr int kMaxLen = CWTHF_MAX_NG / 2;  // longest x pass (the x kernels keep a row in registers)
     static __device__ __forceinline__ int cols(const Plan& p) { return p.C; }
     static __device__ __forceinline__ int len(const Plan& p) { return p.L; }
     static __device__ __forceinline__ int rows(const Plan& p) { return p.L; }
@@ -487,6 +488,7 @@ struct CtFft {
     static constexpr int kMinBlocks = MinBlocks;
     static constexpr bool kGlobalTables = true;  // y/z pass: tables through the cache
     static constexpr bool kBlue = false;
+    static constexpr int kMaxLen = L_;
     static_assert(R0 * R1 * R2 == L_, "radices multiply to the length");
     static __device__ __forceinline__ int cols(const Plan&) { return C_; }
     static __device__ __forceinline__ int len(const Plan&) { return L_; }
@@ -541,6 +543,7 @@ struct CtFft {
 struct BlueFft {
     static constexpr int kThreads = 512, kMinBlocks = 1;
     static constexpr bool kGlobalTables = true, kBlue = true;
+    static constexpr int kMaxLen = CWTHF_MAX_NG / 2;
     static __device__ __forceinline__ int cols(const Plan& p) { return p.C; }
     static __device__ __forceinline__ int len(const Plan& p) { return p.Lb; }
     static __device__ __forceinline__ int rows(const Plan& p) { return p.L; }
@@ -792,13 +795,14 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks) k_fft_x_fwd(XArgs 
     // replaced by the exact row sum below.  The spectrum is in units of 2^-30 of
     // the grid (mass_unit is applied with the wavelet).
     constexpr float kUnit = 9.3132257461547852e-10f;  // 2^-30, exact
+    constexpr int kRowVec = (F::kMaxLen + 31) / 32;  // a row's int64 pairs per lane
     for (int r = warp; r < C; r += nwarp) {
         int64_t row = int64_t(blockIdx.x) * C + r;
-        longlong2 v[16];
+        longlong2 v[kRowVec];
         long long sum = 0;
         const longlong2* src = reinterpret_cast<const longlong2*>(grid + row * a.ng);
 #pragma unroll
-        for (int i = 0; i < 16; i++) {
+        for (int i = 0; i < kRowVec; i++) {
             int k = lane + 32 * i;
             v[i] = (row < a.rows && k < M) ? src[k] : make_longlong2(0, 0);
             sum += v[i].x + v[i].y;
@@ -808,7 +812,7 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks) k_fft_x_fwd(XArgs 
         const long long q0 = sum / a.ng;  // grid values are >= 0
         if (lane == 0) rowdc[r] = double(__ll2float_rn(sum) * kUnit);
 #pragma unroll
-        for (int i = 0; i < 16; i++) {
+        for (int i = 0; i < kRowVec; i++) {
             int k = lane + 32 * i;
             if (k < M) {
                 float re = __ll2float_rn(v[i].x - q0) * kUnit;
@@ -870,7 +874,7 @@ __global__ void __launch_bounds__(F::kThreads, F::kMinBlocks) k_fft_x_inv(XArgs 
     for (int r = warp; r < C; r += nwarp) {
         int64_t row = int64_t(blockIdx.x) * C + r;
         const float2* in = spec + (row < a.rows ? row : 0) * a.P;
-        constexpr int kPairs = 9;  // k = lane + 32 i, i < 9 covers k <= M/2 <= 256
+        constexpr int kPairs = F::kMaxLen / 64 + 1;  // k = lane + 32 i covers k <= M/2
         float2 xk[kPairs], xm[kPairs];
 #pragma unroll
         for (int i = 0; i < kPairs; i++) {
@@ -1405,7 +1409,7 @@ int x_args(cwthf_ctx* ctx, int ng, const Tables* t, XArgs& a) {
 }  // namespace
 
 int transform_forward_xy(cwthf_ctx* ctx, const int64_t* grid, int ng, float2* spec, cudaStream_t s) {
-    if (ng / 2 > 512) return CWTHF_E_UNSUPPORTED_SIZE;
+    if (ng > CWTHF_MAX_NG) return CWTHF_E_UNSUPPORTED_SIZE;
     Tables tb;
     int rc = get_tables(ctx, ng, s, tb);
     if (rc) return rc;
@@ -1466,7 +1470,7 @@ int set_fft_plan(cwthf_ctx* ctx, int ng, int which, int C, const int* rad, int n
 // decides the box, the x passes have a plan of their own.
 bool fft_size_supported(int ng) {
     Plan yz, x;
-    return (ng % 2 == 0) && ng / 2 <= 512 && yz_plan(ng, yz) && plan_boxr(ng, yz) > 0 && x_plan(ng / 2, x);
+    return (ng % 2 == 0) && ng <= CWTHF_MAX_NG && yz_plan(ng, yz) && plan_boxr(ng, yz) > 0 && x_plan(ng / 2, x);
 }
 
 void free_tables(cwthf_ctx* ctx) {

@@ -13,7 +13,7 @@
 // no shared memory and no barrier.  k_seg_chase loads a tile's codes into
 // shared memory as parent pointers and resolves every chain that stays inside
 // the tile.  A chain that leaves the tile is written as a flagged pointer
-// (bit 30) to the first cell outside; the global pass then replaces flagged
+// (-2 - g) to the first cell g outside; the global pass then replaces flagged
 // pointers by the label of their target (bounded walks, then, only if a chain
 // outlived them, pointer-doubling rounds in one cooperative launch; hitting the
 // round bound is reported as CWTHF_E_NOT_CONVERGED).  The result does not
@@ -40,8 +40,10 @@ constexpr int kPlaneL = kPX * kChTY, kPlaneBits = 10;
 constexpr int kLocal = kPlaneL * kChTZ;  // 16384 entries
 constexpr int kRowWords = 2 * kChTZ;     // flagged-cell masks per tile row (32)
 static_assert(kChTX == kPX && kPlaneL == (1 << kPlaneBits) && kRowWords == 32, "local index layout");
-constexpr int32_t kFlag = 1 << 30;
-constexpr int32_t kMask = kFlag - 1;
+// A flagged pointer (a chain still to be followed) to cell g is stored as
+// -2 - g, apart from -1 (no seed) and the final labels (seed cells, >= 0).
+__device__ __forceinline__ bool is_flagged(int32_t v) { return v <= -2; }
+__device__ __forceinline__ int32_t flag_target(int32_t v) { return -2 - v; }
 constexpr int kChaseLimit = 64;  // default: longest chain the global pass follows per cell before doubling rounds
 constexpr int kJumpRoundsInTile = 16;  // in-place jumping rounds (each at least doubles the distance): 2^14 >= cells of a tile
 // Seeds of one tile: at most one local maximum per 2 x 2 x 2 block of cells
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
         if (cur == -1) return -1;
         if (cur <= -2) {
             fl = true;
-            return (-2 - cur) | kFlag;
+            return cur;  // -2 - g: already the flagged pointer to the outside parent g
         }
         const int px = cur & (kPX - 1), py = (cur >> kPXBits) & (kChTY - 1), pz = cur >> kPlaneBits;
         const int32_t g = gbase + (pz * N + py) * N + px;
@@ -402,7 +404,7 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
             return g;
         }
         fl = true;
-        return g | kFlag;  // not finished within the round bound: resume globally
+        return -2 - g;  // not finished within the round bound: resume globally
     };
     int32_t* out = label + (size_t(z0) * N + yc) * N + xc;
     const bool vec = (reinterpret_cast<uintptr_t>(label) & 7u) == 0;  // xc is even: 8-byte label pairs
@@ -486,12 +488,12 @@ __device__ __forceinline__ void resolve_batch(int32_t* __restrict__ label, bool 
     if (valid) {
         int32_t w = label[c];
         int steps = 0;
-        while (w >= 0 && (w & kFlag) && steps < limit) {
-            w = label[w & kMask];
+        while (is_flagged(w) && steps < limit) {
+            w = label[flag_target(w)];
             steps++;
         }
         label[c] = w;
-        if (w >= 0 && (w & kFlag)) left = true;
+        if (is_flagged(w)) left = true;
         else lab = w;
     }
     const unsigned peers = __match_any_sync(0xffffffffu, lab);  // every lane
@@ -601,10 +603,10 @@ __global__ void __launch_bounds__(256) k_seg_fallback(int32_t* __restrict__ labe
         bool any = false;
         for (int64_t c = gid; c < cells; c += stride) {
             const int32_t v = label[c];
-            if (v >= 0 && (v & kFlag)) {
-                const int32_t w = label[v & kMask];
+            if (is_flagged(v)) {
+                const int32_t w = label[flag_target(v)];
                 label[c] = w;
-                any |= (w >= 0 && (w & kFlag));  // still a pointer: another round is needed
+                any |= is_flagged(w);  // still a pointer: another round is needed
             }
         }
         if (__any_sync(0xffffffffu, any) && (threadIdx.x & 31) == 0) atomicOr(&changed[r], 1);

@@ -23,12 +23,13 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_supported_grid_sizes():
-    # every even size from 8 to 1024: radix stages, or Bluestein passes where
-    # the length has a prime factor above 7; odd sizes and sizes out of range
-    # are refused
-    for n in range(8, 1025, 2):
+    # every even size from 8 to 1152 (the paper's largest grid, Int(400 2.5 +
+    # 150) = 1150, included): radix stages, or Bluestein passes where the
+    # length has a prime factor above 7; odd sizes and sizes out of range are
+    # refused
+    for n in range(8, 1153, 2):
         assert pkg.check_ng(n), n
-    for n in (4, 6, 7, 9, 27, 81, 191, 1023, 1026, 1152, 2048, 1150):
+    for n in (4, 6, 7, 9, 27, 81, 191, 1023, 1151, 1154, 1156, 2048):
         assert not pkg.check_ng(n), n
     smooth = sorted({2 ** a * 3 ** b for a in range(1, 11) for b in range(0, 7) if 8 <= 2 ** a * 3 ** b <= 1024})
     assert synth.smooth_ng(190) in smooth and synth.smooth_ng(1150) == 1024
@@ -73,14 +74,16 @@ def test_radix_five_seven_and_bluestein_sizes():
     # 750 = 2 3 5^3; sizes with a larger prime factor (190 = 2 5 19,
     # 1022 = 2 7 73) run Bluestein passes, so the paper's grid rule
     # Int(400 k_w + 150) is taken to the nearest even size
-    for n in (10, 14, 20, 28, 30, 40, 50, 70, 100, 140, 250, 270, 350, 750, 1000, 22, 26, 190, 230, 1022):
+    for n in (10, 14, 20, 28, 30, 40, 50, 70, 100, 140, 250, 270, 350, 750, 1000, 22, 26, 190, 230, 1022, 1150):
         assert pkg.check_ng(n), n
-    for n in (1150, 9, 15, 189):
+    for n in (9, 15, 189, 1151):
         assert not pkg.check_ng(n), n
-    sizes = pkg.supported_sizes(8, 1024)
-    assert sizes == list(range(8, 1025, 2))
+    sizes = pkg.supported_sizes(8, 1152)
+    assert sizes == list(range(8, 1153, 2))
     kws, ws, ngs = pkg.paper_scales(50.0, n=20)
     want = [int(400 * k + 150) for k in kws]
-    # within one cell of the rule up to the largest grid, capped there above it
-    assert all((abs(g - v) <= 1 if v <= 1024 else g == 1024) and g % 2 == 0 for g, v in zip(ngs, want)), (ngs, want)
-    assert ngs[0] == 190
+    # within one cell of the rule at every scale, the paper's 190 and 1150 included
+    assert all(abs(g - v) <= 1 and g % 2 == 0 for g, v in zip(ngs, want)), (ngs, want)
+    assert ngs[0] == 190 and ngs[-1] == 1150
+    # a smaller limit caps the grids
+    assert max(pkg.paper_scales(50.0, n=20, max_ng=1024)[2]) == 1024
