@@ -1,5 +1,5 @@
 // unbind.cu -- the self-boundness check (Sec. 2.3; step 9 of the Sec. 2 step
-// list), one CTA per group.
+// list), one CTA per group, or the whole grid for a large group.
 //
 // For every group g, following Sec. 2.3 in order:
 //   1. the centre is the centre of mass of the current members (mass-weighted
@@ -68,8 +68,9 @@ struct UbArgs {
     double mass_unit, L, G;
     const uint32_t* off;  // [n_groups + 1] first member of each group in mem
     int32_t* mem;         // [np] members, grouped
-    uint64_t* key;        // [2 np] sort keys (group g: from 2 off[g], a power of two >= its size)
-    int32_t* val;         // [2 np] sort values
+    uint64_t* key;        // [2 np] sort keys (group g of n members: 2 n entries from 2 off[g], the
+                          // pairs and the radix sort's other buffer)
+    int32_t* val;         // [2 np] sort values (the same layout)
     int max_iter;
     int64_t grid_min;            // larger groups are left to the whole-grid path
     int64_t n_groups;            // groups (or read from d_groups when given)
