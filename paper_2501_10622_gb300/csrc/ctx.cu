@@ -472,7 +472,7 @@ const char* cwthf_error_string(int code) {
     switch (code) {
         case CWTHF_OK: return "ok";
         case CWTHF_E_INVALID_ARG: return "invalid argument";
-        case CWTHF_E_UNSUPPORTED_SIZE: return "unsupported grid size (need 2^a 3^b 5^c 7^d with a >= 1 and an FFT plan, 8 <= ng <= 1024, within the context's limits)";
+        case CWTHF_E_UNSUPPORTED_SIZE: return "unsupported grid size (need an even ng, 8 <= ng <= 1152, within the context's limits)";
         case CWTHF_E_OVERFLOW: return "integer mass budget exceeded (m_q >= 2^31 or sum m_q >= 2^33)";
         case CWTHF_E_OOM: return "device allocation failed";
         case CWTHF_E_CUDA: return "CUDA runtime error";
