@@ -79,7 +79,9 @@ enum {
     CWTHF_E_CAPACITY = 8,         /* more halos than cat_cap; the count is still reported */
     CWTHF_E_BAD_INPUT = 9,        /* non-finite or out-of-range position / mass / CWT value */
     CWTHF_E_SCRATCH_LIMIT = 10,   /* too large for cwthf_deposit_noalloc's fixed scratch */
-    CWTHF_E_TABLE_CACHE = 11      /* no FFT / wavelet table slot left (see cwthf_create) */
+    CWTHF_E_TABLE_CACHE = 11,     /* no FFT / wavelet table slot left (see cwthf_create) */
+    CWTHF_E_INDEX = 12            /* checked builds only: a data-driven index was out of range; its
+                                     access was skipped and the call's results are unspecified */
 };
 
 typedef struct cwthf_ctx cwthf_ctx;
@@ -391,6 +393,11 @@ CWTHF_API int cwthf_set_fft_plan(cwthf_ctx *ctx, int ng, int which, int C, const
  *       waits for `stream`.
  *   CWTHF_DEBUG_TABLE_FILLS (get only): table slots filled since the context
  *       was created (each a host-side table computation and one copy).
+ *   CWTHF_DEBUG_CHECKED (get only): 1 if this library is the range-checked
+ *       build (compiled with CWTHF_CHECKED: every data-driven index -- record
+ *       slots, label and chain targets, seed slots, group members -- is tested
+ *       before use, and one out of range is skipped and reported as
+ *       CWTHF_E_INDEX), else 0.
  *   CWTHF_DEBUG_UNBIND_GRID_MIN  1..2^31-1 (default 65536): groups of the
  *       self-boundness check with more members than this are processed by
  *       the whole grid (one cooperative launch, one group at a time), smaller
@@ -403,6 +410,7 @@ CWTHF_API int cwthf_set_fft_plan(cwthf_ctx *ctx, int ng, int which, int C, const
 #define CWTHF_DEBUG_FALLBACK_RAN 4
 #define CWTHF_DEBUG_TABLE_FILLS 5
 #define CWTHF_DEBUG_UNBIND_GRID_MIN 6
+#define CWTHF_DEBUG_CHECKED 7
 CWTHF_API int cwthf_debug_set(cwthf_ctx *ctx, int key, int64_t value);
 CWTHF_API int cwthf_debug_get(cwthf_ctx *ctx, int key, int64_t *value, void *stream);
 

@@ -16,18 +16,20 @@ import numpy as np
 
 _PKG = Path(__file__).resolve().parent
 LIB_PATH = _PKG / "libcwthf.so"
+LIB_CHECKED_PATH = _PKG / "libcwthf_checked.so"
 HEADER = _PKG.parent / "include" / "cwthf.h"
 
 OK = 0
 E_INVALID_ARG, E_UNSUPPORTED_SIZE, E_OVERFLOW, E_OOM, E_CUDA, E_NOT_CONVERGED, E_TIMEOUT, E_CAPACITY, E_BAD_INPUT = range(1, 10)
 E_SCRATCH_LIMIT = 10
 E_TABLE_CACHE = 11
+E_INDEX = 12
 CREATE_UNBIND = 1  # cwthf_create_ex: scratch of the self-boundness check
 FRAC_BITS = 10
 MIN_NG, MAX_NG = 8, 1152
 # cwthf_debug_set / cwthf_debug_get keys
 DEBUG_JUMP_ROUNDS, DEBUG_CHASE_LIMIT, DEBUG_TMA_NO_COPY, DEBUG_FALLBACK_RAN, DEBUG_TABLE_FILLS = 1, 2, 3, 4, 5
-DEBUG_UNBIND_GRID_MIN = 6
+DEBUG_UNBIND_GRID_MIN, DEBUG_CHECKED = 6, 7
 
 HALO_DTYPE = np.dtype([("seed", "<i8"), ("n_part", "<i8"), ("n_cells", "<i8"), ("mass", "<f8"),
                        ("centre", "<f8", (3,)), ("peak", "<f4"), ("reserved", "<i4")])
@@ -83,12 +85,15 @@ _lib = None
 
 
 def lib() -> ctypes.CDLL:
-    """Loads the in-tree libcwthf.so (built by __graft_entry__.build())."""
+    """Loads the in-tree libcwthf.so (built by __graft_entry__.build()), or
+    its range-checked variant libcwthf_checked.so when the environment sets
+    CWTHF_CHECKED=1."""
     global _lib
     if _lib is None:
-        if not LIB_PATH.exists():
-            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
-        L = ctypes.CDLL(str(LIB_PATH))
+        path = LIB_CHECKED_PATH if os.environ.get("CWTHF_CHECKED") == "1" else LIB_PATH
+        if not path.exists():
+            raise ImportError(f"{path} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(str(path))
         P, i64, i32, d, f = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_float
         L.cwthf_default_params.argtypes = [d, ctypes.POINTER(Params)]
         L.cwthf_default_params.restype = None

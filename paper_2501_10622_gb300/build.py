@@ -2,7 +2,10 @@
 
 Each translation unit is compiled in parallel, then linked into one shared
 library with the CUDA runtime linked statically.  The library exports only
-the C ABI declared in include/cwthf.h.
+the C ABI declared in include/cwthf.h.  build(checked=True) builds the same
+sources with CWTHF_CHECKED defined into libcwthf_checked.so (device-side
+range checks of data-driven indices; the binding loads it when the
+environment sets CWTHF_CHECKED=1).
 """
 from __future__ import annotations
 
@@ -16,6 +19,7 @@ PKG = Path(__file__).resolve().parent
 ROOT = PKG.parent
 CSRC = PKG / "csrc"
 OUT = PKG / "libcwthf.so"
+OUT_CHECKED = PKG / "libcwthf_checked.so"
 BUILD = ROOT / "_build"
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
@@ -43,12 +47,14 @@ def _stale(target: Path, deps) -> bool:
     return any(d.stat().st_mtime > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> Path:
-    BUILD.mkdir(exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, checked: bool = False) -> Path:
+    out = OUT_CHECKED if checked else OUT
+    bdir = BUILD / "checked" if checked else BUILD
+    bdir.mkdir(parents=True, exist_ok=True)
     headers = list(CSRC.glob("*.cuh")) + [ROOT / "include" / "cwthf.h"]
     srcs = sources()
-    objs = [BUILD / (s.stem + ".o") for s in srcs]
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    objs = [bdir / (s.stem + ".o") for s in srcs]
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DCWTHF_CHECKED"] if checked else [])
 
     def compile_one(pair):
         src, obj = pair
@@ -66,14 +72,20 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         for s, log in zip(srcs, logs):
             if log:
                 print(f"--- {s.name}\n{log}")
-    if force or _stale(OUT, objs):
-        tmp = OUT.with_suffix(f".so.{os.getpid()}")
+    if force or _stale(out, objs):
+        tmp = out.with_suffix(f".so.{os.getpid()}")
         cmd = [nvcc(), ARCH, "-shared", "-Xcompiler", "-fPIC", *map(str, objs), "-ldl", "-o", str(tmp)]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, OUT)
-    return OUT
+        os.replace(tmp, out)
+    return out
+
+
+def build_all(force: bool = False) -> list[Path]:
+    """The library and its checked variant, compiled side by side."""
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        return list(ex.map(lambda c: build(force=force, checked=c), (False, True)))
 
 
 if __name__ == "__main__":

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kHsThreads, hs_ctas_per_sm<kMass>()) k_halo_su
                                                        const uint32_t* __restrict__ prefix,
                                                        const uint32_t* __restrict__ n_slots, HaloAcc* acc,
                                                        int32_t* __restrict__ rec_slot, int slot_stride,
-                                                       u64* __restrict__ mtot, int skip_marked) {
+                                                       u64* __restrict__ mtot, int skip_marked, int* status) {
     constexpr int kW = kMass ? kTab : 1;  // the 64-bit words exist with masses only
     __shared__ uint32_t tkey[kTab], tcnt[kTab], tused[kTab];
     __shared__ uint32_t tm_lo[3][kTab];  // moments (equal masses: the whole 32-bit sum)
@@ -184,9 +184,11 @@ __global__ void __launch_bounds__(kHsThreads, hs_ctas_per_sm<kMass>()) k_halo_su
                 mq[u] = kMass ? rec_mq[r] : 1u;
                 // a record marked in bit 63 (its particle already holds a halo id)
                 // joins no group
-                if (!(skip_marked && (e[u] >> 63)))
-                    lab[u] = label[(size_t(nearest_node(rec_q(e[u], 2), N)) * N + nearest_node(rec_q(e[u], 1), N)) * N +
-                                   nearest_node(rec_q(e[u], 0), N)];
+                if (!(skip_marked && (e[u] >> 63))) {
+                    const int64_t node = (int64_t(nearest_node(rec_q(e[u], 2), N)) * N +
+                                          nearest_node(rec_q(e[u], 1), N)) * N + nearest_node(rec_q(e[u], 0), N);
+                    if (index_ok(node, cells, status)) lab[u] = label[node];
+                }
             }
         }
         uint32_t word[kRecPerThread], pre[kRecPerThread];
@@ -302,18 +304,19 @@ void launch_halo_sums(cwthf_ctx* ctx, cudaStream_t s, int64_t np, const DepArgs&
                       const unsigned long long* rec, const uint32_t* rec_mq, const int32_t* label,
                       const uint32_t* bits, const uint32_t* prefix, const uint32_t* n_slots, HaloAcc* acc,
                       int32_t* rec_slot, int slot_stride, u64* mtot, int skip_marked) {
+    int* st = ctx->d_status;
     const FastDiv dn = make_fastdiv(uint32_t(a.ng));
     const int64_t chunks = div_up(std::max<int64_t>(np, 1), kChunk);
     if (a.mass)
         CWTHF_LAUNCH(ctx, s, "k_halo_sums",
                      k_halo_sums<true><<<int(std::min<int64_t>(chunks, int64_t(ctx->sm_count) * hs_ctas_per_sm<true>())),
                                          kHsThreads, 0, s>>>(a, dn, total, rec, rec_mq, label, bits, prefix, n_slots,
-                                                             acc, rec_slot, slot_stride, mtot, skip_marked));
+                                                             acc, rec_slot, slot_stride, mtot, skip_marked, st));
     else
         CWTHF_LAUNCH(ctx, s, "k_halo_sums",
                      k_halo_sums<false><<<int(std::min<int64_t>(chunks, int64_t(ctx->sm_count) * hs_ctas_per_sm<false>())),
                                           kHsThreads, 0, s>>>(a, dn, total, rec, rec_mq, label, bits, prefix, n_slots,
-                                                              acc, rec_slot, slot_stride, mtot, skip_marked));
+                                                              acc, rec_slot, slot_stride, mtot, skip_marked, st));
 }
 
 struct FilterArgs {

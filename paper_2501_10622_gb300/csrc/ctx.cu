@@ -482,6 +482,7 @@ const char* cwthf_error_string(int code) {
         case CWTHF_E_BAD_INPUT: return "non-finite or out-of-range input value";
         case CWTHF_E_SCRATCH_LIMIT: return "size beyond the fixed scratch of cwthf_deposit_noalloc (ng <= 128, np <= 262144)";
         case CWTHF_E_TABLE_CACHE: return "no free FFT / wavelet table slot (all in use by captured graphs, or a capture needs a new one)";
+        case CWTHF_E_INDEX: return "an index out of range was caught by the checked build (results unspecified)";
         default: return "unknown status";
     }
 }
@@ -525,6 +526,7 @@ int cwthf_debug_get(cwthf_ctx* ctx, int key, int64_t* value, void* stream) {
         case CWTHF_DEBUG_CHASE_LIMIT: *value = ctx->dbg_chase_limit; return CWTHF_OK;
         case CWTHF_DEBUG_TMA_NO_COPY: *value = ctx->dbg_tma_no_copy; return CWTHF_OK;
         case CWTHF_DEBUG_UNBIND_GRID_MIN: *value = ctx->dbg_unbind_grid_min; return CWTHF_OK;
+        case CWTHF_DEBUG_CHECKED: *value = kCheckedBuild ? 1 : 0; return CWTHF_OK;
         case CWTHF_DEBUG_TABLE_FILLS: {
             std::lock_guard<std::mutex> lk(ctx->table_mu);
             *value = int64_t(ctx->table_fills);

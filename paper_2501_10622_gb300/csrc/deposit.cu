@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kCountThreads) k_dep_count(DepArgs a, uint32_t
 __global__ void __launch_bounds__(kCountThreads) k_dep_scatter(DepArgs a, uint32_t* __restrict__ cursor,
                                                               unsigned long long* __restrict__ rec,
                                                               uint32_t* __restrict__ rec_mq,
-                                                              uint32_t* __restrict__ part_rec) {
+                                                              uint32_t* __restrict__ part_rec, int* status) {
     int lane = threadIdx.x & 31;
     int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t base = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); base < a.np; base += stride) {
@@ -109,8 +109,10 @@ __global__ void __launch_bounds__(kCountThreads) k_dep_scatter(DepArgs a, uint32
         slot = __shfl_sync(kFull, slot, leader);
         if (b.key != kInvalidKey) {
             slot += __popc(peers & ((1u << lane) - 1));
-            rec[slot] = b.rec;
-            if (a.mass) rec_mq[slot] = b.mq;
+            if (index_ok(slot, a.np, status)) {
+                rec[slot] = b.rec;
+                if (a.mass) rec_mq[slot] = b.mq;
+            }
         }
         if (part_rec && i < a.np) part_rec[i] = b.key != kInvalidKey ? slot : 0xffffffffu;
     }
@@ -197,7 +199,8 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_dep_tile(DepAr
     uint32_t nb = 0, ne = 0;
     if (warp == 0) fetch(blockIdx.x < nitems ? item_tile(blockIdx.x) : ntiles, nb, ne);
     for (int64_t j = blockIdx.x; j < nitems; j += gridDim.x) {
-        const int64_t t = item_tile(j);
+        const int64_t t = item_tile(j);  // a listed tile out of range fetches no records and writes nothing
+        if (kParts && threadIdx.x == 0) (void)index_ok(t, ntiles, status);
         const int tx = int(t % a.ntx), ty = int((t / a.ntx) % a.nty), tz = int(t / (int64_t(a.ntx) * a.nty));
         const int x0 = tx * kDepTX, y0 = ty * kDepTY, z0 = tz * kDepTZ;
         const int wx = min(kDepTX, a.ng - x0), wy = min(kDepTY, a.ng - y0), wz = min(kDepTZ, a.ng - z0);
@@ -234,13 +237,13 @@ __global__ void __launch_bounds__(kTileThreads, kTileCtasPerSm) k_dep_tile(DepAr
         }
         for (uint32_t k0 = kbeg + (threadIdx.x & ~31u); k0 < kend; k0 += kTileThreads) {  // warp-uniform trip count
             const uint32_t k = k0 + uint32_t(lane);
-            const bool live = k < kend;
             int sgi = 0;  // segment of k: last j with seg_pre[j] <= k
 #pragma unroll
             for (int w = 16; w > 0; w >>= 1)
                 if (sgi + w < kReachSegments && seg_pre[sgi + w] <= k) sgi += w;
             const uint32_t r = seg_beg[sgi] + (k - seg_pre[sgi]);
             const int m = seg_m[sgi];
+            const bool live = k < kend && index_ok(r, a.np, status);
             const u64 e = live ? rec[r] : 0ull;
             const uint32_t mq = live ? (a.mass ? rec_mq[r] : 1u) : 0u;
             const int qx = rec_q(e, 0), qy = rec_q(e, 1), qz = rec_q(e, 2);
@@ -330,7 +333,7 @@ int bin_particles(cwthf_ctx* ctx, const float* pos, const float* mass, double ma
         cudaSuccess)
         return cuda_status(e);
     CWTHF_LAUNCH(ctx, s, "k_dep_scatter", k_dep_scatter<<<blocks, kCountThreads, 0, s>>>(a, ctx->dep_cursor, ctx->dep_rec, ctx->dep_mq,
-                                                                        ctx->part_rec));
+                                                                        ctx->part_rec, ctx->d_status));
     return cuda_status(cudaGetLastError());
 }
 
@@ -374,7 +377,7 @@ int deposit_into_scratch(const DepositScratch& sc, const float* pos, const float
     if (rc) return rc;
     if ((e = cudaMemcpyAsync(sc.cursor, sc.off, size_t(nkeys) * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
         return cuda_status(e);
-    k_dep_scatter<<<blocks, kCountThreads, 0, s>>>(a, sc.cursor, sc.rec, sc.mq, nullptr);
+    k_dep_scatter<<<blocks, kCountThreads, 0, s>>>(a, sc.cursor, sc.rec, sc.mq, nullptr, sc.status);
     int tblocks = int(std::min<int64_t>(g.ntiles, int64_t(sc.sm_count) * kTileCtasPerSm));
     TileParts whole;  // no part list: every tile whole
     whole.list = nullptr;

@@ -223,6 +223,21 @@ namespace cwthf {
 // ---- status helpers ---------------------------------------------------------
 __device__ __forceinline__ void set_status(int* st, int code) { atomicCAS(st, 0, code); }
 
+// Checked builds (CWTHF_CHECKED): a data-driven index -- one read from device
+// memory rather than formed from loop bounds -- is tested before use; one out
+// of [0, n) records CWTHF_E_INDEX and the access is skipped.  Elsewhere the
+// test compiles away.
+#ifdef CWTHF_CHECKED
+constexpr bool kCheckedBuild = true;
+#else
+constexpr bool kCheckedBuild = false;
+#endif
+__device__ __forceinline__ bool index_ok(long long i, long long n, int* status) {
+    if (!kCheckedBuild || (i >= 0 && i < n)) return true;
+    set_status(status, CWTHF_E_INDEX);
+    return false;
+}
+
 // Bounded grid-wide barrier for kernels launched cooperatively (every CTA
 // resident).  bar[0] counts arrivals, bar[1] is the generation.  The wait
 // gives up after kSpinLimit polls, records CWTHF_E_TIMEOUT and returns false;

@@ -44,7 +44,6 @@ static_assert(kChTX == kPX && kPlaneL == (1 << kPlaneBits) && kRowWords == 32, "
 // -2 - g, apart from -1 (no seed) and the final labels (seed cells, >= 0).
 __device__ __forceinline__ bool is_flagged(int32_t v) { return v <= -2; }
 __device__ __forceinline__ int32_t flag_target(int32_t v) { return -2 - v; }
-constexpr int kChaseLimit = 64;  // default: longest chain the global pass follows per cell before doubling rounds
 constexpr int kJumpRoundsInTile = 16;  // in-place jumping rounds (each at least doubles the distance): 2^14 >= cells of a tile
 // Seeds of one tile: at most one local maximum per 2 x 2 x 2 block of cells
 // (any two cells of such a block are neighbours).
@@ -357,10 +356,10 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
     // pointer changes.  A value read while another thread rewrites it is either
     // the old or the new pointer, both points of the same chain.
     auto jump1 = [&](int i, int32_t v, bool& changed) {
-        if (v >= 0 && v != i) {
+        if (v >= 0 && v != i && index_ok(v, kLocal, status)) {
             int32_t w = ptr[v];
             if (w != v) {
-                if (w >= 0) w = ptr[w];
+                if (w >= 0 && index_ok(w, kLocal, status)) w = ptr[w];
                 ptr[i] = w;
                 changed = true;
             }
@@ -396,6 +395,7 @@ __global__ void __launch_bounds__(kChThreads, 3) k_seg_chase(const uint8_t* __re
             fl = true;
             return cur;  // -2 - g: already the flagged pointer to the outside parent g
         }
+        if (!index_ok(cur, kLocal, status)) return -1;
         const int px = cur & (kPX - 1), py = (cur >> kPXBits) & (kChTY - 1), pz = cur >> kPlaneBits;
         const int32_t g = gbase + (pz * N + py) * N + px;
         const int32_t nv = ptr[cur];
@@ -450,7 +450,7 @@ constexpr int kResTabBits = 9, kResTab = 1 << kResTabBits;  // per-tile count ta
 // others).  A warp gathers the flagged cells of a row's non-empty plane masks
 // into a shared batch; every full batch of 32 cells (and the warp's last,
 // partial one of the tile) is resolved by the whole warp: each lane follows
-// its cell's chain through the label grid (at most `limit` steps, kChaseLimit
+// its cell's chain through the label grid (at most `limit` steps, kDefaultChaseLimit
 // by default) and takes the label it reaches.  The tile's cells are counted
 // per seed in a shared table (one entry per distinct seed, one shared atomic
 // per distinct seed of a batch) that is added to the counts kept at the seeds'
@@ -483,12 +483,16 @@ __device__ __forceinline__ void table_add(int32_t* tkey, uint32_t* tcnt, uint32_
 
 __device__ __forceinline__ void resolve_batch(int32_t* __restrict__ label, bool valid, uint32_t c, int32_t* tkey,
                                               uint32_t* tcnt, uint32_t* __restrict__ seed_cells, int limit,
-                                              bool& left) {
+                                              bool& left, int64_t cells, int* status) {
     int32_t lab = -1;
     if (valid) {
         int32_t w = label[c];
         int steps = 0;
         while (is_flagged(w) && steps < limit) {
+            if (!index_ok(flag_target(w), cells, status)) {
+                w = -1;
+                break;
+            }
             w = label[flag_target(w)];
             steps++;
         }
@@ -505,7 +509,8 @@ __global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __rest
                                                                  const uint32_t* __restrict__ ballots,
                                                                  uint32_t* __restrict__ seed_cells,
                                                                  int* __restrict__ changed,
-                                                                 unsigned* __restrict__ next_tile, int limit) {
+                                                                 unsigned* __restrict__ next_tile, int limit,
+                                                                 int* status) {
     __shared__ uint32_t batch[kResolveThreads / 32][64];  // pending cells (fewer than 32 between batches)
     __shared__ int32_t tkey[kResTab];
     __shared__ uint32_t tcnt[kResTab];
@@ -518,6 +523,7 @@ __global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __rest
     const int ntx = (N + kChTX - 1) / kChTX, nty = (N + kChTY - 1) / kChTY, ntz = (N + kChTZ - 1) / kChTZ;
     const unsigned ntiles = unsigned(ntx) * unsigned(nty) * unsigned(ntz);
     const uint32_t plane32 = uint32_t(N) * uint32_t(N);
+    const int64_t cells = int64_t(plane32) * N;
     for (int i = threadIdx.x; i < kResTab; i += blockDim.x) {
         tkey[i] = -1;
         tcnt[i] = 0;
@@ -554,7 +560,7 @@ __global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __rest
                 k += __popc(b);
                 if (k >= 32) {
                     __syncwarp();
-                    resolve_batch(label, true, wl[lane], tkey, tcnt, seed_cells, limit, left);
+                    resolve_batch(label, true, wl[lane], tkey, tcnt, seed_cells, limit, left, cells, status);
                     const uint32_t rest = wl[32 + lane];
                     __syncwarp();
                     if (uint32_t(lane) + 32 < k) wl[lane] = rest;
@@ -566,7 +572,7 @@ __global__ void __launch_bounds__(kResolveThreads) k_seg_resolve(int32_t* __rest
         __syncwarp();
         if (k)
             resolve_batch(label, uint32_t(lane) < k, uint32_t(lane) < k ? wl[lane] : 0u, tkey, tcnt, seed_cells,
-                          limit, left);
+                          limit, left, cells, status);
         __syncthreads();
         // the tile's counts go to the seeds' cells; the table is cleared for the next tile
         for (int i = threadIdx.x; i < kResTab; i += blockDim.x) {
@@ -603,7 +609,7 @@ __global__ void __launch_bounds__(256) k_seg_fallback(int32_t* __restrict__ labe
         bool any = false;
         for (int64_t c = gid; c < cells; c += stride) {
             const int32_t v = label[c];
-            if (is_flagged(v)) {
+            if (is_flagged(v) && index_ok(flag_target(v), cells, status)) {
                 const int32_t w = label[flag_target(v)];
                 label[c] = w;
                 any |= is_flagged(w);  // still a pointer: another round is needed
@@ -769,7 +775,7 @@ int segment_impl(cwthf_ctx* ctx, const float* cwt, int ng, float cwt_min, int32_
     CWTHF_LAUNCH(ctx, s, "k_seg_resolve",
                  k_seg_resolve<<<blocks, kResolveThreads, 0, s>>>(label, ng, ballots, ctx->seed_cells, changed,
                                                                    reinterpret_cast<unsigned*>(changed + kJumpTileCounter),
-                                                                   ctx->dbg_chase_limit));
+                                                                   ctx->dbg_chase_limit, ctx->d_status));
     // pointer doubling and a recount for whatever the bounded walks left
     // (normally nothing: the kernel then returns at once)
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);

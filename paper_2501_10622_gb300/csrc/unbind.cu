@@ -52,12 +52,15 @@ __global__ void k_ub_count(const float* __restrict__ mass, double mass_unit, con
 
 __global__ void k_ub_scatter(const int32_t* __restrict__ group, int64_t np, int64_t n_groups,
                              const uint32_t* __restrict__ d_groups, const uint32_t* __restrict__ off,
-                             uint32_t* __restrict__ cur, int32_t* __restrict__ mem) {
+                             uint32_t* __restrict__ cur, int32_t* __restrict__ mem, int* status) {
     if (d_groups) n_groups = *d_groups;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np; i += stride) {
         const int32_t g = group[i];
-        if (g >= 0 && int64_t(g) < n_groups) mem[off[g] + atomicAdd(&cur[g], 1u)] = int32_t(i);
+        if (g >= 0 && int64_t(g) < n_groups) {
+            const uint32_t k = off[g] + atomicAdd(&cur[g], 1u);
+            if (index_ok(k, np, status)) mem[k] = int32_t(i);
+        }
     }
 }
 
@@ -746,7 +749,8 @@ int unbind_groups(cwthf_ctx* ctx, const float* pos, const float* vel, const floa
     int rc = d_groups ? scan_u32_dev(ctx, cnt, cnt, d_groups, n_groups, s) : scan_u32(ctx, cnt, cnt, n_groups, s);
     if (rc) return rc;
     CWTHF_LAUNCH(ctx, s, "k_ub_scatter",
-                 k_ub_scatter<<<blocks, 256, 0, s>>>(group, np, n_groups, d_groups, cnt, cur, ctx->ub_mem));
+                 k_ub_scatter<<<blocks, 256, 0, s>>>(group, np, n_groups, d_groups, cnt, cur, ctx->ub_mem,
+                                                     ctx->d_status));
     if (n_groups > 0) {
         UbArgs a;
         a.pos = pos;

@@ -22,6 +22,20 @@ def test_library_exports_every_declared_symbol():
     assert all(e.startswith("cwthf_") or e.startswith("_") for e in exported), sorted(exported)[:10]
 
 
+def test_checked_library_exports_the_same_symbols():
+    # the range-checked build (CWTHF_CHECKED) is the same ABI
+    path = pkg._lib.LIB_CHECKED_PATH
+    assert path.exists(), path
+    names = pkg.header_symbols()
+    L = ctypes.CDLL(str(path))
+    for n in names:
+        assert hasattr(L, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", str(path)], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert set(names) <= exported
+    assert all(e.startswith("cwthf_") or e.startswith("_") for e in exported), sorted(exported)[:10]
+
+
 def test_supported_grid_sizes():
     # every even size from 8 to 1152 (the paper's largest grid, Int(400 2.5 +
     # 150) = 1150, included): radix stages, or Bluestein passes where the
