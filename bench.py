@@ -154,6 +154,15 @@ def run_multiscale(args, dev):
             torch.cuda.synchronize(dev)
             ctx.check(what="multi-scale")
             ms = e0.elapsed_time(e1) / reps
+            # one more loop with CUDA events around every launch, outside the timed
+            # region: where the loop's time goes, per kernel
+            ctx.profile(True)
+            run()
+            ctx.check(what="multi-scale profiled loop")
+            prof = ctx.profile_read()
+            ctx.profile(False)
+            top = sorted(prof.items(), key=lambda kv: -kv[1][0])[:12]
+            out[key + "kernels_ms"] = {k: [round(v[0], 2), int(v[1])] for k, v in top}
             n = int(nh[0])
             got = pkg.ms_catalogue_to_numpy(cat, min(n, 1 << 20))
             out.update({key + "ms": ms, key + "mparticles_per_s": npart / ms / 1e3, key + "halos": n,
