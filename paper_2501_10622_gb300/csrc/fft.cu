@@ -250,8 +250,52 @@ __device__ __noinline__ void stage_r(float2* tile, A addr, const float2* tw, int
     __syncthreads();
 }
 
-template <class A>
+// The same stage with two butterflies per thread, for tiles whose C L / R
+// butterflies exceed the block (up to twice its threads): every thread loads
+// both of its butterflies before the barrier and stores them after it, as the
+// in-place stage needs.
+template <int R, class A>
+__device__ __noinline__ void stage_r2(float2* tile, A addr, const float2* tw, int L, int Ns, int C) {
+    const int nb = C * (L / R);
+    float2 v[2][R];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int b = int(threadIdx.x) + k * int(blockDim.x);
+        if (b < nb) bfly_load<R>(tile, addr, tw, L, Ns, b / C, b % C, v[k]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const int b = int(threadIdx.x) + k * int(blockDim.x);
+        if (b < nb) bfly_store<R>(tile, addr, Ns, b / C, b % C, v[k]);
+    }
+    __syncthreads();
+}
+
+// A stage of radix R; with kTwo, a stage of radix <= 16 may take two
+// butterflies per thread (the plan rule keeps larger radices to one).
+template <bool kTwo = false, class A>
 __device__ __forceinline__ void stage(int R, float2* tile, A addr, const float2* tw, int L, int Ns, int C) {
+    if constexpr (kTwo) {
+        if (C * (L / R) > int(blockDim.x)) {
+            switch (R) {
+                case 2: stage_r2<2>(tile, addr, tw, L, Ns, C); return;
+                case 3: stage_r2<3>(tile, addr, tw, L, Ns, C); return;
+                case 4: stage_r2<4>(tile, addr, tw, L, Ns, C); return;
+                case 5: stage_r2<5>(tile, addr, tw, L, Ns, C); return;
+                case 6: stage_r2<6>(tile, addr, tw, L, Ns, C); return;
+                case 7: stage_r2<7>(tile, addr, tw, L, Ns, C); return;
+                case 8: stage_r2<8>(tile, addr, tw, L, Ns, C); return;
+                case 9: stage_r2<9>(tile, addr, tw, L, Ns, C); return;
+                case 10: stage_r2<10>(tile, addr, tw, L, Ns, C); return;
+                case 12: stage_r2<12>(tile, addr, tw, L, Ns, C); return;
+                case 14: stage_r2<14>(tile, addr, tw, L, Ns, C); return;
+                case 15: stage_r2<15>(tile, addr, tw, L, Ns, C); return;
+                case 16: stage_r2<16>(tile, addr, tw, L, Ns, C); return;
+                default: return;
+            }
+        }
+    }
     switch (R) {
         case 2: stage_r<2>(tile, addr, tw, L, Ns, C); break;
         case 3: stage_r<3>(tile, addr, tw, L, Ns, C); break;
@@ -279,13 +323,14 @@ __device__ __forceinline__ void stage(int R, float2* tile, A addr, const float2*
     }
 }
 
-// Forward DFT of all C sequences of the tile (natural order in and out).
-template <class A>
+// Forward DFT of all C sequences of the tile (natural order in and out);
+// kTwo: stages may take two butterflies per thread (Bluestein tiles).
+template <bool kTwo = false, class A>
 __device__ __forceinline__ void fft_tile(const Plan& p, float2* tile, A addr, const float2* tw) {
     const int r0 = p.rad[0], r1 = p.rad[1], r2 = p.rad[2];
-    stage(r0, tile, addr, tw, p.L, 1, p.C);
-    if (p.nst > 1) stage(r1, tile, addr, tw, p.L, r0, p.C);
-    if (p.nst > 2) stage(r2, tile, addr, tw, p.L, r0 * r1, p.C);
+    stage<kTwo>(r0, tile, addr, tw, p.L, 1, p.C);
+    if (p.nst > 1) stage<kTwo>(r1, tile, addr, tw, p.L, r0, p.C);
+    if (p.nst > 2) stage<kTwo>(r2, tile, addr, tw, p.L, r0 * r1, p.C);
 }
 
 // Wavelet multiply between the forward and inverse z transforms, done in the
@@ -564,7 +609,7 @@ struct BlueFft {
             t[addr(l, c)] = v;
         }
         __syncthreads();
-        fft_tile(p, t, addr, tw);
+        fft_tile<true>(p, t, addr, tw);
         // times the transformed chirp (already divided by Mb), conjugated: the
         // second DFT then gives the conjugate of the circular convolution
         for (int i = threadIdx.x; i < Mb * C; i += blockDim.x) {
@@ -572,7 +617,7 @@ struct BlueFft {
             t[addr(l, c)] = conjf2(cmul(t[addr(l, c)], p.bhat[l]));
         }
         __syncthreads();
-        fft_tile(p, t, addr, tw);
+        fft_tile<true>(p, t, addr, tw);
         // X_k = conj(b_k) conv_k = conj(b_k t_k)
         for (int i = threadIdx.x; i < Lb * C; i += blockDim.x) {
             const int l = i / C, c = i - l * C;
@@ -1009,10 +1054,48 @@ int pick_boxr(int L, int C, int rows = 0) {
 }
 int plan_boxr(int L, const Plan& p) { return pick_boxr(L, p.C, p.Lb ? p.L : 0); }
 
+// A Bluestein tile of q.C columns may run its stages with two butterflies per
+// thread (BlueFft, 512 threads): every stage fits in 2 T butterflies, and a
+// stage that needs two per thread has a radix of at most 16.
+bool two_per_thread_ok(const Plan& q, int T) {
+    for (int st = 0; st < q.nst; st++) {
+        const int nb = q.C * (q.L / q.rad[st]);
+        if (nb > 2 * T || (nb > T && q.rad[st] > 16)) return false;
+    }
+    return true;
+}
+
+// Tile width of a Bluestein pass: four or more columns with one butterfly per
+// thread (<= 256, then <= 512 threads, <= 64 KB), else four or more with two
+// butterflies per thread (512 threads, <= 96 KB: three CTAs per SM), else two
+// columns.  Wider tiles move longer row segments per TMA box (two columns are
+// 16 bytes per row).  min_threads(C) is the pass's own least block size,
+// `fits` its other constraints.
+template <class MinT, class Fits>
+bool bluestein_tile(Plan& q, MinT&& min_threads, Fits&& fits) {
+    for (int tmax : {256, 512})
+        for (int C : {16, 8, 4}) {
+            q.C = C;
+            q.T = std::max(plan_threads(q), min_threads(C));
+            if (size_t(q.L) * C * 8 <= 65536 && q.T <= tmax && fits(q)) return true;
+        }
+    for (int C : {16, 8, 4}) {
+        q.C = C;
+        q.T = std::max(std::min(plan_threads(q), 512), min_threads(C));
+        if (size_t(q.L) * C * 8 <= 98304 && q.T <= 512 && two_per_thread_ok(q, q.T) && fits(q)) return true;
+    }
+    q.C = 2;
+    q.T = std::max(plan_threads(q), min_threads(2));
+    return size_t(q.L) * 2 * 8 <= 65536 && q.T <= 512 && fits(q);
+}
+
 // Columns per y/z tile: <= 64 KB of complex data and a valid TMA box,
-// preferring <= 256 threads (two CTAs per SM at 128 registers) over <= 512.
+// preferring <= 256 threads (two CTAs per SM at 128 registers) over <= 512
+// (Bluestein passes: bluestein_tile).
 bool yz_plan(int L, Plan& p) {
     return pass_plan_for(L, p, [L](Plan& q) {
+        if (q.Lb)
+            return bluestein_tile(q, [](int) { return 0; }, [L](const Plan& r) { return plan_boxr(L, r) > 0; });
         for (int tmax : {256, 512})
             for (int C : {16, 8, 4, 2}) {
                 q.C = C;
@@ -1027,6 +1110,8 @@ bool yz_plan(int L, Plan& p) {
 // preferring <= 256 threads (two CTAs per SM) over <= 512.
 bool x_plan(int M, Plan& p) {
     return pass_plan_for(M, p, [](Plan& q) {
+        if (q.Lb)  // at least one warp per row for the row loads
+            return bluestein_tile(q, [](int C) { return 32 * std::min(C, 16); }, [](const Plan&) { return true; });
         for (int tmax : {256, 512})
             for (int C : {16, 8, 4, 2}) {
                 q.C = C;
