@@ -12,6 +12,16 @@ replica (independent synthetic box, no collective on the data path); the
 throughput is the sum over ranks of particles / max-over-ranks step time.
 `--impl reference` times the fp64 CPU oracle on a bounded sample of the same
 workload instead.
+
+Besides the headline the line carries, each measured outside the timed step:
+`e2e` (host buffers and copies every step), `roofline` and `stages` (CUDA
+events per launch in separate steps against the algorithmic bytes, DRAM
+traffic from profiles/traffic.json), `served` and `batched` (the server and
+the graph batch), `cufft` and `stencil` (the library FFT route and the paper's
+direct-space CWT beside this path's transform), `multiscale` (the paper's
+19-scale loop on a 512^3-particle 50 Mpc/h box, without and with the
+self-boundness check, with per-kernel times `kernels_ms` from one more
+profiled loop) and `cpu_baseline` (the oracle).
 """
 from __future__ import annotations
 
